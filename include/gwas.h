@@ -1,0 +1,135 @@
+/*
+ * gwas.h -- C ABI of the GB300 library for the 2-D grid of generalized least-squares (GLS)
+ * problems of mixed-model GWAS (CLAK-Chol / CLAK-Eig, arXiv 1207.2169).
+ *
+ * The operation (Supplementary Note Section 1, Eq. "probDef"): for every SNP i and trait j
+ *
+ *     b_ij  = (X_i^T M_j^-1 X_i)^-1 X_i^T M_j^-1 y_j ,   X_i = [X_L | x_i],
+ *     M_j   = s2_j (h2_j Phi + (1 - h2_j) I),
+ *     Var_ij = (X_i^T M_j^-1 X_i)^-1 ,   wald_ij = b_ij[p-1]^2 / Var_ij[p-1][p-1],
+ *
+ * with n individuals, X_L = [1 | covariates] (q = p - 1 columns, shared by all problems), x_i the
+ * i-th SNP's genotypes (hard calls 0/1/2) and y_j the j-th trait.  The output is the
+ * m x t x p object B of Fig. 1 plus the m x t Wald statistics.
+ *
+ * Two algorithms, both exact rearrangements of the definition:
+ *   CHOL (Algorithm 3): M = L L^T once per trait; each SNP block is whitened by L^-1
+ *         (the aggregated triangular solve of "Sequences of GLS'") and reduced to a bordered
+ *         p x p system solved by its Schur complement.
+ *   EIG  (Algorithm 4): Phi = Z W Z^T once; each SNP block is rotated (Z^T X_R) and every
+ *         (SNP, trait) pair is reduced by trait-weighted inner products to the same bordered
+ *         system.
+ *
+ * Conventions for every call:
+ *   - Matrices are column-major unless stated.  Inputs are borrowed: setup copies what it needs
+ *     to the device; scan reads its genotype block during the call (or, for device pointers,
+ *     until the stream reaches the end of the call's work).
+ *   - Outputs are owned by the caller; the library never allocates them.
+ *   - Every call returns a gwas_status and never aborts the process; gwas_last_error() gives a
+ *     message for the last failure on the calling thread.
+ *   - A handle is used by one host thread at a time.  It owns all device state.
+ *   - A GLS whose Schur complement sigma = x^T M^-1 x - a^T S_TL^-1 a is not positive beyond
+ *     rounding (sigma <= tol * x^T M^-1 x; tol = 1e-12 in FP64, 1e-5 otherwise), e.g. a
+ *     monomorphic SNP, gets NaN in all p coefficients and the Wald value; it is not an error and
+ *     is counted (gwas_singular_count).
+ */
+#ifndef GWAS_GB300_H
+#define GWAS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gwas_handle_s* gwas_handle;
+
+typedef enum {
+  GWAS_OK = 0,
+  GWAS_ERR_ARG = -1,           /* bad pointer, size or option                              */
+  GWAS_ERR_NOT_SPD = -2,       /* M_j (CHOL) or Phi (EIG) is not positive definite          */
+  GWAS_ERR_CUDA = -3,          /* a CUDA runtime call failed                                */
+  GWAS_ERR_OOM = -4,           /* device or pinned-host allocation failed                   */
+  GWAS_ERR_UNSUPPORTED = -5,   /* option combination or size the build does not cover       */
+  GWAS_ERR_GENOTYPE = -6,      /* validate_genotypes found a value outside {0, 1, 2}        */
+  GWAS_ERR_TIMEOUT = -7,       /* a bounded wait gave up                                    */
+  GWAS_ERR_SINGULAR = -8,      /* S_TL = X_L^T M^-1 X_L is singular (collinear covariates)  */
+  GWAS_ERR_NOT_CONVERGED = -9  /* the eigensolver did not converge                          */
+} gwas_status;
+
+enum { GWAS_ALGO_AUTO = 0, GWAS_ALGO_CHOL = 1, GWAS_ALGO_EIG = 2 };
+
+/* Arithmetic of the per-SNP scan (setup is always FP64):
+ *   FP64        plain FP64 CUDA-core kernels;
+ *   FP32        plain FP32 CUDA-core kernels;
+ *   SPLIT_BF16  tensor-core kernels (tcgen05, sm_103a): the non-integer operand of each
+ *               contraction is split into hi + lo BF16 pieces, genotypes are exact in BF16,
+ *               accumulation is FP32; the p x p Schur solve runs in FP32.                     */
+enum { GWAS_PREC_FP64 = 0, GWAS_PREC_FP32 = 1, GWAS_PREC_SPLIT_BF16 = 2 };
+
+typedef struct {
+  int algo;               /* GWAS_ALGO_*; AUTO = CHOL when t == 1, else EIG                   */
+  int precision;          /* GWAS_PREC_*                                                      */
+  int block_snps;         /* SNPs per device block when streaming host input; 0 = default     */
+  int validate_genotypes; /* nonzero: scan checks every genotype is 0, 1 or 2                 */
+  int device;             /* CUDA device ordinal                                              */
+} gwas_options;
+
+/* Fills *opt with AUTO, SPLIT_BF16, block_snps 0, validation off, device 0. */
+void gwas_default_options(gwas_options* opt);
+
+/*
+ * gwas_setup -- the per-cohort precomputation (Algorithm 3 lines 1-3 and 5-7; Algorithm 4
+ * lines 1-2 and 4, plus the per-trait lines 6-11), in FP64 on the GPU.
+ *   Phi  n x n kinship, symmetric; only the lower triangle is read.        (host pointer)
+ *   XL   n x q covariates, column 0 is normally the intercept (all ones).   (host pointer)
+ *   Y    n x t traits.                                                      (host pointer)
+ *   h2   t heritabilities, each in [0, 1).  s2: t total variances, each > 0. (host pointers)
+ *   opt  options (NULL = defaults).  out: receives the handle (set to NULL on failure).
+ * Limits: 1 <= n <= 16384, 1 <= q <= 7, 1 <= t; CHOL additionally needs t * n^2 * 8 bytes.
+ * Returns GWAS_ERR_NOT_SPD if M_j or Phi is not positive definite, GWAS_ERR_SINGULAR if X_L
+ * is rank deficient in the M_j^-1 inner product.  Synchronous.
+ */
+gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q, const double* Y, int t,
+                       const double* h2, const double* s2, const gwas_options* opt,
+                       gwas_handle* out);
+
+/*
+ * gwas_scan -- the GLS sequence over one block of m SNPs (Algorithm 3 lines 4 and 8-11, or
+ * Algorithm 4 lines 3 and 12-16), every trait.
+ *   XR    m x n genotypes, int8 hard calls, SNP-major (SNP i's n calls at XR + i*n).
+ *   B     m x t x p results, B[(i*t + j)*p + k]; k = p-1 is the SNP effect, k < q follow XL.
+ *   wald  m x t Wald statistics, wald[i*t + j].  May be NULL (not written).
+ *   xr_on_device / out_on_device: nonzero when the pointer is device memory.
+ *   stream: cudaStream_t (NULL = legacy default stream).
+ * When XR and all outputs are on the device the call is asynchronous on `stream`.  Otherwise
+ * XR is streamed through the handle's device ring in blocks of block_snps SNPs (host memory
+ * pinned by the caller makes the copies asynchronous and overlapped) and the call returns when
+ * the outputs are complete.
+ */
+gwas_status gwas_scan(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_device, float* B,
+                      float* wald, int out_on_device, void* stream);
+
+/* gwas_scan_f64 -- as gwas_scan with FP64 outputs (meaningful for GWAS_PREC_FP64). */
+gwas_status gwas_scan_f64(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_device,
+                          double* B, double* wald, int out_on_device, void* stream);
+
+/* Milliseconds the FP64 setup took on the device (CUDA events around it). */
+gwas_status gwas_setup_timing(gwas_handle h, double* ms_setup);
+
+/* Sizes and resolved options of a handle (any pointer may be NULL). */
+gwas_status gwas_info(gwas_handle h, int* n, int* q, int* t, int* algo, int* precision);
+
+/* Number of singular pairs (written as NaN) seen by completed scans of this handle, or -1. */
+int64_t gwas_singular_count(gwas_handle h);
+
+/* Message of the last failure on the calling thread ("" if none).  Never NULL. */
+const char* gwas_last_error(void);
+
+/* Frees every resource of the handle.  NULL is ignored. */
+void gwas_destroy(gwas_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GWAS_GB300_H */

@@ -1,0 +1,177 @@
+"""Python binding of libgwasgb.so (include/gwas.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no arithmetic of the
+method: it checks shapes/dtypes, passes pointers (NumPy arrays or torch tensors, host or CUDA)
+and raises GwasError on a non-zero status.  The library must have been built
+(`python -m paper_1207_2169_gb300._build` or __graft_entry__.build()); importing this module
+without it raises ImportError -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgwasgb.so")
+
+ALGO = {"auto": 0, "chol": 1, "eig": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "split_bf16": 2}
+STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ERR_CUDA",
+          -4: "GWAS_ERR_OOM", -5: "GWAS_ERR_UNSUPPORTED", -6: "GWAS_ERR_GENOTYPE",
+          -7: "GWAS_ERR_TIMEOUT", -8: "GWAS_ERR_SINGULAR", -9: "GWAS_ERR_NOT_CONVERGED"}
+
+# every symbol include/gwas.h declares
+EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
+           "gwas_setup_timing", "gwas_info", "gwas_singular_count", "gwas_last_error",
+           "gwas_destroy"]
+
+
+class GwasError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class gwas_options(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int), ("precision", ctypes.c_int), ("block_snps", ctypes.c_int),
+                ("validate_genotypes", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_1207_2169_gb300._build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    lib.gwas_default_options.argtypes = [ctypes.POINTER(gwas_options)]
+    lib.gwas_default_options.restype = None
+    lib.gwas_setup.argtypes = [vp, i32, vp, i32, vp, i32, vp, vp, ctypes.POINTER(gwas_options),
+                               ctypes.POINTER(vp)]
+    lib.gwas_setup.restype = i32
+    for f in (lib.gwas_scan, lib.gwas_scan_f64):
+        f.argtypes = [vp, vp, i64, i32, vp, vp, i32, vp]
+        f.restype = i32
+    lib.gwas_setup_timing.argtypes = [vp, dp]
+    lib.gwas_setup_timing.restype = i32
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.gwas_info.argtypes = [vp, ip, ip, ip, ip, ip]
+    lib.gwas_info.restype = i32
+    lib.gwas_singular_count.argtypes = [vp]
+    lib.gwas_singular_count.restype = i64
+    lib.gwas_last_error.argtypes = []
+    lib.gwas_last_error.restype = ctypes.c_char_p
+    lib.gwas_destroy.argtypes = [vp]
+    lib.gwas_destroy.restype = None
+    return lib
+
+
+lib = _load()
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise GwasError(st, where, gwas_last_error())
+
+
+def _f64_fortran(x, shape, name):
+    a = np.asfortranarray(np.asarray(x, dtype=np.float64))
+    if a.shape != shape:
+        raise ValueError(f"{name}: shape {a.shape}, expected {shape}")
+    return a
+
+
+def _ptr(x):
+    """(address, on_device) of a NumPy array or torch tensor (must be C-contiguous)."""
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), int(x.is_cuda)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def gwas_default_options(**kw) -> gwas_options:
+    o = gwas_options()
+    lib.gwas_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "algo" and isinstance(v, str):
+            v = ALGO[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        setattr(o, k, int(v))
+    return o
+
+
+def gwas_setup(Phi, XL, Y, h2, s2, options: gwas_options | None = None, **kw):
+    """Returns an opaque handle (int).  Phi: n x n, XL: n x q, Y: n x t, h2/s2: t."""
+    Phi = np.asarray(Phi, dtype=np.float64)
+    n = Phi.shape[0]
+    XL = np.asarray(XL, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    if Y.ndim == 1:
+        Y = Y[:, None]
+    q, t = XL.shape[1], Y.shape[1]
+    Phi = _f64_fortran(Phi, (n, n), "Phi")
+    XL = _f64_fortran(XL, (n, q), "XL")
+    Y = _f64_fortran(Y, (n, t), "Y")
+    h2 = np.ascontiguousarray(np.broadcast_to(np.asarray(h2, dtype=np.float64), (t,)))
+    s2 = np.ascontiguousarray(np.broadcast_to(np.asarray(s2, dtype=np.float64), (t,)))
+    o = options if options is not None else gwas_default_options(**kw)
+    h = ctypes.c_void_p()
+    st = lib.gwas_setup(Phi.ctypes.data, n, XL.ctypes.data, q, Y.ctypes.data, t, h2.ctypes.data,
+                        s2.ctypes.data, ctypes.byref(o), ctypes.byref(h))
+    _check(st, "gwas_setup")
+    return h.value
+
+
+def _scan(fn, name, h, XR, m, B, wald, stream):
+    xp, xdev = _ptr(XR)
+    bp, bdev = _ptr(B)
+    wp, wdev = _ptr(wald) if wald is not None else (0, bdev)
+    if wald is not None and wdev != bdev:
+        raise ValueError("B and wald must both be host or both be device buffers")
+    if stream is None and (xdev or bdev):
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    st = fn(h, xp, int(m), xdev, bp, wp or None, bdev, stream or None)
+    _check(st, name)
+
+
+def gwas_scan(h, XR, B, wald=None, stream=None, m=None):
+    """XR: (m, n) int8; B: (m, t, p) float32; wald: (m, t) float32 or None."""
+    _scan(lib.gwas_scan, "gwas_scan", h, XR, XR.shape[0] if m is None else m, B, wald, stream)
+
+
+def gwas_scan_f64(h, XR, B, wald=None, stream=None, m=None):
+    """As gwas_scan with float64 B and wald."""
+    _scan(lib.gwas_scan_f64, "gwas_scan_f64", h, XR, XR.shape[0] if m is None else m, B, wald, stream)
+
+
+def gwas_setup_timing(h) -> float:
+    ms = ctypes.c_double()
+    _check(lib.gwas_setup_timing(h, ctypes.byref(ms)), "gwas_setup_timing")
+    return ms.value
+
+
+def gwas_info(h) -> dict:
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(lib.gwas_info(h, *[ctypes.byref(x) for x in v]), "gwas_info")
+    n, q, t, algo, prec = (x.value for x in v)
+    return dict(n=n, q=q, t=t, p=q + 1, algo=algo, precision=prec)
+
+
+def gwas_singular_count(h) -> int:
+    return int(lib.gwas_singular_count(h))
+
+
+def gwas_last_error() -> str:
+    return lib.gwas_last_error().decode()
+
+
+def gwas_destroy(h) -> None:
+    lib.gwas_destroy(h)

@@ -1,0 +1,536 @@
+// The C ABI (include/gwas.h): handle, FP64 setup on the device and the streamed scan.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+#define GW_API extern "C" __attribute__((visibility("default")))
+
+namespace gw {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+}  // namespace gw
+
+using namespace gw;
+
+struct gwas_handle_s {
+  int dev = 0, n = 0, q = 0, p = 0, t = 0, algo = 0, prec = 0, validate = 0;
+  int block_snps = 0;
+  int ldp = 0;  // n rounded up to 64: leading dimension of padded per-individual operands
+  double setup_ms = 0.0;
+  cudaStream_t st = nullptr, st_h2d = nullptr, st_d2h = nullptr;
+  cudaEvent_t ev_loaded[2] = {}, ev_computed[2] = {}, ev_drained[2] = {};
+  int* flags = nullptr;
+  int* h_flags = nullptr;
+  // per-trait null-model block (both algorithms)
+  double *P = nullptr, *b0 = nullptr, *rw = nullptr;
+  float *P32 = nullptr, *b032 = nullptr, *rw32 = nullptr;
+  // CHOL
+  double *Linv = nullptr, *XLw = nullptr;
+  float *Linv32 = nullptr, *XLw32 = nullptr;
+  // EIG
+  double *Zt = nullptr, *w = nullptr, *XLt = nullptr, *planes = nullptr;
+  float *Zt32 = nullptr, *planes32 = nullptr;
+  // scratch for the rotated block (EIG)
+  void* xt = nullptr;
+  int64_t xt_cap = 0;
+  // streaming ring
+  int8_t* ring[2] = {};
+  void* oring[2] = {};
+  int64_t ring_snps = 0;
+  // tensor-core state
+  TcState* tc = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+void* dalloc(gwas_handle h, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    throw Fail{GWAS_ERR_OOM};
+  }
+  h->allocs.push_back(p);
+  return p;
+}
+
+template <typename T>
+T* dalloc_t(gwas_handle h, size_t count) {
+  return (T*)dalloc(h, count * sizeof(T));
+}
+
+void dfree(gwas_handle h, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    if (h->allocs[i] == p) {
+      cudaFree(p);
+      h->allocs.erase(h->allocs.begin() + i);
+      return;
+    }
+}
+
+void destroy_impl(gwas_handle h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->dev);
+  if (h->st) cudaStreamSynchronize(h->st);
+  if (h->st_h2d) cudaStreamSynchronize(h->st_h2d);
+  if (h->st_d2h) cudaStreamSynchronize(h->st_d2h);
+  if (h->tc) tc_destroy(h->tc);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_flags) cudaFreeHost(h->h_flags);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_loaded[i]) cudaEventDestroy(h->ev_loaded[i]);
+    if (h->ev_computed[i]) cudaEventDestroy(h->ev_computed[i]);
+    if (h->ev_drained[i]) cudaEventDestroy(h->ev_drained[i]);
+  }
+  if (h->st) cudaStreamDestroy(h->st);
+  if (h->st_h2d) cudaStreamDestroy(h->st_h2d);
+  if (h->st_d2h) cudaStreamDestroy(h->st_d2h);
+  delete h;
+  cudaSetDevice(cur);
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    GW_CUDA(cudaSetDevice(dev));
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void read_flags(gwas_handle h, cudaStream_t s) {
+  GW_CUDA(cudaMemcpyAsync(h->h_flags, h->flags, sizeof(int) * FLAG_COUNT, cudaMemcpyDeviceToHost, s));
+  GW_CUDA(cudaStreamSynchronize(s));
+}
+
+void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double* Y,
+                const double* h2, const double* s2) {
+  const int n = h->n, q = h->q, t = h->t;
+  const size_t nn = (size_t)n * n;
+  cudaStream_t s = h->st;
+  double* dPhi = dalloc_t<double>(h, nn);
+  double* dXL = dalloc_t<double>(h, (size_t)n * q);
+  double* dY = dalloc_t<double>(h, (size_t)n * t);
+  double* dh2 = dalloc_t<double>(h, t);
+  double* ds2 = dalloc_t<double>(h, t);
+  GW_CUDA(cudaMemcpyAsync(dPhi, Phi, nn * 8, cudaMemcpyHostToDevice, s));
+  GW_CUDA(cudaMemcpyAsync(dXL, XL, (size_t)n * q * 8, cudaMemcpyHostToDevice, s));
+  GW_CUDA(cudaMemcpyAsync(dY, Y, (size_t)n * t * 8, cudaMemcpyHostToDevice, s));
+  GW_CUDA(cudaMemcpyAsync(dh2, h2, (size_t)t * 8, cudaMemcpyHostToDevice, s));
+  GW_CUDA(cudaMemcpyAsync(ds2, s2, (size_t)t * 8, cudaMemcpyHostToDevice, s));
+  GW_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int) * FLAG_COUNT, s));
+  cudaEvent_t e0, e1;
+  GW_CUDA(cudaEventCreate(&e0));
+  GW_CUDA(cudaEventCreate(&e1));
+  GW_CUDA(cudaEventRecord(e0, s));
+
+  h->P = dalloc_t<double>(h, (size_t)t * q * q);
+  h->b0 = dalloc_t<double>(h, (size_t)t * q);
+  h->rw = dalloc_t<double>(h, (size_t)t * n);
+  double* yw = dalloc_t<double>(h, (size_t)t * n);
+  int sweeps = 0;
+  if (h->algo == GWAS_ALGO_CHOL) {
+    // Algorithm 3 lines 1-3 and 5 for every trait: M_j, L_j, L_j^-1, L_j^-1 X_L, L_j^-1 y_j
+    h->Linv = dalloc_t<double>(h, (size_t)t * nn);
+    h->XLw = dalloc_t<double>(h, (size_t)t * q * n);
+    double* A = dalloc_t<double>(h, nn);
+    double* work = dalloc_t<double>(h, nn);
+    for (int j = 0; j < t; ++j) {
+      double hj = h2[j], sj = s2[j];
+      double* Lj = h->Linv + (size_t)j * nn;
+      form_M(s, n, dPhi, hj, sj, A);
+      cholesky(s, n, A, h->flags);
+      tri_inverse(s, n, A, Lj, work);
+      // XLw_j (q x n, row k) = L^-1 X_L[:, k];  yw_j = L^-1 y_j
+      gemm_f64(s, q, n, n, 1.0, dXL, n, 1, Lj, 1, n, 0.0, h->XLw + (size_t)j * q * n, n, 1);
+      gemm_f64(s, 1, n, n, 1.0, dY + (size_t)j * n, 0, 1, Lj, 1, n, 0.0, yw + (size_t)j * n, 0, 1);
+    }
+    dfree(h, A);
+    dfree(h, work);
+    TraitPackArgs ta{n, q, t, h->XLw, (int64_t)q * n, yw, nullptr, h->P, h->b0, h->rw, h->flags};
+    trait_pack(s, ta);
+  } else {
+    // Algorithm 4 lines 1, 2 and 4: Phi = Z W Z^T, X~_L = Z^T X_L, Y~ = Z^T Y; then per trait
+    // D_j, S_TL, b_T (lines 6-11) and the operand planes of the pair reduction.
+    h->Zt = dalloc_t<double>(h, nn);
+    h->w = dalloc_t<double>(h, n);
+    double* U = dalloc_t<double>(h, nn);
+    sweeps = jacobi_eig(s, n, dPhi, h->Zt, h->w, U, h->flags, 60);
+    dfree(h, U);
+    GW_REQUIRE(sweeps > 0, GWAS_ERR_NOT_CONVERGED, "Jacobi eigensolver did not converge in 60 sweeps");
+    h->XLt = dalloc_t<double>(h, (size_t)q * n);
+    gemm_f64(s, q, n, n, 1.0, dXL, n, 1, h->Zt, 1, n, 0.0, h->XLt, n, 1);
+    gemm_f64(s, t, n, n, 1.0, dY, n, 1, h->Zt, 1, n, 0.0, yw, n, 1);
+    double* d = dalloc_t<double>(h, (size_t)t * n);
+    eig_weights(s, n, t, h->w, dh2, ds2, d, h->flags);
+    TraitPackArgs ta{n, q, t, h->XLt, 0, yw, d, h->P, h->b0, h->rw, h->flags};
+    trait_pack(s, ta);
+    h->planes = dalloc_t<double>(h, (size_t)t * (q + 2) * h->ldp);
+    eig_planes_f64(s, n, q, t, h->ldp, h->XLt, d, h->rw, h->planes);
+    dfree(h, d);
+  }
+  dfree(h, yw);
+
+  if (h->prec == GWAS_PREC_FP32) {
+    h->P32 = dalloc_t<float>(h, (size_t)t * q * q);
+    h->b032 = dalloc_t<float>(h, (size_t)t * q);
+    convert_f64_to_f32(s, h->P, h->P32, (int64_t)t * q * q);
+    convert_f64_to_f32(s, h->b0, h->b032, (int64_t)t * q);
+    if (h->algo == GWAS_ALGO_CHOL) {
+      h->Linv32 = dalloc_t<float>(h, (size_t)t * nn);
+      h->XLw32 = dalloc_t<float>(h, (size_t)t * q * n);
+      h->rw32 = dalloc_t<float>(h, (size_t)t * n);
+      convert_f64_to_f32(s, h->Linv, h->Linv32, (int64_t)t * nn);
+      convert_f64_to_f32(s, h->XLw, h->XLw32, (int64_t)t * q * n);
+      convert_f64_to_f32(s, h->rw, h->rw32, (int64_t)t * n);
+    } else {
+      h->Zt32 = dalloc_t<float>(h, nn);
+      h->planes32 = dalloc_t<float>(h, (size_t)t * (q + 2) * h->ldp);
+      convert_f64_to_f32(s, h->Zt, h->Zt32, (int64_t)nn);
+      convert_f64_to_f32(s, h->planes, h->planes32, (int64_t)t * (q + 2) * h->ldp);
+    }
+  } else if (h->prec == GWAS_PREC_SPLIT_BF16) {
+    TcSetupArgs ta{};
+    ta.algo = h->algo; ta.n = n; ta.q = q; ta.t = t;
+    ta.Linv = h->Linv; ta.XLw = h->XLw; ta.rw = h->rw;
+    ta.Zt = h->Zt; ta.planes = h->planes; ta.ldp = h->ldp;
+    ta.P = h->P; ta.b0 = h->b0;
+    h->tc = tc_setup(s, ta);
+  }
+  GW_CUDA(cudaEventRecord(e1, s));
+  GW_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  GW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  h->setup_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  read_flags(h, s);
+  GW_REQUIRE(!h->h_flags[FLAG_NOT_SPD], GWAS_ERR_NOT_SPD,
+             "M_j = s2 (h2 Phi + (1-h2) I) is not positive definite");
+  GW_REQUIRE(!h->h_flags[FLAG_STL_SINGULAR], GWAS_ERR_SINGULAR,
+             "X_L^T M^-1 X_L is singular: covariates are collinear");
+  GW_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int) * FLAG_COUNT, s));
+  dfree(h, dPhi);
+  dfree(h, dXL);
+  dfree(h, dY);
+  dfree(h, dh2);
+  dfree(h, ds2);
+  if (h->algo == GWAS_ALGO_EIG && h->prec != GWAS_PREC_FP64) {
+    dfree(h, h->planes);
+    h->planes = nullptr;
+  }
+  if (h->algo == GWAS_ALGO_CHOL && h->prec != GWAS_PREC_FP64) {
+    dfree(h, h->Linv);
+    h->Linv = nullptr;
+  }
+  GW_CUDA(cudaStreamSynchronize(s));
+}
+
+// Scratch of the EIG CUDA-core path: the rotated genotypes of up to `snps` SNPs.
+void ensure_xt(gwas_handle h, int64_t snps) {
+  if (h->algo != GWAS_ALGO_EIG || h->prec == GWAS_PREC_SPLIT_BF16) return;
+  if (snps <= h->xt_cap) return;
+  if (h->xt) {
+    GW_CUDA(cudaDeviceSynchronize());
+    dfree(h, h->xt);
+  }
+  const size_t es = h->prec == GWAS_PREC_FP64 ? 8 : 4;
+  h->xt = dalloc(h, (size_t)snps * h->ldp * es);
+  h->xt_cap = snps;
+}
+
+// One block of SNPs already on the device, outputs on the device; asynchronous on s.
+void scan_block(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* wald, bool out_f64,
+                cudaStream_t s) {
+  if (h->validate) validate_genotypes(s, XR, m * h->n, h->flags);
+  const int n = h->n, q = h->q, t = h->t;
+  if (h->prec == GWAS_PREC_SPLIT_BF16) {
+    TcScanArgs a{};
+    a.XR = XR; a.m = m; a.B = (float*)B; a.wald = (float*)wald; a.flags = h->flags;
+    tc_scan(s, h->tc, a);
+    return;
+  }
+  if (h->algo == GWAS_ALGO_CHOL) {
+    for (int j = 0; j < t; ++j) {
+      if (h->prec == GWAS_PREC_FP64) {
+        CholScanArgs<double> a{n, q, t, j, h->Linv + (size_t)j * n * n, h->XLw + (size_t)j * q * n,
+                               h->rw + (size_t)j * n, h->P + (size_t)j * q * q, h->b0 + (size_t)j * q,
+                               XR, m, 0, B, wald, out_f64, 1e-12, h->flags};
+        chol_scan_simt<double>(s, a);
+      } else {
+        CholScanArgs<float> a{n, q, t, j, h->Linv32 + (size_t)j * n * n, h->XLw32 + (size_t)j * q * n,
+                              h->rw32 + (size_t)j * n, h->P32 + (size_t)j * q * q, h->b032 + (size_t)j * q,
+                              XR, m, 0, B, wald, out_f64, 1e-5f, h->flags};
+        chol_scan_simt<float>(s, a);
+      }
+    }
+    return;
+  }
+  // EIG on CUDA cores: chunks that fit the scratch (same stream, so chunks serialise)
+  const int64_t cap = h->xt_cap;
+  for (int64_t off = 0; off < m; off += cap) {
+    const int64_t mm = m - off < cap ? m - off : cap;
+    const size_t ob = out_f64 ? 8 : 4;
+    void* Bc = (char*)B + (size_t)off * t * (q + 1) * ob;
+    void* Wc = wald ? (char*)wald + (size_t)off * t * ob : nullptr;
+    if (h->prec == GWAS_PREC_FP64) {
+      EigScanArgs<double> a{n, q, t, h->Zt, h->planes, h->ldp, h->P, h->b0, XR + off * n, mm, 0,
+                            Bc, Wc, out_f64, 1e-12, (double*)h->xt, h->flags};
+      eig_scan_simt<double>(s, a);
+    } else {
+      EigScanArgs<float> a{n, q, t, h->Zt32, h->planes32, h->ldp, h->P32, h->b032, XR + off * n, mm,
+                           0, Bc, Wc, out_f64, 1e-5f, (float*)h->xt, h->flags};
+      eig_scan_simt<float>(s, a);
+    }
+  }
+}
+
+gwas_status scan_impl(gwas_handle h, const int8_t* XR, int64_t m, int xr_dev, void* B, void* wald,
+                      int out_dev, void* stream, bool out_f64) {
+  GW_REQUIRE(h != nullptr, GWAS_ERR_ARG, "null handle");
+  GW_REQUIRE(m >= 0, GWAS_ERR_ARG, "m < 0");
+  if (m == 0) return GWAS_OK;
+  GW_REQUIRE(XR != nullptr && B != nullptr, GWAS_ERR_ARG, "null XR or B");
+  GW_REQUIRE(!(out_f64 && h->prec == GWAS_PREC_SPLIT_BF16), GWAS_ERR_UNSUPPORTED,
+             "gwas_scan_f64 needs the FP64 or FP32 precision mode");
+  DeviceGuard dg(h->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = h->n, t = h->t, p = h->p;
+  const size_t ob = out_f64 ? 8 : 4;
+  if (xr_dev && out_dev) {
+    ensure_xt(h, m < h->block_snps ? m : h->block_snps);
+    scan_block(h, XR, m, B, wald, out_f64, s);
+    if (h->validate) {
+      read_flags(h, s);
+      GW_REQUIRE(!h->h_flags[FLAG_GENOTYPE], GWAS_ERR_GENOTYPE, "genotype outside {0,1,2}");
+    }
+    return GWAS_OK;
+  }
+  // Streamed: double-buffered H2D of genotype blocks (copy stream), compute on `s`,
+  // D2H of each block's outputs (second copy stream).
+  const int64_t blk = h->block_snps;
+  if (h->ring_snps < blk) {
+    GW_CUDA(cudaStreamSynchronize(s));
+    GW_CUDA(cudaStreamSynchronize(h->st_h2d));
+    GW_CUDA(cudaStreamSynchronize(h->st_d2h));
+    for (int i = 0; i < 2; ++i) {
+      dfree(h, h->ring[i]);
+      dfree(h, h->oring[i]);
+      h->ring[i] = (int8_t*)dalloc(h, (size_t)blk * n);
+      h->oring[i] = dalloc(h, (size_t)blk * t * (p + 1) * 8);
+    }
+    h->ring_snps = blk;
+  }
+  ensure_xt(h, blk);
+  const int nblocks = ceil_div(m, blk);
+  for (int b = 0; b < nblocks; ++b) {
+    const int buf = b & 1;
+    const int64_t off = (int64_t)b * blk;
+    const int64_t mm = m - off < blk ? m - off : blk;
+    const int8_t* src = XR + off * n;
+    if (!xr_dev) {
+      GW_CUDA(cudaStreamWaitEvent(h->st_h2d, h->ev_computed[buf], 0));
+      GW_CUDA(cudaMemcpyAsync(h->ring[buf], src, (size_t)mm * n, cudaMemcpyHostToDevice, h->st_h2d));
+      GW_CUDA(cudaEventRecord(h->ev_loaded[buf], h->st_h2d));
+      GW_CUDA(cudaStreamWaitEvent(s, h->ev_loaded[buf], 0));
+      src = h->ring[buf];
+    }
+    void* Bo;
+    void* Wo;
+    if (out_dev) {
+      Bo = (char*)B + (size_t)off * t * p * ob;
+      Wo = wald ? (char*)wald + (size_t)off * t * ob : nullptr;
+    } else {
+      GW_CUDA(cudaStreamWaitEvent(s, h->ev_drained[buf], 0));
+      Bo = h->oring[buf];
+      Wo = wald ? (char*)h->oring[buf] + (size_t)blk * t * p * ob : nullptr;
+    }
+    scan_block(h, src, mm, Bo, Wo, out_f64, s);
+    GW_CUDA(cudaEventRecord(h->ev_computed[buf], s));
+    if (!out_dev) {
+      GW_CUDA(cudaStreamWaitEvent(h->st_d2h, h->ev_computed[buf], 0));
+      GW_CUDA(cudaMemcpyAsync((char*)B + (size_t)off * t * p * ob, Bo, (size_t)mm * t * p * ob,
+                              cudaMemcpyDeviceToHost, h->st_d2h));
+      if (wald)
+        GW_CUDA(cudaMemcpyAsync((char*)wald + (size_t)off * t * ob, Wo, (size_t)mm * t * ob,
+                                cudaMemcpyDeviceToHost, h->st_d2h));
+      GW_CUDA(cudaEventRecord(h->ev_drained[buf], h->st_d2h));
+    }
+  }
+  GW_CUDA(cudaStreamSynchronize(s));
+  GW_CUDA(cudaStreamSynchronize(h->st_h2d));
+  GW_CUDA(cudaStreamSynchronize(h->st_d2h));
+  if (h->validate) {
+    read_flags(h, s);
+    GW_REQUIRE(!h->h_flags[FLAG_GENOTYPE], GWAS_ERR_GENOTYPE, "genotype outside {0,1,2}");
+  }
+  return GWAS_OK;
+}
+
+}  // namespace
+
+GW_API void gwas_default_options(gwas_options* opt) {
+  if (!opt) return;
+  opt->algo = GWAS_ALGO_AUTO;
+  opt->precision = GWAS_PREC_SPLIT_BF16;
+  opt->block_snps = 0;
+  opt->validate_genotypes = 0;
+  opt->device = 0;
+}
+
+GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q, const double* Y,
+                              int t, const double* h2, const double* s2, const gwas_options* opt,
+                              gwas_handle* out) {
+  if (out) *out = nullptr;
+  gwas_handle h = nullptr;
+  try {
+    GW_REQUIRE(out != nullptr, GWAS_ERR_ARG, "out is NULL");
+    GW_REQUIRE(Phi && XL && Y && h2 && s2, GWAS_ERR_ARG, "null input pointer");
+    GW_REQUIRE(n >= 1 && n <= 16384, GWAS_ERR_ARG, "n=%d outside [1,16384]", n);
+    GW_REQUIRE(q >= 1 && q <= 7, GWAS_ERR_ARG, "q=%d outside [1,7]", q);
+    GW_REQUIRE(t >= 1, GWAS_ERR_ARG, "t=%d < 1", t);
+    for (int j = 0; j < t; ++j) {
+      GW_REQUIRE(h2[j] >= 0.0 && h2[j] < 1.0, GWAS_ERR_ARG, "h2[%d]=%g outside [0,1)", j, h2[j]);
+      GW_REQUIRE(s2[j] > 0.0 && isfinite(s2[j]), GWAS_ERR_ARG, "s2[%d]=%g not > 0", j, s2[j]);
+    }
+    gwas_options o;
+    gwas_default_options(&o);
+    if (opt) o = *opt;
+    GW_REQUIRE(o.algo >= 0 && o.algo <= 2, GWAS_ERR_ARG, "bad algo %d", o.algo);
+    GW_REQUIRE(o.precision >= 0 && o.precision <= 2, GWAS_ERR_ARG, "bad precision %d", o.precision);
+    GW_REQUIRE(o.block_snps >= 0, GWAS_ERR_ARG, "block_snps < 0");
+    h = new gwas_handle_s();
+    h->dev = o.device;
+    h->n = n;
+    h->q = q;
+    h->p = q + 1;
+    h->t = t;
+    h->algo = o.algo == GWAS_ALGO_AUTO ? (t == 1 ? GWAS_ALGO_CHOL : GWAS_ALGO_EIG) : o.algo;
+    h->prec = o.precision;
+    h->validate = o.validate_genotypes ? 1 : 0;
+    h->ldp = (int)round_up(n, 64);
+    if (h->algo == GWAS_ALGO_CHOL)
+      GW_REQUIRE((double)t * n * n * 8.0 <= 64e9, GWAS_ERR_UNSUPPORTED,
+                 "CHOL keeps one n x n factor per trait: t=%d, n=%d is too large (use EIG)", t, n);
+    if (h->prec == GWAS_PREC_SPLIT_BF16) tc_check_supported(h->algo, n, q, t);
+    int ndev = 0;
+    GW_CUDA(cudaGetDeviceCount(&ndev));
+    GW_REQUIRE(h->dev >= 0 && h->dev < ndev, GWAS_ERR_ARG, "device %d not present", h->dev);
+    DeviceGuard dg(h->dev);
+    // default block: CHOL 64 Ki SNPs; EIG bounded so a block's FP64 outputs stay <= 2 GB
+    int64_t blk = o.block_snps > 0 ? o.block_snps : (h->algo == GWAS_ALGO_CHOL ? 65536 : 32768);
+    const int64_t out_cap = (int64_t)(2e9 / ((double)t * (q + 2) * 8));
+    if (blk > out_cap) blk = out_cap;
+    if (blk < 64) blk = 64;
+    h->block_snps = (int)blk;
+    GW_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    GW_CUDA(cudaStreamCreateWithFlags(&h->st_h2d, cudaStreamNonBlocking));
+    GW_CUDA(cudaStreamCreateWithFlags(&h->st_d2h, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      GW_CUDA(cudaEventCreateWithFlags(&h->ev_loaded[i], cudaEventDisableTiming));
+      GW_CUDA(cudaEventCreateWithFlags(&h->ev_computed[i], cudaEventDisableTiming));
+      GW_CUDA(cudaEventCreateWithFlags(&h->ev_drained[i], cudaEventDisableTiming));
+    }
+    h->flags = (int*)dalloc(h, sizeof(int) * FLAG_COUNT);
+    GW_CUDA(cudaMallocHost(&h->h_flags, sizeof(int) * FLAG_COUNT));
+    setup_impl(h, Phi, XL, Y, h2, s2);
+    *out = h;
+    set_error("%s", "");
+    return GWAS_OK;
+  } catch (const Fail& f) {
+    destroy_impl(h);
+    return f.st;
+  } catch (...) {
+    set_error("unexpected C++ exception in gwas_setup");
+    destroy_impl(h);
+    return GWAS_ERR_CUDA;
+  }
+}
+
+GW_API gwas_status gwas_scan(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_device,
+                             float* B, float* wald, int out_on_device, void* stream) {
+  try {
+    return scan_impl(h, XR, m, xr_on_device, B, wald, out_on_device, stream, false);
+  } catch (const Fail& f) {
+    return f.st;
+  } catch (...) {
+    set_error("unexpected C++ exception in gwas_scan");
+    return GWAS_ERR_CUDA;
+  }
+}
+
+GW_API gwas_status gwas_scan_f64(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_device,
+                                 double* B, double* wald, int out_on_device, void* stream) {
+  try {
+    return scan_impl(h, XR, m, xr_on_device, B, wald, out_on_device, stream, true);
+  } catch (const Fail& f) {
+    return f.st;
+  } catch (...) {
+    set_error("unexpected C++ exception in gwas_scan_f64");
+    return GWAS_ERR_CUDA;
+  }
+}
+
+GW_API gwas_status gwas_setup_timing(gwas_handle h, double* ms_setup) {
+  if (!h || !ms_setup) {
+    set_error("null argument");
+    return GWAS_ERR_ARG;
+  }
+  *ms_setup = h->setup_ms;
+  return GWAS_OK;
+}
+
+GW_API gwas_status gwas_info(gwas_handle h, int* n, int* q, int* t, int* algo, int* precision) {
+  if (!h) {
+    set_error("null handle");
+    return GWAS_ERR_ARG;
+  }
+  if (n) *n = h->n;
+  if (q) *q = h->q;
+  if (t) *t = h->t;
+  if (algo) *algo = h->algo;
+  if (precision) *precision = h->prec;
+  return GWAS_OK;
+}
+
+GW_API int64_t gwas_singular_count(gwas_handle h) {
+  if (!h) return -1;
+  try {
+    DeviceGuard dg(h->dev);
+    GW_CUDA(cudaDeviceSynchronize());
+    read_flags(h, h->st);
+    return h->h_flags[FLAG_SINGULAR];
+  } catch (const Fail&) {
+    return -1;
+  }
+}
+
+GW_API const char* gwas_last_error(void) { return gw::g_err.c_str(); }
+
+GW_API void gwas_destroy(gwas_handle h) { destroy_impl(h); }

@@ -1,0 +1,143 @@
+// Shared helpers of the CUDA library: error plumbing, the handle layout and launch prototypes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gwas.h"
+
+namespace gw {
+
+// Thread-local message behind gwas_last_error().
+void set_error(const char* fmt, ...);
+
+struct Fail {
+  gwas_status st;
+};
+
+#define GW_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      ::gw::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,     \
+                      __LINE__);                                                           \
+      throw ::gw::Fail{e_ == cudaErrorMemoryAllocation ? GWAS_ERR_OOM : GWAS_ERR_CUDA};    \
+    }                                                                                      \
+  } while (0)
+
+#define GW_CHECK_LAUNCH() GW_CUDA(cudaGetLastError())
+
+#define GW_REQUIRE(cond, status, ...)                                                      \
+  do {                                                                                     \
+    if (!(cond)) {                                                                         \
+      ::gw::set_error(__VA_ARGS__);                                                        \
+      throw ::gw::Fail{status};                                                            \
+    }                                                                                      \
+  } while (0)
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Device flags word layout (int32 array in the handle).
+enum { FLAG_GENOTYPE = 0, FLAG_SINGULAR = 1, FLAG_NOT_SPD = 2, FLAG_ROTATIONS = 3,
+       FLAG_TIMEOUT = 4, FLAG_STL_SINGULAR = 5, FLAG_COUNT = 8 };
+
+// ------------------------------------------------------------------------------------------
+// Setup kernels (FP64), setup_f64.cu
+// ------------------------------------------------------------------------------------------
+// C = alpha * op(A) * op(B) + beta * C with arbitrary element strides:
+//   A(i,k) = A[i*sai + k*sak], B(k,j) = B[k*sbk + j*sbj], C(i,j) = C[i*sci + j*scj].
+// lower_only: skip 64x64 tiles of C that lie strictly above the diagonal.
+void gemm_f64(cudaStream_t s, int M, int N, int K, double alpha, const double* A, int64_t sai,
+              int64_t sak, const double* B, int64_t sbk, int64_t sbj, double beta, double* C,
+              int64_t sci, int64_t scj, bool lower_only = false);
+// A (n x n, column-major, lower) := M = s2 (h2 Phi + (1-h2) I).
+void form_M(cudaStream_t s, int n, const double* Phi, double h2, double s2, double* A);
+// In-place lower Cholesky of A (column-major, ld n); upper part zeroed.  Sets flags[NOT_SPD].
+void cholesky(cudaStream_t s, int n, double* A, int* flags);
+// Linv (row-major, n x n, zeros above the diagonal) := L^-1 for lower L (column-major).
+void tri_inverse(cudaStream_t s, int n, const double* L, double* Linv, double* work);
+// One-sided Jacobi eigendecomposition of SPD Phi: Zt (row r = eigenvector r), w.  Returns
+// sweeps used, or -1 when not converged within max_sweeps.
+int jacobi_eig(cudaStream_t s, int n, const double* Phi, double* Zt, double* w, double* U,
+               int* flags, int max_sweeps);
+
+// Per-trait null-model precompute shared by both algorithms (bordered-system top block).
+//   XLw (q x n, row k = k-th whitened covariate), yw (n) for each trait, weights d (n; all
+//   ones for CHOL, D_j for EIG).  Produces P = S_TL^-1 (q x q), b0 = P X_L^T D y, and the
+//   weighted residual rw = D (y - X_L b0) scaled for the scan (see trait_pack in setup_f64.cu).
+struct TraitPackArgs {
+  int n, q, t;
+  const double* XLw;   // q x n (shared by all traits; EIG: Z^T X_L; CHOL: per trait)
+  int64_t xlw_trait_stride;
+  const double* yw;    // t x n (EIG: Z^T Y; CHOL: L_j^-1 y_j)
+  const double* d;     // t x n weights or NULL (all ones)
+  double* P;           // t x q x q
+  double* b0;          // t x q
+  double* rw;          // t x n: weighted residual d * (yw - XLw^T b0)
+  int* flags;
+};
+void trait_pack(cudaStream_t s, const TraitPackArgs& a);
+// EIG weights d_j[r] = 1 / (s2_j (h2_j w_r + 1 - h2_j)), t x n.
+void eig_weights(cudaStream_t s, int n, int t, const double* w, const double* h2,
+                 const double* s2, double* d, int* flags);
+// EIG B-operand planes, K-major: planes[(j*(q+2)+c)*ldp + r] = d_j[r]*XLt[c][r] (c<q),
+// rw_j[r] (c=q; already weighted), d_j[r] (c=q+1).  Zero for r >= n.
+void eig_planes_f64(cudaStream_t s, int n, int q, int t, int ldp, const double* XLt,
+                    const double* d, const double* rw, double* planes);
+
+// Conversions.
+void convert_f64_to_f32(cudaStream_t s, const double* x, float* y, int64_t count);
+// hi = bf16(x), lo = bf16(x - hi) for a rows x cols row-major matrix with leading dims.
+void split_bf16(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx,
+                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo);
+
+// ------------------------------------------------------------------------------------------
+// Scan kernels, scan_simt.cu (plain FP64 / FP32 CUDA-core forms)
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct CholScanArgs {
+  int n, q, t, j;            // sizes, trait index j of this pass
+  const T* Linv;             // n x n row-major lower (L_j^-1)
+  const T* XLw;              // q x n whitened covariates
+  const T* rw;               // n whitened null residual
+  const T* P;                // q x q = S_TL^-1
+  const T* b0;               // q null-model coefficients
+  const int8_t* XR;          // m x n
+  int64_t m;
+  int64_t out_offset;        // first SNP's index in the output arrays
+  void* B;                   // float or double, (m_total x t x p)
+  void* wald;                // may be NULL
+  bool out_f64;
+  T sing_tol;
+  int* flags;
+};
+template <typename T> void chol_scan_simt(cudaStream_t s, const CholScanArgs<T>& a);
+
+template <typename T>
+struct EigScanArgs {
+  int n, q, t;
+  const T* Zt;               // n x n, row r = eigenvector r
+  const T* planes;           // t x (q+2) x ldp
+  int ldp;
+  const T* P;                // t x q x q
+  const T* b0;               // t x q
+  const int8_t* XR;
+  int64_t m;
+  int64_t out_offset;
+  void* B;
+  void* wald;
+  bool out_f64;
+  T sing_tol;
+  T* xt;                     // scratch: m x ldp rotated genotypes
+  int* flags;
+};
+template <typename T> void eig_scan_simt(cudaStream_t s, const EigScanArgs<T>& a);
+
+// Genotype check: flags[GENOTYPE] = 1 if any value is outside {0,1,2}.
+void validate_genotypes(cudaStream_t s, const int8_t* XR, int64_t count, int* flags);
+
+}  // namespace gw

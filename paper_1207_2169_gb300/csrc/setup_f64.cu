@@ -1,0 +1,536 @@
+// FP64 setup kernels: the once-per-cohort and once-per-trait work of Algorithms 3 and 4.
+//
+//   form_M       Supplementary Note Section 1 / Algorithm 3 line 1: M = s2 (h2 Phi + (1-h2) I)
+//   cholesky     Algorithm 3 line 2: L L^T = M (blocked right-looking, 32-wide panels)
+//   tri_inverse  L^-1, so that the per-block whitening of Algorithm 3 line 4 is one product
+//   jacobi_eig   Algorithm 4 line 1: Phi = Z W Z^T (one-sided Jacobi, FP64)
+//   trait_pack   Algorithm 3 lines 6-7 / Algorithm 4 lines 6-11: S_TL, b_T, P = S_TL^-1,
+//                b0 = P b_T and the weighted null residual used by the bordered solve
+//
+// All of it runs on CUDA cores in FP64; none of it is on the per-SNP path.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace gw {
+
+// ------------------------------------------------------------------------------------------
+// Generic strided FP64 GEMM (64 x 64 tiles, 256 threads, 4 x 4 per thread)
+// ------------------------------------------------------------------------------------------
+namespace {
+constexpr int GT = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_kernel(int M, int N, int K, double alpha,
+                                                       const double* __restrict__ A, int64_t sai,
+                                                       int64_t sak, const double* __restrict__ B,
+                                                       int64_t sbk, int64_t sbj, double beta,
+                                                       double* __restrict__ C, int64_t sci,
+                                                       int64_t scj, int lower_only) {
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (lower_only && bj * GT > bi * GT + GT - 1) return;
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int i0 = bi * GT, j0 = bj * GT;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += GK) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int e = tid + 256 * l;
+      int i, k;
+      if (sai == 1) { i = e % GT; k = e / GT; } else { k = e % GK; i = e / GK; }
+      const int gi = i0 + i, gk = k0 + k;
+      As[k][i] = (gi < M && gk < K) ? A[gi * sai + gk * sak] : 0.0;
+      int j;
+      if (sbj == 1) { j = e % GT; k = e / GT; } else { k = e % GK; j = e / GK; }
+      const int gj = j0 + j, gk2 = k0 + k;
+      Bs[k][j] = (gj < N && gk2 < K) ? B[gk2 * sbk + gj * sbj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { a[u] = As[k][ty + 16 * u]; b[u] = Bs[k][tx + 16 * u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int gi = i0 + ty + 16 * u, gj = j0 + tx + 16 * v;
+      if (gi < M && gj < N) {
+        double* c = C + gi * sci + gj * scj;
+        *c = alpha * acc[u][v] + (beta == 0.0 ? 0.0 : beta * *c);
+      }
+    }
+}
+}  // namespace
+
+void gemm_f64(cudaStream_t s, int M, int N, int K, double alpha, const double* A, int64_t sai,
+              int64_t sak, const double* B, int64_t sbk, int64_t sbj, double beta, double* C,
+              int64_t sci, int64_t scj, bool lower_only) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid(ceil_div(N, GT), ceil_div(M, GT));
+  gemm_f64_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci,
+                                       scj, lower_only ? 1 : 0);
+  GW_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------------------------------
+// M and its Cholesky factor
+// ------------------------------------------------------------------------------------------
+namespace {
+__global__ void form_M_kernel(int n, const double* __restrict__ Phi, double h2, double s2,
+                              double* __restrict__ A) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e % n), c = (int)(e / n);  // column-major (i, c)
+  // only the lower triangle of Phi is read; M is stored symmetric-lower
+  const double phi = (i >= c) ? Phi[e] : Phi[c + (int64_t)i * n];
+  A[e] = s2 * (h2 * phi + (i == c ? 1.0 - h2 : 0.0));
+}
+
+constexpr int NB = 32;
+
+__global__ void potrf_diag_kernel(int n, double* A, int j0, int jb, int* flags) {
+  __shared__ double a[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // (col, row)
+  if (ty < jb && tx < jb) a[ty][tx] = A[(j0 + ty) + (int64_t)(j0 + tx) * n];
+  for (int k = 0; k < jb; ++k) {
+    __syncthreads();
+    if (tx == 0 && ty == 0) {
+      double d = a[k][k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicExch(&flags[FLAG_NOT_SPD], 1);
+        d = 1.0;
+      }
+      a[k][k] = sqrt(d);
+    }
+    __syncthreads();
+    if (tx == 0 && ty > k && ty < jb) a[ty][k] /= a[k][k];
+    __syncthreads();
+    if (ty > k && ty < jb && tx > k && tx <= ty) a[ty][tx] -= a[ty][k] * a[tx][k];
+  }
+  __syncthreads();
+  if (ty < jb && tx < jb && tx <= ty) A[(j0 + ty) + (int64_t)(j0 + tx) * n] = a[ty][tx];
+}
+
+// Rows below the diagonal block: x L_jj^T = a, one thread per row.
+__global__ void trsm_panel_kernel(int n, double* A, int j0, int jb) {
+  __shared__ double L[NB][NB + 1];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    L[r][c] = (r < jb && c < jb) ? A[(j0 + r) + (int64_t)(j0 + c) * n] : 0.0;
+  }
+  __syncthreads();
+  const int i = j0 + jb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    if (k < jb) {
+      double v = A[i + (int64_t)(j0 + k) * n];
+#pragma unroll
+      for (int l = 0; l < k; ++l) v -= x[l] * L[k][l];
+      x[k] = v / L[k][k];
+      A[i + (int64_t)(j0 + k) * n] = x[k];
+    } else {
+      x[k] = 0.0;
+    }
+  }
+}
+
+__global__ void zero_upper_kernel(int n, double* A) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e % n), c = (int)(e / n);
+  if (c > i) A[e] = 0.0;
+}
+}  // namespace
+
+void form_M(cudaStream_t s, int n, const double* Phi, double h2, double s2, double* A) {
+  const int64_t nn = (int64_t)n * n;
+  form_M_kernel<<<ceil_div(nn, 256), 256, 0, s>>>(n, Phi, h2, s2, A);
+  GW_CHECK_LAUNCH();
+}
+
+void cholesky(cudaStream_t s, int n, double* A, int* flags) {
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int jb = n - j0 < NB ? n - j0 : NB;
+    potrf_diag_kernel<<<1, dim3(NB, NB), 0, s>>>(n, A, j0, jb, flags);
+    GW_CHECK_LAUNCH();
+    const int rest = n - j0 - jb;
+    if (rest > 0) {
+      trsm_panel_kernel<<<ceil_div(rest, 128), 128, 0, s>>>(n, A, j0, jb);
+      GW_CHECK_LAUNCH();
+      double* P = A + (j0 + jb) + (int64_t)j0 * n;
+      gemm_f64(s, rest, rest, jb, -1.0, P, 1, n, P, n, 1, 1.0,
+               A + (j0 + jb) + (int64_t)(j0 + jb) * n, 1, n, /*lower_only=*/true);
+    }
+  }
+  const int64_t nn = (int64_t)n * n;
+  zero_upper_kernel<<<ceil_div(nn, 256), 256, 0, s>>>(n, A);
+  GW_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------------------------------
+// L^-1 (row-major output)
+// ------------------------------------------------------------------------------------------
+namespace {
+// Inverse of each 32 x 32 diagonal block; thread c computes column c by forward substitution.
+__global__ void diag_inv_kernel(int n, const double* __restrict__ L, double* __restrict__ Linv) {
+  __shared__ double Lb[NB][NB + 1];
+  __shared__ double X[NB][NB + 1];
+  const int j0 = blockIdx.x * NB;
+  const int jb = n - j0 < NB ? n - j0 : NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    Lb[r][c] = (r < jb && c < jb) ? L[(j0 + r) + (int64_t)(j0 + c) * n] : 0.0;
+    X[r][c] = 0.0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < jb) {
+    X[c][c] = 1.0 / Lb[c][c];
+    for (int r = c + 1; r < jb; ++r) {
+      double v = 0.0;
+      for (int k = c; k < r; ++k) v += Lb[r][k] * X[k][c];
+      X[r][c] = -v / Lb[r][r];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+    const int r = e / jb, cc = e % jb;
+    Linv[(int64_t)(j0 + r) * n + j0 + cc] = X[r][cc];
+  }
+}
+}  // namespace
+
+void tri_inverse(cudaStream_t s, int n, const double* L, double* Linv, double* work) {
+  GW_CUDA(cudaMemsetAsync(Linv, 0, sizeof(double) * (size_t)n * n, s));
+  const int nblk = ceil_div(n, NB);
+  diag_inv_kernel<<<nblk, NB, 0, s>>>(n, L, Linv);
+  GW_CHECK_LAUNCH();
+  for (int bi = 1; bi < nblk; ++bi) {
+    const int i0 = bi * NB;
+    const int jb = n - i0 < NB ? n - i0 : NB;
+    // work(jb x i0) = L[i0:i0+jb, 0:i0] * Linv[0:i0, 0:i0]
+    gemm_f64(s, jb, i0, i0, 1.0, L + i0, 1, n, Linv, n, 1, 0.0, work, n, 1);
+    // Linv[i0:i0+jb, 0:i0] = -Dinv * work
+    gemm_f64(s, jb, i0, jb, -1.0, Linv + (int64_t)i0 * n + i0, n, 1, work, n, 1, 0.0,
+             Linv + (int64_t)i0 * n, n, 1);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// One-sided Jacobi eigendecomposition (Hestenes).  U starts as Phi, V as I; every round of a
+// sweep orthogonalises n/2 disjoint column pairs (round-robin order), until no pair's cosine
+// exceeds tol.  Then U = Phi V has orthogonal columns, so V diagonalises Phi^2 and, for SPD Phi,
+// Phi; its columns are the eigenvectors.
+// ------------------------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32, nw = blockDim.x / 32;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  return t;
+}
+
+__global__ void jacobi_init_kernel(int n, const double* __restrict__ Phi, double* U, double* V) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e % n), c = (int)(e / n);
+  U[e] = (i >= c) ? Phi[e] : Phi[c + (int64_t)i * n];
+  V[e] = (i == c) ? 1.0 : 0.0;
+}
+
+__global__ void __launch_bounds__(256) jacobi_round_kernel(int n, int N, int round, double* U,
+                                                           double* V, int* flags, double tol) {
+  __shared__ double red[8];
+  const int k = blockIdx.x;
+  auto idx = [&](int x) { return (x + round) % (N - 1) + 1; };
+  int a, b;
+  if (k == 0) { a = 0; b = idx(0); } else { a = idx(k); b = idx(N - 1 - k); }
+  if (a >= n || b >= n) return;  // the dummy player of an odd n
+  double* ua = U + (int64_t)a * n;
+  double* ub = U + (int64_t)b * n;
+  double al = 0.0, be = 0.0, ga = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = ua[i], y = ub[i];
+    al = fma(x, x, al);
+    be = fma(y, y, be);
+    ga = fma(x, y, ga);
+  }
+  al = block_sum(al, red);
+  be = block_sum(be, red);
+  ga = block_sum(ga, red);
+  if (!(fabs(ga) > tol * sqrt(al * be))) return;
+  if (threadIdx.x == 0) atomicAdd(&flags[FLAG_ROTATIONS], 1);
+  const double zeta = (be - al) / (2.0 * ga);
+  const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+  double* va = V + (int64_t)a * n;
+  double* vb = V + (int64_t)b * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = ua[i], y = ub[i];
+    ua[i] = c * x - sn * y;
+    ub[i] = sn * x + c * y;
+    const double xv = va[i], yv = vb[i];
+    va[i] = c * xv - sn * yv;
+    vb[i] = sn * xv + c * yv;
+  }
+}
+
+// Eigenvalue r as the Rayleigh quotient v_r^T Phi v_r = v_r^T u_r (keeps the sign, so an
+// indefinite Phi is detected downstream).
+__global__ void rayleigh_kernel(int n, const double* __restrict__ U, const double* __restrict__ V,
+                                double* w) {
+  __shared__ double red[8];
+  const double* u = U + (int64_t)blockIdx.x * n;
+  const double* v = V + (int64_t)blockIdx.x * n;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a = fma(u[i], v[i], a);
+  a = block_sum(a, red);
+  if (threadIdx.x == 0) w[blockIdx.x] = a;
+}
+}  // namespace
+
+int jacobi_eig(cudaStream_t s, int n, const double* Phi, double* Zt, double* w, double* U,
+               int* flags, int max_sweeps) {
+  const int64_t nn = (int64_t)n * n;
+  jacobi_init_kernel<<<ceil_div(nn, 256), 256, 0, s>>>(n, Phi, U, Zt);
+  GW_CHECK_LAUNCH();
+  if (n == 1) {
+    rayleigh_kernel<<<1, 256, 0, s>>>(n, U, Zt, w);
+    GW_CHECK_LAUNCH();
+    return 0;
+  }
+  const int N = n + (n & 1);
+  const double tol = fmax(1e-15, 2.0 * n * 2.220446049250313e-16);
+  // One sweep = N-1 rounds, captured once as a CUDA graph and replayed.
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  cudaStream_t cap;
+  GW_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  GW_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  for (int r = 0; r < N - 1; ++r)
+    jacobi_round_kernel<<<N / 2, 256, 0, cap>>>(n, N, r, U, Zt, flags, tol);
+  cudaError_t le = cudaGetLastError();
+  GW_CUDA(cudaStreamEndCapture(cap, &graph));
+  GW_CUDA(le);
+  GW_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  int sweeps = -1;
+  int* h_rot = nullptr;
+  GW_CUDA(cudaMallocHost(&h_rot, sizeof(int)));
+  for (int sw = 1; sw <= max_sweeps; ++sw) {
+    GW_CUDA(cudaMemsetAsync(flags + FLAG_ROTATIONS, 0, sizeof(int), s));
+    GW_CUDA(cudaGraphLaunch(exec, s));
+    GW_CUDA(cudaMemcpyAsync(h_rot, flags + FLAG_ROTATIONS, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GW_CUDA(cudaStreamSynchronize(s));
+    if (*h_rot == 0) { sweeps = sw; break; }
+  }
+  cudaFreeHost(h_rot);
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  rayleigh_kernel<<<n, 256, 0, s>>>(n, U, Zt, w);
+  GW_CHECK_LAUNCH();
+  return sweeps;
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-trait null-model block of the bordered system
+// ------------------------------------------------------------------------------------------
+namespace {
+constexpr int QMAX = 7;
+constexpr int NRED = QMAX * (QMAX + 1) / 2 + QMAX;
+
+__global__ void __launch_bounds__(256) trait_pack_kernel(TraitPackArgs a) {
+  __shared__ double red[NRED][8];
+  __shared__ double sb0[QMAX];
+  const int j = blockIdx.x, q = a.q, n = a.n;
+  const double* xl = a.XLw + j * a.xlw_trait_stride;
+  const double* y = a.yw + (int64_t)j * n;
+  const double* d = a.d ? a.d + (int64_t)j * n : nullptr;
+  double acc[NRED];
+#pragma unroll
+  for (int u = 0; u < NRED; ++u) acc[u] = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const double dr = d ? d[r] : 1.0;
+    double x[QMAX];
+#pragma unroll
+    for (int k = 0; k < QMAX; ++k) x[k] = k < q ? xl[(int64_t)k * n + r] : 0.0;
+    int u = 0;
+#pragma unroll
+    for (int k = 0; k < QMAX; ++k)
+#pragma unroll
+      for (int l = 0; l <= k; ++l) acc[u++] += dr * x[k] * x[l];
+#pragma unroll
+    for (int k = 0; k < QMAX; ++k) acc[u++] += dr * x[k] * y[r];
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+#pragma unroll
+  for (int u = 0; u < NRED; ++u) {
+    double v = acc[u];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) red[u][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot[NRED];
+    for (int u = 0; u < NRED; ++u) {
+      double v = 0.0;
+      for (int i = 0; i < (int)(blockDim.x / 32); ++i) v += red[u][i];
+      tot[u] = v;
+    }
+    double S[QMAX][QMAX], bT[QMAX];
+    int u = 0;
+    for (int k = 0; k < QMAX; ++k)
+      for (int l2 = 0; l2 <= k; ++l2) { S[k][l2] = tot[u]; S[l2][k] = tot[u]; ++u; }
+    for (int k = 0; k < QMAX; ++k) bT[k] = tot[u++];
+    // S = C C^T, then P = C^-T C^-1
+    double C[QMAX][QMAX] = {}, Ci[QMAX][QMAX] = {};
+    bool ok = true;
+    for (int k = 0; k < q; ++k) {
+      double dd = S[k][k];
+      for (int m = 0; m < k; ++m) dd -= C[k][m] * C[k][m];
+      if (!(dd > 1e-13 * S[k][k])) { ok = false; dd = 1.0; }
+      C[k][k] = sqrt(dd);
+      for (int i = k + 1; i < q; ++i) {
+        double v = S[i][k];
+        for (int m = 0; m < k; ++m) v -= C[i][m] * C[k][m];
+        C[i][k] = v / C[k][k];
+      }
+    }
+    if (!ok) atomicExch(&a.flags[FLAG_STL_SINGULAR], 1);
+    for (int i = 0; i < q; ++i) {
+      Ci[i][i] = 1.0 / C[i][i];
+      for (int c = 0; c < i; ++c) {
+        double v = 0.0;
+        for (int m = c; m < i; ++m) v += C[i][m] * Ci[m][c];
+        Ci[i][c] = -v / C[i][i];
+      }
+    }
+    double* P = a.P + (int64_t)j * q * q;
+    for (int i = 0; i < q; ++i)
+      for (int c = 0; c < q; ++c) {
+        double v = 0.0;
+        for (int m = (i > c ? i : c); m < q; ++m) v += Ci[m][i] * Ci[m][c];
+        P[i * q + c] = v;
+      }
+    for (int i = 0; i < q; ++i) {
+      double v = 0.0;
+      for (int c = 0; c < q; ++c) v += P[i * q + c] * bT[c];
+      sb0[i] = v;
+      a.b0[(int64_t)j * q + i] = v;
+    }
+  }
+  __syncthreads();
+  double* rw = a.rw + (int64_t)j * n;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    double v = y[r];
+    for (int k = 0; k < q; ++k) v -= xl[(int64_t)k * n + r] * sb0[k];
+    rw[r] = (d ? d[r] : 1.0) * v;
+  }
+}
+
+__global__ void eig_weights_kernel(int n, int t, const double* __restrict__ w,
+                                   const double* __restrict__ h2, const double* __restrict__ s2,
+                                   double* __restrict__ d, int* flags) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * t) return;
+  const int j = (int)(e / n), r = (int)(e % n);
+  const double v = s2[j] * (h2[j] * w[r] + (1.0 - h2[j]));
+  if (!(v > 0.0)) atomicExch(&flags[FLAG_NOT_SPD], 1);  // M_j = Z diag(v) Z^T not SPD
+  d[e] = v > 0.0 ? 1.0 / v : 0.0;
+}
+
+__global__ void eig_planes_kernel(int n, int q, int t, int ldp, const double* __restrict__ XLt,
+                                  const double* __restrict__ d, const double* __restrict__ rw,
+                                  double* __restrict__ planes) {
+  const int64_t total = (int64_t)t * (q + 2) * ldp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % ldp);
+    const int64_t row = e / ldp;
+    const int c = (int)(row % (q + 2));
+    const int j = (int)(row / (q + 2));
+    double v = 0.0;
+    if (r < n) {
+      const double dr = d[(int64_t)j * n + r];
+      if (c < q) v = dr * XLt[(int64_t)c * n + r];
+      else if (c == q) v = rw[(int64_t)j * n + r];
+      else v = dr;
+    }
+    planes[e] = v;
+  }
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ x, float* __restrict__ y,
+                                  int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = (float)x[e];
+}
+
+__global__ void split_bf16_kernel(const double* __restrict__ x, int rows, int cols, int64_t ldx,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                  int64_t ldo) {
+  const int64_t total = (int64_t)rows * ldo;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ldo), c = (int)(e % ldo);
+    const double v = c < cols ? x[(int64_t)r * ldx + c] : 0.0;
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    hi[e] = h;
+    lo[e] = __double2bfloat16(v - (double)__bfloat162float(h));
+  }
+}
+}  // namespace
+
+void trait_pack(cudaStream_t s, const TraitPackArgs& a) {
+  GW_REQUIRE(a.q >= 1 && a.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", a.q, QMAX);
+  trait_pack_kernel<<<a.t, 256, 0, s>>>(a);
+  GW_CHECK_LAUNCH();
+}
+
+void eig_weights(cudaStream_t s, int n, int t, const double* w, const double* h2,
+                 const double* s2, double* d, int* flags) {
+  const int64_t tot = (int64_t)n * t;
+  eig_weights_kernel<<<ceil_div(tot, 256), 256, 0, s>>>(n, t, w, h2, s2, d, flags);
+  GW_CHECK_LAUNCH();
+}
+
+void eig_planes_f64(cudaStream_t s, int n, int q, int t, int ldp, const double* XLt,
+                    const double* d, const double* rw, double* planes) {
+  eig_planes_kernel<<<1184, 256, 0, s>>>(n, q, t, ldp, XLt, d, rw, planes);
+  GW_CHECK_LAUNCH();
+}
+
+void convert_f64_to_f32(cudaStream_t s, const double* x, float* y, int64_t count) {
+  if (count <= 0) return;
+  f64_to_f32_kernel<<<1184, 256, 0, s>>>(x, y, count);
+  GW_CHECK_LAUNCH();
+}
+
+void split_bf16(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx,
+                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo) {
+  split_bf16_kernel<<<1184, 256, 0, s>>>(x, rows, cols, ldx, hi, lo, ldo);
+  GW_CHECK_LAUNCH();
+}
+
+}  // namespace gw

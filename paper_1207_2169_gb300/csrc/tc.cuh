@@ -1,0 +1,36 @@
+// Tensor-core (tcgen05, sm_103a) split-BF16 scan path: state and entry points.
+#pragma once
+
+#include "common.cuh"
+
+namespace gw {
+
+struct TcState;
+
+struct TcSetupArgs {
+  int algo, n, q, t;
+  const double* Linv;    // CHOL: t x n x n row-major lower (FP64)
+  const double* XLw;     // CHOL: t x q x n
+  const double* rw;      // t x n: CHOL whitened null residual / EIG weighted residual
+  const double* Zt;      // EIG: n x n, row r = eigenvector r
+  const double* planes;  // EIG: t x (q+2) x ldp FP64 planes
+  int ldp;
+  const double* P;       // t x q x q
+  const double* b0;      // t x q
+};
+
+struct TcScanArgs {
+  const int8_t* XR;  // m x n device
+  int64_t m;
+  float* B;          // m x t x p device
+  float* wald;       // m x t device or NULL
+  int* flags;
+};
+
+// Throws Fail{GWAS_ERR_UNSUPPORTED} for sizes the tensor-core kernels do not cover.
+void tc_check_supported(int algo, int n, int q, int t);
+TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a);
+void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a);
+void tc_destroy(TcState* st);
+
+}  // namespace gw

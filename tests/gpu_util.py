@@ -1,0 +1,32 @@
+"""Helpers shared by the GPU parity tests: run the library through its C ABI, compare with the
+oracle using the error measures of oracle.gls (relative where large, in standard errors near 0)."""
+import numpy as np
+
+from oracle import gls
+
+
+def run(g, c, algo, precision, XR=None, device=True, block_snps=0, f64=False):
+    import torch
+    XR = c.XR if XR is None else XR
+    h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, algo=algo, precision=precision,
+                     block_snps=block_snps)
+    try:
+        m, t, p = XR.shape[0], c.t, c.p
+        dt = torch.float64 if f64 else torch.float32
+        dev = "cuda" if device else "cpu"
+        xr = torch.from_numpy(np.ascontiguousarray(XR)).to(dev)
+        B = torch.full((m, t, p), float("nan"), dtype=dt, device=dev)
+        W = torch.full((m, t), float("nan"), dtype=dt, device=dev)
+        (g.gwas_scan_f64 if f64 else g.gwas_scan)(h, xr, B, W)
+        if device:
+            torch.cuda.synchronize()
+        nsing = g.gwas_singular_count(h)
+        return B.cpu().numpy().astype(np.float64), W.cpu().numpy().astype(np.float64), nsing
+    finally:
+        g.gwas_destroy(h)
+
+
+def max_errors(B, W, Bref, Wref, Vref):
+    eb = gls.rel_err_b(B, Bref, Vref)
+    ew = gls.rel_err_wald(W, Wref)
+    return float(np.nanmax(eb)), float(np.nanmax(ew))

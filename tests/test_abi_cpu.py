@@ -1,0 +1,90 @@
+"""The C-ABI library loads and exports what include/gwas.h declares; argument checks (CPU only).
+
+No call here reaches a CUDA compute path: argument validation runs before any device work.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.abspath(os.path.join(os.path.dirname(__file__), ".."))
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_1207_2169_gb300 import _build
+    _build.build()
+    import paper_1207_2169_gb300 as g
+    return g
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(gwas_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(g):
+    declared = _declared()
+    assert declared, "no declarations parsed"
+    out = subprocess.run(["nm", "-D", "--defined-only", g.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (gwas_[a-z0-9_]+)", out))
+    assert declared <= exported, declared - exported
+    assert set(g.EXPORTS) == declared
+    for name in declared:
+        assert hasattr(g.lib, name)
+
+
+def test_default_options(g):
+    o = g.gwas_default_options()
+    assert (o.algo, o.precision, o.block_snps, o.validate_genotypes, o.device) == (0, 2, 0, 0, 0)
+
+
+def test_destroy_null_is_noop(g):
+    g.lib.gwas_destroy(None)
+
+
+@pytest.mark.parametrize("case", ["n0", "q0", "q8", "t0", "h2_one", "h2_neg", "s2_zero", "algo", "prec"])
+def test_setup_rejects_bad_arguments(g, case):
+    n, q, t = 6, 2, 2
+    Phi = np.eye(n); XL = np.ones((n, q)); Y = np.zeros((n, t))
+    h2 = np.full(t, 0.5); s2 = np.ones(t)
+    opt = g.gwas_default_options()
+    nn, qq, tt = n, q, t
+    if case == "n0": nn = 0
+    if case == "q0": qq = 0
+    if case == "q8": qq = 8
+    if case == "t0": tt = 0
+    if case == "h2_one": h2[1] = 1.0
+    if case == "h2_neg": h2[0] = -0.1
+    if case == "s2_zero": s2[0] = 0.0
+    if case == "algo": opt.algo = 7
+    if case == "prec": opt.precision = 9
+    XLb = np.ones((n, 8))
+    out = ctypes.c_void_p(123)
+    st = g.lib.gwas_setup(Phi.ctypes.data, nn, XLb.ctypes.data, qq, Y.ctypes.data, tt,
+                          h2.ctypes.data, s2.ctypes.data, ctypes.byref(opt), ctypes.byref(out))
+    assert st == -1, (case, st, g.gwas_last_error())
+    assert out.value is None
+    assert g.gwas_last_error() != ""
+
+
+def test_setup_null_pointers(g):
+    out = ctypes.c_void_p()
+    assert g.lib.gwas_setup(None, 4, None, 1, None, 1, None, None, None, ctypes.byref(out)) == -1
+    assert g.lib.gwas_setup(None, 4, None, 1, None, 1, None, None, None, None) == -1
+
+
+def test_null_handle_calls(g):
+    assert g.lib.gwas_scan(None, None, 10, 1, None, None, 1, None) == -1
+    assert g.lib.gwas_singular_count(None) == -1
+    ms = ctypes.c_double()
+    assert g.lib.gwas_setup_timing(None, ctypes.byref(ms)) == -1
+    assert g.lib.gwas_info(None, None, None, None, None, None) == -1
