@@ -3,7 +3,7 @@
 Every function here has the name of the C entry point it calls and does no arithmetic of the
 method: it checks shapes/dtypes, passes pointers (NumPy arrays or torch tensors, host or CUDA)
 and raises GwasError on a non-zero status.  The library must have been built
-(`python -m paper_1207_2169_gb300._build` or __graft_entry__.build()); importing this module
+(`python paper_1207_2169_gb300/_build.py` or __graft_entry__.build()); importing this module
 without it raises ImportError -- there is no fallback.
 """
 from __future__ import annotations
@@ -42,7 +42,7 @@ class gwas_options(ctypes.Structure):
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with "
-                          "`python -m paper_1207_2169_gb300._build` (needs nvcc)")
+                          "`python paper_1207_2169_gb300/_build.py` (needs nvcc)")
     lib = ctypes.CDLL(LIB_PATH)
     vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
     lib.gwas_default_options.argtypes = [ctypes.POINTER(gwas_options)]

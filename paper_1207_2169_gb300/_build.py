@@ -2,7 +2,7 @@
 
 Each .cu file is compiled to an object in parallel, then linked into one shared library with
 the CUDA runtime linked statically.  Rebuilds only when a source or header is newer than the
-library.  Usage: python -m paper_1207_2169_gb300._build [-v] [--force]
+library.  Usage: python paper_1207_2169_gb300/_build.py [-v] [--force]
 """
 from __future__ import annotations
 

@@ -323,6 +323,8 @@ gwas_status scan_impl(gwas_handle h, const int8_t* XR, int64_t m, int xr_dev, vo
   cudaStream_t s = (cudaStream_t)stream;
   const int n = h->n, t = h->t, p = h->p;
   const size_t ob = out_f64 ? 8 : 4;
+  if (h->validate)  // each call reports only its own genotypes
+    GW_CUDA(cudaMemsetAsync(h->flags + FLAG_GENOTYPE, 0, sizeof(int), s));
   if (xr_dev && out_dev) {
     ensure_xt(h, m < h->block_snps ? m : h->block_snps);
     scan_block(h, XR, m, B, wald, out_f64, s);

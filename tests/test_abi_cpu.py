@@ -15,8 +15,8 @@ ROOT = os.path.abspath(os.path.join(os.path.dirname(__file__), ".."))
 
 @pytest.fixture(scope="module")
 def g():
-    from paper_1207_2169_gb300 import _build
-    _build.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1207_2169_gb300 as g
     return g
 
