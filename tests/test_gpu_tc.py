@@ -1,0 +1,75 @@
+"""Parity of the split-BF16 tensor-core path (tcgen05) with the FP64 oracle.
+
+Tolerance 1e-4 in the error measure of oracle.gls (relative error, or error in standard-error
+units where the coefficient is near zero), the bound the split path is specified to meet.
+Shapes cover several 128-SNP tiles with ragged tails, n not a multiple of 8 / 64 / 256, p from 2
+to 8, more than one trait, the full workload-1 size on a slice, and singular SNPs.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gls
+from gpu_util import run, max_errors
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1207_2169_gb300 as g
+    return g
+
+
+def test_chol_golden_pedigree(g, golden_pedigree):
+    gp = golden_pedigree
+    for j in range(2):
+        c = synth.Cohort(Phi=gp["Phi"], XL=gp["XL"], Y=gp["Y"][:, j:j + 1], h2=gp["h2"][j:j + 1],
+                         s2=gp["s2"][j:j + 1], XR=gp["XR"], beta=None)
+        B, W, _ = run(g, c, "chol", "split_bf16")
+        eb, ew = max_errors(B, W, gp["B"][:, j:j + 1], gp["W"][:, j:j + 1], gp["Vd"][:, j:j + 1])
+        assert eb < TOL and ew < TOL, (eb, ew)
+
+
+@pytest.mark.parametrize("n,q,m,t", [(256, 3, 1000, 1), (97, 1, 131, 1), (200, 3, 300, 2),
+                                     (130, 7, 257, 1), (520, 2, 129, 1), (64, 3, 1, 1)])
+def test_chol_split_ragged(g, n, q, m, t):
+    c = synth.small_problem(3 * n + q + m, n=n, q=q, m=m, t=t)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
+    B, W, nsing = run(g, c, "chol", "split_bf16")
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < TOL and ew < TOL, (eb, ew)
+    assert nsing == 0
+
+
+def test_chol_split_workload0(g):
+    c = synth.make_cohort(0)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
+    B, W, _ = run(g, c, "chol", "split_bf16")
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < TOL and ew < TOL, (eb, ew)
+
+
+def test_chol_split_workload1_slice(g):
+    """Workload 1's shape (n = 1000, h2 = 0.5) on 3,000 SNPs, every SNP checked."""
+    c = synth.make_cohort(1, m=3000)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
+    B, W, _ = run(g, c, "chol", "split_bf16")
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < TOL and ew < TOL, (eb, ew)
+
+
+def test_chol_split_singular_and_streamed(g):
+    c = synth.small_problem(21, n=300, q=3, m=700, t=1)
+    XR = c.XR.copy()
+    XR[[0, 255, 699]] = 2
+    Bd, Wd, nsing = run(g, c, "chol", "split_bf16", XR=XR)
+    assert nsing == 3
+    assert np.all(np.isnan(Bd[[0, 255, 699]])) and np.all(np.isnan(Wd[[0, 255, 699]]))
+    Bh, Wh, _ = run(g, c, "chol", "split_bf16", XR=XR, device=False, block_snps=256)
+    assert np.array_equal(np.isnan(Bd), np.isnan(Bh))
+    ok = ~np.isnan(Bd)
+    assert np.array_equal(Bd[ok], Bh[ok])
