@@ -97,7 +97,7 @@ __device__ __forceinline__ void store_tile(uint8_t* tile, const uint2 (&v)[8], i
   for (int l = 0; l < 8; ++l) {
     const int e = ct + 128 * l, r = e >> 3, jc = e & 7;
     uint8_t* dst = tile + (r >> 3) * 1024 + (r & 7) * 128 + ((jc ^ (r & 7)) << 4);
-    *reinterpret_cast<uint4*>(dst) = i8x8_to_bf16x8(v[l]);
+    *reinterpret_cast<uint4*>(dst) = geno8_to_bf16x8(v[l]);
   }
 }
 

@@ -1,0 +1,456 @@
+// EIG on the tensor cores (tcgen05 / TMEM / TMA, sm_103a): Algorithm 4 lines 3 and 12-16.
+//
+// Per SNP i and trait j the bordered system needs three reductions over the n individuals:
+//     a_ij[k] = x_i^T M_j^-1 X_L[:,k],   c_ij = x_i^T M_j^-1 r_j,   s_ij = x_i^T M_j^-1 x_i,
+// with r_j = y_j - X_L b0_j the null-model residual.  With Phi = Z W Z^T, M_j^-1 = Z D_j Z^T.
+// a and c are linear in the raw genotypes, so they are contracted against the precomputed
+// columns U_j = Z D_j Z^T [X_L | r_j] (exact genotype operand, U split hi + lo: 2 products);
+// s needs the eigenbasis: s_ij = sum_r (Z^T x_i)_r^2 d_j[r].  Three kernels share one template:
+//   ROT  Xsq = (Z^T X_R)^2, written as hi + lo BF16 planes  (A: genotypes, B: Z^T split)
+//   SQ   s_ij = Xsq_i . d_j                                  (A: Xsq split, B: d split, 3 products)
+//   AC   a, c from the genotypes, then the Schur-complement solve in FP32 with s_ij
+//                                                            (A: genotypes, B: U split)
+// A persistent CTA walks (128-SNP tile, 256-column block) work items, eight SNP tiles per
+// column block at a time so that both operands are reused from L2.
+//
+// Warp roles (320 threads): 0-3 epilogue (one SNP per TMEM lane), 4 TMA producer, 5 MMA issuer
+// and TMEM owner (two 256-column FP32 accumulators), 6-9 genotype converters (ROT and AC).
+#include "tc_kernels.cuh"
+#include "tc_ptx.cuh"
+
+namespace gw {
+using namespace tc;
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 64;
+constexpr int SA = 4;
+constexpr int SB = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int NUM_THREADS = 320;
+constexpr int TMEM_COLS = 512;
+constexpr int GROUP_M = 8;
+constexpr int QMAX = 7;
+constexpr int CST_FLOATS = 64 * (QMAX * QMAX + QMAX) + 256;  // AC: P_j and b0_j of a block
+constexpr uint64_t WAIT_NS = 4000000000ull;
+
+enum { EPI_ROT = 0, EPI_SQ = 1, EPI_AC = 2 };
+
+struct __align__(8) Bars {
+  uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full[2], acc_empty[2], done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+constexpr size_t SMEM_BYTES = 1024 + SA * A_BYTES + SB * B_BYTES + CST_FLOATS * 4 + sizeof(Bars);
+
+__device__ __forceinline__ void work_coords(int64_t w, int64_t mtiles, int nblk, int64_t& tile,
+                                            int& nb) {
+  const int64_t per_group = (int64_t)GROUP_M * nblk;
+  const int64_t g = w / per_group;
+  const int64_t r = w % per_group;
+  const int64_t first = g * GROUP_M;
+  const int64_t rows = mtiles - first < GROUP_M ? mtiles - first : GROUP_M;
+  nb = (int)(r / rows);
+  tile = first + r % rows;
+}
+
+__device__ __forceinline__ void load_geno(uint2 (&v)[8], const int8_t* XR, int64_t m, int n,
+                                          int ct, int64_t tile, int ks, bool aligned8) {
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    const int e = ct + 128 * l, r = e >> 3, jc = e & 7;
+    const int64_t snp = tile * BM + r;
+    const int k = ks * BK + jc * 8;
+    v[l] = make_uint2(0u, 0u);
+    if (snp < m && k < n) {
+      const int8_t* src = XR + snp * n + k;
+      if (aligned8) {
+        v[l] = __ldg(reinterpret_cast<const uint2*>(src));
+      } else {
+        uint32_t w[2] = {0u, 0u};
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+          if (k + b < n) w[b >> 2] |= (uint32_t)(uint8_t)src[b] << (8 * (b & 3));
+        v[l] = make_uint2(w[0], w[1]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void store_geno(uint8_t* tile, const uint2 (&v)[8], int ct) {
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    const int e = ct + 128 * l, r = e >> 3, jc = e & 7;
+    uint8_t* dst = tile + (r >> 3) * 1024 + (r & 7) * 128 + ((jc ^ (r & 7)) << 4);
+    *reinterpret_cast<uint4*>(dst) = geno8_to_bf16x8(v[l]);
+  }
+}
+
+// 4 or 8 consecutive FP32 TMEM columns of this warp's lanes (no wait).
+template <int QP>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[QP]);
+template <>
+__device__ __forceinline__ void tmem_ld_cols<4>(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+template <>
+__device__ __forceinline__ void tmem_ld_cols<8>(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+template <int EPI, int QP>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    eig_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const EigTcParams p) {
+  constexpr bool CONV = EPI != EPI_SQ;  // A operand = genotypes through the converters
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + SA * A_BYTES;
+  float* cst = (float*)(sB + SB * B_BYTES);
+  Bars* bars = (Bars*)(cst + CST_FLOATS);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t mtiles = (p.m + BM - 1) / BM;
+  const int64_t nwork = mtiles * p.nblk;
+  const int nk = p.kpad / BK;
+  int* tflag = p.flags + FLAG_TIMEOUT;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < SA; ++i) {
+      mbar_init(&bars->a_full[i], CONV ? 128 : 1);
+      mbar_init(&bars->a_empty[i], 1);
+    }
+    for (int i = 0; i < SB; ++i) {
+      mbar_init(&bars->b_full[i], 1);
+      mbar_init(&bars->b_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bars->acc_full[i], 1);
+      mbar_init(&bars->acc_empty[i], 4);
+    }
+    mbar_init(&bars->done, 1);
+    bars->abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 5) {
+    tmem_alloc(&bars->tmem_base, TMEM_COLS);
+    tmem_relinquish();
+  }
+  if (warp == 4 && lane == 0) {
+    if (!CONV) prefetch_tensormap(&mapA);
+    prefetch_tensormap(&mapB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  volatile int* abort = &bars->abort;
+
+  if (warp == 4) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int as = 0, bs = 0;
+      uint32_t aph = 0, bph = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+        int64_t tile;
+        int nb;
+        work_coords(w, mtiles, p.nblk, tile, nb);
+        for (int ks = 0; ks < nk && ok; ++ks) {
+          if (!CONV) {
+            for (int piece = 0; piece < 2 && ok; ++piece) {
+              ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
+              if (!ok) break;
+              mbar_arrive_expect_tx(&bars->a_full[as], A_BYTES);
+              tma_load_2d(sA + as * A_BYTES, &mapA, &bars->a_full[as], ks * BK,
+                          (int32_t)(piece * p.a_piece_rows + tile * BM));
+              if (++as == SA) { as = 0; aph ^= 1; }
+            }
+          }
+          for (int piece = 0; piece < 2 && ok; ++piece) {
+            ok = mbar_wait(&bars->b_empty[bs], bph ^ 1, abort, tflag, WAIT_NS);
+            if (!ok) break;
+            mbar_arrive_expect_tx(&bars->b_full[bs], B_BYTES);
+            tma_load_2d(sB + bs * B_BYTES, &mapB, &bars->b_full[bs], ks * BK,
+                        piece * p.b_piece_rows + nb * p.b_rows_per_blk);
+            if (++bs == SB) { bs = 0; bph ^= 1; }
+          }
+        }
+      }
+    }
+  } else if (warp == 5) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int as = 0, bs = 0, buf = 0;
+      uint32_t aph = 0, bph = 0, accph = 0;
+      bool ok = true;
+      const uint32_t idesc = idesc_bf16(BM, BN);
+      for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+        ok = mbar_wait(&bars->acc_empty[buf], accph ^ 1, abort, tflag, WAIT_NS);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + buf * BN;
+        for (int ks = 0; ks < nk && ok; ++ks) {
+          if (CONV) {
+            // products (x, U_hi), (x, U_lo) -- the genotype operand is exact
+            ok = mbar_wait(&bars->a_full[as], aph, abort, tflag, WAIT_NS);
+            if (!ok) break;
+            tc_fence_after();
+            const uint64_t ad = sw128_desc(sA + as * A_BYTES);
+            for (int piece = 0; piece < 2 && ok; ++piece) {
+              ok = mbar_wait(&bars->b_full[bs], bph, abort, tflag, WAIT_NS);
+              if (!ok) break;
+              tc_fence_after();
+              const uint64_t bd = sw128_desc(sB + bs * B_BYTES);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(dt, ad + 2 * kk, bd + 2 * kk, idesc, (ks | piece | kk) != 0);
+              mma_commit(&bars->b_empty[bs]);
+              if (++bs == SB) { bs = 0; bph ^= 1; }
+            }
+            mma_commit(&bars->a_empty[as]);
+            if (++as == SA) { as = 0; aph ^= 1; }
+          } else {
+            // products (A_hi, B_hi), (A_lo, B_hi), (A_hi, B_lo)
+            const int a0 = as, b0s = bs;
+            int a1 = as + 1 == SA ? 0 : as + 1;
+            int b1 = bs + 1 == SB ? 0 : bs + 1;
+            const uint32_t aph1 = a1 == 0 ? aph ^ 1 : aph, bph1 = b1 == 0 ? bph ^ 1 : bph;
+            ok = mbar_wait(&bars->a_full[a0], aph, abort, tflag, WAIT_NS) &&
+                 mbar_wait(&bars->a_full[a1], aph1, abort, tflag, WAIT_NS) &&
+                 mbar_wait(&bars->b_full[b0s], bph, abort, tflag, WAIT_NS);
+            if (!ok) break;
+            tc_fence_after();
+            const uint64_t ah = sw128_desc(sA + a0 * A_BYTES), al = sw128_desc(sA + a1 * A_BYTES);
+            const uint64_t bh = sw128_desc(sB + b0s * B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              mma_bf16(dt, ah + 2 * kk, bh + 2 * kk, idesc, (ks | kk) != 0);
+              mma_bf16(dt, al + 2 * kk, bh + 2 * kk, idesc, 1u);
+            }
+            mma_commit(&bars->b_empty[b0s]);
+            ok = mbar_wait(&bars->b_full[b1], bph1, abort, tflag, WAIT_NS);
+            if (!ok) break;
+            tc_fence_after();
+            const uint64_t bl = sw128_desc(sB + b1 * B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) mma_bf16(dt, ah + 2 * kk, bl + 2 * kk, idesc, 1u);
+            mma_commit(&bars->b_empty[b1]);
+            mma_commit(&bars->a_empty[a0]);
+            mma_commit(&bars->a_empty[a1]);
+            as = a1 + 1 == SA ? 0 : a1 + 1;
+            if (as == 0 || a1 == 0) aph ^= 1;
+            bs = b1 + 1 == SB ? 0 : b1 + 1;
+            if (bs == 0 || b1 == 0) bph ^= 1;
+          }
+        }
+        if (ok) mma_commit(&bars->acc_full[buf]);
+        if (++buf == 2) { buf = 0; accph ^= 1; }
+      }
+      mma_commit(&bars->done);
+      mbar_wait(&bars->done, 0, abort, tflag, WAIT_NS);
+    }
+  } else if (warp >= 6) {
+    // ------------------------------------------------------------ genotype converters
+    if (CONV) {
+      const int ct = threadIdx.x - 192;
+      const bool aligned8 = (p.n % 8 == 0) && ((reinterpret_cast<uintptr_t>(p.XR) & 7) == 0);
+      int as = 0;
+      uint32_t aph = 0;
+      bool ok = true;
+      uint2 v0[8], v1[8];
+      for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+        int64_t tile;
+        int nb;
+        work_coords(w, mtiles, p.nblk, tile, nb);
+        // two K steps of loads in flight
+        load_geno(v0, p.XR, p.m, p.n, ct, tile, 0, aligned8);
+        if (nk > 1) load_geno(v1, p.XR, p.m, p.n, ct, tile, 1, aligned8);
+        for (int ks = 0; ks < nk && ok; ks += 2) {
+          ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
+          if (!ok) break;
+          store_geno(sA + as * A_BYTES, v0, ct);
+          fence_proxy_async_smem();
+          mbar_arrive(&bars->a_full[as]);
+          if (++as == SA) { as = 0; aph ^= 1; }
+          if (ks + 2 < nk) load_geno(v0, p.XR, p.m, p.n, ct, tile, ks + 2, aligned8);
+          if (ks + 1 >= nk) break;
+          ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
+          if (!ok) break;
+          store_geno(sA + as * A_BYTES, v1, ct);
+          fence_proxy_async_smem();
+          mbar_arrive(&bars->a_full[as]);
+          if (++as == SA) { as = 0; aph ^= 1; }
+          if (ks + 3 < nk) load_geno(v1, p.XR, p.m, p.n, ct, tile, ks + 3, aligned8);
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 0-3)
+    int buf = 0;
+    uint32_t accph = 0;
+    bool ok = true;
+    const int q = p.q, q1 = q + 1;
+    for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
+      int64_t tile;
+      int nb;
+      work_coords(w, mtiles, p.nblk, tile, nb);
+      const int64_t snp = tile * BM + 32 * warp + lane;
+      if (EPI == EPI_AC) {
+        // P_j and b0_j of this block's traits, FP32, into shared memory
+        named_bar(1, 128);
+        const int j0 = nb * p.traits_per_blk;
+        const int per = q * q + q;
+        for (int e = threadIdx.x; e < p.traits_per_blk * per; e += 128) {
+          const int jl = e / per, u = e % per, j = j0 + jl;
+          float v = 0.f;
+          if (j < p.t) v = u < q * q ? p.P[(int64_t)j * q * q + u] : p.b0[(int64_t)j * q + u - q * q];
+          cst[e] = v;
+        }
+        named_bar(1, 128);
+      }
+      if (ok) ok = mbar_wait(&bars->acc_full[buf], accph, abort, tflag, WAIT_NS);
+      if (ok) {
+        tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + buf * BN;
+        if (EPI == EPI_ROT) {
+          for (int c = 0; c < BN / 32; ++c) {
+            float v[32];
+            tmem_ld32(base + 32 * c, v);
+            const int col0 = nb * BN + 32 * c;
+            if (snp < p.m && col0 < p.kpad) {
+              uint32_t hi[16], lo[16];
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const float s0 = v[2 * i] * v[2 * i], s1 = v[2 * i + 1] * v[2 * i + 1];
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(s0), h1 = __float2bfloat16_rn(s1);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(s0 - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(s1 - __bfloat162float(h1));
+                hi[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                lo[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+              }
+              uint4* dh = reinterpret_cast<uint4*>(p.xsq + snp * p.kpad + col0);
+              uint4* dl = reinterpret_cast<uint4*>(p.xsq + (p.a_piece_rows + snp) * p.kpad + col0);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                dh[u] = make_uint4(hi[4 * u], hi[4 * u + 1], hi[4 * u + 2], hi[4 * u + 3]);
+                dl[u] = make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]);
+              }
+            }
+          }
+        } else if (EPI == EPI_SQ) {
+          for (int c = 0; c < BN / 32; ++c) {
+            float v[32];
+            tmem_ld32(base + 32 * c, v);
+            if (snp < p.m) {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                const int j = nb * BN + 32 * c + i;
+                if (j < p.t) p.sbuf[(int64_t)j * p.lds + snp] = v[i];
+              }
+            }
+          }
+        } else {
+          const int T = p.traits_per_blk;
+          for (int j8 = 0; j8 < T; j8 += 8) {
+            uint32_t r[8][QP];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) tmem_ld_cols<QP>(base + (j8 + u) * q1, r[u]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int jl = j8 + u, j = nb * T + jl;
+              if (jl >= T || j >= p.t || snp >= p.m) continue;
+              const float* Pj = cst + jl * (q * q + q);
+              float a[QMAX], vq[QMAX], aPa = 0.f;
+#pragma unroll
+              for (int k = 0; k < QMAX; ++k) a[k] = k < q ? __uint_as_float(r[u][k < QP ? k : 0]) : 0.f;
+              float cval = 0.f;
+#pragma unroll
+              for (int k = 0; k < QP; ++k)
+                if (k == q) cval = __uint_as_float(r[u][k]);
+#pragma unroll
+              for (int k = 0; k < QMAX; ++k) {
+                float acc = 0.f;
+                if (k < q) {
+#pragma unroll
+                  for (int l = 0; l < QMAX; ++l)
+                    if (l < q) acc = fmaf(Pj[k * q + l], a[l], acc);
+                  aPa = fmaf(a[k], acc, aPa);
+                }
+                vq[k] = acc;
+              }
+              const float s = p.sbuf[(int64_t)j * p.lds + snp];
+              const float sigma = s - aPa;
+              float* Bo = p.B + (snp * p.t + j) * q1;
+              if (sigma > 1e-5f * s) {
+                const float bs = cval / sigma;
+#pragma unroll
+                for (int k = 0; k < QMAX; ++k)
+                  if (k < q) Bo[k] = Pj[q * q + k] - vq[k] * bs;
+                Bo[q] = bs;
+                if (p.W) p.W[snp * p.t + j] = bs * cval;
+              } else {
+                for (int k = 0; k < q1; ++k) Bo[k] = __int_as_float(0x7fc00000);
+                if (p.W) p.W[snp * p.t + j] = __int_as_float(0x7fc00000);
+                atomicAdd(&p.flags[FLAG_SINGULAR], 1);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
+      }
+      if (++buf == 2) { buf = 0; accph ^= 1; }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+template <int EPI, int QP>
+void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
+                const EigTcParams& p, int num_sms) {
+  static bool prepared = false;
+  if (!prepared) {
+    GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    prepared = true;
+  }
+  const int64_t work = ((p.m + BM - 1) / BM) * p.nblk;
+  const unsigned grid = (unsigned)(work < num_sms ? work : num_sms);
+  eig_tc_kernel<EPI, QP><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mapA, mapB, p);
+  GW_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUtensorMap& mapB,
+                   const EigTcParams& p, int num_sms) {
+  if (p.m <= 0 || p.nblk <= 0) return;
+  GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q out of range");
+  const bool small_q = p.q + 1 <= 4;
+  switch (stage) {
+    case 0: launch_one<EPI_ROT, 4>(s, mapA, mapB, p, num_sms); break;
+    case 1: launch_one<EPI_SQ, 4>(s, mapA, mapB, p, num_sms); break;
+    default:
+      if (small_q) launch_one<EPI_AC, 4>(s, mapA, mapB, p, num_sms);
+      else launch_one<EPI_AC, 8>(s, mapA, mapB, p, num_sms);
+  }
+}
+
+}  // namespace gw

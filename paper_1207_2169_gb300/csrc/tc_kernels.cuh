@@ -31,4 +31,31 @@ void chol_tc_launch(cudaStream_t s, const CUtensorMap& map256, const CUtensorMap
                     const CholTcParams& p, int num_sms);
 void chol_tc_prepare();
 
+// ------------------------------------------------------------------------------------------
+// EIG stages (tc_eig.cu): 0 = ROT (Xsq = (Z^T X_R)^2 split), 1 = SQ (s_ij), 2 = AC (a, c, Schur)
+// ------------------------------------------------------------------------------------------
+struct EigTcParams {
+  const int8_t* XR;        // m x n genotypes (ROT, AC)
+  int64_t m;
+  int n, q, t, kpad;
+  int nblk;                // 256-column blocks of the accumulator
+  int b_piece_rows;        // row of the lo piece in the B tensor map
+  int b_rows_per_blk;      // B rows per column block
+  int a_piece_rows;        // Xsq capacity: row of the lo piece (SQ map, ROT output)
+  int traits_per_blk;      // AC: traits per column block
+  __nv_bfloat16* xsq;      // ROT output: hi rows [0, cap), lo rows [cap, 2 cap), ld kpad
+  float* sbuf;             // SQ output / AC input: s_ij at sbuf[j * lds + i]
+  int64_t lds;
+  const float* P;          // AC: t x q x q
+  const float* b0;         // AC: t x q
+  float* B;                // AC: m x t x p
+  float* W;                // AC: m x t or NULL
+  int* flags;
+};
+// mapA: the Xsq planes (SQ only; ignored otherwise).  mapB: Z^T split (ROT), d split (SQ),
+// U split (AC).  All BF16, 64-column boxes, 128-byte swizzle; mapA has 128-row boxes and mapB
+// 256-row boxes.
+void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUtensorMap& mapB,
+                   const EigTcParams& p, int num_sms);
+
 }  // namespace gw

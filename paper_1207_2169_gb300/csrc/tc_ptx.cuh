@@ -176,6 +176,23 @@ __device__ __forceinline__ void named_bar(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Four genotype bytes (each 0, 1 or 2) -> four BF16 values (0x0000, 0x3F80, 0x4000) in two
+// words, by a byte-permute table lookup: for a pair of genotypes (g0, g1) the selector nibbles
+// are (g0, g0+4, g1, g1+4), picking the low byte from {00,80,00} and the high byte from
+// {00,3F,40}.  (t * 17 spreads the two genotype bytes of t into nibbles 0 and 2.)  Values
+// outside {0,1,2} give unspecified BF16 values; validate_genotypes rejects them.
+__device__ __forceinline__ uint2 geno4_to_bf16x4(uint32_t w) {
+  constexpr uint32_t LO = 0x00008000u, HI = 0x00403F00u;
+  const uint32_t s0 = (w & 0xFFFFu) * 17u + 0x4040u;
+  const uint32_t s1 = (w >> 16) * 17u + 0x4040u;
+  return make_uint2(__byte_perm(LO, HI, s0), __byte_perm(LO, HI, s1));
+}
+
+__device__ __forceinline__ uint4 geno8_to_bf16x8(uint2 w) {
+  const uint2 a = geno4_to_bf16x4(w.x), b = geno4_to_bf16x4(w.y);
+  return make_uint4(a.x, a.y, b.x, b.y);
+}
+
 // Eight int8 values -> eight BF16 (exact for |v| <= 256) packed in a uint4.
 __device__ __forceinline__ uint4 i8x8_to_bf16x8(uint2 w) {
   uint32_t o[4];
