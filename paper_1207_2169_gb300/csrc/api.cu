@@ -221,6 +221,10 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     ta.Linv = h->Linv; ta.XLw = h->XLw; ta.rw = h->rw;
     ta.Zt = h->Zt; ta.planes = h->planes; ta.ldp = h->ldp;
     ta.P = h->P; ta.b0 = h->b0;
+    ta.block_snps = h->block_snps;
+    ta.intercept = 1;
+    for (int i = 0; i < n; ++i)
+      if (XL[i] != 1.0) ta.intercept = 0;
     h->tc = tc_setup(s, ta);
   }
   GW_CUDA(cudaEventRecord(e1, s));

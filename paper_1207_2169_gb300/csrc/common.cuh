@@ -94,6 +94,10 @@ void convert_f64_to_f32(cudaStream_t s, const double* x, float* y, int64_t count
 // hi = bf16(x), lo = bf16(x - hi) for a rows x cols row-major matrix with leading dims.
 void split_bf16(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx,
                 __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo);
+// As split_bf16, with output row r taken from input row (r / gout) * gin + r % gout + off
+// (selects `gout` of every `gin` input rows, starting at `off`).
+void split_bf16_rows(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx, int gin,
+                     int gout, int off, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo);
 
 // ------------------------------------------------------------------------------------------
 // Scan kernels, scan_simt.cu (plain FP64 / FP32 CUDA-core forms)

@@ -500,7 +500,30 @@ __global__ void split_bf16_kernel(const double* __restrict__ x, int rows, int co
     lo[e] = __double2bfloat16(v - (double)__bfloat162float(h));
   }
 }
+
+__global__ void split_bf16_rows_kernel(const double* __restrict__ x, int rows, int cols,
+                                       int64_t ldx, int gin, int gout, int off,
+                                       __nv_bfloat16* __restrict__ hi,
+                                       __nv_bfloat16* __restrict__ lo, int64_t ldo) {
+  const int64_t total = (int64_t)rows * ldo;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ldo;
+    const int c = (int)(e % ldo);
+    const int64_t src = (r / gout) * gin + r % gout + off;
+    const double v = c < cols ? x[src * ldx + c] : 0.0;
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    hi[e] = h;
+    lo[e] = __double2bfloat16(v - (double)__bfloat162float(h));
+  }
+}
 }  // namespace
+
+void split_bf16_rows(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx, int gin,
+                     int gout, int off, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo) {
+  split_bf16_rows_kernel<<<1184, 256, 0, s>>>(x, rows, cols, ldx, gin, gout, off, hi, lo, ldo);
+  GW_CHECK_LAUNCH();
+}
 
 void trait_pack(cudaStream_t s, const TraitPackArgs& a) {
   GW_REQUIRE(a.q >= 1 && a.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", a.q, QMAX);

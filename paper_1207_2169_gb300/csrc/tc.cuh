@@ -17,6 +17,8 @@ struct TcSetupArgs {
   int ldp;
   const double* P;       // t x q x q
   const double* b0;      // t x q
+  int block_snps;        // EIG: SNPs per internal chunk (sizes the per-chunk scratch)
+  int intercept;         // column 0 of X_L is all ones: SNPs may be centred (EIG)
 };
 
 struct TcScanArgs {

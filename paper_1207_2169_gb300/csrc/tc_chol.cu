@@ -34,7 +34,7 @@ constexpr int SB = 4;                   // L^-1 tile ring (one piece per slot)
 constexpr int A_BYTES = BM * BK * 2;    // 16 KB
 constexpr int B_BYTES = BN * BK * 2;    // 32 KB
 constexpr int QMAX = 7;
-constexpr int CST_FLOATS = (QMAX + 1) * BN;
+constexpr int CST_FLOATS = 8192;  // 32 KB: per-row epilogue constants
 constexpr int NUM_THREADS = 320;
 constexpr int TMEM_COLS = 512;
 constexpr uint64_t WAIT_NS = 4000000000ull;
@@ -101,6 +101,8 @@ __device__ __forceinline__ void store_tile(uint8_t* tile, const uint2 (&v)[8], i
   }
 }
 
+// QM: compile-time bound on q (3 or 7), so the epilogue's per-column arrays stay in registers.
+template <int QM>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     chol_tc_kernel(const __grid_constant__ CUtensorMap map256,
                    const __grid_constant__ CUtensorMap map128, const CholTcParams p) {
@@ -251,42 +253,89 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int buf = 0;
     uint32_t accph = 0;
     bool ok = true;
+    // Per-row constants [k][row] (k < q: L^-1 X_L columns, k = q: whitened residual).  When all
+    // rows fit they are loaded once; otherwise the 256 rows of each block are reloaded.
+    const bool resident = (q + 1) * p.rpad <= CST_FLOATS;
+    const int cstride = resident ? p.rpad : BN;
+    if (resident) {
+      for (int e = threadIdx.x; e < (q + 1) * p.rpad; e += 128) {
+        const int k = e / p.rpad, r = e % p.rpad;
+        cst[e] = r < p.n ? (k < q ? p.XLw[(int64_t)k * p.n + r] : p.rw[r]) : 0.f;
+      }
+      named_bar(1, 128);
+    }
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      double S = 0.0, C = 0.0, A[QMAX];
+      double S = 0.0, C = 0.0, A[QM];
 #pragma unroll
-      for (int k = 0; k < QMAX; ++k) A[k] = 0.0;
+      for (int k = 0; k < QM; ++k) A[k] = 0.0;
       for (int nb = 0; nb < nblocks; ++nb) {
-        named_bar(1, 128);  // the previous block's constants are no longer read
-        for (int e = threadIdx.x; e < (q + 1) * BN; e += 128) {
-          const int k = e / BN, i = e % BN, r = nb * BN + i;
-          cst[e] = r < p.n ? (k < q ? p.XLw[(int64_t)k * p.n + r] : p.rw[r]) : 0.f;
+        if (!resident) {
+          named_bar(1, 128);  // the previous block's constants are no longer read
+          for (int e = threadIdx.x; e < (q + 1) * BN; e += 128) {
+            const int k = e / BN, i = e % BN, r = nb * BN + i;
+            cst[e] = r < p.n ? (k < q ? p.XLw[(int64_t)k * p.n + r] : p.rw[r]) : 0.f;
+          }
+          named_bar(1, 128);
         }
-        named_bar(1, 128);
+        const float* cb = resident ? cst + nb * BN : cst;
         if (ok) ok = mbar_wait(&bars->acc_full[buf], accph, abort, tflag, WAIT_NS);
         if (ok) {
           tc_fence_after();
           const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + buf * BN;
-          for (int c = 0; c < BN / 32; ++c) {
-            float v[32];
-            tmem_ld32(base + 32 * c, v);
-            float ss = 0.f, cc = 0.f, aa[QMAX];
+          // FP32 over the block's 256 rows (two levels: 32-row chunks, then chunks), FP64 over
+          // blocks; TMEM loads of the next chunk overlap the arithmetic on the current one.
+          float bs_ = 0.f, bc = 0.f, ba[QM];
 #pragma unroll
-            for (int k = 0; k < QMAX; ++k) aa[k] = 0.f;
-            const float* cr = cst + 32 * c;
+          for (int k = 0; k < QM; ++k) ba[k] = 0.f;
+          uint32_t ra[32], rb[32];
+          auto chunk = [&](const uint32_t (&r)[32], int c) {
+            float ss = 0.f, cc = 0.f, aa[QM];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float x = v[i];
-              ss = fmaf(x, x, ss);
-              cc = fmaf(cr[q * BN + i], x, cc);
+            for (int k = 0; k < QM; ++k) aa[k] = 0.f;
+            const float* cr = cb + 32 * c;
 #pragma unroll
-              for (int k = 0; k < QMAX; ++k)
-                if (k < q) aa[k] = fmaf(cr[k * BN + i], x, aa[k]);
+            for (int i4 = 0; i4 < 8; ++i4) {
+              const float4 cv = *reinterpret_cast<const float4*>(cr + q * cstride + 4 * i4);
+              float4 av[QM];
+#pragma unroll
+              for (int k = 0; k < QM; ++k)
+                if (k < q) av[k] = *reinterpret_cast<const float4*>(cr + k * cstride + 4 * i4);
+              const float x[4] = {__uint_as_float(r[4 * i4]), __uint_as_float(r[4 * i4 + 1]),
+                                  __uint_as_float(r[4 * i4 + 2]), __uint_as_float(r[4 * i4 + 3])};
+              const float cw[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                ss = fmaf(x[e], x[e], ss);
+                cc = fmaf(cw[e], x[e], cc);
+#pragma unroll
+                for (int k = 0; k < QM; ++k) {
+                  if (k < q) {
+                    const float w = e == 0 ? av[k].x : e == 1 ? av[k].y : e == 2 ? av[k].z : av[k].w;
+                    aa[k] = fmaf(w, x[e], aa[k]);
+                  }
+                }
+              }
             }
-            S += ss;
-            C += cc;
+            bs_ += ss;
+            bc += cc;
 #pragma unroll
-            for (int k = 0; k < QMAX; ++k) A[k] += aa[k];
+            for (int k = 0; k < QM; ++k) ba[k] += aa[k];
+          };
+          tmem_ld32_async(base, ra);
+          tmem_wait32(ra);
+#pragma unroll 1
+          for (int c = 0; c < BN / 32; c += 2) {
+            tmem_ld32_async(base + 32 * (c + 1), rb);
+            chunk(ra, c);
+            tmem_wait32(rb);
+            if (c + 2 < BN / 32) tmem_ld32_async(base + 32 * (c + 2), ra);
+            chunk(rb, c + 1);
+            if (c + 2 < BN / 32) tmem_wait32(ra);
           }
+          S += bs_;
+          C += bc;
+#pragma unroll
+          for (int k = 0; k < QM; ++k) A[k] += ba[k];
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
@@ -295,13 +344,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       const int64_t snp = tile * BM + 32 * warp + lane;
       if (ok && snp < p.m) {
-        double v[QMAX], aPa = 0.0;
+        double v[QM], aPa = 0.0;
 #pragma unroll
-        for (int k = 0; k < QMAX; ++k) {
+        for (int k = 0; k < QM; ++k) {
           double acc = 0.0;
           if (k < q) {
 #pragma unroll
-            for (int l = 0; l < QMAX; ++l)
+            for (int l = 0; l < QM; ++l)
               if (l < q) acc += __ldg(&p.P[k * q + l]) * A[l];
             aPa += A[k] * acc;
           }
@@ -313,7 +362,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (sigma > 1e-5 * S) {
           const double bs = C / sigma;
 #pragma unroll
-          for (int k = 0; k < QMAX; ++k)
+          for (int k = 0; k < QM; ++k)
             if (k < q) Bo[k] = (float)(__ldg(&p.b0[k]) - v[k] * bs);
           Bo[q] = (float)bs;
           if (p.W) p.W[snp * p.t + p.j] = (float)(bs * C);
@@ -336,16 +385,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 }  // namespace
 
 void chol_tc_prepare() {
-  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SMEM_BYTES));
+  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)SMEM_BYTES));
 }
 
 void chol_tc_launch(cudaStream_t s, const CUtensorMap& map256, const CUtensorMap& map128,
                     const CholTcParams& p, int num_sms) {
   if (p.m <= 0) return;
+  GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", p.q, QMAX);
   const int64_t tiles = (p.m + BM - 1) / BM;
   const unsigned grid = (unsigned)(tiles < num_sms ? tiles : num_sms);
-  chol_tc_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(map256, map128, p);
+  if (p.q <= 3)
+    chol_tc_kernel<3><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(map256, map128, p);
+  else
+    chol_tc_kernel<QMAX><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(map256, map128, p);
   GW_CHECK_LAUNCH();
 }
 

@@ -81,12 +81,16 @@ __device__ __forceinline__ void load_geno(uint2 (&v)[8], const int8_t* XR, int64
   }
 }
 
-__device__ __forceinline__ void store_geno(uint8_t* tile, const uint2 (&v)[8], int ct) {
+// Genotype tile in the swizzled K-major layout, each value centred by its row's table.  Zero
+// padding (rows past m, columns past n) stays 0: byte 0 maps to -mu, but such rows and columns
+// meet only zero operand rows of the other side (ROT, AC) or are discarded.
+__device__ __forceinline__ void store_geno(uint8_t* tile, const uint2 (&v)[8], int ct,
+                                           const uint32_t (&lo)[8], const uint32_t (&hi)[8]) {
 #pragma unroll
   for (int l = 0; l < 8; ++l) {
     const int e = ct + 128 * l, r = e >> 3, jc = e & 7;
     uint8_t* dst = tile + (r >> 3) * 1024 + (r & 7) * 128 + ((jc ^ (r & 7)) << 4);
-    *reinterpret_cast<uint4*>(dst) = geno8_to_bf16x8(v[l]);
+    *reinterpret_cast<uint4*>(dst) = geno8_to_bf16x8_lut(v[l], lo[l], hi[l]);
   }
 }
 
@@ -268,17 +272,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t aph = 0;
       bool ok = true;
       uint2 v0[8], v1[8];
+      uint32_t lutlo[8], luthi[8];
       for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
         int64_t tile;
         int nb;
         work_coords(w, mtiles, p.nblk, tile, nb);
+        // byte tables of this thread's 8 rows: g - mu_i (mu_i = 0 without centring)
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+          const int64_t snp = tile * BM + ((ct + 128 * l) >> 3);
+          centred_lut(p.mu && snp < p.m ? p.mu[snp] : 0.f, lutlo[l], luthi[l]);
+        }
         // two K steps of loads in flight
         load_geno(v0, p.XR, p.m, p.n, ct, tile, 0, aligned8);
         if (nk > 1) load_geno(v1, p.XR, p.m, p.n, ct, tile, 1, aligned8);
         for (int ks = 0; ks < nk && ok; ks += 2) {
           ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
-          store_geno(sA + as * A_BYTES, v0, ct);
+          store_geno(sA + as * A_BYTES, v0, ct, lutlo, luthi);
           fence_proxy_async_smem();
           mbar_arrive(&bars->a_full[as]);
           if (++as == SA) { as = 0; aph ^= 1; }
@@ -286,7 +297,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (ks + 1 >= nk) break;
           ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
-          store_geno(sA + as * A_BYTES, v1, ct);
+          store_geno(sA + as * A_BYTES, v1, ct, lutlo, luthi);
           fence_proxy_async_smem();
           mbar_arrive(&bars->a_full[as]);
           if (++as == SA) { as = 0; aph ^= 1; }
@@ -305,6 +316,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int nb;
       work_coords(w, mtiles, p.nblk, tile, nb);
       const int64_t snp = tile * BM + 32 * warp + lane;
+      const float mu_snp = (p.mu && snp < p.m) ? p.mu[snp] : 0.f;
       if (EPI == EPI_AC) {
         // P_j and b0_j of this block's traits, FP32, into shared memory
         named_bar(1, 128);
@@ -364,8 +376,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           for (int j8 = 0; j8 < T; j8 += 8) {
             uint32_t r[8][QP];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) tmem_ld_cols<QP>(base + (j8 + u) * q1, r[u]);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int u = 0; u < 8; ++u) {
+              // columns of traits past the block end are not read (their loads would leave the
+              // accumulator); those lanes of r are unused
+              const int jl = j8 + u < T ? j8 + u : 0;
+              tmem_ld_cols<QP>(base + jl * q1, r[u]);
+            }
+            // the wait names every destination register, so no use is scheduled before it
+#pragma unroll
+            for (int h = 0; h < QP / 4; ++h)
+              tmem_wait32(*reinterpret_cast<uint32_t(*)[32]>(&r[4 * h][0]));
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               const int jl = j8 + u, j = nb * T + jl;
@@ -397,6 +417,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                 for (int k = 0; k < QMAX; ++k)
                   if (k < q) Bo[k] = Pj[q * q + k] - vq[k] * bs;
+                // centred SNP x - mu: the intercept (column 0 of X_L) absorbs mu * b_snp
+                if (p.mu) Bo[0] -= mu_snp * bs;
                 Bo[q] = bs;
                 if (p.W) p.W[snp * p.t + j] = bs * cval;
               } else {
@@ -437,7 +459,29 @@ void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB
   GW_CHECK_LAUNCH();
 }
 
+__global__ void snp_centres_kernel(const int8_t* __restrict__ XR, int64_t m, int n,
+                                   float* __restrict__ mu) {
+  const int64_t snp = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (snp >= m) return;
+  const int8_t* x = XR + snp * n;
+  int sum = 0;
+  for (int k = lane; k < n; k += 32) sum += x[k];
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) {
+    // clamp to [0, 2] so g - mu stays within 8 significant bits (exact in BF16)
+    float c = rintf(64.f * (float)sum / (float)n) / 64.f;
+    mu[snp] = fminf(fmaxf(c, 0.f), 2.f);
+  }
+}
+
 }  // namespace
+
+void snp_centres(cudaStream_t s, const int8_t* XR, int64_t m, int n, float* mu) {
+  if (m <= 0) return;
+  snp_centres_kernel<<<(unsigned)((m + 7) / 8), 256, 0, s>>>(XR, m, n, mu);
+  GW_CHECK_LAUNCH();
+}
 
 void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUtensorMap& mapB,
                    const EigTcParams& p, int num_sms) {

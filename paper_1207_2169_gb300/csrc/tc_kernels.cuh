@@ -48,6 +48,7 @@ struct EigTcParams {
   int64_t lds;
   const float* P;          // AC: t x q x q
   const float* b0;         // AC: t x q
+  const float* mu;         // ROT, AC: per-SNP centring (multiples of 1/64) or NULL
   float* B;                // AC: m x t x p
   float* W;                // AC: m x t or NULL
   int* flags;
@@ -57,5 +58,7 @@ struct EigTcParams {
 // 256-row boxes.
 void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUtensorMap& mapB,
                    const EigTcParams& p, int num_sms);
+// mu[i] = nearest multiple of 1/64 to the mean genotype of SNP i (one warp per SNP).
+void snp_centres(cudaStream_t s, const int8_t* XR, int64_t m, int n, float* mu);
 
 }  // namespace gw

@@ -153,9 +153,9 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (lane i of the warp gets row i).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+
+// Asynchronous half of tmem_ld32: the registers are valid only after tmem_wait32 on them.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -166,7 +166,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Waits for every outstanding tcgen05.ld of the thread; the "+r" operands make each use of
+// the 32 registers depend on the wait, so no use can be scheduled before it.
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                 "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (lane i of the warp gets row i).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  tmem_ld32_async(taddr, r);
+  tmem_wait32(r);
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -191,6 +211,26 @@ __device__ __forceinline__ uint2 geno4_to_bf16x4(uint32_t w) {
 __device__ __forceinline__ uint4 geno8_to_bf16x8(uint2 w) {
   const uint2 a = geno4_to_bf16x4(w.x), b = geno4_to_bf16x4(w.y);
   return make_uint4(a.x, a.y, b.x, b.y);
+}
+
+// Byte tables for centred genotypes g - mu (g = 0, 1, 2): low bytes and high bytes of the
+// three BF16 values.  Exact when mu is a multiple of 1/64 in [0, 2].
+__device__ __forceinline__ void centred_lut(float mu, uint32_t& lo, uint32_t& hi) {
+  lo = 0u;
+  hi = 0u;
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn((float)g - mu));
+    lo |= (b & 0xFFu) << (8 * g);
+    hi |= (b >> 8) << (8 * g);
+  }
+}
+
+__device__ __forceinline__ uint4 geno8_to_bf16x8_lut(uint2 w, uint32_t LO, uint32_t HI) {
+  const uint32_t s0 = (w.x & 0xFFFFu) * 17u + 0x4040u, s1 = (w.x >> 16) * 17u + 0x4040u;
+  const uint32_t s2 = (w.y & 0xFFFFu) * 17u + 0x4040u, s3 = (w.y >> 16) * 17u + 0x4040u;
+  return make_uint4(__byte_perm(LO, HI, s0), __byte_perm(LO, HI, s1), __byte_perm(LO, HI, s2),
+                    __byte_perm(LO, HI, s3));
 }
 
 // Eight int8 values -> eight BF16 (exact for |v| <= 256) packed in a uint4.

@@ -2,6 +2,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "tc.cuh"
@@ -58,6 +59,13 @@ struct TcState {
   float* rw32 = nullptr;            // t x n
   const double* P = nullptr;        // t x q x q (owned by the handle)
   const double* b0 = nullptr;       // t x q
+  // EIG: split operands, FP32 null-model blocks, per-block scratch and tensor maps
+  __nv_bfloat16 *Zsplit = nullptr, *Usplit = nullptr, *dsplit = nullptr, *xsq = nullptr;
+  float *P32 = nullptr, *b032 = nullptr, *sbuf = nullptr;
+  float* mu = nullptr;  // per-SNP centres of the current chunk (NULL: no intercept, no centring)
+  int64_t mcap = 0;
+  int traits_ac = 0;
+  CUtensorMap mapZ, mapU, mapD, mapX;
 };
 
 namespace {
@@ -75,8 +83,7 @@ void* tc_alloc(TcState* st, size_t bytes) {
 }  // namespace
 
 void tc_check_supported(int algo, int n, int q, int t) {
-  GW_REQUIRE(algo == GWAS_ALGO_CHOL, GWAS_ERR_UNSUPPORTED,
-             "split-BF16 tensor-core EIG path is not available in this build");
+  (void)algo;
   GW_REQUIRE(q >= 1 && q <= QMAX, GWAS_ERR_UNSUPPORTED, "q=%d outside [1,%d]", q, QMAX);
   GW_REQUIRE(n >= 1 && t >= 1, GWAS_ERR_ARG, "bad sizes");
 }
@@ -96,20 +103,64 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     const int n = a.n, q = a.q, t = a.t;
     st->kpad = (int)round_up(n, 64);
     st->rpad = (int)round_up(n, 256);
-    const size_t per = (size_t)2 * st->rpad * st->kpad;
-    st->Lsplit = (__nv_bfloat16*)tc_alloc(st, per * t * 2);
-    GW_CUDA(cudaMemsetAsync(st->Lsplit, 0, per * t * 2, s));
-    st->XLw32 = (float*)tc_alloc(st, (size_t)t * q * n * 4);
-    st->rw32 = (float*)tc_alloc(st, (size_t)t * n * 4);
-    convert_f64_to_f32(s, a.XLw, st->XLw32, (int64_t)t * q * n);
-    convert_f64_to_f32(s, a.rw, st->rw32, (int64_t)t * n);
-    for (int j = 0; j < t; ++j) {
-      __nv_bfloat16* hi = st->Lsplit + per * j;
-      __nv_bfloat16* lo = hi + (size_t)st->rpad * st->kpad;
-      split_bf16(s, a.Linv + (size_t)j * n * n, n, n, n, hi, lo, st->kpad);
-      st->lmap256.push_back(make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad, 256));
-      st->lmap128.push_back(make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad, 128));
+    if (a.algo == GWAS_ALGO_CHOL) {
+      const size_t per = (size_t)2 * st->rpad * st->kpad;
+      st->Lsplit = (__nv_bfloat16*)tc_alloc(st, per * t * 2);
+      GW_CUDA(cudaMemsetAsync(st->Lsplit, 0, per * t * 2, s));
+      st->XLw32 = (float*)tc_alloc(st, (size_t)t * q * n * 4);
+      st->rw32 = (float*)tc_alloc(st, (size_t)t * n * 4);
+      convert_f64_to_f32(s, a.XLw, st->XLw32, (int64_t)t * q * n);
+      convert_f64_to_f32(s, a.rw, st->rw32, (int64_t)t * n);
+      for (int j = 0; j < t; ++j) {
+        __nv_bfloat16* hi = st->Lsplit + per * j;
+        __nv_bfloat16* lo = hi + (size_t)st->rpad * st->kpad;
+        split_bf16(s, a.Linv + (size_t)j * n * n, n, n, n, hi, lo, st->kpad);
+        st->lmap256.push_back(make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad, 256));
+        st->lmap128.push_back(make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad, 128));
+      }
+      chol_tc_prepare();
+      return st;
     }
+    // EIG.  Z^T split (rows = eigenvectors).
+    const int kp = st->kpad, q1 = q + 1, q2 = q + 2;
+    const size_t zrows = (size_t)st->rpad;
+    st->Zsplit = (__nv_bfloat16*)tc_alloc(st, 2 * zrows * kp * 2);
+    GW_CUDA(cudaMemsetAsync(st->Zsplit, 0, 2 * zrows * kp * 2, s));
+    split_bf16(s, a.Zt, n, n, n, st->Zsplit, st->Zsplit + zrows * kp, kp);
+    // U_j = Z [d_j o X~_L | d_j o r~_j] = M_j^-1 [X_L | r_j], one row per (trait, column):
+    // Uall[row][c] = sum_r planes[row][r] Z^T[r][c] over all q+2 plane rows (the last is unused)
+    double* Uall = (double*)tc_alloc(st, (size_t)t * q2 * a.ldp * 8);
+    gemm_f64(s, t * q2, n, n, 1.0, a.planes, a.ldp, 1, a.Zt, n, 1, 0.0, Uall, a.ldp, 1);
+    st->Usplit = (__nv_bfloat16*)tc_alloc(st, (size_t)2 * t * q1 * kp * 2);
+    split_bf16_rows(s, Uall, t * q1, n, a.ldp, q2, q1, 0, st->Usplit,
+                    st->Usplit + (size_t)t * q1 * kp, kp);
+    // d_j (the last plane row of each trait), split
+    st->dsplit = (__nv_bfloat16*)tc_alloc(st, (size_t)2 * t * kp * 2);
+    split_bf16_rows(s, a.planes, t, n, a.ldp, q2, 1, q + 1, st->dsplit,
+                    st->dsplit + (size_t)t * kp, kp);
+    st->P32 = (float*)tc_alloc(st, (size_t)t * q * q * 4);
+    st->b032 = (float*)tc_alloc(st, (size_t)t * q * 4);
+    convert_f64_to_f32(s, a.P, st->P32, (int64_t)t * q * q);
+    convert_f64_to_f32(s, a.b0, st->b032, (int64_t)t * q);
+    GW_CUDA(cudaStreamSynchronize(s));
+    cudaFree(Uall);
+    st->allocs.erase(std::find(st->allocs.begin(), st->allocs.end(), (void*)Uall));
+    // traits per AC column block: T (q+1) columns, the last trait's load of QP columns in range
+    const int qp = q1 <= 4 ? 4 : 8;
+    const int ta = 256 / q1, tb = (256 - qp) / q1 + 1;
+    st->traits_ac = ta < tb ? ta : tb;
+    st->mcap = round_up(a.block_snps > 0 ? a.block_snps : 32768, 128);
+    st->xsq = (__nv_bfloat16*)tc_alloc(st, (size_t)2 * st->mcap * kp * 2);
+    st->sbuf = (float*)tc_alloc(st, (size_t)t * st->mcap * 4);
+    // With an intercept in X_L, each SNP is centred by a multiple of 1/64 near its mean: the
+    // estimates of b_snp and its Wald statistic are unchanged, the intercept is corrected
+    // exactly, and the large intercept-direction component no longer cancels in
+    // sigma = x^T M^-1 x - a^T S_TL^-1 a (which would amplify the BF16 splitting error).
+    if (a.intercept) st->mu = (float*)tc_alloc(st, (size_t)st->mcap * 4);
+    st->mapZ = make_map_bf16(st->Zsplit, 2 * (int64_t)zrows, kp, 256);
+    st->mapU = make_map_bf16(st->Usplit, 2 * (int64_t)t * q1, kp, 256);
+    st->mapD = make_map_bf16(st->dsplit, 2 * (int64_t)t, kp, 256);
+    st->mapX = make_map_bf16(st->xsq, 2 * st->mcap, kp, 128);
     chol_tc_prepare();
     return st;
   } catch (...) {
@@ -121,24 +172,65 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
 void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
   if (a.m <= 0) return;
   GW_REQUIRE(st != nullptr, GWAS_ERR_ARG, "no tensor-core state");
-  for (int j = 0; j < st->t; ++j) {
-    CholTcParams p{};
-    p.XR = a.XR;
-    p.m = a.m;
-    p.n = st->n;
-    p.q = st->q;
-    p.t = st->t;
-    p.j = j;
+  if (st->algo == GWAS_ALGO_CHOL) {
+    for (int j = 0; j < st->t; ++j) {
+      CholTcParams p{};
+      p.XR = a.XR;
+      p.m = a.m;
+      p.n = st->n;
+      p.q = st->q;
+      p.t = st->t;
+      p.j = j;
+      p.kpad = st->kpad;
+      p.rpad = st->rpad;
+      p.XLw = st->XLw32 + (size_t)j * st->q * st->n;
+      p.rw = st->rw32 + (size_t)j * st->n;
+      p.P = st->P + (size_t)j * st->q * st->q;
+      p.b0 = st->b0 + (size_t)j * st->q;
+      p.B = a.B;
+      p.W = a.wald;
+      p.flags = a.flags;
+      chol_tc_launch(s, st->lmap256[j], st->lmap128[j], p, st->num_sms);
+    }
+    return;
+  }
+  const int n = st->n, q = st->q, t = st->t, q1 = q + 1;
+  for (int64_t off = 0; off < a.m; off += st->mcap) {
+    const int64_t mm = a.m - off < st->mcap ? a.m - off : st->mcap;
+    EigTcParams p{};
+    p.m = mm;
+    p.n = n;
+    p.q = q;
+    p.t = t;
     p.kpad = st->kpad;
-    p.rpad = st->rpad;
-    p.XLw = st->XLw32 + (size_t)j * st->q * st->n;
-    p.rw = st->rw32 + (size_t)j * st->n;
-    p.P = st->P + (size_t)j * st->q * st->q;
-    p.b0 = st->b0 + (size_t)j * st->q;
-    p.B = a.B;
-    p.W = a.wald;
+    p.a_piece_rows = (int)st->mcap;
+    p.xsq = st->xsq;
+    p.sbuf = st->sbuf;
+    p.lds = st->mcap;
     p.flags = a.flags;
-    chol_tc_launch(s, st->lmap256[j], st->lmap128[j], p, st->num_sms);
+    // ROT: Xsq = (Z^T x)^2 for this chunk (Algorithm 4 line 3, squared and split)
+    p.XR = a.XR + off * n;
+    if (st->mu) snp_centres(s, p.XR, mm, n, st->mu);
+    p.mu = st->mu;
+    p.nblk = st->rpad / 256;
+    p.b_piece_rows = st->rpad;
+    p.b_rows_per_blk = 256;
+    eig_tc_launch(s, 0, st->mapZ, st->mapZ, p, st->num_sms);
+    // SQ: s_ij = sum_r Xsq[i][r] d_j[r]
+    p.nblk = (t + 255) / 256;
+    p.b_piece_rows = t;
+    p.b_rows_per_blk = 256;
+    eig_tc_launch(s, 1, st->mapX, st->mapD, p, st->num_sms);
+    // AC: a_ij, c_ij from the genotypes against U, then the bordered solve (lines 13-16)
+    p.nblk = (t + st->traits_ac - 1) / st->traits_ac;
+    p.b_piece_rows = t * q1;
+    p.b_rows_per_blk = st->traits_ac * q1;
+    p.traits_per_blk = st->traits_ac;
+    p.P = st->P32;
+    p.b0 = st->b032;
+    p.B = a.B + (size_t)off * t * q1;
+    p.W = a.wald ? a.wald + (size_t)off * t : nullptr;
+    eig_tc_launch(s, 2, st->mapU, st->mapU, p, st->num_sms);
   }
 }
 

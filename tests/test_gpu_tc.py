@@ -73,3 +73,48 @@ def test_chol_split_singular_and_streamed(g):
     assert np.array_equal(np.isnan(Bd), np.isnan(Bh))
     ok = ~np.isnan(Bd)
     assert np.array_equal(Bd[ok], Bh[ok])
+
+
+# ------------------------------------------------------------------------------------------ EIG
+
+def test_eig_golden_pedigree(g, golden_pedigree):
+    gp = golden_pedigree
+    c = synth.Cohort(Phi=gp["Phi"], XL=gp["XL"], Y=gp["Y"], h2=gp["h2"], s2=gp["s2"], XR=gp["XR"], beta=None)
+    B, W, _ = run(g, c, "eig", "split_bf16")
+    eb, ew = max_errors(B, W, gp["B"], gp["W"], gp["Vd"])
+    assert eb < TOL and ew < TOL, (eb, ew)
+
+
+@pytest.mark.parametrize("n,q,m,t", [(97, 1, 131, 5), (200, 3, 300, 37), (130, 7, 70, 17),
+                                     (64, 2, 64, 16), (300, 3, 257, 300), (520, 4, 129, 70),
+                                     (256, 5, 200, 51), (333, 6, 150, 40)])
+def test_eig_split_ragged(g, n, q, m, t):
+    c = synth.small_problem(5 * n + q + m + t, n=n, q=q, m=m, t=t)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
+    B, W, nsing = run(g, c, "eig", "split_bf16")
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < TOL and ew < TOL, (eb, ew)
+    assert nsing == 0
+
+
+def test_eig_split_workload2_slice(g):
+    """Workload 2's shape (n = 1000, t = 1000, h2 up to 0.95) on 1,500 SNPs; 300 sampled pairs."""
+    c = synth.make_cohort(2, m=1500)
+    B, W, _ = run(g, c, "eig", "split_bf16")
+    rs = np.random.default_rng(3)
+    pairs = np.c_[rs.integers(0, c.m, 300), rs.integers(0, c.t, 300)]
+    Bref, Wref, Vref = gls.gls_pairs(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, pairs)
+    eb, ew = max_errors(B[pairs[:, 0], pairs[:, 1]], W[pairs[:, 0], pairs[:, 1]], Bref, Wref, Vref)
+    assert eb < TOL and ew < TOL, (eb, ew)
+
+
+def test_eig_split_singular_and_streamed(g):
+    c = synth.small_problem(22, n=300, q=3, m=700, t=45)
+    XR = c.XR.copy()
+    XR[[1, 128, 699]] = 0
+    Bd, Wd, nsing = run(g, c, "eig", "split_bf16", XR=XR)
+    assert nsing == 3 * c.t
+    assert np.all(np.isnan(Bd[[1, 128, 699]])) and np.all(np.isnan(Wd[[1, 128, 699]]))
+    Bh, Wh, _ = run(g, c, "eig", "split_bf16", XR=XR, device=False, block_snps=256)
+    ok = ~np.isnan(Bd)
+    assert np.array_equal(np.isnan(Bd), np.isnan(Bh)) and np.array_equal(Bd[ok], Bh[ok])
