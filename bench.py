@@ -1,13 +1,15 @@
 #!/usr/bin/env python
 """Throughput of the GLS grid scan on one GB300: (SNP x trait) GLS solves per second.
 
-Default workload: single-trait genome scan, CLAK-Chol with the split-BF16 tensor-core whitening:
-n = 1,000 individuals, p = 4 (intercept, two covariates, SNP), m = 2,000,000 SNPs as int8 hard
-calls, h2 = 0.5, s2 = 1.  One step = one gwas_scan over all m SNPs (every SNP's GLS solved and
-its Wald statistic written).  `value` is measured with the genotypes already resident in HBM
-(2 GB, larger than L2, so no flush is needed between steps); `e2e` is the same metric through
-the same C call with pinned HOST genotype and output buffers (the library streams 64 Ki-SNP
-blocks with double-buffered copies).  `--impl reference` times the FP64 CPU oracle instead.
+Headline workload: single-trait genome scan, CLAK-Chol with the split-BF16 tensor-core
+whitening: n = 1,000 individuals, p = 4 (intercept, two covariates, SNP), m = 2,000,000 SNPs as
+int8 hard calls, h2 = 0.5, s2 = 1.  One step = one gwas_scan over all m SNPs (every SNP's GLS
+solved and its Wald statistic written).  `value` is measured with the genotypes already resident
+in HBM (2 GB, larger than the 129 MB L2, so no flush is needed between steps); `e2e` is the same
+metric through the same C call with pinned HOST genotype and output buffers (the library streams
+64 Ki-SNP blocks with double-buffered copies).  The line also carries the many-trait CLAK-Eig
+workload (n = 1,000, t = 1,000, m = 100,000) under "other_workloads", measured the same way.
+`--impl reference` times the FP64 CPU oracle instead.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--workload 1|0|2] [--precision P]
 Under torchrun (N > 1) every rank scans its own replica of the workload (weak scaling, no
@@ -16,6 +18,7 @@ collective on the data path); rank 0 prints the max-over-ranks time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -32,13 +35,14 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "(SNP x trait) GLS solves/s at <=1e-4 rel err vs FP64"
+KERNEL_SRC = {"chol": "paper_1207_2169_gb300/csrc/tc_chol.cu",
+              "eig": "paper_1207_2169_gb300/csrc/tc_eig.cu"}
 
 
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            d = json.load(f)
-        return d, "measured"
+            return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
@@ -62,6 +66,7 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(0.3)
         except OSError:
             self.proc = None
         return self
@@ -97,10 +102,8 @@ class ClockSampler:
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def _max_over_ranks(x: float, ws: int) -> float:
@@ -119,16 +122,11 @@ def _barrier(ws):
         dist.barrier()
 
 
-def workload_spec(idx: int):
-    s = dict(synth.WORKLOADS[idx])
-    return s
-
-
 def make_inputs(idx: int, m: int | None = None):
-    s = workload_spec(idx)
+    """Workload `idx` with its genotypes drawn block by block (each block its own stream)."""
+    s = dict(synth.WORKLOADS[idx])
     m = s["m"] if m is None else m
     c = synth.make_cohort(idx, m=0, with_genotypes=False)
-    # genotypes in lazily drawn blocks (each block has its own seeded stream)
     blk = s["block"]
     XR = np.empty((m, s["n"]), dtype=np.int8)
     for b in range((m + blk - 1) // blk):
@@ -136,6 +134,60 @@ def make_inputs(idx: int, m: int | None = None):
         XR[lo:hi] = synth.snp_block(idx, s["n"], blk, b)[:hi - lo]
     c.XR = XR
     return c
+
+
+def _config(s, precision, m):
+    return {"workload": s["name"], "n": s["n"], "p": s["q"] + 1, "m": m, "t": s["t"],
+            "algo": s["algo"], "precision": precision, "block_snps": s["block"],
+            "l2": "inputs (m x n int8 = %.2f GB) exceed the 129 MB L2 and are streamed once per "
+                  "step; no flush" % (m * s["n"] / 1e9)}
+
+
+# ------------------------------------------------------------------------------------------
+# algorithmic work (per unit) and traffic of the dominant kernel
+# ------------------------------------------------------------------------------------------
+
+def algorithmic_flops(s, m):
+    """Algorithmic FLOPs of one step.  CHOL: the lower-triangular whitening x' = L^-1 x costs
+    n(n+1) flops per SNP, the reductions a, c, s 2n(q+2).  EIG: per pair 2n(q+2) for a, c, s,
+    plus the rotation Z^T x (2n^2 per SNP)."""
+    n, q, t = s["n"], s["q"], s["t"]
+    if s["algo"] == "chol":
+        return m * t * (n * (n + 1) + 2 * n * (q + 2))
+    return m * t * 2 * n * (q + 2) + m * 2 * n * n
+
+
+def executed_flops(s, m):
+    """Tensor-core FLOPs the split kernels issue (padding and split products included)."""
+    n, q, t = s["n"], s["q"], s["t"]
+    kpad = -(-n // 64) * 64
+    rpad = -(-n // 256) * 256
+    if s["algo"] == "chol":
+        macs = 0
+        for nb in range(rpad // 256):
+            nk = min(4 * (nb + 1), kpad // 64)
+            for ks in range(nk):
+                macs += 64 * (128 if ks >= 4 * nb + 2 else 256)
+        return 2 * 2 * macs * m * t
+    rot = 2 * 2 * rpad * kpad * m
+    sq = 3 * 2 * kpad * t * m
+    ac = 2 * 2 * kpad * (q + 1) * t * m
+    return rot + sq + ac
+
+
+def traffic_per_launch(algo, m):
+    """DRAM bytes of the dominant kernel from the committed ncu summary, scaled to m SNPs, or
+    None if the kernel source changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)[algo]
+        with open(os.path.join(ROOT, KERNEL_SRC[algo]), "rb") as f:
+            sha = hashlib.sha1(f.read()).hexdigest()
+        if sha != d["source_sha1"]:
+            return None
+        return d["dram_bytes_per_snp"] * m
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 # ------------------------------------------------------------------------------------------
@@ -146,7 +198,7 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     from oracle import gls
-    s = workload_spec(args.workload)
+    s = dict(synth.WORKLOADS[args.workload])
     sample = args.ref_sample
     c = make_inputs(args.workload, m=sample)
     pairs_per_step = sample * c.t
@@ -165,18 +217,13 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config(args, s),
+        "data": "synthetic", "config": _config(s, "fp64", s["m"]),
         "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"first {sample} SNPs of the workload per step"},
+                         "sample": f"first {sample} SNPs x {c.t} trait(s) of the workload per step, "
+                                   "FP64 oracle (Algorithm 1 per GLS)"},
         "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
-
-def _config(args, s):
-    return {"workload": s["name"], "n": s["n"], "p": s["q"] + 1, "m": s["m"], "t": s["t"],
-            "algo": s["algo"], "precision": args.precision, "block_snps": s["block"],
-            "l2": "inputs (m x n int8 = %.1f GB) exceed the 129 MB L2; no flush" % (s["m"] * s["n"] / 1e9)}
 
 
 # ------------------------------------------------------------------------------------------
@@ -191,11 +238,11 @@ def cpu_baseline(idx: int, sample: int):
     dt = time.perf_counter() - t0
     return {"value": sample * c.t / dt, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"first {sample} SNPs x {c.t} trait(s) of the workload, FP64 oracle "
-                      f"(Algorithm 1 per GLS), {dt:.1f} s"}
+                      f"(Algorithm 1 per GLS, BLAS threads = all cores), {dt:.1f} s"}
 
 
-def parity_sample(g, h, c, Bd, Wd, count=256):
-    """Max errors of the bench run's own outputs against the oracle on sampled pairs."""
+def parity_sample(c, Bd, Wd, count=256):
+    """Max errors of the run's own outputs against the oracle on sampled (SNP, trait) pairs."""
     from oracle import gls
     rs = np.random.default_rng(1)
     snps = np.sort(rs.choice(c.m, size=min(count, c.m), replace=False))
@@ -208,115 +255,132 @@ def parity_sample(g, h, c, Bd, Wd, count=256):
             float(np.nanmax(gls.rel_err_wald(W, Wref))), len(pairs))
 
 
-def run_ours(args, ws, rank, local):
+def measure(args, idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5):
+    """Setup + timed device steps + end-to-end host steps + parity sample for one workload."""
     import torch
     import paper_1207_2169_gb300 as g
+    s = dict(synth.WORKLOADS[idx])
+    c = make_inputs(idx, m=m)
+    mm, n, t, p = c.m, c.n, c.t, c.p
+    opt = g.gwas_default_options(algo=s["algo"], precision=precision, device=local)
+    h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, options=opt)
+    try:
+        setup_ms = g.gwas_setup_timing(h)
+        xr_d = torch.from_numpy(c.XR).cuda()
+        B_d = torch.empty((mm, t, p), dtype=torch.float32, device="cuda")
+        W_d = torch.empty((mm, t), dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
 
+        def step():
+            g.gwas_scan(h, xr_d, B_d, W_d, stream=stream.cuda_stream)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            _barrier(ws)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(steps):
+                step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            _barrier(ws)
+        ms = _max_over_ranks(ev0.elapsed_time(ev1) / steps, ws)
+        eb, ew, npairs = parity_sample(c, B_d.cpu().numpy(), W_d.cpu().numpy())
+        # end to end: pinned host genotypes in, pinned host results out, through the same call
+        xr_h = torch.from_numpy(c.XR).pin_memory()
+        B_h = torch.empty((mm, t, p), dtype=torch.float32).pin_memory()
+        W_h = torch.empty((mm, t), dtype=torch.float32).pin_memory()
+        g.gwas_scan(h, xr_h, B_h, W_h)
+        _barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            g.gwas_scan(h, xr_h, B_h, W_h)
+        e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
+        same = bool(torch.equal(B_h, B_d.cpu()))
+    finally:
+        g.gwas_destroy(h)
+    pairs = mm * t
+    res = {
+        "s": s, "m": mm, "ms": ms, "value": pairs * ws / (ms * 1e-3), "setup_ms": setup_ms,
+        "clocks": clk.summary(), "parity": {"max_rel_err_b": eb, "max_rel_err_wald": ew,
+                                            "pairs_checked": npairs,
+                                            "tolerance": 1e-4 if precision != "fp64" else 1e-6},
+        "e2e": {"value": pairs * ws / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": mm * n,
+                "d2h_bytes_per_step": mm * t * (p + 1) * 4, "ms_per_step": e2e_s * 1e3,
+                "matches_device_run": same},
+    }
+    return res
+
+
+def roofline(res, precision):
+    """Roofline entry of the step's dominant kernel.  For CHOL a step is exactly one launch of the
+    whiten-and-reduce kernel, so the CUDA-event step time is that kernel's launch duration.  For
+    EIG a step is four launches (centres, rotation, s, a/c+Schur); the entry then covers the
+    whole step (labelled so)."""
+    s, m, ms = res["s"], res["m"], res["ms"]
+    peaks, kind = _peaks()
+    alg = algorithmic_flops(s, m) / (ms * 1e-3) / 1e12
+    if precision != "split_bf16":
+        return {"bound": "alu", "achieved": alg, "unit": "TFLOP/s", "peak": None, "frac": None,
+                "traffic": None, "kernel": s["algo"] + " CUDA-core scan",
+                "note": "plain FP64/FP32 comparator; no tensor-core roofline"}
+    peak = peaks["bf16_tflops_sustained"]
+    exe = executed_flops(s, m) / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s",
+            "frac": alg / peak, "traffic": traffic_per_launch(s["algo"], m) if s["algo"] == "chol" else None,
+            "kernel": "chol_tc_kernel (whiten + reduce + Schur)" if s["algo"] == "chol"
+            else "whole EIG step (rotation, s, a/c + Schur)",
+            "peak_source": f"bf16_tflops_sustained, {kind} (MEASURED_PEAKS.json)",
+            "executed_tflops": exe, "executed_frac": exe / peak,
+            "algorithmic_flops_per_launch": algorithmic_flops(s, m)}
+
+
+def launches_per_scan(s, precision, m):
+    """Kernels of ours per gwas_scan on device buffers (validation off)."""
+    if s["algo"] == "chol":
+        return s["t"]
+    if precision == "split_bf16":
+        return 4 * -(-m // s["block"])
+    return 2 * -(-m // s["block"])
+
+
+def run_ours(args, ws, rank, local):
+    import torch
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    s = workload_spec(args.workload)
-    c = make_inputs(args.workload, m=args.m)
-    m, n, t, p = c.m, c.n, c.t, c.p
-    opt = g.gwas_default_options(algo=s["algo"], precision=args.precision, device=local)
-    h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, options=opt)
-    setup_ms = g.gwas_setup_timing(h)
-    xr_d = torch.from_numpy(c.XR).cuda()
-    B_d = torch.empty((m, t, p), dtype=torch.float32, device="cuda")
-    W_d = torch.empty((m, t), dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def step():
-        g.gwas_scan(h, xr_d, B_d, W_d, stream=stream.cuda_stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        _barrier(ws)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        _barrier(ws)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ms = _max_over_ranks(ms, ws)
-    pairs = m * t
-    value = pairs * ws / (ms * 1e-3)
-    clocks = clk.summary()
-    eb, ew, npairs = parity_sample(g, h, c, B_d.cpu().numpy(), W_d.cpu().numpy())
-
-    # end to end: pinned host genotypes in, pinned host results out, through the same call
-    xr_h = torch.from_numpy(c.XR).pin_memory()
-    B_h = torch.empty((m, t, p), dtype=torch.float32).pin_memory()
-    W_h = torch.empty((m, t), dtype=torch.float32).pin_memory()
-    g.gwas_scan(h, xr_h, B_h, W_h)  # warm the ring
-    e2e_steps = max(1, min(args.steps, 5))
-    _barrier(ws)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        g.gwas_scan(h, xr_h, B_h, W_h)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_s = _max_over_ranks(e2e_s, ws)
-    same = bool(torch.equal(B_h, B_d.cpu()))
-
-    peaks, peak_kind = _peaks()
-    kinfo = g_kernel_info(args, s, m, t, ms)
-    roof = None
-    if kinfo:
-        peak = peaks["bf16_tflops_sustained"] if kinfo["unit"] == "TFLOP/s" else peaks["hbm_gbs"]
-        roof = {"bound": kinfo["bound"], "achieved": kinfo["achieved"], "peak": peak,
-                "unit": kinfo["unit"], "frac": kinfo["achieved"] / peak, "traffic": kinfo.get("traffic"),
-                "kernel": kinfo["kernel"], "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)",
-                "executed": kinfo.get("executed")}
-    g.gwas_destroy(h)
+    res = measure(args, args.workload, args.precision, args.steps, args.warmup, local, ws, m=args.m)
+    s = res["s"]
+    other = []
+    if not args.no_other and args.workload == 1 and args.m is None:
+        o = measure(args, 2, args.precision, max(3, args.steps // 2), args.warmup, local, ws)
+        other.append({"config": _config(o["s"], args.precision, o["m"]), "value": o["value"],
+                      "unit": "pairs/s", "ms_per_step": o["ms"], "e2e": o["e2e"],
+                      "parity": o["parity"], "setup_ms": o["setup_ms"],
+                      "roofline": roofline(o, args.precision),
+                      "gpu_launches": max(3, args.steps // 2) * launches_per_scan(o["s"], args.precision, o["m"])})
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"split_bf16": "bf16x2->f32", "fp32": "f32", "fp64": "f64"}[args.precision],
-        "data": "synthetic", "config": _config(args, s),
-        "e2e": {"value": pairs * ws / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": m * n,
-                "d2h_bytes_per_step": m * t * (p + 1) * 4, "ms_per_step": e2e_s * 1e3,
-                "matches_device_run": same},
-        "gpu_launches": args.steps * launches_per_scan(args, s, m),
-        "roofline": roof,
-        "parity": {"max_rel_err_b": eb, "max_rel_err_wald": ew, "pairs_checked": npairs,
-                   "tolerance": 1e-4 if args.precision != "fp64" else 1e-6},
-        "setup_ms": setup_ms,
-        "clocks": clocks,
+        "metric": METRIC, "value": res["value"], "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"split_bf16": "bf16x2->f32", "fp32": "f32", "fp64": "f64"}[args.precision],
+        "data": "synthetic", "config": _config(s, args.precision, res["m"]),
+        "e2e": res["e2e"],
+        "gpu_launches": args.steps * launches_per_scan(s, args.precision, res["m"]),
+        "roofline": roofline(res, args.precision),
+        "parity": res["parity"], "setup_ms": res["setup_ms"], "clocks": res["clocks"],
     }
+    if other:
+        line["other_workloads"] = other
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
     print(json.dumps(line), flush=True)
-
-
-def launches_per_scan(args, s, m):
-    if s["algo"] == "chol":
-        return 1 if args.precision == "split_bf16" else 1
-    return 2
-
-
-def g_kernel_info(args, s, m, t, ms_step):
-    """Algorithmic work of the dominant kernel per launch over its measured time.
-
-    CHOL whitening + reduction: n(n+1) flops per SNP for X' = L^-1 x (a lower-triangular product)
-    plus 2n(q+2) for the reductions.  The step is one launch of that kernel, so the step time
-    bounds its duration from above."""
-    n, q = s["n"], s["q"]
-    if s["algo"] == "chol":
-        flops = m * (n * (n + 1) + 2 * n * (q + 2))
-        achieved = flops / (ms_step * 1e-3) / 1e12
-        pieces = 2 if args.precision == "split_bf16" else 1
-        return {"bound": "tensor" if args.precision == "split_bf16" else "alu", "unit": "TFLOP/s",
-                "achieved": achieved, "kernel": "chol whiten+reduce",
-                "executed": achieved * pieces}
-    return None
 
 
 def main():
@@ -327,10 +391,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=1)
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "fp64"])
-    ap.add_argument("--m", type=int, default=None, help="override the SNP count (testing only)")
-    ap.add_argument("--cpu-sample", type=int, default=100_000)
+    ap.add_argument("--m", type=int, default=None, help="override the SNP count (profiling only)")
+    ap.add_argument("--cpu-sample", type=int, default=400_000)
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip the EIG workload measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = _dist()

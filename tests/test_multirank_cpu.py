@@ -1,0 +1,64 @@
+"""The N > 1 host path of bench.py (weak scaling, barrier + max-over-ranks timing) on two gloo
+ranks on CPU.  The GPU work of each rank is an independent replica; only the timing reduction
+crosses ranks, so that is what is exercised here."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    ws, r, local = bench._dist()
+    assert (ws, r, local) == (world, rank, rank)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    bench._barrier(ws)
+    mx = bench._max_over_ranks(1.5 + rank, ws)  # rank-dependent "step time"
+    out[rank] = mx
+    bench._barrier(ws)
+    dist.destroy_process_group()
+
+
+def test_two_rank_max_timing():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert dict(out) == {0: 2.5, 1: 2.5}
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench._max_over_ranks(3.25, 1) == 3.25
+    bench._barrier(1)
+
+
+def test_work_accounting():
+    """Algorithmic and executed FLOP counts used by the roofline."""
+    import bench
+    import synth
+    s = dict(synth.WORKLOADS[1])
+    n, q = s["n"], s["q"]
+    assert bench.algorithmic_flops(s, 10) == 10 * (n * (n + 1) + 2 * n * (q + 2))
+    # executed: 2 pieces x 2 flops x MACs of the 256/128-granular triangle over kpad = 1024
+    macs = sum(64 * (128 if ks >= 4 * nb + 2 else 256) for nb in range(4) for ks in range(min(4 * (nb + 1), 16)))
+    assert bench.executed_flops(s, 1) == 4 * macs
+    assert bench.executed_flops(s, 1) > 2 * bench.algorithmic_flops(s, 1)
