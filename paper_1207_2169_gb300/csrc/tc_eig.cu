@@ -27,25 +27,45 @@ constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int BK = 64;
 constexpr int SA = 4;
-constexpr int SB = 4;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int NUM_THREADS = 320;
 constexpr int TMEM_COLS = 512;
 constexpr int GROUP_M = 8;
 constexpr int QMAX = 7;
-constexpr int CST_FLOATS = 64 * (QMAX * QMAX + QMAX) + 256;  // AC: P_j and b0_j of a block
 constexpr uint64_t WAIT_NS = 4000000000ull;
 
 enum { EPI_ROT = 0, EPI_SQ = 1, EPI_AC = 2 };
 
-struct __align__(8) Bars {
-  uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full[2], acc_empty[2], done;
+// B-tile ring depth: AC gives one slot to the shared memory that stages its output rows.
+__host__ __device__ constexpr int sb_of(int epi) { return epi == EPI_AC ? 3 : 4; }
+// AC is compiled per q (QQ = q, 1..7); ROT and SQ use QQ = 0.  QP = TMEM columns loaded per
+// trait (q + 1 rounded up to 4 or 8).
+__host__ __device__ constexpr int qp_of(int qq) { return qq + 1 <= 4 ? 4 : 8; }
+// AC staging row stride in floats: 8 traits x (q + 1) coefficients.  For q = 3 each trait is one
+// float4 and rows are 36 floats (16-byte aligned, conflict-free float4 access); otherwise rows
+// are 8 QP + 1 floats (odd: conflict-free scalar access).
+__host__ __device__ constexpr int stg_rb(int qq) { return qq == 3 ? 36 : 8 * qp_of(qq) + 1; }
+// AC shared floats: P_j, b0_j of a block (<= 2048), then per epilogue warp a staging area of
+// 32 rows of coefficients and 32 x 9 Wald values.
+__host__ __device__ constexpr int stg_b(int qq) { return 32 * stg_rb(qq); }
+constexpr int STG_W = 32 * 9;
+constexpr int PB_FLOATS = 2048;
+__host__ __device__ constexpr int cst_of(int epi, int qq) {
+  return epi == EPI_AC ? PB_FLOATS + 4 * (stg_b(qq) + STG_W) : 0;
+}
+
+template <int NSB>
+struct __align__(8) BarsT {
+  uint64_t a_full[SA], a_empty[SA], b_full[NSB], b_empty[NSB], acc_full[2], acc_empty[2], done;
   uint32_t tmem_base;
   int abort;
 };
 
-constexpr size_t SMEM_BYTES = 1024 + SA * A_BYTES + SB * B_BYTES + CST_FLOATS * 4 + sizeof(Bars);
+__host__ __device__ constexpr size_t smem_of(int epi, int qp) {
+  return 1024 + SA * A_BYTES + (size_t)sb_of(epi) * B_BYTES + (size_t)cst_of(epi, qp) * 4 +
+         sizeof(BarsT<4>);
+}
 
 __device__ __forceinline__ void work_coords(int64_t w, int64_t mtiles, int nblk, int64_t& tile,
                                             int& nb) {
@@ -111,17 +131,20 @@ __device__ __forceinline__ void tmem_ld_cols<8>(uint32_t taddr, uint32_t (&r)[8]
                : "r"(taddr));
 }
 
-template <int EPI, int QP>
+template <int EPI, int QQ>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     eig_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const EigTcParams p) {
+  constexpr int QP = qp_of(QQ);
   constexpr bool CONV = EPI != EPI_SQ;  // A operand = genotypes through the converters
+  constexpr int SB = sb_of(EPI);
+  using Bars = BarsT<SB>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = sA + SA * A_BYTES;
   float* cst = (float*)(sB + SB * B_BYTES);
-  Bars* bars = (Bars*)(cst + CST_FLOATS);
+  Bars* bars = (Bars*)(cst + cst_of(EPI, QQ));
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t mtiles = (p.m + BM - 1) / BM;
   const int64_t nwork = mtiles * p.nblk;
@@ -271,37 +294,55 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int as = 0;
       uint32_t aph = 0;
       bool ok = true;
-      uint2 v0[8], v1[8];
+      // PF K steps of loads in flight per thread, continuing across work items; the store side
+      // follows its own (work item, k step) cursor and refreshes the row tables on a new tile.
+      constexpr int PF = 2;
+      uint2 v[PF][8];
       uint32_t lutlo[8], luthi[8];
-      for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-        int64_t tile;
-        int nb;
-        work_coords(w, mtiles, p.nblk, tile, nb);
-        // byte tables of this thread's 8 rows: g - mu_i (mu_i = 0 without centring)
-#pragma unroll
-        for (int l = 0; l < 8; ++l) {
-          const int64_t snp = tile * BM + ((ct + 128 * l) >> 3);
-          centred_lut(p.mu && snp < p.m ? p.mu[snp] : 0.f, lutlo[l], luthi[l]);
+      const int64_t mine = blockIdx.x < nwork ? (nwork - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+      const int64_t total = mine * nk;
+      int64_t lw = blockIdx.x, ltile = 0;
+      int lks = 0, lnb = 0;
+      if (mine) work_coords(lw, mtiles, p.nblk, ltile, lnb);
+      auto load_next = [&](uint2 (&dst)[8]) {
+        load_geno(dst, p.XR, p.m, p.n, ct, ltile, lks, aligned8);
+        if (++lks == nk) {
+          lks = 0;
+          lw += gridDim.x;
+          if (lw < nwork) work_coords(lw, mtiles, p.nblk, ltile, lnb);
         }
-        // two K steps of loads in flight
-        load_geno(v0, p.XR, p.m, p.n, ct, tile, 0, aligned8);
-        if (nk > 1) load_geno(v1, p.XR, p.m, p.n, ct, tile, 1, aligned8);
-        for (int ks = 0; ks < nk && ok; ks += 2) {
+      };
+#pragma unroll
+      for (int d = 0; d < PF; ++d)
+        if (d < total) load_next(v[d]);
+      int64_t sw = blockIdx.x, stile = -1;
+      int sks = 0;
+      for (int64_t g = 0; g < total && ok; g += PF) {
+#pragma unroll
+        for (int d = 0; d < PF; ++d) {
+          if (g + d >= total || !ok) break;
+          if (sks == 0) {
+            int snb;
+            int64_t t2;
+            work_coords(sw, mtiles, p.nblk, t2, snb);
+            if (t2 != stile) {
+              stile = t2;
+              // byte tables of this thread's 8 rows: g - mu_i (mu_i = 0 without centring)
+#pragma unroll
+              for (int l = 0; l < 8; ++l) {
+                const int64_t snp = stile * BM + ((ct + 128 * l) >> 3);
+                centred_lut(p.mu && snp < p.m ? p.mu[snp] : 0.f, lutlo[l], luthi[l]);
+              }
+            }
+          }
           ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
-          store_geno(sA + as * A_BYTES, v0, ct, lutlo, luthi);
+          store_geno(sA + as * A_BYTES, v[d], ct, lutlo, luthi);
           fence_proxy_async_smem();
           mbar_arrive(&bars->a_full[as]);
           if (++as == SA) { as = 0; aph ^= 1; }
-          if (ks + 2 < nk) load_geno(v0, p.XR, p.m, p.n, ct, tile, ks + 2, aligned8);
-          if (ks + 1 >= nk) break;
-          ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
-          if (!ok) break;
-          store_geno(sA + as * A_BYTES, v1, ct, lutlo, luthi);
-          fence_proxy_async_smem();
-          mbar_arrive(&bars->a_full[as]);
-          if (++as == SA) { as = 0; aph ^= 1; }
-          if (ks + 3 < nk) load_geno(v1, p.XR, p.m, p.n, ct, tile, ks + 3, aligned8);
+          if (++sks == nk) { sks = 0; sw += gridDim.x; }
+          if (g + d + PF < total) load_next(v[d]);
         }
       }
     }
@@ -310,7 +351,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int buf = 0;
     uint32_t accph = 0;
     bool ok = true;
-    const int q = p.q, q1 = q + 1;
+    // AC is compiled for one q, so the Schur loops below are fully unrolled
+    const int q = EPI == EPI_AC ? QQ : p.q, q1 = q + 1;
     for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
       int64_t tile;
       int nb;
@@ -372,8 +414,35 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
           }
         } else {
+          // Per batch of 8 traits: TMEM -> (a, c), s from the SQ pass (loaded one batch ahead,
+          // read-only path), FP32 Schur solve, results staged per warp in shared memory and
+          // written row by row so every store is contiguous within one SNP's output.
           const int T = p.traits_per_blk;
+          const int j0 = nb * T;
+          const int jend = (j0 + T < p.t ? j0 + T : p.t);
+          float* stgB = cst + PB_FLOATS + warp * (stg_b(QQ) + STG_W);
+          float* stgW = stgB + stg_b(QQ);
+          constexpr int RB = stg_rb(QQ);
+          const bool live = snp < p.m;
+          float snext[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int j = j0 + u;
+            snext[u] = (live && j < jend) ? __ldg(&p.sbuf[(int64_t)j * p.lds + snp]) : 1.f;
+          }
+          int nsing = 0;
+          const int64_t row0 = tile * BM + 32 * warp;
           for (int j8 = 0; j8 < T; j8 += 8) {
+            float scur[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) scur[u] = snext[u];
+            if (j8 + 8 < T) {
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int j = j0 + j8 + 8 + u;
+                snext[u] = (live && j < jend) ? __ldg(&p.sbuf[(int64_t)j * p.lds + snp]) : 1.f;
+              }
+            }
             uint32_t r[8][QP];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -386,48 +455,92 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
             for (int h = 0; h < QP / 4; ++h)
               tmem_wait32(*reinterpret_cast<uint32_t(*)[32]>(&r[4 * h][0]));
+            const int nval = jend - (j0 + j8) < 8 ? jend - (j0 + j8) : 8;  // valid traits
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-              const int jl = j8 + u, j = nb * T + jl;
-              if (jl >= T || j >= p.t || snp >= p.m) continue;
-              const float* Pj = cst + jl * (q * q + q);
-              float a[QMAX], vq[QMAX], aPa = 0.f;
+              if (u >= nval) continue;
+              const float* Pj = cst + (j8 + u) * (QQ * QQ + QQ);
+              float a[QQ + 1], vq[QQ + 1], aPa = 0.f;
 #pragma unroll
-              for (int k = 0; k < QMAX; ++k) a[k] = k < q ? __uint_as_float(r[u][k < QP ? k : 0]) : 0.f;
-              float cval = 0.f;
+              for (int k = 0; k < QQ; ++k) a[k] = __uint_as_float(r[u][k]);
+              const float cval = __uint_as_float(r[u][QQ]);
 #pragma unroll
-              for (int k = 0; k < QP; ++k)
-                if (k == q) cval = __uint_as_float(r[u][k]);
-#pragma unroll
-              for (int k = 0; k < QMAX; ++k) {
+              for (int k = 0; k < QQ; ++k) {
                 float acc = 0.f;
-                if (k < q) {
 #pragma unroll
-                  for (int l = 0; l < QMAX; ++l)
-                    if (l < q) acc = fmaf(Pj[k * q + l], a[l], acc);
-                  aPa = fmaf(a[k], acc, aPa);
-                }
+                for (int l = 0; l < QQ; ++l) acc = fmaf(Pj[k * QQ + l], a[l], acc);
+                aPa = fmaf(a[k], acc, aPa);
                 vq[k] = acc;
               }
-              const float s = p.sbuf[(int64_t)j * p.lds + snp];
+              const float s = scur[u];
               const float sigma = s - aPa;
-              float* Bo = p.B + (snp * p.t + j) * q1;
+              float o[QQ + 1];
+              float wv;
               if (sigma > 1e-5f * s) {
-                const float bs = cval / sigma;
+                const float bs = __fdividef(cval, sigma);
 #pragma unroll
-                for (int k = 0; k < QMAX; ++k)
-                  if (k < q) Bo[k] = Pj[q * q + k] - vq[k] * bs;
+                for (int k = 0; k < QQ; ++k) o[k] = Pj[QQ * QQ + k] - vq[k] * bs;
                 // centred SNP x - mu: the intercept (column 0 of X_L) absorbs mu * b_snp
-                if (p.mu) Bo[0] -= mu_snp * bs;
-                Bo[q] = bs;
-                if (p.W) p.W[snp * p.t + j] = bs * cval;
+                if (p.mu) o[0] -= mu_snp * bs;
+                o[QQ] = bs;
+                wv = bs * cval;
               } else {
-                for (int k = 0; k < q1; ++k) Bo[k] = __int_as_float(0x7fc00000);
-                if (p.W) p.W[snp * p.t + j] = __int_as_float(0x7fc00000);
-                atomicAdd(&p.flags[FLAG_SINGULAR], 1);
+#pragma unroll
+                for (int k = 0; k <= QQ; ++k) o[k] = __int_as_float(0x7fc00000);
+                wv = __int_as_float(0x7fc00000);
+                nsing += live;
+              }
+              float* so = stgB + lane * RB + u * (QQ + 1);
+              if (QQ == 3) {
+                *reinterpret_cast<float4*>(so) = make_float4(o[0], o[1], o[2], o[QQ]);
+              } else {
+#pragma unroll
+                for (int k = 0; k <= QQ; ++k) so[k] = o[k];
+              }
+              stgW[lane * 9 + u] = wv;
+            }
+            __syncwarp();
+            // Write the warp's 32 SNP rows: each row holds nval (q+1) contiguous floats of B
+            // and nval of wald; consecutive lanes take consecutive floats of a row.
+            const int64_t jb = j0 + j8;
+            if (QQ == 3 && nval == 8) {
+              // 8 float4 per row, 4 rows per instruction
+#pragma unroll
+              for (int it = 0; it < 8; ++it) {
+                const int rr = it * 4 + (lane >> 3), c4 = lane & 7;
+                const int64_t sn = row0 + rr;
+                if (sn < p.m) {
+                  const float4 v = *reinterpret_cast<const float4*>(stgB + rr * RB + c4 * 4);
+                  *reinterpret_cast<float4*>(p.B + (sn * p.t + jb) * 4 + c4 * 4) = v;
+                }
+              }
+            } else {
+              const int nb_f = nval * q1;
+              for (int e = lane; e < 32 * nb_f; e += 32) {
+                const int rr = e / nb_f, c = e - rr * nb_f;
+                const int64_t sn = row0 + rr;
+                if (sn < p.m) p.B[(sn * p.t + jb) * q1 + c] = stgB[rr * RB + c];
               }
             }
+            if (p.W) {
+              if (nval == 8) {
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                  const int rr = it * 4 + (lane >> 3), c = lane & 7;
+                  const int64_t sn = row0 + rr;
+                  if (sn < p.m) p.W[sn * p.t + jb + c] = stgW[rr * 9 + c];
+                }
+              } else {
+                for (int e = lane; e < 32 * nval; e += 32) {
+                  const int rr = e / nval, c = e - rr * nval;
+                  const int64_t sn = row0 + rr;
+                  if (sn < p.m) p.W[sn * p.t + jb + c] = stgW[rr * 9 + c];
+                }
+              }
+            }
+            __syncwarp();
           }
+          if (nsing) atomicAdd(&p.flags[FLAG_SINGULAR], nsing);
         }
         tc_fence_before();
         __syncwarp();
@@ -444,18 +557,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
-template <int EPI, int QP>
+template <int EPI, int QQ>
 void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
                 const EigTcParams& p, int num_sms) {
+  constexpr size_t SMEM = smem_of(EPI, QQ);
+  static_assert(SMEM <= 232448, "shared memory over the sm_103 opt-in limit");
   static bool prepared = false;
   if (!prepared) {
-    GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QP>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QQ>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
     prepared = true;
   }
   const int64_t work = ((p.m + BM - 1) / BM) * p.nblk;
   const unsigned grid = (unsigned)(work < num_sms ? work : num_sms);
-  eig_tc_kernel<EPI, QP><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mapA, mapB, p);
+  eig_tc_kernel<EPI, QQ><<<grid, NUM_THREADS, SMEM, s>>>(mapA, mapB, p);
   GW_CHECK_LAUNCH();
 }
 
@@ -487,13 +602,19 @@ void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUt
                    const EigTcParams& p, int num_sms) {
   if (p.m <= 0 || p.nblk <= 0) return;
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q out of range");
-  const bool small_q = p.q + 1 <= 4;
   switch (stage) {
-    case 0: launch_one<EPI_ROT, 4>(s, mapA, mapB, p, num_sms); break;
-    case 1: launch_one<EPI_SQ, 4>(s, mapA, mapB, p, num_sms); break;
+    case 0: launch_one<EPI_ROT, 0>(s, mapA, mapB, p, num_sms); break;
+    case 1: launch_one<EPI_SQ, 0>(s, mapA, mapB, p, num_sms); break;
     default:
-      if (small_q) launch_one<EPI_AC, 4>(s, mapA, mapB, p, num_sms);
-      else launch_one<EPI_AC, 8>(s, mapA, mapB, p, num_sms);
+      switch (p.q) {
+        case 1: launch_one<EPI_AC, 1>(s, mapA, mapB, p, num_sms); break;
+        case 2: launch_one<EPI_AC, 2>(s, mapA, mapB, p, num_sms); break;
+        case 3: launch_one<EPI_AC, 3>(s, mapA, mapB, p, num_sms); break;
+        case 4: launch_one<EPI_AC, 4>(s, mapA, mapB, p, num_sms); break;
+        case 5: launch_one<EPI_AC, 5>(s, mapA, mapB, p, num_sms); break;
+        case 6: launch_one<EPI_AC, 6>(s, mapA, mapB, p, num_sms); break;
+        default: launch_one<EPI_AC, 7>(s, mapA, mapB, p, num_sms); break;
+      }
   }
 }
 
