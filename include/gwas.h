@@ -114,6 +114,33 @@ gwas_status gwas_scan(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_devi
 gwas_status gwas_scan_f64(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_device,
                           double* B, double* wald, int out_on_device, void* stream);
 
+/*
+ * gwas_scan_static -- a scan that allocates no device memory.  (Not from the paper, which has
+ * no counterpart: this is a deployment variant of gwas_scan.)
+ *
+ * Some callers cannot let a library call cudaMalloc during a scan: code that runs while a
+ * stream is being captured into a CUDA graph (cudaMalloc is not a capturable operation),
+ * latency-critical loops where cudaMalloc's implicit device synchronisation stalls other work,
+ * and applications whose device memory is owned entirely by their own allocator or budget.
+ * gwas_scan may allocate on its first call (the EIG CUDA-core path's scratch for the rotated
+ * genotypes Z^T X_R, and the host-streaming ring); this entry point never does.  It runs the
+ * EIG CUDA-core scan (handles set up with algo EIG and precision FP64 or FP32) with that
+ * scratch in one fixed 16 MiB device array that the library holds on every GPU that loads it,
+ * from load until process exit.
+ *   XR, B, wald: device pointers, as in gwas_scan (wald may be NULL); stream: cudaStream_t.
+ *   Limit: m * ldp * e <= 16 MiB, where ldp = n rounded up to 64 and e = 8 (FP64) or 4 (FP32)
+ *   bytes; larger m returns GWAS_ERR_ARG (scan such genotypes in several calls).  Other
+ *   handles return GWAS_ERR_UNSUPPORTED.
+ * Asynchronous on `stream`.  The first call on a device looks up the array's device address
+ * (once per device; a cudaGetSymbolAddress, not an allocation): make that first call before
+ * any stream capture.  Every call shares the one array and finds it holding the previous
+ * call's data (the scan overwrites everything it reads), so calls whose work overlaps on the
+ * GPU -- other streams, other threads, other handles -- race on it and must be serialised
+ * by the caller (e.g. one stream).
+ */
+gwas_status gwas_scan_static(gwas_handle h, const int8_t* XR, int64_t m, float* B, float* wald,
+                             void* stream);
+
 /* Milliseconds the FP64 setup took on the device (CUDA events around it). */
 gwas_status gwas_setup_timing(gwas_handle h, double* ms_setup);
 

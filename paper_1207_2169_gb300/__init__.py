@@ -24,8 +24,8 @@ STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ER
 
 # every symbol include/gwas.h declares
 EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
-           "gwas_setup_timing", "gwas_info", "gwas_singular_count", "gwas_last_error",
-           "gwas_destroy"]
+           "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
+           "gwas_last_error", "gwas_destroy"]
 
 
 class GwasError(RuntimeError):
@@ -53,6 +53,8 @@ def _load():
     for f in (lib.gwas_scan, lib.gwas_scan_f64):
         f.argtypes = [vp, vp, i64, i32, vp, vp, i32, vp]
         f.restype = i32
+    lib.gwas_scan_static.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.gwas_scan_static.restype = i32
     lib.gwas_setup_timing.argtypes = [vp, dp]
     lib.gwas_setup_timing.restype = i32
     ip = ctypes.POINTER(ctypes.c_int)
@@ -150,6 +152,21 @@ def gwas_scan(h, XR, B, wald=None, stream=None, m=None):
 def gwas_scan_f64(h, XR, B, wald=None, stream=None, m=None):
     """As gwas_scan with float64 B and wald."""
     _scan(lib.gwas_scan_f64, "gwas_scan_f64", h, XR, XR.shape[0] if m is None else m, B, wald, stream)
+
+
+def gwas_scan_static(h, XR, B, wald=None, stream=None, m=None):
+    """As gwas_scan on device buffers, without any device allocation (EIG CUDA-core handles;
+    see include/gwas.h for the size limit and the rules on sharing its fixed scratch)."""
+    xp, xdev = _ptr(XR)
+    bp, bdev = _ptr(B)
+    wp = _ptr(wald)[0] if wald is not None else 0
+    if not (xdev and bdev):
+        raise ValueError("gwas_scan_static takes device buffers only")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    m = XR.shape[0] if m is None else m
+    _check(lib.gwas_scan_static(h, xp, int(m), bp, wp or None, stream or None), "gwas_scan_static")
 
 
 def gwas_setup_timing(h) -> float:

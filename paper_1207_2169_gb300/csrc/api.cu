@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -540,3 +541,72 @@ GW_API int64_t gwas_singular_count(gwas_handle h) {
 GW_API const char* gwas_last_error(void) { return gw::g_err.c_str(); }
 
 GW_API void gwas_destroy(gwas_handle h) { destroy_impl(h); }
+
+// ------------------------------------------------------------------------------------------
+// gwas_scan_static: the CUDA-core EIG scan of a handle with its per-block scratch (the rotated
+// genotypes Z^T X_R) in a fixed device array of this file instead of memory the call allocates.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t STATIC_SCRATCH_BYTES = (size_t)16 << 20;  // 16 MiB on every device
+static __device__ __align__(256) unsigned char g_scan_scratch[STATIC_SCRATCH_BYTES];
+
+std::mutex g_scratch_mu;
+constexpr int MAX_DEVICES = 64;
+void* g_scratch_addr[MAX_DEVICES] = {};
+
+// Device address of g_scan_scratch on the current device, looked up once per device.  In host
+// code g_scan_scratch names a host-side stand-in, never the device array itself.
+void* static_scratch(int dev) {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  GW_REQUIRE(dev >= 0 && dev < MAX_DEVICES, GWAS_ERR_ARG, "device %d out of range", dev);
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    GW_CUDA(cudaGetSymbolAddress(&ptr, g_scan_scratch));
+    GW_REQUIRE(ptr != nullptr, GWAS_ERR_CUDA, "no device address for the static scratch");
+    g_scratch_addr[dev] = ptr;
+  }
+  return g_scratch_addr[dev];
+}
+
+}  // namespace
+
+GW_API gwas_status gwas_scan_static(gwas_handle h, const int8_t* XR, int64_t m, float* B,
+                                    float* wald, void* stream) {
+  try {
+    GW_REQUIRE(h != nullptr, GWAS_ERR_ARG, "null handle");
+    GW_REQUIRE(m >= 0, GWAS_ERR_ARG, "m < 0");
+    if (m == 0) return GWAS_OK;
+    GW_REQUIRE(XR != nullptr && B != nullptr, GWAS_ERR_ARG, "null XR or B");
+    GW_REQUIRE(h->algo == GWAS_ALGO_EIG &&
+                   (h->prec == GWAS_PREC_FP64 || h->prec == GWAS_PREC_FP32),
+               GWAS_ERR_UNSUPPORTED,
+               "gwas_scan_static needs an EIG handle with FP64 or FP32 precision");
+    const size_t es = h->prec == GWAS_PREC_FP64 ? 8 : 4;
+    const size_t per_snp = (size_t)h->ldp * es;
+    GW_REQUIRE((size_t)m * per_snp <= STATIC_SCRATCH_BYTES, GWAS_ERR_ARG,
+               "m=%lld SNPs need %zu bytes of scratch; the static scratch holds %zu bytes "
+               "(at most %zu SNPs per call for this handle)",
+               (long long)m, (size_t)m * per_snp, STATIC_SCRATCH_BYTES,
+               STATIC_SCRATCH_BYTES / per_snp);
+    DeviceGuard dg(h->dev);
+    void* xt = static_scratch(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = h->n, q = h->q, t = h->t;
+    if (h->prec == GWAS_PREC_FP64) {
+      EigScanArgs<double> a{n, q, t, h->Zt, h->planes, h->ldp, h->P, h->b0, XR, m, 0,
+                            B, wald, false, 1e-12, (double*)xt, h->flags};
+      eig_scan_simt<double>(s, a);
+    } else {
+      EigScanArgs<float> a{n, q, t, h->Zt32, h->planes32, h->ldp, h->P32, h->b032, XR, m, 0,
+                           B, wald, false, 1e-5f, (float*)xt, h->flags};
+      eig_scan_simt<float>(s, a);
+    }
+    return GWAS_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  } catch (...) {
+    set_error("unexpected C++ exception in gwas_scan_static");
+    return GWAS_ERR_CUDA;
+  }
+}
