@@ -69,38 +69,6 @@ __device__ __forceinline__ void advance(Step& s, int nblocks, int kpad) {
   s.tile += gridDim.x;
 }
 
-__device__ __forceinline__ void load_genotypes(uint2 (&v)[8], const CholTcParams& p, int ct,
-                                               const Step& st, bool aligned8) {
-#pragma unroll
-  for (int l = 0; l < 8; ++l) {
-    const int e = ct + 128 * l, r = e >> 3, jc = e & 7;
-    const int64_t snp = st.tile * BM + r;
-    const int k = st.ks * BK + jc * 8;
-    v[l] = make_uint2(0u, 0u);
-    if (snp < p.m && k < p.n) {
-      const int8_t* src = p.XR + snp * p.n + k;
-      if (aligned8) {
-        v[l] = __ldg(reinterpret_cast<const uint2*>(src));
-      } else {
-        uint32_t w[2] = {0u, 0u};
-#pragma unroll
-        for (int b = 0; b < 8; ++b)
-          if (k + b < p.n) w[b >> 2] |= (uint32_t)(uint8_t)src[b] << (8 * (b & 3));
-        v[l] = make_uint2(w[0], w[1]);
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void store_tile(uint8_t* tile, const uint2 (&v)[8], int ct) {
-#pragma unroll
-  for (int l = 0; l < 8; ++l) {
-    const int e = ct + 128 * l, r = e >> 3, jc = e & 7;
-    uint8_t* dst = tile + (r >> 3) * 1024 + (r & 7) * 128 + ((jc ^ (r & 7)) << 4);
-    *reinterpret_cast<uint4*>(dst) = geno8_to_bf16x8(v[l]);
-  }
-}
-
 // QM: compile-time bound on q (3 or 7), so the epilogue's per-column arrays stay in registers.
 template <int QM>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
@@ -119,7 +87,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < SA; ++i) {
-      mbar_init(&bars->a_full[i], 128);
+      mbar_init(&bars->a_full[i], 4);  // one arrive per converter warp
       mbar_init(&bars->a_empty[i], 1);
     }
     for (int i = 0; i < SB; ++i) {
@@ -226,13 +194,49 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int64_t mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
       total = mine * per_tile;
     }
+    // Thread ct owns rows r0 + 16 l (l < 8) and the 8-genotype column chunk jc of every K step:
+    // its shared-memory offsets differ only by 2048 l, its global rows by 16 n l.
+    const int r0 = ct >> 3, jc = ct & 7;
+    const uint32_t soff = (r0 >> 3) * 1024 + (r0 & 7) * 128 + ((jc ^ (r0 & 7)) << 4);
+    const int64_t rstride = 16 * (int64_t)p.n;
     // PF K steps of genotype loads in flight per thread (register ring, static indices)
     constexpr int PF = 2;  // measured: 4 in flight was slower than 2 (5.36 vs 4.52 ms, n=1000)
     Step ld{blockIdx.x, 0, 0};
+    int64_t ld_tile = -1;
+    const int8_t* rowp = nullptr;
+    uint32_t rowok = 0;  // bit l: row r0 + 16 l of the tile exists
+    auto load_next = [&](uint2 (&v)[8]) {
+      if (ld.tile != ld_tile) {
+        ld_tile = ld.tile;
+        const int64_t first = ld_tile * BM + r0;
+        rowp = p.XR + first * p.n + jc * 8;
+        rowok = 0;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) rowok |= (first + 16 * l < p.m ? 1u : 0u) << l;
+      }
+      const int k = ld.ks * BK + jc * 8;
+      const int8_t* src = rowp + ld.ks * BK;
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        v[l] = make_uint2(0u, 0u);
+        if (((rowok >> l) & 1u) && k < p.n) {
+          if (aligned8) {
+            v[l] = __ldg(reinterpret_cast<const uint2*>(src + l * rstride));
+          } else {
+            uint32_t w[2] = {0u, 0u};
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+              if (k + b < p.n) w[b >> 2] |= (uint32_t)(uint8_t)src[l * rstride + b] << (8 * (b & 3));
+            v[l] = make_uint2(w[0], w[1]);
+          }
+        }
+      }
+      advance(ld, nblocks, p.kpad);
+    };
     uint2 v[PF][8];
 #pragma unroll
     for (int d = 0; d < PF; ++d)
-      if (d < total) { load_genotypes(v[d], p, ct, ld, aligned8); advance(ld, nblocks, p.kpad); }
+      if (d < total) load_next(v[d]);
     int as = 0;
     uint32_t aph = 0;
     bool ok = true;
@@ -242,11 +246,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (g + d >= total || !ok) break;
         ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
         if (!ok) break;
-        store_tile(sA + as * A_BYTES, v[d], ct);
+        uint8_t* dst = sA + as * A_BYTES + soff;
+#pragma unroll
+        for (int l = 0; l < 8; ++l)
+          *reinterpret_cast<uint4*>(dst + 2048 * l) = geno8_to_bf16x8(v[d][l]);
+        // every lane's writes are ordered before the async proxy, then one arrive per warp
         fence_proxy_async_smem();
-        mbar_arrive(&bars->a_full[as]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->a_full[as]);
         if (++as == SA) { as = 0; aph ^= 1; }
-        if (g + d + PF < total) { load_genotypes(v[d], p, ct, ld, aligned8); advance(ld, nblocks, p.kpad); }
+        if (g + d + PF < total) load_next(v[d]);
       }
     }
   } else {

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < SA; ++i) {
-      mbar_init(&bars->a_full[i], CONV ? 128 : 1);
+      mbar_init(&bars->a_full[i], CONV ? 4 : 1);  // converters: one arrive per warp
       mbar_init(&bars->a_empty[i], 1);
     }
     for (int i = 0; i < SB; ++i) {
@@ -301,15 +301,51 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t lutlo[8], luthi[8];
       const int64_t mine = blockIdx.x < nwork ? (nwork - 1 - blockIdx.x) / gridDim.x + 1 : 0;
       const int64_t total = mine * nk;
+      // thread ct owns rows r0 + 16 l (l < 8) and column chunk jc of every K step
+      const int r0 = ct >> 3, jc = ct & 7;
+      const uint32_t soff = (r0 >> 3) * 1024 + (r0 & 7) * 128 + ((jc ^ (r0 & 7)) << 4);
+      const int64_t rstride = 16 * (int64_t)p.n;
       int64_t lw = blockIdx.x, ltile = 0;
       int lks = 0, lnb = 0;
-      if (mine) work_coords(lw, mtiles, p.nblk, ltile, lnb);
+      const int8_t* rowp = nullptr;
+      uint32_t rowok = 0;
+      auto set_rows = [&]() {
+        const int64_t first = ltile * BM + r0;
+        rowp = p.XR + first * p.n + jc * 8;
+        rowok = 0;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) rowok |= (first + 16 * l < p.m ? 1u : 0u) << l;
+      };
+      if (mine) {
+        work_coords(lw, mtiles, p.nblk, ltile, lnb);
+        set_rows();
+      }
       auto load_next = [&](uint2 (&dst)[8]) {
-        load_geno(dst, p.XR, p.m, p.n, ct, ltile, lks, aligned8);
+        const int k = lks * BK + jc * 8;
+        const int8_t* src = rowp + lks * BK;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+          dst[l] = make_uint2(0u, 0u);
+          if (((rowok >> l) & 1u) && k < p.n) {
+            if (aligned8) {
+              dst[l] = __ldg(reinterpret_cast<const uint2*>(src + l * rstride));
+            } else {
+              uint32_t w2[2] = {0u, 0u};
+#pragma unroll
+              for (int b = 0; b < 8; ++b)
+                if (k + b < p.n) w2[b >> 2] |= (uint32_t)(uint8_t)src[l * rstride + b] << (8 * (b & 3));
+              dst[l] = make_uint2(w2[0], w2[1]);
+            }
+          }
+        }
         if (++lks == nk) {
           lks = 0;
           lw += gridDim.x;
-          if (lw < nwork) work_coords(lw, mtiles, p.nblk, ltile, lnb);
+          if (lw < nwork) {
+            const int64_t prev = ltile;
+            work_coords(lw, mtiles, p.nblk, ltile, lnb);
+            if (ltile != prev) set_rows();
+          }
         }
       };
 #pragma unroll
@@ -330,16 +366,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               // byte tables of this thread's 8 rows: g - mu_i (mu_i = 0 without centring)
 #pragma unroll
               for (int l = 0; l < 8; ++l) {
-                const int64_t snp = stile * BM + ((ct + 128 * l) >> 3);
+                const int64_t snp = stile * BM + r0 + 16 * l;
                 centred_lut(p.mu && snp < p.m ? p.mu[snp] : 0.f, lutlo[l], luthi[l]);
               }
             }
           }
           ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
-          store_geno(sA + as * A_BYTES, v[d], ct, lutlo, luthi);
+          uint8_t* dst = sA + as * A_BYTES + soff;
+#pragma unroll
+          for (int l = 0; l < 8; ++l)
+            *reinterpret_cast<uint4*>(dst + 2048 * l) = geno8_to_bf16x8_lut(v[d][l], lutlo[l], luthi[l]);
+          // every lane's writes are ordered before the async proxy, then one arrive per warp
           fence_proxy_async_smem();
-          mbar_arrive(&bars->a_full[as]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars->a_full[as]);
           if (++as == SA) { as = 0; aph ^= 1; }
           if (++sks == nk) { sks = 0; sw += gridDim.x; }
           if (g + d + PF < total) load_next(v[d]);

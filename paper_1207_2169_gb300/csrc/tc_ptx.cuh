@@ -83,6 +83,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// L2 prefetch hint for the bytes of [lo, hi) that lie on whole 16-byte units inside the range
+// (bulk prefetch; no data is delivered to the SM).  Issued in pieces of at most 32 KB.
+__device__ __forceinline__ void prefetch_l2_range(const void* lo, const void* hi) {
+  uintptr_t a = ((uintptr_t)lo + 15) & ~(uintptr_t)15;
+  const uintptr_t b = (uintptr_t)hi & ~(uintptr_t)15;
+  while (a < b) {
+    const uint32_t sz = (uint32_t)(b - a < 32768 ? b - a : 32768);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(sz) : "memory");
+    a += sz;
+  }
+}
+
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }

@@ -149,7 +149,12 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     const int qp = q1 <= 4 ? 4 : 8;
     const int ta = 256 / q1, tb = (256 - qp) / q1 + 1;
     st->traits_ac = ta < tb ? ta : tb;
-    st->mcap = round_up(a.block_snps > 0 ? a.block_snps : 32768, 128);
+    // SNPs per internal chunk: at least the streaming block, up to 32 Ki while the s scratch
+    // (t x chunk FP32) stays within 4 GB, so that many-trait scans keep every SM busy
+    int64_t cap = (int64_t)(4e9 / (4.0 * t));
+    cap = cap < 32768 ? cap : 32768;
+    cap = cap > a.block_snps ? cap : a.block_snps;
+    st->mcap = round_up(cap > 128 ? cap : 128, 128);
     st->xsq = (__nv_bfloat16*)tc_alloc(st, (size_t)2 * st->mcap * kp * 2);
     st->sbuf = (float*)tc_alloc(st, (size_t)t * st->mcap * 4);
     // With an intercept in X_L, each SNP is centred by a multiple of 1/64 near its mean: the
