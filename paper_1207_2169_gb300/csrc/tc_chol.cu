@@ -12,11 +12,11 @@
 // in FP32 over 32 columns and FP64 across them, and finishes each tile with the Schur-complement
 // solve in FP64.  X' = L^-1 X_R is never written to memory.
 //
-// Warp roles (320 threads):
+// Warp roles (448 threads):
 //   0-3  epilogue: one SNP per thread (TMEM lane 32*warp + lane)
 //   4    TMA producer of the L^-1 tiles (one elected lane)
 //   5    MMA issuer (one elected lane); owns the 512 TMEM columns (two 256-column accumulators)
-//   6-9  genotype converters: int8 global -> BF16 tiles in the 128-byte-swizzled K-major layout,
+//   6-13 genotype converters: int8 global -> BF16 tiles in the 128-byte-swizzled K-major layout,
 //        with two K steps of loads in flight per thread
 #include "tc_kernels.cuh"
 #include "tc_ptx.cuh"
@@ -35,7 +35,10 @@ constexpr int A_BYTES = BM * BK * 2;    // 16 KB
 constexpr int B_BYTES = BN * BK * 2;    // 32 KB
 constexpr int QMAX = 7;
 constexpr int CST_FLOATS = 8192;  // 32 KB: per-row epilogue constants
-constexpr int NUM_THREADS = 320;
+constexpr int NCONV = 8;                 // genotype converter warps
+constexpr int RS = 4 * NCONV;            // row step between one thread's rows
+constexpr int RPT = BM / RS;             // rows per converter thread
+constexpr int NUM_THREADS = 192 + 32 * NCONV;
 constexpr int TMEM_COLS = 512;
 constexpr uint64_t WAIT_NS = 4000000000ull;
 
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < SA; ++i) {
-      mbar_init(&bars->a_full[i], 4);  // one arrive per converter warp
+      mbar_init(&bars->a_full[i], NCONV);  // one arrive per converter warp
       mbar_init(&bars->a_empty[i], 1);
     }
     for (int i = 0; i < SB; ++i) {
@@ -194,30 +197,30 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int64_t mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
       total = mine * per_tile;
     }
-    // Thread ct owns rows r0 + 16 l (l < 8) and the 8-genotype column chunk jc of every K step:
-    // its shared-memory offsets differ only by 2048 l, its global rows by 16 n l.
+    // Thread ct owns rows r0 + RS l (l < RPT) and the 8-genotype column chunk jc of every K step:
+    // its shared-memory offsets differ only by 128 RS l, its global rows by RS n l.
     const int r0 = ct >> 3, jc = ct & 7;
     const uint32_t soff = (r0 >> 3) * 1024 + (r0 & 7) * 128 + ((jc ^ (r0 & 7)) << 4);
-    const int64_t rstride = 16 * (int64_t)p.n;
+    const int64_t rstride = RS * (int64_t)p.n;
     // PF K steps of genotype loads in flight per thread (register ring, static indices)
     constexpr int PF = 2;  // measured: 4 in flight was slower than 2 (5.36 vs 4.52 ms, n=1000)
     Step ld{blockIdx.x, 0, 0};
     int64_t ld_tile = -1;
     const int8_t* rowp = nullptr;
-    uint32_t rowok = 0;  // bit l: row r0 + 16 l of the tile exists
-    auto load_next = [&](uint2 (&v)[8]) {
+    uint32_t rowok = 0;  // bit l: row r0 + RS l of the tile exists
+    auto load_next = [&](uint2 (&v)[RPT]) {
       if (ld.tile != ld_tile) {
         ld_tile = ld.tile;
         const int64_t first = ld_tile * BM + r0;
         rowp = p.XR + first * p.n + jc * 8;
         rowok = 0;
 #pragma unroll
-        for (int l = 0; l < 8; ++l) rowok |= (first + 16 * l < p.m ? 1u : 0u) << l;
+        for (int l = 0; l < RPT; ++l) rowok |= (first + RS * l < p.m ? 1u : 0u) << l;
       }
       const int k = ld.ks * BK + jc * 8;
       const int8_t* src = rowp + ld.ks * BK;
 #pragma unroll
-      for (int l = 0; l < 8; ++l) {
+      for (int l = 0; l < RPT; ++l) {
         v[l] = make_uint2(0u, 0u);
         if (((rowok >> l) & 1u) && k < p.n) {
           if (aligned8) {
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       advance(ld, nblocks, p.kpad);
     };
-    uint2 v[PF][8];
+    uint2 v[PF][RPT];
 #pragma unroll
     for (int d = 0; d < PF; ++d)
       if (d < total) load_next(v[d]);
@@ -248,8 +251,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (!ok) break;
         uint8_t* dst = sA + as * A_BYTES + soff;
 #pragma unroll
-        for (int l = 0; l < 8; ++l)
-          *reinterpret_cast<uint4*>(dst + 2048 * l) = geno8_to_bf16x8(v[d][l]);
+        for (int l = 0; l < RPT; ++l)
+          *reinterpret_cast<uint4*>(dst + 128 * RS * l) = geno8_to_bf16x8(v[d][l]);
         // every lane's writes are ordered before the async proxy, then one arrive per warp
         fence_proxy_async_smem();
         __syncwarp();
@@ -294,11 +297,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           tc_fence_after();
           const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + buf * BN;
           // FP32 over the block's 256 rows (two levels: 32-row chunks, then chunks), FP64 over
-          // blocks; TMEM loads of the next chunk overlap the arithmetic on the current one.
+          // blocks.
           float bs_ = 0.f, bc = 0.f, ba[QM];
 #pragma unroll
           for (int k = 0; k < QM; ++k) ba[k] = 0.f;
-          uint32_t ra[32], rb[32];
+          uint32_t ra[32];
           auto chunk = [&](const uint32_t (&r)[32], int c) {
             float ss = 0.f, cc = 0.f, aa[QM];
 #pragma unroll
@@ -332,16 +335,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
             for (int k = 0; k < QM; ++k) ba[k] += aa[k];
           };
-          tmem_ld32_async(base, ra);
-          tmem_wait32(ra);
+          // one 32-column TMEM load at a time: the epilogue has slack, and its registers go to
+          // the eight converter warps (448 threads leave 128 registers per thread)
 #pragma unroll 1
-          for (int c = 0; c < BN / 32; c += 2) {
-            tmem_ld32_async(base + 32 * (c + 1), rb);
+          for (int c = 0; c < BN / 32; ++c) {
+            tmem_ld32_async(base + 32 * c, ra);
+            tmem_wait32(ra);
             chunk(ra, c);
-            tmem_wait32(rb);
-            if (c + 2 < BN / 32) tmem_ld32_async(base + 32 * (c + 2), ra);
-            chunk(rb, c + 1);
-            if (c + 2 < BN / 32) tmem_wait32(ra);
           }
           S += bs_;
           C += bc;

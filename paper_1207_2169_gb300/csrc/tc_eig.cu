@@ -13,8 +13,8 @@
 // A persistent CTA walks (128-SNP tile, 256-column block) work items, eight SNP tiles per
 // column block at a time so that both operands are reused from L2.
 //
-// Warp roles (320 threads): 0-3 epilogue (one SNP per TMEM lane), 4 TMA producer, 5 MMA issuer
-// and TMEM owner (two 256-column FP32 accumulators), 6-9 genotype converters (ROT and AC).
+// Warp roles (448 threads): 0-3 epilogue (one SNP per TMEM lane), 4 TMA producer, 5 MMA issuer
+// and TMEM owner (two 256-column FP32 accumulators), 6-13 genotype converters (ROT and AC).
 #include "tc_kernels.cuh"
 #include "tc_ptx.cuh"
 
@@ -29,7 +29,10 @@ constexpr int BK = 64;
 constexpr int SA = 4;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
-constexpr int NUM_THREADS = 320;
+constexpr int NCONV = 8;                 // genotype converter warps (ROT, AC)
+constexpr int RS = 4 * NCONV;            // row step between one thread's rows
+constexpr int RPT = BM / RS;             // rows per converter thread
+constexpr int NUM_THREADS = 192 + 32 * NCONV;
 constexpr int TMEM_COLS = 512;
 constexpr int GROUP_M = 8;
 constexpr int QMAX = 7;
@@ -78,42 +81,6 @@ __device__ __forceinline__ void work_coords(int64_t w, int64_t mtiles, int nblk,
   tile = first + r % rows;
 }
 
-__device__ __forceinline__ void load_geno(uint2 (&v)[8], const int8_t* XR, int64_t m, int n,
-                                          int ct, int64_t tile, int ks, bool aligned8) {
-#pragma unroll
-  for (int l = 0; l < 8; ++l) {
-    const int e = ct + 128 * l, r = e >> 3, jc = e & 7;
-    const int64_t snp = tile * BM + r;
-    const int k = ks * BK + jc * 8;
-    v[l] = make_uint2(0u, 0u);
-    if (snp < m && k < n) {
-      const int8_t* src = XR + snp * n + k;
-      if (aligned8) {
-        v[l] = __ldg(reinterpret_cast<const uint2*>(src));
-      } else {
-        uint32_t w[2] = {0u, 0u};
-#pragma unroll
-        for (int b = 0; b < 8; ++b)
-          if (k + b < n) w[b >> 2] |= (uint32_t)(uint8_t)src[b] << (8 * (b & 3));
-        v[l] = make_uint2(w[0], w[1]);
-      }
-    }
-  }
-}
-
-// Genotype tile in the swizzled K-major layout, each value centred by its row's table.  Zero
-// padding (rows past m, columns past n) stays 0: byte 0 maps to -mu, but such rows and columns
-// meet only zero operand rows of the other side (ROT, AC) or are discarded.
-__device__ __forceinline__ void store_geno(uint8_t* tile, const uint2 (&v)[8], int ct,
-                                           const uint32_t (&lo)[8], const uint32_t (&hi)[8]) {
-#pragma unroll
-  for (int l = 0; l < 8; ++l) {
-    const int e = ct + 128 * l, r = e >> 3, jc = e & 7;
-    uint8_t* dst = tile + (r >> 3) * 1024 + (r & 7) * 128 + ((jc ^ (r & 7)) << 4);
-    *reinterpret_cast<uint4*>(dst) = geno8_to_bf16x8_lut(v[l], lo[l], hi[l]);
-  }
-}
-
 // 4 or 8 consecutive FP32 TMEM columns of this warp's lanes (no wait).
 template <int QP>
 __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[QP]);
@@ -153,7 +120,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < SA; ++i) {
-      mbar_init(&bars->a_full[i], CONV ? 4 : 1);  // converters: one arrive per warp
+      mbar_init(&bars->a_full[i], CONV ? NCONV : 1);  // converters: one arrive per warp
       mbar_init(&bars->a_empty[i], 1);
     }
     for (int i = 0; i < SB; ++i) {
@@ -297,14 +264,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       // PF K steps of loads in flight per thread, continuing across work items; the store side
       // follows its own (work item, k step) cursor and refreshes the row tables on a new tile.
       constexpr int PF = 2;
-      uint2 v[PF][8];
-      uint32_t lutlo[8], luthi[8];
+      uint2 v[PF][RPT];
+      uint32_t lutlo[RPT], luthi[RPT];
       const int64_t mine = blockIdx.x < nwork ? (nwork - 1 - blockIdx.x) / gridDim.x + 1 : 0;
       const int64_t total = mine * nk;
-      // thread ct owns rows r0 + 16 l (l < 8) and column chunk jc of every K step
+      // thread ct owns rows r0 + RS l (l < RPT) and column chunk jc of every K step
       const int r0 = ct >> 3, jc = ct & 7;
       const uint32_t soff = (r0 >> 3) * 1024 + (r0 & 7) * 128 + ((jc ^ (r0 & 7)) << 4);
-      const int64_t rstride = 16 * (int64_t)p.n;
+      const int64_t rstride = RS * (int64_t)p.n;
       int64_t lw = blockIdx.x, ltile = 0;
       int lks = 0, lnb = 0;
       const int8_t* rowp = nullptr;
@@ -314,17 +281,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         rowp = p.XR + first * p.n + jc * 8;
         rowok = 0;
 #pragma unroll
-        for (int l = 0; l < 8; ++l) rowok |= (first + 16 * l < p.m ? 1u : 0u) << l;
+        for (int l = 0; l < RPT; ++l) rowok |= (first + RS * l < p.m ? 1u : 0u) << l;
       };
       if (mine) {
         work_coords(lw, mtiles, p.nblk, ltile, lnb);
         set_rows();
       }
-      auto load_next = [&](uint2 (&dst)[8]) {
+      auto load_next = [&](uint2 (&dst)[RPT]) {
         const int k = lks * BK + jc * 8;
         const int8_t* src = rowp + lks * BK;
 #pragma unroll
-        for (int l = 0; l < 8; ++l) {
+        for (int l = 0; l < RPT; ++l) {
           dst[l] = make_uint2(0u, 0u);
           if (((rowok >> l) & 1u) && k < p.n) {
             if (aligned8) {
@@ -365,8 +332,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               stile = t2;
               // byte tables of this thread's 8 rows: g - mu_i (mu_i = 0 without centring)
 #pragma unroll
-              for (int l = 0; l < 8; ++l) {
-                const int64_t snp = stile * BM + r0 + 16 * l;
+              for (int l = 0; l < RPT; ++l) {
+                const int64_t snp = stile * BM + r0 + RS * l;
                 centred_lut(p.mu && snp < p.m ? p.mu[snp] : 0.f, lutlo[l], luthi[l]);
               }
             }
@@ -375,8 +342,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (!ok) break;
           uint8_t* dst = sA + as * A_BYTES + soff;
 #pragma unroll
-          for (int l = 0; l < 8; ++l)
-            *reinterpret_cast<uint4*>(dst + 2048 * l) = geno8_to_bf16x8_lut(v[d][l], lutlo[l], luthi[l]);
+          for (int l = 0; l < RPT; ++l)
+            *reinterpret_cast<uint4*>(dst + 128 * RS * l) =
+                geno8_to_bf16x8_lut(v[d][l], lutlo[l], luthi[l]);
           // every lane's writes are ordered before the async proxy, then one arrive per warp
           fence_proxy_async_smem();
           __syncwarp();
