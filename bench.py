@@ -124,23 +124,21 @@ def _barrier(ws):
 
 def make_inputs(idx: int, m: int | None = None):
     """Workload `idx` with its genotypes drawn block by block (each block its own stream)."""
-    s = dict(synth.WORKLOADS[idx])
-    m = s["m"] if m is None else m
     c = synth.make_cohort(idx, m=0, with_genotypes=False)
-    blk = s["block"]
-    XR = np.empty((m, s["n"]), dtype=np.int8)
-    for b in range((m + blk - 1) // blk):
-        lo, hi = b * blk, min(m, (b + 1) * blk)
-        XR[lo:hi] = synth.snp_block(idx, s["n"], blk, b)[:hi - lo]
-    c.XR = XR
+    c.XR = synth.workload_genotypes(idx, m)
     return c
 
 
-def _config(s, precision, m):
+def _row_bytes(n, fmt):
+    return n if fmt == "int8" else -(-n // 64) * 16
+
+
+def _config(s, precision, m, fmt):
+    gb = m * _row_bytes(s["n"], fmt) / 1e9
     return {"workload": s["name"], "n": s["n"], "p": s["q"] + 1, "m": m, "t": s["t"],
             "algo": s["algo"], "precision": precision, "block_snps": s["block"],
-            "l2": "inputs (m x n int8 = %.2f GB) exceed the 129 MB L2 and are streamed once per "
-                  "step; no flush" % (m * s["n"] / 1e9)}
+            "genotypes": fmt, "l2": "inputs (%s genotypes, %.2f GB) exceed the 129 MB L2 and are "
+            "streamed once per step; no flush" % (fmt, gb)}
 
 
 # ------------------------------------------------------------------------------------------
@@ -217,7 +215,7 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config(s, "fp64", s["m"]),
+        "data": "synthetic", "config": _config(s, "fp64", s["m"], "int8"),
         "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"first {sample} SNPs x {c.t} trait(s) of the workload per step, "
                                    "FP64 oracle (Algorithm 1 per GLS)"},
@@ -255,8 +253,11 @@ def parity_sample(c, Bd, Wd, count=256):
             float(np.nanmax(gls.rel_err_wald(W, Wref))), len(pairs))
 
 
-def measure(args, idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=True):
-    """Setup + timed device steps + end-to-end host steps + parity sample for one workload."""
+def measure(args, idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=True,
+            fmt="packed"):
+    """Setup + timed device steps + end-to-end host steps + parity sample for one workload.
+    fmt: the genotype input format, "packed" (2-bit rows, gwas_scan_packed) or "int8"
+    (gwas_scan; the tensor-core path packs on the device inside the step)."""
     import torch
     import paper_1207_2169_gb300 as g
     s = dict(synth.WORKLOADS[idx])
@@ -267,12 +268,17 @@ def measure(args, idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5,
     try:
         setup_ms = g.gwas_setup_timing(h)
         xr_d = torch.from_numpy(c.XR).cuda()
+        scan = g.gwas_scan
+        if fmt == "packed":  # packed once, outside the timed region: it is the input format
+            xr_d = g.gwas_pack_genotypes(xr_d)
+            torch.cuda.synchronize()
+            scan = g.gwas_scan_packed
         B_d = torch.empty((mm, t, p), dtype=torch.float32, device="cuda")
         W_d = torch.empty((mm, t), dtype=torch.float32, device="cuda")
         stream = torch.cuda.current_stream()
 
         def step():
-            g.gwas_scan(h, xr_d, B_d, W_d, stream=stream.cuda_stream)
+            scan(h, xr_d, B_d, W_d, stream=stream.cuda_stream)
 
         for _ in range(warmup):
             step()
@@ -292,14 +298,15 @@ def measure(args, idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5,
         # end to end: pinned host genotypes in, pinned host results out, through the same call
         e2e_s, same = None, None
         if e2e:
-            xr_h = torch.from_numpy(c.XR).pin_memory()
+            xr_h = xr_d.cpu().pin_memory()
+            del xr_d
             B_h = torch.empty((mm, t, p), dtype=torch.float32).pin_memory()
             W_h = torch.empty((mm, t), dtype=torch.float32).pin_memory()
-            g.gwas_scan(h, xr_h, B_h, W_h)
+            scan(h, xr_h, B_h, W_h)
             _barrier(ws)
             t0 = time.perf_counter()
             for _ in range(e2e_steps):
-                g.gwas_scan(h, xr_h, B_h, W_h)
+                scan(h, xr_h, B_h, W_h)
             e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
             same = bool(torch.equal(B_h, B_d.cpu()))
     finally:
@@ -311,7 +318,8 @@ def measure(args, idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5,
                                             "pairs_checked": npairs,
                                             "tolerance": 1e-4 if precision != "fp64" else 1e-6},
         "e2e": None if e2e_s is None else {
-            "value": pairs * ws / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": mm * n,
+            "value": pairs * ws / e2e_s, "unit": "pairs/s",
+            "h2d_bytes_per_step": mm * _row_bytes(n, fmt),
             "d2h_bytes_per_step": mm * t * (p + 1) * 4, "ms_per_step": e2e_s * 1e3,
             "matches_device_run": same},
     }
@@ -341,13 +349,24 @@ def roofline(res, precision):
             "algorithmic_flops_per_launch": algorithmic_flops(s, m)}
 
 
-def launches_per_scan(s, precision, m):
-    """Kernels of ours per gwas_scan on device buffers (validation off)."""
-    if s["algo"] == "chol":
-        return s["t"]
-    if precision == "split_bf16":
-        return 4 * -(-m // 32768)
-    return 2 * -(-m // s["block"])
+def launches_per_scan(s, precision, m, fmt):
+    """Kernels of ours per scan on device buffers (validation off).  Input in the other format
+    than the kernels read (int8 for the tensor-core path, packed for the CUDA-core paths) is
+    converted first, one launch per chunk of up to 1 GiB of converted rows."""
+    n, t, blk = s["n"], s["t"], s["block"]
+    tc = precision == "split_bf16"
+    convert = (fmt == "int8") == tc
+    row = _row_bytes(n, "packed") if tc else n
+    cc = max(min(m, (1 << 30) // row), min(m, blk)) if convert else m
+
+    def kernels(mm):
+        if s["algo"] == "chol":
+            return t
+        if tc:
+            return 4 * -(-mm // 32768)  # centres, rotation, s, a/c + Schur per 32 Ki SNPs
+        return 2 * -(-mm // min(m, blk))
+
+    return sum(int(convert) + kernels(min(cc, m - off)) for off in range(0, m, cc))
 
 
 def run_ours(args, ws, rank, local):
@@ -356,7 +375,8 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    res = measure(args, args.workload, args.precision, args.steps, args.warmup, local, ws, m=args.m)
+    res = measure(args, args.workload, args.precision, args.steps, args.warmup, local, ws, m=args.m,
+                  fmt=args.format)
     s = res["s"]
     other = []
     if not args.no_other and args.workload == 1 and args.m is None:
@@ -365,12 +385,15 @@ def run_ours(args, ws, rank, local):
         # consumed block by block), device-resident only
         for idx, m_other, with_e2e in ((2, None, True), (3, 32768, False)):
             k = max(3, args.steps // 2)
-            o = measure(args, idx, args.precision, k, args.warmup, local, ws, m=m_other, e2e=with_e2e)
-            other.append({"config": _config(o["s"], args.precision, o["m"]), "value": o["value"],
+            o = measure(args, idx, args.precision, k, args.warmup, local, ws, m=m_other, e2e=with_e2e,
+                        fmt=args.format)
+            other.append({"config": _config(o["s"], args.precision, o["m"], args.format),
+                          "value": o["value"],
                           "unit": "pairs/s", "ms_per_step": o["ms"], "e2e": o["e2e"],
                           "parity": o["parity"], "setup_ms": o["setup_ms"],
                           "roofline": roofline(o, args.precision),
-                          "gpu_launches": k * launches_per_scan(o["s"], args.precision, o["m"])})
+                          "gpu_launches": k * launches_per_scan(o["s"], args.precision, o["m"],
+                                                                args.format)})
     if rank != 0:
         return
     line = {
@@ -378,9 +401,9 @@ def run_ours(args, ws, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"split_bf16": "bf16x2->f32", "fp32": "f32", "fp64": "f64"}[args.precision],
-        "data": "synthetic", "config": _config(s, args.precision, res["m"]),
+        "data": "synthetic", "config": _config(s, args.precision, res["m"], args.format),
         "e2e": res["e2e"],
-        "gpu_launches": args.steps * launches_per_scan(s, args.precision, res["m"]),
+        "gpu_launches": args.steps * launches_per_scan(s, args.precision, res["m"], args.format),
         "roofline": roofline(res, args.precision),
         "parity": res["parity"], "setup_ms": res["setup_ms"], "clocks": res["clocks"],
     }
@@ -399,6 +422,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=1)
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "fp64"])
+    ap.add_argument("--format", default="packed", choices=["packed", "int8"],
+                    help="genotype input format of the timed scans")
     ap.add_argument("--m", type=int, default=None, help="override the SNP count (profiling only)")
     ap.add_argument("--cpu-sample", type=int, default=400_000)
     ap.add_argument("--ref-sample", type=int, default=20_000)

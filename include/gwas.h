@@ -115,6 +115,37 @@ gwas_status gwas_scan_f64(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_
                           double* B, double* wald, int out_on_device, void* stream);
 
 /*
+ * Packed genotype format (a storage format; the paper's X_R is the same m x n matrix of hard
+ * calls, Section 2 "Notation"): SNP i occupies gwas_packed_row_bytes(n) = ceil(n / 64) * 16
+ * bytes starting at G + i * gwas_packed_row_bytes(n); the genotype of individual k sits in byte
+ * k / 4 at bits 2 (k % 4) and 2 (k % 4) + 1 and holds the allele count 0, 1 or 2.  Code 3 is
+ * invalid and every code past the n-th of a row is 0.  Four genotypes per byte: a quarter of the
+ * int8 bytes to stream from host memory and HBM, and the tensor-core kernels read these rows
+ * directly (int8 input is packed on the device first).
+ */
+int gwas_packed_row_bytes(int n); /* 0 for n < 1 */
+
+/*
+ * gwas_pack_genotypes -- int8 m x n hard calls X -> packed rows G (m * gwas_packed_row_bytes(n)
+ * bytes, caller-owned).  on_device = 0: both host pointers, synchronous; a value outside
+ * {0,1,2} is written as code 3 and the call returns GWAS_ERR_GENOTYPE after packing every row.
+ * on_device != 0: both device pointers on the current device, asynchronous on `stream`
+ * (cudaStream_t); values outside {0,1,2} become code 3, which a scan with validate_genotypes
+ * reports.
+ */
+gwas_status gwas_pack_genotypes(const int8_t* X, int64_t m, int n, uint8_t* G, int on_device,
+                                void* stream);
+
+/*
+ * gwas_scan_packed -- gwas_scan on packed genotype rows G (m rows; device pointers must be
+ * 16-byte aligned, else GWAS_ERR_ARG).  Every other argument, the streaming of host input
+ * (now gwas_packed_row_bytes(n) bytes per SNP) and the synchronisation rules are gwas_scan's.
+ * With validate_genotypes, a code 3 or a nonzero code past the n-th is GWAS_ERR_GENOTYPE.
+ */
+gwas_status gwas_scan_packed(gwas_handle h, const uint8_t* G, int64_t m, int g_on_device,
+                             float* B, float* wald, int out_on_device, void* stream);
+
+/*
  * gwas_scan_static -- a scan that allocates no device memory.  (Not from the paper, which has
  * no counterpart: this is a deployment variant of gwas_scan.)
  *

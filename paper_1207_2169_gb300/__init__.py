@@ -24,6 +24,7 @@ STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ER
 
 # every symbol include/gwas.h declares
 EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
+           "gwas_packed_row_bytes", "gwas_pack_genotypes", "gwas_scan_packed",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
            "gwas_last_error", "gwas_destroy"]
 
@@ -50,9 +51,13 @@ def _load():
     lib.gwas_setup.argtypes = [vp, i32, vp, i32, vp, i32, vp, vp, ctypes.POINTER(gwas_options),
                                ctypes.POINTER(vp)]
     lib.gwas_setup.restype = i32
-    for f in (lib.gwas_scan, lib.gwas_scan_f64):
+    for f in (lib.gwas_scan, lib.gwas_scan_f64, lib.gwas_scan_packed):
         f.argtypes = [vp, vp, i64, i32, vp, vp, i32, vp]
         f.restype = i32
+    lib.gwas_packed_row_bytes.argtypes = [i32]
+    lib.gwas_packed_row_bytes.restype = i32
+    lib.gwas_pack_genotypes.argtypes = [vp, i64, i32, vp, i32, vp]
+    lib.gwas_pack_genotypes.restype = i32
     lib.gwas_scan_static.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.gwas_scan_static.restype = i32
     lib.gwas_setup_timing.argtypes = [vp, dp]
@@ -152,6 +157,39 @@ def gwas_scan(h, XR, B, wald=None, stream=None, m=None):
 def gwas_scan_f64(h, XR, B, wald=None, stream=None, m=None):
     """As gwas_scan with float64 B and wald."""
     _scan(lib.gwas_scan_f64, "gwas_scan_f64", h, XR, XR.shape[0] if m is None else m, B, wald, stream)
+
+
+def gwas_packed_row_bytes(n: int) -> int:
+    return int(lib.gwas_packed_row_bytes(int(n)))
+
+
+def gwas_pack_genotypes(X, G=None, stream=None):
+    """X: (m, n) int8, host array or CUDA tensor.  Returns G, (m, gwas_packed_row_bytes(n))
+    uint8 in the same place as X (allocated here when G is None)."""
+    m, n = X.shape
+    rb = gwas_packed_row_bytes(n)
+    xp, xdev = _ptr(X)
+    if G is None:
+        if xdev:
+            import torch
+            G = torch.empty((m, rb), dtype=torch.uint8, device=X.device)
+        else:
+            G = np.empty((m, rb), dtype=np.uint8)
+    gp, gdev = _ptr(G)
+    if gdev != xdev or tuple(G.shape) != (m, rb):
+        raise ValueError(f"G must be a ({m}, {rb}) uint8 buffer beside X")
+    if xdev and stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib.gwas_pack_genotypes(xp, int(m), int(n), gp, xdev, stream or None),
+           "gwas_pack_genotypes")
+    return G
+
+
+def gwas_scan_packed(h, G, B, wald=None, stream=None, m=None):
+    """G: (m, gwas_packed_row_bytes(n)) uint8 packed rows; B, wald as gwas_scan."""
+    _scan(lib.gwas_scan_packed, "gwas_scan_packed", h, G, G.shape[0] if m is None else m, B, wald,
+          stream)
 
 
 def gwas_scan_static(h, XR, B, wald=None, stream=None, m=None):

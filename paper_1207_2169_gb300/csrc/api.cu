@@ -52,10 +52,16 @@ struct gwas_handle_s {
   // scratch for the rotated block (EIG)
   void* xt = nullptr;
   int64_t xt_cap = 0;
-  // streaming ring
-  int8_t* ring[2] = {};
+  // streaming ring (genotype bytes and outputs of one block per buffer)
+  uint8_t* ring[2] = {};
   void* oring[2] = {};
-  int64_t ring_snps = 0;
+  size_t ring_bytes = 0, oring_bytes = 0;
+  // format conversion scratch: packed rows for the tensor-core path (int8 input), int8 rows for
+  // the CUDA-core paths (packed input)
+  uint8_t* pk = nullptr;
+  int64_t pk_cap = 0;
+  int8_t* u8 = nullptr;
+  int64_t u8_cap = 0;
   // tensor-core state
   TcState* tc = nullptr;
   std::vector<void*> allocs;
@@ -270,17 +276,37 @@ void ensure_xt(gwas_handle h, int64_t snps) {
   h->xt_cap = snps;
 }
 
-// One block of SNPs already on the device, outputs on the device; asynchronous on s.
-void scan_block(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* wald, bool out_f64,
-                cudaStream_t s) {
-  if (h->validate) validate_genotypes(s, XR, m * h->n, h->flags);
-  const int n = h->n, q = h->q, t = h->t;
-  if (h->prec == GWAS_PREC_SPLIT_BF16) {
-    TcScanArgs a{};
-    a.XR = XR; a.m = m; a.B = (float*)B; a.wald = (float*)wald; a.flags = h->flags;
-    tc_scan(s, h->tc, a);
-    return;
+enum { FMT_INT8 = 0, FMT_PACKED2 = 1 };
+
+size_t row_bytes_of(gwas_handle h, int fmt) {
+  return fmt == FMT_PACKED2 ? (size_t)packed_row_bytes(h->n) : (size_t)h->n;
+}
+
+// Grows a conversion scratch of `snps` rows of `row_bytes` (waits for queued work first).
+template <typename T>
+void ensure_rows(gwas_handle h, T*& buf, int64_t& cap, int64_t snps, size_t row_bytes) {
+  if (snps <= cap) return;
+  if (buf) {
+    GW_CUDA(cudaDeviceSynchronize());
+    dfree(h, buf);
+    buf = nullptr;
   }
+  buf = (T*)dalloc(h, (size_t)snps * row_bytes);
+  cap = snps;
+}
+
+// SNPs converted per pass when a scan's input format differs from its kernels' format: the
+// streaming block, or up to 1 GiB of converted rows for device-resident input.
+int64_t convert_chunk(gwas_handle h, int64_t m, size_t row_bytes) {
+  int64_t c = (int64_t)(((size_t)1 << 30) / row_bytes);
+  c = m < c ? m : c;
+  return c > h->block_snps ? c : (m < h->block_snps ? m : h->block_snps);
+}
+
+// CUDA-core scan of int8 rows already on the device; asynchronous on s.
+void scan_block_simt(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* wald,
+                     bool out_f64, cudaStream_t s) {
+  const int n = h->n, q = h->q, t = h->t;
   if (h->algo == GWAS_ALGO_CHOL) {
     for (int j = 0; j < t; ++j) {
       if (h->prec == GWAS_PREC_FP64) {
@@ -316,23 +342,77 @@ void scan_block(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* wald,
   }
 }
 
-gwas_status scan_impl(gwas_handle h, const int8_t* XR, int64_t m, int xr_dev, void* B, void* wald,
-                      int out_dev, void* stream, bool out_f64) {
+// One block of m SNPs already on the device (int8 rows or packed rows, `fmt`), outputs on the
+// device; asynchronous on s.  The tensor-core kernels read packed rows, the CUDA-core kernels
+// int8 rows: input in the other format is converted chunk by chunk into the handle's scratch.
+void scan_block(gwas_handle h, const void* X, int fmt, int64_t m, void* B, void* wald,
+                bool out_f64, cudaStream_t s) {
+  const int n = h->n, t = h->t, p = h->p;
+  const size_t rbi = row_bytes_of(h, fmt);
+  const size_t ob = out_f64 ? 8 : 4;
+  if (h->prec == GWAS_PREC_SPLIT_BF16) {
+    TcScanArgs a{};
+    a.flags = h->flags;
+    if (fmt == FMT_PACKED2) {
+      GW_REQUIRE(((uintptr_t)X & 15) == 0, GWAS_ERR_ARG,
+                 "packed genotypes on the device must start on a 16-byte boundary");
+      if (h->validate) validate_packed(s, (const uint8_t*)X, m, n, h->flags);
+      a.G = (const uint8_t*)X;
+      a.m = m;
+      a.B = (float*)B;
+      a.wald = (float*)wald;
+      tc_scan(s, h->tc, a);
+      return;
+    }
+    const size_t rb = (size_t)packed_row_bytes(n);
+    const int64_t chunk = convert_chunk(h, m, rb);
+    ensure_rows(h, h->pk, h->pk_cap, chunk, rb);
+    for (int64_t off = 0; off < m; off += chunk) {
+      const int64_t mm = m - off < chunk ? m - off : chunk;
+      pack_genotypes(s, (const int8_t*)X + off * n, mm, n, h->pk, h->flags, h->validate != 0);
+      a.G = h->pk;
+      a.m = mm;
+      a.B = (float*)B + (size_t)off * t * p;
+      a.wald = wald ? (float*)wald + (size_t)off * t : nullptr;
+      tc_scan(s, h->tc, a);
+    }
+    return;
+  }
+  if (fmt == FMT_INT8) {
+    if (h->validate) validate_genotypes(s, (const int8_t*)X, m * n, h->flags);
+    scan_block_simt(h, (const int8_t*)X, m, B, wald, out_f64, s);
+    return;
+  }
+  const int64_t chunk = convert_chunk(h, m, (size_t)n);
+  ensure_rows(h, h->u8, h->u8_cap, chunk, (size_t)n);
+  for (int64_t off = 0; off < m; off += chunk) {
+    const int64_t mm = m - off < chunk ? m - off : chunk;
+    const uint8_t* src = (const uint8_t*)X + off * rbi;
+    if (h->validate) validate_packed(s, src, mm, n, h->flags);
+    unpack_genotypes(s, src, mm, n, h->u8);
+    scan_block_simt(h, h->u8, mm, (char*)B + (size_t)off * t * p * ob,
+                    wald ? (char*)wald + (size_t)off * t * ob : nullptr, out_f64, s);
+  }
+}
+
+gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_dev, void* B,
+                      void* wald, int out_dev, void* stream, bool out_f64) {
   GW_REQUIRE(h != nullptr, GWAS_ERR_ARG, "null handle");
   GW_REQUIRE(m >= 0, GWAS_ERR_ARG, "m < 0");
   if (m == 0) return GWAS_OK;
-  GW_REQUIRE(XR != nullptr && B != nullptr, GWAS_ERR_ARG, "null XR or B");
+  GW_REQUIRE(X != nullptr && B != nullptr, GWAS_ERR_ARG, "null genotypes or B");
   GW_REQUIRE(!(out_f64 && h->prec == GWAS_PREC_SPLIT_BF16), GWAS_ERR_UNSUPPORTED,
              "gwas_scan_f64 needs the FP64 or FP32 precision mode");
   DeviceGuard dg(h->dev);
   cudaStream_t s = (cudaStream_t)stream;
-  const int n = h->n, t = h->t, p = h->p;
+  const int t = h->t, p = h->p;
   const size_t ob = out_f64 ? 8 : 4;
+  const size_t rbi = row_bytes_of(h, fmt);
   if (h->validate)  // each call reports only its own genotypes
     GW_CUDA(cudaMemsetAsync(h->flags + FLAG_GENOTYPE, 0, sizeof(int), s));
   if (xr_dev && out_dev) {
     ensure_xt(h, m < h->block_snps ? m : h->block_snps);
-    scan_block(h, XR, m, B, wald, out_f64, s);
+    scan_block(h, X, fmt, m, B, wald, out_f64, s);
     if (h->validate) {
       read_flags(h, s);
       GW_REQUIRE(!h->h_flags[FLAG_GENOTYPE], GWAS_ERR_GENOTYPE, "genotype outside {0,1,2}");
@@ -342,17 +422,25 @@ gwas_status scan_impl(gwas_handle h, const int8_t* XR, int64_t m, int xr_dev, vo
   // Streamed: double-buffered H2D of genotype blocks (copy stream), compute on `s`,
   // D2H of each block's outputs (second copy stream).
   const int64_t blk = h->block_snps;
-  if (h->ring_snps < blk) {
+  const size_t gbytes = (size_t)blk * rbi, obytes = (size_t)blk * t * (p + 1) * 8;
+  if (h->ring_bytes < gbytes || h->oring_bytes < obytes) {
     GW_CUDA(cudaStreamSynchronize(s));
     GW_CUDA(cudaStreamSynchronize(h->st_h2d));
     GW_CUDA(cudaStreamSynchronize(h->st_d2h));
     for (int i = 0; i < 2; ++i) {
       dfree(h, h->ring[i]);
       dfree(h, h->oring[i]);
-      h->ring[i] = (int8_t*)dalloc(h, (size_t)blk * n);
-      h->oring[i] = dalloc(h, (size_t)blk * t * (p + 1) * 8);
+      h->ring[i] = nullptr;
+      h->oring[i] = nullptr;
     }
-    h->ring_snps = blk;
+    const size_t gb = gbytes > h->ring_bytes ? gbytes : h->ring_bytes;
+    const size_t obb = obytes > h->oring_bytes ? obytes : h->oring_bytes;
+    for (int i = 0; i < 2; ++i) {
+      h->ring[i] = (uint8_t*)dalloc(h, gb);
+      h->oring[i] = dalloc(h, obb);
+    }
+    h->ring_bytes = gb;
+    h->oring_bytes = obb;
   }
   ensure_xt(h, blk);
   const int nblocks = ceil_div(m, blk);
@@ -360,10 +448,11 @@ gwas_status scan_impl(gwas_handle h, const int8_t* XR, int64_t m, int xr_dev, vo
     const int buf = b & 1;
     const int64_t off = (int64_t)b * blk;
     const int64_t mm = m - off < blk ? m - off : blk;
-    const int8_t* src = XR + off * n;
+    const uint8_t* src = (const uint8_t*)X + off * rbi;
     if (!xr_dev) {
       GW_CUDA(cudaStreamWaitEvent(h->st_h2d, h->ev_computed[buf], 0));
-      GW_CUDA(cudaMemcpyAsync(h->ring[buf], src, (size_t)mm * n, cudaMemcpyHostToDevice, h->st_h2d));
+      GW_CUDA(cudaMemcpyAsync(h->ring[buf], src, (size_t)mm * rbi, cudaMemcpyHostToDevice,
+                              h->st_h2d));
       GW_CUDA(cudaEventRecord(h->ev_loaded[buf], h->st_h2d));
       GW_CUDA(cudaStreamWaitEvent(s, h->ev_loaded[buf], 0));
       src = h->ring[buf];
@@ -378,7 +467,7 @@ gwas_status scan_impl(gwas_handle h, const int8_t* XR, int64_t m, int xr_dev, vo
       Bo = h->oring[buf];
       Wo = wald ? (char*)h->oring[buf] + (size_t)blk * t * p * ob : nullptr;
     }
-    scan_block(h, src, mm, Bo, Wo, out_f64, s);
+    scan_block(h, src, fmt, mm, Bo, Wo, out_f64, s);
     GW_CUDA(cudaEventRecord(h->ev_computed[buf], s));
     if (!out_dev) {
       GW_CUDA(cudaStreamWaitEvent(h->st_d2h, h->ev_computed[buf], 0));
@@ -483,7 +572,7 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
 GW_API gwas_status gwas_scan(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_device,
                              float* B, float* wald, int out_on_device, void* stream) {
   try {
-    return scan_impl(h, XR, m, xr_on_device, B, wald, out_on_device, stream, false);
+    return scan_impl(h, XR, FMT_INT8, m, xr_on_device, B, wald, out_on_device, stream, false);
   } catch (const Fail& f) {
     return f.st;
   } catch (...) {
@@ -495,11 +584,63 @@ GW_API gwas_status gwas_scan(gwas_handle h, const int8_t* XR, int64_t m, int xr_
 GW_API gwas_status gwas_scan_f64(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_device,
                                  double* B, double* wald, int out_on_device, void* stream) {
   try {
-    return scan_impl(h, XR, m, xr_on_device, B, wald, out_on_device, stream, true);
+    return scan_impl(h, XR, FMT_INT8, m, xr_on_device, B, wald, out_on_device, stream, true);
   } catch (const Fail& f) {
     return f.st;
   } catch (...) {
     set_error("unexpected C++ exception in gwas_scan_f64");
+    return GWAS_ERR_CUDA;
+  }
+}
+
+GW_API gwas_status gwas_scan_packed(gwas_handle h, const uint8_t* G, int64_t m, int g_on_device,
+                                    float* B, float* wald, int out_on_device, void* stream) {
+  try {
+    return scan_impl(h, G, FMT_PACKED2, m, g_on_device, B, wald, out_on_device, stream, false);
+  } catch (const Fail& f) {
+    return f.st;
+  } catch (...) {
+    set_error("unexpected C++ exception in gwas_scan_packed");
+    return GWAS_ERR_CUDA;
+  }
+}
+
+GW_API int gwas_packed_row_bytes(int n) { return n >= 1 ? packed_row_bytes(n) : 0; }
+
+GW_API gwas_status gwas_pack_genotypes(const int8_t* X, int64_t m, int n, uint8_t* G,
+                                       int on_device, void* stream) {
+  try {
+    GW_REQUIRE(m >= 0 && n >= 1, GWAS_ERR_ARG, "bad sizes m=%lld n=%d", (long long)m, n);
+    if (m == 0) return GWAS_OK;
+    GW_REQUIRE(X != nullptr && G != nullptr, GWAS_ERR_ARG, "null X or G");
+    if (on_device) {
+      pack_genotypes((cudaStream_t)stream, X, m, n, G, nullptr, false);
+      return GWAS_OK;
+    }
+    const int rb = packed_row_bytes(n);
+    bool bad = false;
+    for (int64_t i = 0; i < m; ++i) {
+      const uint8_t* x = (const uint8_t*)X + i * n;
+      uint8_t* g = G + i * rb;
+      for (int b = 0; b < rb; ++b) {
+        unsigned v = 0;
+        for (int u = 0; u < 4; ++u) {
+          const int k = 4 * b + u;
+          if (k < n) {
+            const unsigned c = x[k];
+            bad |= c > 2;
+            v |= (c > 2 ? 3u : c) << (2 * u);
+          }
+        }
+        g[b] = (uint8_t)v;
+      }
+    }
+    GW_REQUIRE(!bad, GWAS_ERR_GENOTYPE, "genotype outside {0,1,2} (packed as the invalid code 3)");
+    return GWAS_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  } catch (...) {
+    set_error("unexpected C++ exception in gwas_pack_genotypes");
     return GWAS_ERR_CUDA;
   }
 }

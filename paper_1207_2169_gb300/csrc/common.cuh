@@ -144,4 +144,16 @@ template <typename T> void eig_scan_simt(cudaStream_t s, const EigScanArgs<T>& a
 // Genotype check: flags[GENOTYPE] = 1 if any value is outside {0,1,2}.
 void validate_genotypes(cudaStream_t s, const int8_t* XR, int64_t count, int* flags);
 
+// ------------------------------------------------------------------------------------------
+// Genotype formats, genotypes.cu (2-bit packed rows of packed_row_bytes(n) bytes)
+// ------------------------------------------------------------------------------------------
+int packed_row_bytes(int n);
+// int8 m x n -> packed m x row_bytes (values outside {0,1,2} become code 3); with validate,
+// flags[GENOTYPE] = 1 for such values.
+void pack_genotypes(cudaStream_t s, const int8_t* x, int64_t m, int n, uint8_t* out, int* flags,
+                    bool validate);
+void unpack_genotypes(cudaStream_t s, const uint8_t* in, int64_t m, int n, int8_t* out);
+void validate_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, int* flags);
+void snp_centres_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, float* mu);
+
 }  // namespace gw

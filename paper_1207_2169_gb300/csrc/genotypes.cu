@@ -1,0 +1,121 @@
+// Genotype formats: int8 hard calls and 2-bit packed codes.
+//
+// Packed layout (GWAS_GENO_PACKED2): SNP i occupies row_bytes = ceil(n / 64) * 16 bytes at
+// XR + i * row_bytes; genotype k sits in byte k / 4, bits 2 (k % 4) .. 2 (k % 4) + 1, holding the
+// allele count 0, 1 or 2 (3 is invalid); codes for k >= n are 0.  Rows are whole 16-byte units,
+// so the tensor-core kernels fetch 64-genotype slices of 128 SNPs as one TMA box.
+#include "common.cuh"
+
+namespace gw {
+namespace {
+
+// One thread per 32-bit word of packed output (16 genotypes).
+__global__ void pack2_kernel(const int8_t* __restrict__ x, int64_t m, int n, int row_bytes,
+                             uint32_t* __restrict__ out, int* flags, int validate) {
+  const int words = row_bytes / 4;
+  const int64_t total = m * words;
+  bool bad = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t snp = e / words;
+    const int wd = (int)(e % words);
+    const int8_t* row = x + snp * n;
+    uint32_t w = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int k = wd * 16 + i;
+      if (k < n) {
+        const uint32_t g = (uint8_t)row[k];
+        bad |= g > 2;
+        w |= (g > 2 ? 3u : g) << (2 * i);  // invalid values become the invalid code 3
+      }
+    }
+    out[e] = w;
+  }
+  if (validate && __syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&flags[FLAG_GENOTYPE], 1);
+}
+
+__global__ void unpack2_kernel(const uint8_t* __restrict__ in, int64_t m, int n, int row_bytes,
+                               int8_t* __restrict__ out) {
+  const int64_t total = m * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t snp = e / n;
+    const int k = (int)(e % n);
+    out[e] = (int8_t)((in[snp * row_bytes + k / 4] >> (2 * (k % 4))) & 3u);
+  }
+}
+
+// Packed codes must be 0, 1 or 2, and 0 past the n-th genotype of a row.
+__global__ void validate_packed_kernel(const uint32_t* __restrict__ in, int64_t m, int n,
+                                       int row_bytes, int* flags) {
+  const int words = row_bytes / 4;
+  const int64_t total = m * words;
+  bool bad = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t w = in[e];
+    bad |= (w & (w >> 1) & 0x55555555u) != 0u;  // a code 3
+    const int k0 = (int)(e % words) * 16;
+    if (k0 + 16 > n) {
+      const int keep = n - k0 > 0 ? n - k0 : 0;  // valid codes in this word
+      const uint32_t mask = keep >= 16 ? 0u : ~0u << (2 * keep);
+      bad |= (w & mask) != 0u;
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&flags[FLAG_GENOTYPE], 1);
+}
+
+// mu[i] = nearest multiple of 1/64 to SNP i's mean genotype, from packed codes (one warp per SNP).
+__global__ void centres_packed_kernel(const uint32_t* __restrict__ in, int64_t m, int n,
+                                      int row_bytes, float* __restrict__ mu) {
+  const int64_t snp = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (snp >= m) return;
+  const int words = row_bytes / 4;
+  const uint32_t* row = in + snp * words;
+  int sum = 0;
+  for (int w = lane; w < words; w += 32) {
+    const uint32_t v = row[w];
+    sum += __popc(v & 0x55555555u) + 2 * __popc(v & 0xAAAAAAAAu);
+  }
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) {
+    const float c = rintf(64.f * (float)sum / (float)n) / 64.f;
+    mu[snp] = fminf(fmaxf(c, 0.f), 2.f);
+  }
+}
+
+}  // namespace
+
+int packed_row_bytes(int n) { return ((n + 63) / 64) * 16; }
+
+void pack_genotypes(cudaStream_t s, const int8_t* x, int64_t m, int n, uint8_t* out, int* flags,
+                    bool validate) {
+  if (m <= 0) return;
+  pack2_kernel<<<2368, 256, 0, s>>>(x, m, n, packed_row_bytes(n), (uint32_t*)out, flags,
+                                    validate ? 1 : 0);
+  GW_CHECK_LAUNCH();
+}
+
+void unpack_genotypes(cudaStream_t s, const uint8_t* in, int64_t m, int n, int8_t* out) {
+  if (m <= 0) return;
+  unpack2_kernel<<<2368, 256, 0, s>>>(in, m, n, packed_row_bytes(n), out);
+  GW_CHECK_LAUNCH();
+}
+
+void validate_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, int* flags) {
+  if (m <= 0) return;
+  validate_packed_kernel<<<1184, 256, 0, s>>>((const uint32_t*)in, m, n, packed_row_bytes(n),
+                                              flags);
+  GW_CHECK_LAUNCH();
+}
+
+void snp_centres_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, float* mu) {
+  if (m <= 0) return;
+  centres_packed_kernel<<<(unsigned)((m + 7) / 8), 256, 0, s>>>((const uint32_t*)in, m, n,
+                                                               packed_row_bytes(n), mu);
+  GW_CHECK_LAUNCH();
+}
+
+}  // namespace gw

@@ -22,7 +22,8 @@ struct TcSetupArgs {
 };
 
 struct TcScanArgs {
-  const int8_t* XR;  // m x n device
+  const uint8_t* G;  // m rows of packed_row_bytes(n) bytes, 2-bit genotype codes; device,
+                     // 16-byte aligned
   int64_t m;
   float* B;          // m x t x p device
   float* wald;       // m x t device or NULL

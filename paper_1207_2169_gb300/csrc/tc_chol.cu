@@ -14,10 +14,10 @@
 //
 // Warp roles (448 threads):
 //   0-3  epilogue: one SNP per thread (TMEM lane 32*warp + lane)
-//   4    TMA producer of the L^-1 tiles (one elected lane)
+//   4    TMA producers: lane 0 the L^-1 tiles, lane 1 the 2-bit packed genotype slices
 //   5    MMA issuer (one elected lane); owns the 512 TMEM columns (two 256-column accumulators)
-//   6-13 genotype converters: int8 global -> BF16 tiles in the 128-byte-swizzled K-major layout,
-//        with two K steps of loads in flight per thread
+//   6-13 genotype converters: packed slices (shared memory) -> BF16 tiles in the
+//        128-byte-swizzled K-major layout
 #include "tc_kernels.cuh"
 #include "tc_ptx.cuh"
 
@@ -34,21 +34,23 @@ constexpr int SB = 4;                   // L^-1 tile ring (one piece per slot)
 constexpr int A_BYTES = BM * BK * 2;    // 16 KB
 constexpr int B_BYTES = BN * BK * 2;    // 32 KB
 constexpr int QMAX = 7;
-constexpr int CST_FLOATS = 8192;  // 32 KB: per-row epilogue constants
-constexpr int NCONV = 8;                 // genotype converter warps
-constexpr int RS = 4 * NCONV;            // row step between one thread's rows
-constexpr int RPT = BM / RS;             // rows per converter thread
+constexpr int CST_FLOATS = 4096;  // 16 KB: per-row epilogue constants
+constexpr int PR = 8;                   // packed-genotype slice ring
+constexpr int PK_BYTES = BM * 16;       // 64 genotypes of 128 SNPs, 2-bit codes: 2 KB
+constexpr int NCONV = 8;                // genotype converter warps: 2 threads per row
 constexpr int NUM_THREADS = 192 + 32 * NCONV;
 constexpr int TMEM_COLS = 512;
 constexpr uint64_t WAIT_NS = 4000000000ull;
 
 struct __align__(8) Bars {
-  uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full[2], acc_empty[2], done;
+  uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], pk_full[PR], pk_empty[PR];
+  uint64_t acc_full[2], acc_empty[2], done;
   uint32_t tmem_base;
   int abort;
 };
 
-constexpr size_t SMEM_BYTES = 1024 + SA * A_BYTES + SB * B_BYTES + CST_FLOATS * 4 + sizeof(Bars);
+constexpr size_t SMEM_BYTES =
+    1024 + SA * A_BYTES + SB * B_BYTES + PR * PK_BYTES + CST_FLOATS * 4 + sizeof(Bars);
 
 __device__ __forceinline__ int ksteps(int nb, int kpad) {
   const int k = (nb + 1) * (BN / BK);
@@ -76,12 +78,14 @@ __device__ __forceinline__ void advance(Step& s, int nblocks, int kpad) {
 template <int QM>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     chol_tc_kernel(const __grid_constant__ CUtensorMap map256,
-                   const __grid_constant__ CUtensorMap map128, const CholTcParams p) {
+                   const __grid_constant__ CUtensorMap map128,
+                   const __grid_constant__ CUtensorMap mapG, const CholTcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = sA + SA * A_BYTES;
-  float* cst = (float*)(sB + SB * B_BYTES);
+  uint8_t* sP = sB + SB * B_BYTES;
+  float* cst = (float*)(sP + PR * PK_BYTES);
   Bars* bars = (Bars*)(cst + CST_FLOATS);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t ntiles = (p.m + BM - 1) / BM;
@@ -96,6 +100,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     for (int i = 0; i < SB; ++i) {
       mbar_init(&bars->b_full[i], 1);
       mbar_init(&bars->b_empty[i], 1);
+    }
+    for (int i = 0; i < PR; ++i) {
+      mbar_init(&bars->pk_full[i], 1);
+      mbar_init(&bars->pk_empty[i], NCONV);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bars->acc_full[i], 1);
@@ -112,6 +120,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (warp == 4 && lane == 0) {
     prefetch_tensormap(&map256);
     prefetch_tensormap(&map128);
+    prefetch_tensormap(&mapG);
   }
   tc_fence_before();
   __syncthreads();
@@ -142,6 +151,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (++bs == SB) { bs = 0; bph ^= 1; }
         }
         if (!ok) break;
+      }
+    } else if (lane == 1) {
+      // packed genotype slices (64 genotypes x 128 SNPs, 2 KB) via TMA, in the K-step order the
+      // converters consume them; rows past m read as zero
+      int ps = 0;
+      uint32_t pph = 0;
+      for (Step st{blockIdx.x, 0, 0}; st.tile < ntiles; advance(st, nblocks, p.kpad)) {
+        if (!mbar_wait(&bars->pk_empty[ps], pph ^ 1, abort, tflag, WAIT_NS)) break;
+        mbar_arrive_expect_tx(&bars->pk_full[ps], PK_BYTES);
+        tma_load_2d(sP + ps * PK_BYTES, &mapG, &bars->pk_full[ps], st.ks * 16,
+                    (int32_t)(st.tile * BM));
+        if (++ps == PR) { ps = 0; pph ^= 1; }
       }
     }
   } else if (warp == 5) {
@@ -188,8 +209,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else if (warp >= 6) {
     // ------------------------------------------------------------ genotype converters
+    // Thread ct converts half hh of row r of each K step: packed bytes 8 hh .. 8 hh + 7 (32
+    // genotypes) into BF16 chunks 4 hh .. 4 hh + 3 of the row's swizzled 128-byte line.
     const int ct = threadIdx.x - 192;
-    const bool aligned8 = (p.n % 8 == 0) && ((reinterpret_cast<uintptr_t>(p.XR) & 7) == 0);
+    const int r = ct >> 1, hh = ct & 1;
+    const uint32_t line = (r >> 3) * 1024 + (r & 7) * 128;
     int64_t total = 0;
     {
       int per_tile = 0;
@@ -197,69 +221,32 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int64_t mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
       total = mine * per_tile;
     }
-    // Thread ct owns rows r0 + RS l (l < RPT) and the 8-genotype column chunk jc of every K step:
-    // its shared-memory offsets differ only by 128 RS l, its global rows by RS n l.
-    const int r0 = ct >> 3, jc = ct & 7;
-    const uint32_t soff = (r0 >> 3) * 1024 + (r0 & 7) * 128 + ((jc ^ (r0 & 7)) << 4);
-    const int64_t rstride = RS * (int64_t)p.n;
-    // PF K steps of genotype loads in flight per thread (register ring, static indices)
-    constexpr int PF = 2;  // measured: 4 in flight was slower than 2 (5.36 vs 4.52 ms, n=1000)
-    Step ld{blockIdx.x, 0, 0};
-    int64_t ld_tile = -1;
-    const int8_t* rowp = nullptr;
-    uint32_t rowok = 0;  // bit l: row r0 + RS l of the tile exists
-    auto load_next = [&](uint2 (&v)[RPT]) {
-      if (ld.tile != ld_tile) {
-        ld_tile = ld.tile;
-        const int64_t first = ld_tile * BM + r0;
-        rowp = p.XR + first * p.n + jc * 8;
-        rowok = 0;
+    int as = 0, ps = 0;
+    uint32_t aph = 0, pph = 0;
+    for (int64_t g = 0; g < total; ++g) {
+      // warp-uniform exits: every lane leaves together if any wait gave up
+      if (!__all_sync(0xffffffffu, mbar_wait(&bars->pk_full[ps], pph, abort, tflag, WAIT_NS))) break;
+      const uint2 w = *reinterpret_cast<const uint2*>(sP + ps * PK_BYTES + r * 16 + hh * 8);
+      // the slot is refilled by TMA (async proxy): order these generic reads before it
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->pk_empty[ps]);
+      if (++ps == PR) { ps = 0; pph ^= 1; }
+      uint4 o[4];
+      packed8_to_bf16x32(w, GENO_LO, GENO_HI, o);
+      if (!__all_sync(0xffffffffu, mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS)))
+        break;
+      uint8_t* dst = sA + as * A_BYTES + line;
 #pragma unroll
-        for (int l = 0; l < RPT; ++l) rowok |= (first + RS * l < p.m ? 1u : 0u) << l;
+      for (int i = 0; i < 4; ++i) {
+        const int j = 4 * hh + i;
+        *reinterpret_cast<uint4*>(dst + ((j ^ (r & 7)) << 4)) = o[i];
       }
-      const int k = ld.ks * BK + jc * 8;
-      const int8_t* src = rowp + ld.ks * BK;
-#pragma unroll
-      for (int l = 0; l < RPT; ++l) {
-        v[l] = make_uint2(0u, 0u);
-        if (((rowok >> l) & 1u) && k < p.n) {
-          if (aligned8) {
-            v[l] = __ldg(reinterpret_cast<const uint2*>(src + l * rstride));
-          } else {
-            uint32_t w[2] = {0u, 0u};
-#pragma unroll
-            for (int b = 0; b < 8; ++b)
-              if (k + b < p.n) w[b >> 2] |= (uint32_t)(uint8_t)src[l * rstride + b] << (8 * (b & 3));
-            v[l] = make_uint2(w[0], w[1]);
-          }
-        }
-      }
-      advance(ld, nblocks, p.kpad);
-    };
-    uint2 v[PF][RPT];
-#pragma unroll
-    for (int d = 0; d < PF; ++d)
-      if (d < total) load_next(v[d]);
-    int as = 0;
-    uint32_t aph = 0;
-    bool ok = true;
-    for (int64_t g = 0; g < total && ok; g += PF) {
-#pragma unroll
-      for (int d = 0; d < PF; ++d) {
-        if (g + d >= total || !ok) break;
-        ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
-        if (!ok) break;
-        uint8_t* dst = sA + as * A_BYTES + soff;
-#pragma unroll
-        for (int l = 0; l < RPT; ++l)
-          *reinterpret_cast<uint4*>(dst + 128 * RS * l) = geno8_to_bf16x8(v[d][l]);
-        // every lane's writes are ordered before the async proxy, then one arrive per warp
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bars->a_full[as]);
-        if (++as == SA) { as = 0; aph ^= 1; }
-        if (g + d + PF < total) load_next(v[d]);
-      }
+      // every lane's writes are ordered before the async proxy, then one arrive per warp
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->a_full[as]);
+      if (++as == SA) { as = 0; aph ^= 1; }
     }
   } else {
     // ------------------------------------------------------------ epilogue (warps 0-3)
@@ -292,7 +279,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           named_bar(1, 128);
         }
         const float* cb = resident ? cst + nb * BN : cst;
-        if (ok) ok = mbar_wait(&bars->acc_full[buf], accph, abort, tflag, WAIT_NS);
+        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full[buf], accph, abort, tflag, WAIT_NS));
         if (ok) {
           tc_fence_after();
           const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + buf * BN;
@@ -403,15 +390,15 @@ void chol_tc_prepare() {
 }
 
 void chol_tc_launch(cudaStream_t s, const CUtensorMap& map256, const CUtensorMap& map128,
-                    const CholTcParams& p, int num_sms) {
+                    const CUtensorMap& mapG, const CholTcParams& p, int num_sms) {
   if (p.m <= 0) return;
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", p.q, QMAX);
   const int64_t tiles = (p.m + BM - 1) / BM;
   const unsigned grid = (unsigned)(tiles < num_sms ? tiles : num_sms);
   if (p.q <= 3)
-    chol_tc_kernel<3><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(map256, map128, p);
+    chol_tc_kernel<3><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(map256, map128, mapG, p);
   else
-    chol_tc_kernel<QMAX><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(map256, map128, p);
+    chol_tc_kernel<QMAX><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(map256, map128, mapG, p);
   GW_CHECK_LAUNCH();
 }
 

@@ -13,8 +13,10 @@
 // A persistent CTA walks (128-SNP tile, 256-column block) work items, eight SNP tiles per
 // column block at a time so that both operands are reused from L2.
 //
-// Warp roles (448 threads): 0-3 epilogue (one SNP per TMEM lane), 4 TMA producer, 5 MMA issuer
-// and TMEM owner (two 256-column FP32 accumulators), 6-13 genotype converters (ROT and AC).
+// Warp roles (448 threads): 0-3 epilogue (one SNP per TMEM lane), 4 TMA producers (lane 0: the
+// B operand and SQ's A operand; lane 1: 2-bit packed genotype slices for ROT and AC), 5 MMA
+// issuer and TMEM owner (two 256-column FP32 accumulators), 6-13 genotype converters (packed
+// slices in shared memory -> centred BF16 tiles; ROT and AC).
 #include "tc_kernels.cuh"
 #include "tc_ptx.cuh"
 
@@ -29,10 +31,10 @@ constexpr int BK = 64;
 constexpr int SA = 4;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
-constexpr int NCONV = 8;                 // genotype converter warps (ROT, AC)
-constexpr int RS = 4 * NCONV;            // row step between one thread's rows
-constexpr int RPT = BM / RS;             // rows per converter thread
+constexpr int NCONV = 8;                 // genotype converter warps (ROT, AC): 2 threads per row
 constexpr int NUM_THREADS = 192 + 32 * NCONV;
+constexpr int PR = 8;                    // packed-genotype slice ring
+constexpr int PK_BYTES = BM * 16;        // 64 genotypes of 128 SNPs, 2-bit codes: 2 KB
 constexpr int TMEM_COLS = 512;
 constexpr int GROUP_M = 8;
 constexpr int QMAX = 7;
@@ -60,14 +62,15 @@ __host__ __device__ constexpr int cst_of(int epi, int qq) {
 
 template <int NSB>
 struct __align__(8) BarsT {
-  uint64_t a_full[SA], a_empty[SA], b_full[NSB], b_empty[NSB], acc_full[2], acc_empty[2], done;
+  uint64_t a_full[SA], a_empty[SA], b_full[NSB], b_empty[NSB], pk_full[PR], pk_empty[PR];
+  uint64_t acc_full[2], acc_empty[2], done;
   uint32_t tmem_base;
   int abort;
 };
 
 __host__ __device__ constexpr size_t smem_of(int epi, int qp) {
-  return 1024 + SA * A_BYTES + (size_t)sb_of(epi) * B_BYTES + (size_t)cst_of(epi, qp) * 4 +
-         sizeof(BarsT<4>);
+  return 1024 + SA * A_BYTES + (size_t)sb_of(epi) * B_BYTES + PR * PK_BYTES +
+         (size_t)cst_of(epi, qp) * 4 + sizeof(BarsT<4>);
 }
 
 __device__ __forceinline__ void work_coords(int64_t w, int64_t mtiles, int nblk, int64_t& tile,
@@ -101,7 +104,7 @@ __device__ __forceinline__ void tmem_ld_cols<8>(uint32_t taddr, uint32_t (&r)[8]
 template <int EPI, int QQ>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     eig_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                  const EigTcParams p) {
+                  const __grid_constant__ CUtensorMap mapG, const EigTcParams p) {
   constexpr int QP = qp_of(QQ);
   constexpr bool CONV = EPI != EPI_SQ;  // A operand = genotypes through the converters
   constexpr int SB = sb_of(EPI);
@@ -110,7 +113,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = sA + SA * A_BYTES;
-  float* cst = (float*)(sB + SB * B_BYTES);
+  uint8_t* sP = sB + SB * B_BYTES;
+  float* cst = (float*)(sP + PR * PK_BYTES);
   Bars* bars = (Bars*)(cst + cst_of(EPI, QQ));
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t mtiles = (p.m + BM - 1) / BM;
@@ -127,6 +131,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mbar_init(&bars->b_full[i], 1);
       mbar_init(&bars->b_empty[i], 1);
     }
+    for (int i = 0; i < PR; ++i) {
+      mbar_init(&bars->pk_full[i], 1);
+      mbar_init(&bars->pk_empty[i], NCONV);
+    }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bars->acc_full[i], 1);
       mbar_init(&bars->acc_empty[i], 4);
@@ -141,6 +149,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   if (warp == 4 && lane == 0) {
     if (!CONV) prefetch_tensormap(&mapA);
+    if (CONV) prefetch_tensormap(&mapG);
     prefetch_tensormap(&mapB);
   }
   tc_fence_before();
@@ -178,6 +187,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         piece * p.b_piece_rows + nb * p.b_rows_per_blk);
             if (++bs == SB) { bs = 0; bph ^= 1; }
           }
+        }
+      }
+    } else if (lane == 1 && CONV) {
+      // packed genotype slices (64 genotypes x 128 SNPs, 2 KB) via TMA, in the order the
+      // converters consume them; rows past m read as zero
+      int ps = 0;
+      uint32_t pph = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+        int64_t tile;
+        int nb;
+        work_coords(w, mtiles, p.nblk, tile, nb);
+        for (int ks = 0; ks < nk; ++ks) {
+          ok = mbar_wait(&bars->pk_empty[ps], pph ^ 1, abort, tflag, WAIT_NS);
+          if (!ok) break;
+          mbar_arrive_expect_tx(&bars->pk_full[ps], PK_BYTES);
+          tma_load_2d(sP + ps * PK_BYTES, &mapG, &bars->pk_full[ps], ks * 16, (int32_t)(tile * BM));
+          if (++ps == PR) { ps = 0; pph ^= 1; }
         }
       }
     }
@@ -255,103 +282,53 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else if (warp >= 6) {
     // ------------------------------------------------------------ genotype converters
+    // Thread ct converts half hh of row r of each K step: packed bytes 8 hh .. 8 hh + 7 (32
+    // genotypes) into BF16 chunks 4 hh .. 4 hh + 3 of the row's swizzled 128-byte line, through
+    // the row's byte tables of g - mu (mu = 0 without centring).  Codes past n are 0 and map to
+    // -mu; the B operand is zero there, so they add nothing.
     if (CONV) {
       const int ct = threadIdx.x - 192;
-      const bool aligned8 = (p.n % 8 == 0) && ((reinterpret_cast<uintptr_t>(p.XR) & 7) == 0);
-      int as = 0;
-      uint32_t aph = 0;
-      bool ok = true;
-      // PF K steps of loads in flight per thread, continuing across work items; the store side
-      // follows its own (work item, k step) cursor and refreshes the row tables on a new tile.
-      constexpr int PF = 2;
-      uint2 v[PF][RPT];
-      uint32_t lutlo[RPT], luthi[RPT];
+      const int r = ct >> 1, hh = ct & 1;
+      const uint32_t line = (r >> 3) * 1024 + (r & 7) * 128;
       const int64_t mine = blockIdx.x < nwork ? (nwork - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-      const int64_t total = mine * nk;
-      // thread ct owns rows r0 + RS l (l < RPT) and column chunk jc of every K step
-      const int r0 = ct >> 3, jc = ct & 7;
-      const uint32_t soff = (r0 >> 3) * 1024 + (r0 & 7) * 128 + ((jc ^ (r0 & 7)) << 4);
-      const int64_t rstride = RS * (int64_t)p.n;
-      int64_t lw = blockIdx.x, ltile = 0;
-      int lks = 0, lnb = 0;
-      const int8_t* rowp = nullptr;
-      uint32_t rowok = 0;
-      auto set_rows = [&]() {
-        const int64_t first = ltile * BM + r0;
-        rowp = p.XR + first * p.n + jc * 8;
-        rowok = 0;
-#pragma unroll
-        for (int l = 0; l < RPT; ++l) rowok |= (first + RS * l < p.m ? 1u : 0u) << l;
-      };
-      if (mine) {
-        work_coords(lw, mtiles, p.nblk, ltile, lnb);
-        set_rows();
-      }
-      auto load_next = [&](uint2 (&dst)[RPT]) {
-        const int k = lks * BK + jc * 8;
-        const int8_t* src = rowp + lks * BK;
-#pragma unroll
-        for (int l = 0; l < RPT; ++l) {
-          dst[l] = make_uint2(0u, 0u);
-          if (((rowok >> l) & 1u) && k < p.n) {
-            if (aligned8) {
-              dst[l] = __ldg(reinterpret_cast<const uint2*>(src + l * rstride));
-            } else {
-              uint32_t w2[2] = {0u, 0u};
-#pragma unroll
-              for (int b = 0; b < 8; ++b)
-                if (k + b < p.n) w2[b >> 2] |= (uint32_t)(uint8_t)src[l * rstride + b] << (8 * (b & 3));
-              dst[l] = make_uint2(w2[0], w2[1]);
-            }
-          }
+      int as = 0, ps = 0;
+      uint32_t aph = 0, pph = 0, lutlo = 0, luthi = 0;
+      int64_t cur_tile = -1;
+      bool ok = true;
+      for (int64_t i = 0; i < mine && ok; ++i) {
+        int64_t tile;
+        int nb;
+        work_coords(blockIdx.x + i * gridDim.x, mtiles, p.nblk, tile, nb);
+        if (tile != cur_tile) {
+          cur_tile = tile;
+          const int64_t snp = tile * BM + r;
+          centred_lut(p.mu && snp < p.m ? p.mu[snp] : 0.f, lutlo, luthi);
         }
-        if (++lks == nk) {
-          lks = 0;
-          lw += gridDim.x;
-          if (lw < nwork) {
-            const int64_t prev = ltile;
-            work_coords(lw, mtiles, p.nblk, ltile, lnb);
-            if (ltile != prev) set_rows();
-          }
-        }
-      };
-#pragma unroll
-      for (int d = 0; d < PF; ++d)
-        if (d < total) load_next(v[d]);
-      int64_t sw = blockIdx.x, stile = -1;
-      int sks = 0;
-      for (int64_t g = 0; g < total && ok; g += PF) {
-#pragma unroll
-        for (int d = 0; d < PF; ++d) {
-          if (g + d >= total || !ok) break;
-          if (sks == 0) {
-            int snb;
-            int64_t t2;
-            work_coords(sw, mtiles, p.nblk, t2, snb);
-            if (t2 != stile) {
-              stile = t2;
-              // byte tables of this thread's 8 rows: g - mu_i (mu_i = 0 without centring)
-#pragma unroll
-              for (int l = 0; l < RPT; ++l) {
-                const int64_t snp = stile * BM + r0 + RS * l;
-                centred_lut(p.mu && snp < p.m ? p.mu[snp] : 0.f, lutlo[l], luthi[l]);
-              }
-            }
-          }
-          ok = mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS);
+        for (int ks = 0; ks < nk; ++ks) {
+          // warp-uniform exits: every lane leaves together if any wait gave up
+          ok = __all_sync(0xffffffffu, mbar_wait(&bars->pk_full[ps], pph, abort, tflag, WAIT_NS));
           if (!ok) break;
-          uint8_t* dst = sA + as * A_BYTES + soff;
+          const uint2 w = *reinterpret_cast<const uint2*>(sP + ps * PK_BYTES + r * 16 + hh * 8);
+          // the slot is refilled by TMA (async proxy): order these generic reads before it
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars->pk_empty[ps]);
+          if (++ps == PR) { ps = 0; pph ^= 1; }
+          uint4 o[4];
+          packed8_to_bf16x32(w, lutlo, luthi, o);
+          ok = __all_sync(0xffffffffu, mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS));
+          if (!ok) break;
+          uint8_t* dst = sA + as * A_BYTES + line;
 #pragma unroll
-          for (int l = 0; l < RPT; ++l)
-            *reinterpret_cast<uint4*>(dst + 128 * RS * l) =
-                geno8_to_bf16x8_lut(v[d][l], lutlo[l], luthi[l]);
+          for (int u = 0; u < 4; ++u) {
+            const int j = 4 * hh + u;
+            *reinterpret_cast<uint4*>(dst + ((j ^ (r & 7)) << 4)) = o[u];
+          }
           // every lane's writes are ordered before the async proxy, then one arrive per warp
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) mbar_arrive(&bars->a_full[as]);
           if (++as == SA) { as = 0; aph ^= 1; }
-          if (++sks == nk) { sks = 0; sw += gridDim.x; }
-          if (g + d + PF < total) load_next(v[d]);
         }
       }
     }
@@ -381,7 +358,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         named_bar(1, 128);
       }
-      if (ok) ok = mbar_wait(&bars->acc_full[buf], accph, abort, tflag, WAIT_NS);
+      if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full[buf], accph, abort, tflag, WAIT_NS));
       if (ok) {
         tc_fence_after();
         const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + buf * BN;
@@ -568,7 +545,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 template <int EPI, int QQ>
 void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
-                const EigTcParams& p, int num_sms) {
+                const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {
   constexpr size_t SMEM = smem_of(EPI, QQ);
   static_assert(SMEM <= 232448, "shared memory over the sm_103 opt-in limit");
   static bool prepared = false;
@@ -579,50 +556,28 @@ void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB
   }
   const int64_t work = ((p.m + BM - 1) / BM) * p.nblk;
   const unsigned grid = (unsigned)(work < num_sms ? work : num_sms);
-  eig_tc_kernel<EPI, QQ><<<grid, NUM_THREADS, SMEM, s>>>(mapA, mapB, p);
+  eig_tc_kernel<EPI, QQ><<<grid, NUM_THREADS, SMEM, s>>>(mapA, mapB, mapG, p);
   GW_CHECK_LAUNCH();
-}
-
-__global__ void snp_centres_kernel(const int8_t* __restrict__ XR, int64_t m, int n,
-                                   float* __restrict__ mu) {
-  const int64_t snp = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x % 32;
-  if (snp >= m) return;
-  const int8_t* x = XR + snp * n;
-  int sum = 0;
-  for (int k = lane; k < n; k += 32) sum += x[k];
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if (lane == 0) {
-    // clamp to [0, 2] so g - mu stays within 8 significant bits (exact in BF16)
-    float c = rintf(64.f * (float)sum / (float)n) / 64.f;
-    mu[snp] = fminf(fmaxf(c, 0.f), 2.f);
-  }
 }
 
 }  // namespace
 
-void snp_centres(cudaStream_t s, const int8_t* XR, int64_t m, int n, float* mu) {
-  if (m <= 0) return;
-  snp_centres_kernel<<<(unsigned)((m + 7) / 8), 256, 0, s>>>(XR, m, n, mu);
-  GW_CHECK_LAUNCH();
-}
-
 void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUtensorMap& mapB,
-                   const EigTcParams& p, int num_sms) {
+                   const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {
   if (p.m <= 0 || p.nblk <= 0) return;
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q out of range");
   switch (stage) {
-    case 0: launch_one<EPI_ROT, 0>(s, mapA, mapB, p, num_sms); break;
-    case 1: launch_one<EPI_SQ, 0>(s, mapA, mapB, p, num_sms); break;
+    case 0: launch_one<EPI_ROT, 0>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 1: launch_one<EPI_SQ, 0>(s, mapA, mapB, mapG, p, num_sms); break;
     default:
       switch (p.q) {
-        case 1: launch_one<EPI_AC, 1>(s, mapA, mapB, p, num_sms); break;
-        case 2: launch_one<EPI_AC, 2>(s, mapA, mapB, p, num_sms); break;
-        case 3: launch_one<EPI_AC, 3>(s, mapA, mapB, p, num_sms); break;
-        case 4: launch_one<EPI_AC, 4>(s, mapA, mapB, p, num_sms); break;
-        case 5: launch_one<EPI_AC, 5>(s, mapA, mapB, p, num_sms); break;
-        case 6: launch_one<EPI_AC, 6>(s, mapA, mapB, p, num_sms); break;
-        default: launch_one<EPI_AC, 7>(s, mapA, mapB, p, num_sms); break;
+        case 1: launch_one<EPI_AC, 1>(s, mapA, mapB, mapG, p, num_sms); break;
+        case 2: launch_one<EPI_AC, 2>(s, mapA, mapB, mapG, p, num_sms); break;
+        case 3: launch_one<EPI_AC, 3>(s, mapA, mapB, mapG, p, num_sms); break;
+        case 4: launch_one<EPI_AC, 4>(s, mapA, mapB, mapG, p, num_sms); break;
+        case 5: launch_one<EPI_AC, 5>(s, mapA, mapB, mapG, p, num_sms); break;
+        case 6: launch_one<EPI_AC, 6>(s, mapA, mapB, mapG, p, num_sms); break;
+        default: launch_one<EPI_AC, 7>(s, mapA, mapB, mapG, p, num_sms); break;
       }
   }
 }

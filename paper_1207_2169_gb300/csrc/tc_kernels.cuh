@@ -11,8 +11,7 @@ namespace gw {
 // CHOL fused whiten-and-reduce (tc_chol.cu)
 // ------------------------------------------------------------------------------------------
 struct CholTcParams {
-  const int8_t* XR;   // m x n genotypes (device)
-  int64_t m;
+  int64_t m;          // SNPs of this launch (genotypes come through the mapG tensor map)
   int n, q, t, j;     // sizes; j = trait of this launch
   int kpad;           // n rounded up to 64: K extent of the split L^-1 rows
   int rpad;           // n rounded up to 256: rows of each piece of the split L^-1
@@ -26,17 +25,19 @@ struct CholTcParams {
 };
 constexpr int CHOL_TC_BM = 128;  // SNPs per tile
 // Tensor maps: rows = 2 * rpad (hi piece then lo piece), cols = kpad, BF16, 128-byte swizzle;
-// map256 has 64 x 256 boxes, map128 64 x 128 boxes.
+// map256 has 64 x 256 boxes, map128 64 x 128 boxes.  mapG: the 2-bit packed genotypes of the
+// launch, uint8 [m][packed_row_bytes(n)], boxes of 16 bytes x 128 rows, no swizzle.
 void chol_tc_launch(cudaStream_t s, const CUtensorMap& map256, const CUtensorMap& map128,
-                    const CholTcParams& p, int num_sms);
+                    const CUtensorMap& mapG, const CholTcParams& p, int num_sms);
+// uint8 map over packed genotype rows (boxes 16 bytes x 128 rows).
+CUtensorMap make_map_packed(const void* base, int64_t rows, int row_bytes);
 void chol_tc_prepare();
 
 // ------------------------------------------------------------------------------------------
 // EIG stages (tc_eig.cu): 0 = ROT (Xsq = (Z^T X_R)^2 split), 1 = SQ (s_ij), 2 = AC (a, c, Schur)
 // ------------------------------------------------------------------------------------------
 struct EigTcParams {
-  const int8_t* XR;        // m x n genotypes (ROT, AC)
-  int64_t m;
+  int64_t m;               // SNPs of this launch (ROT, AC: genotypes through mapG)
   int n, q, t, kpad;
   int nblk;                // 256-column blocks of the accumulator
   int b_piece_rows;        // row of the lo piece in the B tensor map
@@ -55,10 +56,8 @@ struct EigTcParams {
 };
 // mapA: the Xsq planes (SQ only; ignored otherwise).  mapB: Z^T split (ROT), d split (SQ),
 // U split (AC).  All BF16, 64-column boxes, 128-byte swizzle; mapA has 128-row boxes and mapB
-// 256-row boxes.
+// 256-row boxes.  mapG: packed genotypes as for CHOL (ROT, AC; ignored by SQ).
 void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUtensorMap& mapB,
-                   const EigTcParams& p, int num_sms);
-// mu[i] = nearest multiple of 1/64 to the mean genotype of SNP i (one warp per SNP).
-void snp_centres(cudaStream_t s, const int8_t* XR, int64_t m, int n, float* mu);
+                   const CUtensorMap& mapG, const EigTcParams& p, int num_sms);
 
 }  // namespace gw

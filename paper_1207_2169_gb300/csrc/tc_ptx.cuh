@@ -225,6 +225,31 @@ __device__ __forceinline__ uint4 geno8_to_bf16x8(uint2 w) {
   return make_uint4(a.x, a.y, b.x, b.y);
 }
 
+// 2-bit packed genotypes -> BF16.  For a byte b holding codes c0..c3 (bits 0-1 .. 6-7), the
+// pair (c0, c1) becomes the selector value c0 | c1 << 8 (then * 17 + 0x4040 as above), and
+// likewise (c2, c3).  LO / HI are the byte tables of the three values (plain: 0x00/0x80/0x00 and
+// 0x00/0x3F/0x40; centred: see centred_lut).  Eight bytes -> 32 BF16 values in out[0..3].
+__device__ __forceinline__ void packed8_to_bf16x32(uint2 w, uint32_t LO, uint32_t HI,
+                                                   uint4 (&out)[4]) {
+  uint32_t o[16];
+  const uint32_t wd[2] = {w.x, w.y};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int bi = 0; bi < 4; ++bi) {
+      const uint32_t b = (wd[h] >> (8 * bi)) & 0xFFu;
+      const uint32_t t0 = (b & 3u) | ((b << 6) & 0x300u);
+      const uint32_t t1 = ((b >> 4) & 3u) | ((b << 2) & 0x300u);
+      o[8 * h + 2 * bi] = __byte_perm(LO, HI, t0 * 17u + 0x4040u);
+      o[8 * h + 2 * bi + 1] = __byte_perm(LO, HI, t1 * 17u + 0x4040u);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = make_uint4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+}
+
+constexpr uint32_t GENO_LO = 0x00008000u, GENO_HI = 0x00403F00u;
+
 // Byte tables for centred genotypes g - mu (g = 0, 1, 2): low bytes and high bytes of the
 // three BF16 values.  Exact when mu is a multiple of 1/64 in [0, 2].
 __device__ __forceinline__ void centred_lut(float mu, uint32_t& lo, uint32_t& hi) {

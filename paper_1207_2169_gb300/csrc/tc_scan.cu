@@ -48,6 +48,25 @@ CUtensorMap make_map_bf16(const void* base, int64_t rows, int64_t cols, int box_
   return m;
 }
 
+// 2-D uint8 map over packed genotype rows [rows][row_bytes] (row_bytes a multiple of 16, base
+// 16-byte aligned), boxes of 16 bytes x 128 rows, no swizzle; rows past the end read as zero.
+CUtensorMap make_map_packed(const void* base, int64_t rows, int row_bytes) {
+  GW_REQUIRE(row_bytes % 16 == 0 && ((uintptr_t)base & 15) == 0 && rows >= 1 &&
+                 rows <= ((int64_t)1 << 32),
+             GWAS_ERR_ARG, "packed genotypes not TMA-aligned (base and rows need 16 bytes)");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)row_bytes, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  cuuint32_t box[2] = {16, 128};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims,
+                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  GW_REQUIRE(r == CUDA_SUCCESS, GWAS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return m;
+}
+
 struct TcState {
   int algo = 0, n = 0, q = 0, t = 0;
   int kpad = 0, rpad = 0, num_sms = 0;
@@ -177,10 +196,11 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
 void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
   if (a.m <= 0) return;
   GW_REQUIRE(st != nullptr, GWAS_ERR_ARG, "no tensor-core state");
+  const int rb = packed_row_bytes(st->n);
   if (st->algo == GWAS_ALGO_CHOL) {
+    const CUtensorMap mapG = make_map_packed(a.G, a.m, rb);
     for (int j = 0; j < st->t; ++j) {
       CholTcParams p{};
-      p.XR = a.XR;
       p.m = a.m;
       p.n = st->n;
       p.q = st->q;
@@ -195,7 +215,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
       p.B = a.B;
       p.W = a.wald;
       p.flags = a.flags;
-      chol_tc_launch(s, st->lmap256[j], st->lmap128[j], p, st->num_sms);
+      chol_tc_launch(s, st->lmap256[j], st->lmap128[j], mapG, p, st->num_sms);
     }
     return;
   }
@@ -214,18 +234,19 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.lds = st->mcap;
     p.flags = a.flags;
     // ROT: Xsq = (Z^T x)^2 for this chunk (Algorithm 4 line 3, squared and split)
-    p.XR = a.XR + off * n;
-    if (st->mu) snp_centres(s, p.XR, mm, n, st->mu);
+    const uint8_t* Gc = a.G + off * rb;
+    const CUtensorMap mapG = make_map_packed(Gc, mm, rb);
+    if (st->mu) snp_centres_packed(s, Gc, mm, n, st->mu);
     p.mu = st->mu;
     p.nblk = st->rpad / 256;
     p.b_piece_rows = st->rpad;
     p.b_rows_per_blk = 256;
-    eig_tc_launch(s, 0, st->mapZ, st->mapZ, p, st->num_sms);
+    eig_tc_launch(s, 0, st->mapZ, st->mapZ, mapG, p, st->num_sms);
     // SQ: s_ij = sum_r Xsq[i][r] d_j[r]
     p.nblk = (t + 255) / 256;
     p.b_piece_rows = t;
     p.b_rows_per_blk = 256;
-    eig_tc_launch(s, 1, st->mapX, st->mapD, p, st->num_sms);
+    eig_tc_launch(s, 1, st->mapX, st->mapD, mapG, p, st->num_sms);
     // AC: a_ij, c_ij from the genotypes against U, then the bordered solve (lines 13-16)
     p.nblk = (t + st->traits_ac - 1) / st->traits_ac;
     p.b_piece_rows = t * q1;
@@ -235,7 +256,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.b0 = st->b032;
     p.B = a.B + (size_t)off * t * q1;
     p.W = a.wald ? a.wald + (size_t)off * t : nullptr;
-    eig_tc_launch(s, 2, st->mapU, st->mapU, p, st->num_sms);
+    eig_tc_launch(s, 2, st->mapU, st->mapU, mapG, p, st->num_sms);
   }
 }
 

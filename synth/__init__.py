@@ -176,6 +176,19 @@ def snp_block(workload: int, n: int, m: int, block_index: int) -> np.ndarray:
     return genotypes(rng(workload, 1000 + block_index), n, m)
 
 
+def workload_genotypes(workload: int, m: int | None = None) -> np.ndarray:
+    """The first m SNPs (default: all) of workload `workload`'s genome, m x n int8, assembled
+    from its per-block streams (snp_block) so that any prefix is the same at every m."""
+    spec = WORKLOADS[workload]
+    n, blk = spec["n"], spec["block"]
+    m = spec["m"] if m is None else m
+    XR = np.empty((m, n), dtype=np.int8)
+    for b in range((m + blk - 1) // blk):
+        lo, hi = b * blk, min(m, (b + 1) * blk)
+        XR[lo:hi] = snp_block(workload, n, blk, b)[:hi - lo]
+    return XR
+
+
 def small_problem(seed: int, n: int, q: int, m: int, t: int, h2=None, s2=None) -> Cohort:
     """Small random problem for parity tests (any n, q, m, t)."""
     g = np.random.Generator(np.random.PCG64([SEED_BASE, 77, seed]))

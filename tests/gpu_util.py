@@ -5,19 +5,29 @@ import numpy as np
 from oracle import gls
 
 
-def run(g, c, algo, precision, XR=None, device=True, block_snps=0, f64=False):
+def run(g, c, algo, precision, XR=None, device=True, block_snps=0, f64=False, packed=False,
+        validate=False):
+    """packed: pass the genotypes as packed rows (gwas_pack_genotypes on the host, then
+    gwas_scan_packed) instead of int8 rows (gwas_scan)."""
     import torch
     XR = c.XR if XR is None else XR
     h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, algo=algo, precision=precision,
-                     block_snps=block_snps)
+                     block_snps=block_snps, validate_genotypes=int(validate))
     try:
         m, t, p = XR.shape[0], c.t, c.p
         dt = torch.float64 if f64 else torch.float32
         dev = "cuda" if device else "cpu"
-        xr = torch.from_numpy(np.ascontiguousarray(XR)).to(dev)
+        X = np.ascontiguousarray(XR)
+        if packed:
+            X = g.gwas_pack_genotypes(X)
+        xr = torch.from_numpy(X).to(dev)
         B = torch.full((m, t, p), float("nan"), dtype=dt, device=dev)
         W = torch.full((m, t), float("nan"), dtype=dt, device=dev)
-        (g.gwas_scan_f64 if f64 else g.gwas_scan)(h, xr, B, W)
+        if packed:
+            assert not f64
+            g.gwas_scan_packed(h, xr, B, W)
+        else:
+            (g.gwas_scan_f64 if f64 else g.gwas_scan)(h, xr, B, W)
         if device:
             torch.cuda.synchronize()
         nsing = g.gwas_singular_count(h)

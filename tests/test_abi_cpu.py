@@ -88,3 +88,48 @@ def test_null_handle_calls(g):
     ms = ctypes.c_double()
     assert g.lib.gwas_setup_timing(None, ctypes.byref(ms)) == -1
     assert g.lib.gwas_info(None, None, None, None, None, None) == -1
+
+
+def _decode_packed(G, n):
+    """Reads genotype k of each row from byte k // 4, bits 2 (k % 4) .. +1 (the documented
+    layout), one genotype at a time."""
+    m = G.shape[0]
+    out = np.zeros((m, n), np.int64)
+    for k in range(n):
+        out[:, k] = (G[:, k // 4].astype(np.int64) >> (2 * (k % 4))) & 3
+    return out
+
+
+def test_packed_row_bytes(g):
+    assert [g.gwas_packed_row_bytes(n) for n in (0, 1, 63, 64, 65, 1000, 16384)] == \
+        [0, 16, 16, 16, 32, 256, 4096]
+
+
+@pytest.mark.parametrize("n", [1, 7, 64, 97, 130])
+def test_host_packing_layout(g, n):
+    rs = np.random.default_rng(n)
+    X = rs.integers(0, 3, size=(37, n)).astype(np.int8)
+    G = g.gwas_pack_genotypes(X)
+    rb = g.gwas_packed_row_bytes(n)
+    assert G.shape == (37, rb) and G.dtype == np.uint8
+    assert np.array_equal(_decode_packed(G, n), X)
+    # every code past the n-th genotype of a row is zero
+    assert np.all(_decode_packed(G, 4 * rb)[:, n:] == 0)
+
+
+def test_host_packing_rejects_invalid_values(g):
+    X = np.zeros((3, 10), np.int8)
+    X[1, 4] = 3
+    X[2, 9] = -1
+    G = np.zeros((3, 16), np.uint8)
+    st = g.lib.gwas_pack_genotypes(X.ctypes.data, 3, 10, G.ctypes.data, 0, None)
+    assert st == -6
+    d = _decode_packed(G, 10)
+    assert d[1, 4] == 3 and d[2, 9] == 3 and d.sum() == 6  # invalid values -> code 3, rest packed
+    assert g.lib.gwas_pack_genotypes(None, 3, 10, G.ctypes.data, 0, None) == -1
+    assert g.lib.gwas_pack_genotypes(X.ctypes.data, 3, 0, G.ctypes.data, 0, None) == -1
+    assert g.lib.gwas_pack_genotypes(X.ctypes.data, 0, 10, None, 0, None) == 0
+
+
+def test_scan_packed_null_handle(g):
+    assert g.lib.gwas_scan_packed(None, None, 10, 1, None, None, 1, None) == -1
