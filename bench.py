@@ -165,7 +165,7 @@ def executed_flops(s, m):
         for nb in range(rpad // 256):
             nk = min(4 * (nb + 1), kpad // 64)
             for ks in range(nk):
-                macs += 64 * (128 if ks >= 4 * nb + 2 else 256)
+                macs += 64 * (256 - 64 * max(0, ks - 4 * nb))  # rows on/below the diagonal
         return 2 * 2 * macs * m * t
     rot = 2 * 2 * rpad * kpad * m
     sq = 3 * 2 * kpad * t * m
@@ -361,7 +361,7 @@ def launches_per_scan(s, precision, m, fmt):
 
     def kernels(mm):
         if s["algo"] == "chol":
-            return t
+            return t + int(tc)  # the tensor-core scan first computes the SNP centres
         if tc:
             return 4 * -(-mm // 32768)  # centres, rotation, s, a/c + Schur per 32 Ki SNPs
         return 2 * -(-mm // min(m, blk))

@@ -9,25 +9,46 @@
 namespace gw {
 namespace {
 
-// One thread per 32-bit word of packed output (16 genotypes).
+// Four int8 calls (one 32-bit word) -> four 2-bit codes in the low byte; a byte outside
+// {0, 1, 2} (including negative ones) becomes code 3 and sets *bad.
+__device__ __forceinline__ uint32_t pack4(uint32_t x, bool& bad) {
+  const uint32_t big = (x | ((x & 0x7F7F7F7Fu) + 0x7D7D7D7Du)) & 0x80808080u;  // byte >= 3
+  bad |= big != 0u;
+  const uint32_t v = (x & 0x03030303u) | (big >> 6) | (big >> 7);
+  const uint32_t t = v | (v >> 6);  // codes 0,1 in bits 0-3, codes 2,3 in bits 16-19
+  return (t & 0xFu) | ((t >> 12) & 0xF0u);
+}
+
+// One thread per 32-bit word of packed output (16 calls).  Rows whose start is 8-byte aligned
+// (n a multiple of 8) are read as two 8-byte words per thread.
 __global__ void pack2_kernel(const int8_t* __restrict__ x, int64_t m, int n, int row_bytes,
                              uint32_t* __restrict__ out, int* flags, int validate) {
   const int words = row_bytes / 4;
   const int64_t total = m * words;
+  const bool vec = (n % 8 == 0) && ((reinterpret_cast<uintptr_t>(x) & 7) == 0);
   bool bad = false;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t snp = e / words;
-    const int wd = (int)(e % words);
+    const int k0 = (int)(e % words) * 16;
     const int8_t* row = x + snp * n;
     uint32_t w = 0;
+    if (vec && k0 + 16 <= n) {
+      const uint2 a = __ldg(reinterpret_cast<const uint2*>(row + k0));
+      const uint2 b = __ldg(reinterpret_cast<const uint2*>(row + k0 + 8));
+      w = pack4(a.x, bad) | pack4(a.y, bad) << 8 | pack4(b.x, bad) << 16 | pack4(b.y, bad) << 24;
+    } else if (vec && k0 + 8 <= n) {
+      const uint2 a = __ldg(reinterpret_cast<const uint2*>(row + k0));
+      w = pack4(a.x, bad) | pack4(a.y, bad) << 8;
+    } else if (k0 < n) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int k = wd * 16 + i;
-      if (k < n) {
-        const uint32_t g = (uint8_t)row[k];
-        bad |= g > 2;
-        w |= (g > 2 ? 3u : g) << (2 * i);  // invalid values become the invalid code 3
+      for (int i = 0; i < 16; ++i) {
+        const int k = k0 + i;
+        if (k < n) {
+          const uint32_t g = (uint8_t)row[k];
+          bad |= g > 2;
+          w |= (g > 2 ? 3u : g) << (2 * i);  // invalid values become the invalid code 3
+        }
       }
     }
     out[e] = w;

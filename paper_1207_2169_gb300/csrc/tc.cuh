@@ -18,7 +18,7 @@ struct TcSetupArgs {
   const double* P;       // t x q x q
   const double* b0;      // t x q
   int block_snps;        // EIG: SNPs per internal chunk (sizes the per-chunk scratch)
-  int intercept;         // column 0 of X_L is all ones: SNPs may be centred (EIG)
+  int intercept;         // column 0 of X_L is all ones: SNPs are centred (CHOL, EIG)
 };
 
 struct TcScanArgs {

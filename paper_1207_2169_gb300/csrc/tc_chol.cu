@@ -1,16 +1,22 @@
 // CHOL fused whiten-and-reduce on the tensor cores (tcgen05 / TMEM / TMA, sm_103a).
 //
-// Algorithm 3 lines 4 and 8-11 for one trait.  A persistent CTA walks 128-SNP tiles.  For each
-// block of 256 rows of L^-1 it accumulates D[snp][r] = (L^-1 x_snp)_r in TMEM, over only the
-// K range c <= r where L^-1 can be nonzero (the aggregated triangular solve of "Sequences of
-// GLS'", done as one product with the precomputed inverse).  L^-1 = hi + lo in BF16 pieces and
-// genotypes are exact in BF16, so D = X hi^T + X lo^T carries ~16 significant bits of L^-1 with
-// FP32 accumulation.  Where a K step lies entirely above the diagonal of the lower 128 rows of a
-// block, only the upper 128 rows are multiplied.  The epilogue reduces each finished block
-// straight out of TMEM into the bordered-system entries of every SNP,
-//     s = x'^T x',   c = r'^T x',   a_k = (L^-1 X_L)_k^T x'     (x' = L^-1 x),
-// in FP32 over 32 columns and FP64 across them, and finishes each tile with the Schur-complement
-// solve in FP64.  X' = L^-1 X_R is never written to memory.
+// Algorithm 3 lines 4 and 8-11 for one trait.  A persistent CTA walks 128-SNP tiles.  The B
+// operand is L^-1 augmented with q + 1 rows: u_k = M^-1 X_L[:,k] (k < q) and M^-1 r (r the
+// null residual), so one product gives, per SNP, the whitened genotypes x' = L^-1 x (columns
+// < n) and, being linear in x, a_k = x^T M^-1 X_L[:,k] and c = x^T M^-1 r (columns n .. n+q).
+// For each block of 256 rows it accumulates D[snp][r] in TMEM over only the K range c <= r
+// where L^-1 can be nonzero (the aggregated triangular solve of "Sequences of GLS'", done as
+// one product with the precomputed inverse); the augmented rows take the full K range.  On the
+// diagonal of a block a K step of 64 columns multiplies only the rows it meets (narrower MMAs
+// into the matching accumulator columns), and the last block stops at row n + q.  The
+// augmented matrix is split into BF16 hi + lo pieces and genotypes are exact in BF16, so
+// D = X hi^T + X lo^T carries ~16 significant bits with FP32 accumulation.  The epilogue sums
+// s = x'^T x' out of TMEM (FP32 within a block, FP64 across blocks), picks up a and c, and
+// finishes each tile with the Schur-complement solve in FP64.  X' is never written to memory.
+// With an intercept in X_L each SNP is centred by mu, the multiple of 1/64 nearest its mean
+// (exact in BF16): s - a^T P a then no longer cancels the large intercept component, whose BF16
+// splitting errors in s and in a are not correlated; b_snp and the Wald statistic are unchanged
+// and the intercept estimate is corrected by -mu b_snp.
 //
 // Warp roles (448 threads):
 //   0-3  epilogue: one SNP per thread (TMEM lane 32*warp + lane)
@@ -29,12 +35,11 @@ namespace {
 constexpr int BM = CHOL_TC_BM;
 constexpr int BN = 256;
 constexpr int BK = 64;
-constexpr int SA = 4;                   // genotype tile ring
-constexpr int SB = 4;                   // L^-1 tile ring (one piece per slot)
+constexpr int SA = 3;                   // genotype tile ring
+constexpr int SB = 5;                   // L^-1 tile ring (one piece per slot)
 constexpr int A_BYTES = BM * BK * 2;    // 16 KB
 constexpr int B_BYTES = BN * BK * 2;    // 32 KB
 constexpr int QMAX = 7;
-constexpr int CST_FLOATS = 4096;  // 16 KB: per-row epilogue constants
 constexpr int PR = 8;                   // packed-genotype slice ring
 constexpr int PK_BYTES = BM * 16;       // 64 genotypes of 128 SNPs, 2-bit codes: 2 KB
 constexpr int NCONV = 8;                // genotype converter warps: 2 threads per row
@@ -49,17 +54,28 @@ struct __align__(8) Bars {
   int abort;
 };
 
-constexpr size_t SMEM_BYTES =
-    1024 + SA * A_BYTES + SB * B_BYTES + PR * PK_BYTES + CST_FLOATS * 4 + sizeof(Bars);
+constexpr size_t SMEM_BYTES = 1024 + SA * A_BYTES + SB * B_BYTES + PR * PK_BYTES + sizeof(Bars);
+static_assert(SMEM_BYTES <= 232448, "shared memory over the sm_103 opt-in limit");
 
 __device__ __forceinline__ int ksteps(int nb, int kpad) {
   const int k = (nb + 1) * (BN / BK);
   const int kmax = kpad / BK;
   return k < kmax ? k : kmax;
 }
-// K steps at or beyond this one only meet the upper 128 rows of block nb (the lower rows of
-// L^-1 are zero there).
-__device__ __forceinline__ int half_from(int nb) { return nb * (BN / BK) + 2; }
+// Rows of block nb that K step ks meets, in units of 64: L^-1 is lower triangular, so a K step
+// on the diagonal (ks = 4 nb + j) meets only rows 64 j .. 255 of the block; j = 0 below it.
+__device__ __forceinline__ int diag_skip(int nb, int ks) {
+  const int j = ks - nb * (BN / BK);
+  return j > 0 ? j : 0;
+}
+
+// Live accumulator columns of block nb: rows of the augmented matrix below n + q + 1, rounded
+// up to the MMA's N granularity (16).
+__device__ __forceinline__ int block_cols(int nb, int n, int q) {
+  const int live = n + q + 1 - nb * BN;
+  const int c = (live + 15) & ~15;
+  return c < BN ? c : BN;
+}
 
 // (tile, block, k-step) sequence shared by every role of a CTA.
 struct Step {
@@ -77,16 +93,14 @@ __device__ __forceinline__ void advance(Step& s, int nblocks, int kpad) {
 // QM: compile-time bound on q (3 or 7), so the epilogue's per-column arrays stay in registers.
 template <int QM>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-    chol_tc_kernel(const __grid_constant__ CUtensorMap map256,
-                   const __grid_constant__ CUtensorMap map128,
-                   const __grid_constant__ CUtensorMap mapG, const CholTcParams p) {
+    chol_tc_kernel(const __grid_constant__ CholMaps lmaps, const __grid_constant__ CUtensorMap mapG,
+                   const CholTcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = sA + SA * A_BYTES;
   uint8_t* sP = sB + SB * B_BYTES;
-  float* cst = (float*)(sP + PR * PK_BYTES);
-  Bars* bars = (Bars*)(cst + CST_FLOATS);
+  Bars* bars = (Bars*)(sP + PR * PK_BYTES);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t ntiles = (p.m + BM - 1) / BM;
   const int nblocks = p.rpad / BN;
@@ -118,8 +132,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tmem_relinquish();
   }
   if (warp == 4 && lane == 0) {
-    prefetch_tensormap(&map256);
-    prefetch_tensormap(&map128);
+    for (int j = 0; j < 4; ++j) prefetch_tensormap(&lmaps.m[j]);
     prefetch_tensormap(&mapG);
   }
   tc_fence_before();
@@ -134,20 +147,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int bs = 0;
       uint32_t bph = 0;
       for (Step st{blockIdx.x, 0, 0}; st.tile < ntiles; advance(st, nblocks, p.kpad)) {
-        const bool half = st.ks >= half_from(st.nb);
+        const int j = diag_skip(st.nb, st.ks);  // rows 64 j .. 255 of the block
         bool ok = true;
         for (int piece = 0; piece < 2; ++piece) {
           ok = mbar_wait(&bars->b_empty[bs], bph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
-          const int y = piece * p.rpad + st.nb * BN;
-          if (half) {
-            mbar_arrive_expect_tx(&bars->b_full[bs], B_BYTES / 2);
-            tma_load_2d(sB + bs * B_BYTES + B_BYTES / 2, &map128, &bars->b_full[bs], st.ks * BK,
-                        y + BN / 2);
-          } else {
-            mbar_arrive_expect_tx(&bars->b_full[bs], B_BYTES);
-            tma_load_2d(sB + bs * B_BYTES, &map256, &bars->b_full[bs], st.ks * BK, y);
-          }
+          const int y = piece * p.rpad + st.nb * BN + 64 * j;
+          mbar_arrive_expect_tx(&bars->b_full[bs], (B_BYTES / 4) * (4 - j));
+          tma_load_2d(sB + bs * B_BYTES + (B_BYTES / 4) * j, &lmaps.m[j], &bars->b_full[bs],
+                      st.ks * BK, y);
           if (++bs == SB) { bs = 0; bph ^= 1; }
         }
         if (!ok) break;
@@ -171,29 +179,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int as = 0, bs = 0, buf = 0;
       uint32_t aph = 0, bph = 0, accph = 0;
       bool ok = true;
-      const uint32_t id_full = idesc_bf16(BM, BN), id_half = idesc_bf16(BM, BN / 2);
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         for (int nb = 0; nb < nblocks && ok; ++nb) {
           ok = mbar_wait(&bars->acc_empty[buf], accph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
           tc_fence_after();
           const uint32_t dt = tmem + buf * BN;
-          const int nk = ksteps(nb, p.kpad), hf = half_from(nb);
+          const int nk = ksteps(nb, p.kpad), ncols = block_cols(nb, p.n, p.q);
           for (int ks = 0; ks < nk && ok; ++ks) {
             ok = mbar_wait(&bars->a_full[as], aph, abort, tflag, WAIT_NS);
             if (!ok) break;
             tc_fence_after();
             const uint64_t ad = sw128_desc(sA + as * A_BYTES);
-            const bool half = ks >= hf;
+            const int j = diag_skip(nb, ks);  // accumulator columns 64 j .. ncols - 1
+            const uint32_t idesc = idesc_bf16(BM, ncols - 64 * j);
             for (int piece = 0; piece < 2; ++piece) {
               ok = mbar_wait(&bars->b_full[bs], bph, abort, tflag, WAIT_NS);
               if (!ok) break;
               tc_fence_after();
-              const uint64_t bd = sw128_desc(sB + bs * B_BYTES + (half ? B_BYTES / 2 : 0));
+              const uint64_t bd = sw128_desc(sB + bs * B_BYTES + (B_BYTES / 4) * j);
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk)
-                mma_bf16(half ? dt + BN / 2 : dt, ad + 2 * kk, bd + 2 * kk,
-                         half ? id_half : id_full, (ks | piece | kk) != 0);
+                mma_bf16(dt + 64 * j, ad + 2 * kk, bd + 2 * kk, idesc, (ks | piece | kk) != 0);
               mma_commit(&bars->b_empty[bs]);
               if (++bs == SB) { bs = 0; bph ^= 1; }
             }
@@ -214,126 +221,93 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int ct = threadIdx.x - 192;
     const int r = ct >> 1, hh = ct & 1;
     const uint32_t line = (r >> 3) * 1024 + (r & 7) * 128;
-    int64_t total = 0;
-    {
-      int per_tile = 0;
-      for (int nb = 0; nb < nblocks; ++nb) per_tile += ksteps(nb, p.kpad);
-      const int64_t mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-      total = mine * per_tile;
-    }
+    int per_tile = 0;
+    for (int nb = 0; nb < nblocks; ++nb) per_tile += ksteps(nb, p.kpad);
     int as = 0, ps = 0;
     uint32_t aph = 0, pph = 0;
-    for (int64_t g = 0; g < total; ++g) {
-      // warp-uniform exits: every lane leaves together if any wait gave up
-      if (!__all_sync(0xffffffffu, mbar_wait(&bars->pk_full[ps], pph, abort, tflag, WAIT_NS))) break;
-      const uint2 w = *reinterpret_cast<const uint2*>(sP + ps * PK_BYTES + r * 16 + hh * 8);
-      // the slot is refilled by TMA (async proxy): order these generic reads before it
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars->pk_empty[ps]);
-      if (++ps == PR) { ps = 0; pph ^= 1; }
-      uint4 o[4];
-      packed8_to_bf16x32(w, GENO_LO, GENO_HI, o);
-      if (!__all_sync(0xffffffffu, mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS)))
-        break;
-      uint8_t* dst = sA + as * A_BYTES + line;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int j = 4 * hh + i;
-        *reinterpret_cast<uint4*>(dst + ((j ^ (r & 7)) << 4)) = o[i];
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      // byte tables of this row: g - mu (mu = 0 without centring)
+      uint32_t lutlo = GENO_LO, luthi = GENO_HI;
+      if (p.mu) {
+        const int64_t snp = tile * BM + r;
+        centred_lut(snp < p.m ? p.mu[snp] : 0.f, lutlo, luthi);
       }
-      // every lane's writes are ordered before the async proxy, then one arrive per warp
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars->a_full[as]);
-      if (++as == SA) { as = 0; aph ^= 1; }
+      for (int g = 0; g < per_tile; ++g) {
+        // warp-uniform exits: every lane leaves together if any wait gave up
+        ok = __all_sync(0xffffffffu, mbar_wait(&bars->pk_full[ps], pph, abort, tflag, WAIT_NS));
+        if (!ok) break;
+        const uint2 w = *reinterpret_cast<const uint2*>(sP + ps * PK_BYTES + r * 16 + hh * 8);
+        // the slot is refilled by TMA (async proxy): order these generic reads before it
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->pk_empty[ps]);
+        if (++ps == PR) { ps = 0; pph ^= 1; }
+        uint4 o[4];
+        packed8_to_bf16x32(w, lutlo, luthi, o);
+        ok = __all_sync(0xffffffffu, mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS));
+        if (!ok) break;
+        uint8_t* dst = sA + as * A_BYTES + line;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int j = 4 * hh + i;
+          *reinterpret_cast<uint4*>(dst + ((j ^ (r & 7)) << 4)) = o[i];
+        }
+        // every lane's writes are ordered before the async proxy, then one arrive per warp
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->a_full[as]);
+        if (++as == SA) { as = 0; aph ^= 1; }
+      }
     }
   } else {
     // ------------------------------------------------------------ epilogue (warps 0-3)
-    const int q = p.q;
+    // Per block: s += sum of squares of the whitened genotype columns (rows < n); columns
+    // n .. n+q of the last block hold a_k and c.  FP32 within a block, FP64 across blocks.
+    const int q = p.q, n = p.n;
     int buf = 0;
     uint32_t accph = 0;
     bool ok = true;
-    // Per-row constants [k][row] (k < q: L^-1 X_L columns, k = q: whitened residual).  When all
-    // rows fit they are loaded once; otherwise the 256 rows of each block are reloaded.
-    const bool resident = (q + 1) * p.rpad <= CST_FLOATS;
-    const int cstride = resident ? p.rpad : BN;
-    if (resident) {
-      for (int e = threadIdx.x; e < (q + 1) * p.rpad; e += 128) {
-        const int k = e / p.rpad, r = e % p.rpad;
-        cst[e] = r < p.n ? (k < q ? p.XLw[(int64_t)k * p.n + r] : p.rw[r]) : 0.f;
-      }
-      named_bar(1, 128);
-    }
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      double S = 0.0, C = 0.0, A[QM];
+      double S = 0.0;
+      float A[QM], C = 0.f;
 #pragma unroll
-      for (int k = 0; k < QM; ++k) A[k] = 0.0;
+      for (int k = 0; k < QM; ++k) A[k] = 0.f;
       for (int nb = 0; nb < nblocks; ++nb) {
-        if (!resident) {
-          named_bar(1, 128);  // the previous block's constants are no longer read
-          for (int e = threadIdx.x; e < (q + 1) * BN; e += 128) {
-            const int k = e / BN, i = e % BN, r = nb * BN + i;
-            cst[e] = r < p.n ? (k < q ? p.XLw[(int64_t)k * p.n + r] : p.rw[r]) : 0.f;
-          }
-          named_bar(1, 128);
-        }
-        const float* cb = resident ? cst + nb * BN : cst;
         if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full[buf], accph, abort, tflag, WAIT_NS));
         if (ok) {
           tc_fence_after();
           const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + buf * BN;
-          // FP32 over the block's 256 rows (two levels: 32-row chunks, then chunks), FP64 over
-          // blocks.
-          float bs_ = 0.f, bc = 0.f, ba[QM];
-#pragma unroll
-          for (int k = 0; k < QM; ++k) ba[k] = 0.f;
+          const int c0 = nb * BN, ncols = block_cols(nb, n, q);
+          float bs_ = 0.f;
           uint32_t ra[32];
-          auto chunk = [&](const uint32_t (&r)[32], int c) {
-            float ss = 0.f, cc = 0.f, aa[QM];
+#pragma unroll 1
+          for (int c = 0; c < ncols; c += 32) {
+            tmem_ld32_async(base + c, ra);
+            tmem_wait32(ra);
+            float ss = 0.f;
+            if (c0 + c + 32 <= n) {
 #pragma unroll
-            for (int k = 0; k < QM; ++k) aa[k] = 0.f;
-            const float* cr = cb + 32 * c;
+              for (int i = 0; i < 32; ++i) {
+                const float x = __uint_as_float(ra[i]);
+                ss = fmaf(x, x, ss);
+              }
+            } else {
+              // the chunk holding row n: genotype columns, then a_0 .. a_{q-1}, c
 #pragma unroll
-            for (int i4 = 0; i4 < 8; ++i4) {
-              const float4 cv = *reinterpret_cast<const float4*>(cr + q * cstride + 4 * i4);
-              float4 av[QM];
+              for (int i = 0; i < 32; ++i) {
+                const int col = c0 + c + i;
+                const float x = __uint_as_float(ra[i]);
+                if (col < n) ss = fmaf(x, x, ss);
 #pragma unroll
-              for (int k = 0; k < QM; ++k)
-                if (k < q) av[k] = *reinterpret_cast<const float4*>(cr + k * cstride + 4 * i4);
-              const float x[4] = {__uint_as_float(r[4 * i4]), __uint_as_float(r[4 * i4 + 1]),
-                                  __uint_as_float(r[4 * i4 + 2]), __uint_as_float(r[4 * i4 + 3])};
-              const float cw[4] = {cv.x, cv.y, cv.z, cv.w};
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                ss = fmaf(x[e], x[e], ss);
-                cc = fmaf(cw[e], x[e], cc);
-#pragma unroll
-                for (int k = 0; k < QM; ++k) {
-                  if (k < q) {
-                    const float w = e == 0 ? av[k].x : e == 1 ? av[k].y : e == 2 ? av[k].z : av[k].w;
-                    aa[k] = fmaf(w, x[e], aa[k]);
-                  }
-                }
+                for (int k = 0; k < QM; ++k)
+                  if (k < q && col == n + k) A[k] = x;
+                if (col == n + q) C = x;
               }
             }
             bs_ += ss;
-            bc += cc;
-#pragma unroll
-            for (int k = 0; k < QM; ++k) ba[k] += aa[k];
-          };
-          // one 32-column TMEM load at a time: the epilogue has slack, and its registers go to
-          // the eight converter warps (448 threads leave 128 registers per thread)
-#pragma unroll 1
-          for (int c = 0; c < BN / 32; ++c) {
-            tmem_ld32_async(base + 32 * c, ra);
-            tmem_wait32(ra);
-            chunk(ra, c);
           }
           S += bs_;
-          C += bc;
-#pragma unroll
-          for (int k = 0; k < QM; ++k) A[k] += ba[k];
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
@@ -349,8 +323,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (k < q) {
 #pragma unroll
             for (int l = 0; l < QM; ++l)
-              if (l < q) acc += __ldg(&p.P[k * q + l]) * A[l];
-            aPa += A[k] * acc;
+              if (l < q) acc += __ldg(&p.P[k * q + l]) * (double)A[l];
+            aPa += (double)A[k] * acc;
           }
           v[k] = acc;
         }
@@ -358,12 +332,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int pp = q + 1;
         float* Bo = p.B + (snp * p.t + p.j) * pp;
         if (sigma > 1e-5 * S) {
-          const double bs = C / sigma;
+          const double bs = (double)C / sigma;
+#pragma unroll
+          double bl[QM];
+#pragma unroll
+          for (int k = 0; k < QM; ++k) bl[k] = k < q ? __ldg(&p.b0[k]) - v[k] * bs : 0.0;
+          // centred SNP x - mu: the intercept (column 0 of X_L) absorbs mu * b_snp
+          if (p.mu) bl[0] -= (double)p.mu[snp] * bs;
 #pragma unroll
           for (int k = 0; k < QM; ++k)
-            if (k < q) Bo[k] = (float)(__ldg(&p.b0[k]) - v[k] * bs);
+            if (k < q) Bo[k] = (float)bl[k];
           Bo[q] = (float)bs;
-          if (p.W) p.W[snp * p.t + p.j] = (float)(bs * C);
+          if (p.W) p.W[snp * p.t + p.j] = (float)(bs * (double)C);
         } else {
           for (int k = 0; k < pp; ++k) Bo[k] = __int_as_float(0x7fc00000);
           if (p.W) p.W[snp * p.t + p.j] = __int_as_float(0x7fc00000);
@@ -389,16 +369,16 @@ void chol_tc_prepare() {
                                (int)SMEM_BYTES));
 }
 
-void chol_tc_launch(cudaStream_t s, const CUtensorMap& map256, const CUtensorMap& map128,
-                    const CUtensorMap& mapG, const CholTcParams& p, int num_sms) {
+void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& mapG,
+                    const CholTcParams& p, int num_sms) {
   if (p.m <= 0) return;
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", p.q, QMAX);
   const int64_t tiles = (p.m + BM - 1) / BM;
   const unsigned grid = (unsigned)(tiles < num_sms ? tiles : num_sms);
   if (p.q <= 3)
-    chol_tc_kernel<3><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(map256, map128, mapG, p);
+    chol_tc_kernel<3><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
   else
-    chol_tc_kernel<QMAX><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(map256, map128, mapG, p);
+    chol_tc_kernel<QMAX><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
   GW_CHECK_LAUNCH();
 }
 

@@ -13,22 +13,26 @@ namespace gw {
 struct CholTcParams {
   int64_t m;          // SNPs of this launch (genotypes come through the mapG tensor map)
   int n, q, t, j;     // sizes; j = trait of this launch
-  int kpad;           // n rounded up to 64: K extent of the split L^-1 rows
-  int rpad;           // n rounded up to 256: rows of each piece of the split L^-1
-  const float* XLw;   // q x n  whitened covariates L^-1 X_L of trait j
-  const float* rw;    // n      whitened null residual of trait j
+  int kpad;           // n rounded up to 64: K extent of the split rows
+  int rpad;           // n + q + 1 rounded up to 256: rows of each piece of the split matrix
+                      // [L^-1; (M^-1 X_L)^T; (M^-1 r)^T] of trait j
   const double* P;    // q x q  (X_L^T M^-1 X_L)^-1
   const double* b0;   // q      null-model coefficients
+  const float* mu;    // m      per-SNP centres (multiples of 1/64), or NULL: no centring
   float* B;           // m x t x p
   float* W;           // m x t or NULL
   int* flags;
 };
 constexpr int CHOL_TC_BM = 128;  // SNPs per tile
-// Tensor maps: rows = 2 * rpad (hi piece then lo piece), cols = kpad, BF16, 128-byte swizzle;
-// map256 has 64 x 256 boxes, map128 64 x 128 boxes.  mapG: the 2-bit packed genotypes of the
-// launch, uint8 [m][packed_row_bytes(n)], boxes of 16 bytes x 128 rows, no swizzle.
-void chol_tc_launch(cudaStream_t s, const CUtensorMap& map256, const CUtensorMap& map128,
-                    const CUtensorMap& mapG, const CholTcParams& p, int num_sms);
+// Tensor maps of one trait's split augmented L^-1: rows = 2 * rpad (hi piece then lo piece), cols = kpad,
+// BF16, 128-byte swizzle, 64-column boxes of 256, 192, 128 and 64 rows (m[j]: 256 - 64 j rows).
+struct CholMaps {
+  CUtensorMap m[4];
+};
+// mapG: the 2-bit packed genotypes of the launch, uint8 [m][packed_row_bytes(n)], boxes of
+// 16 bytes x 128 rows, no swizzle.
+void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& mapG,
+                    const CholTcParams& p, int num_sms);
 // uint8 map over packed genotype rows (boxes 16 bytes x 128 rows).
 CUtensorMap make_map_packed(const void* base, int64_t rows, int row_bytes);
 void chol_tc_prepare();

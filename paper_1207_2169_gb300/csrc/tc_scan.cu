@@ -71,18 +71,19 @@ struct TcState {
   int algo = 0, n = 0, q = 0, t = 0;
   int kpad = 0, rpad = 0, num_sms = 0;
   std::vector<void*> allocs;
-  // CHOL, per trait: split L^-1 (hi rows then lo rows) and its two tensor maps
-  std::vector<CUtensorMap> lmap256, lmap128;
+  // CHOL, per trait: split L^-1 (hi rows then lo rows) and its tensor maps
+  std::vector<CholMaps> lmaps;
   __nv_bfloat16* Lsplit = nullptr;  // t x (2 rpad) x kpad
-  float* XLw32 = nullptr;           // t x q x n
-  float* rw32 = nullptr;            // t x n
   const double* P = nullptr;        // t x q x q (owned by the handle)
   const double* b0 = nullptr;       // t x q
   // EIG: split operands, FP32 null-model blocks, per-block scratch and tensor maps
   __nv_bfloat16 *Zsplit = nullptr, *Usplit = nullptr, *dsplit = nullptr, *xsq = nullptr;
   float *P32 = nullptr, *b032 = nullptr, *sbuf = nullptr;
-  float* mu = nullptr;  // per-SNP centres of the current chunk (NULL: no intercept, no centring)
-  int64_t mcap = 0;
+  // per-SNP centres (NULL: no intercept, no centring); EIG: of the current chunk (mcap SNPs),
+  // CHOL: of the current call (grown to the largest call, mu_cap SNPs)
+  float* mu = nullptr;
+  int64_t mcap = 0, mu_cap = 0;
+  bool intercept = false;
   int traits_ac = 0;
   CUtensorMap mapZ, mapU, mapD, mapX;
 };
@@ -116,6 +117,7 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     st->t = a.t;
     st->P = a.P;
     st->b0 = a.b0;
+    st->intercept = a.intercept != 0;
     int dev = 0;
     GW_CUDA(cudaGetDevice(&dev));
     GW_CUDA(cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -123,20 +125,32 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     st->kpad = (int)round_up(n, 64);
     st->rpad = (int)round_up(n, 256);
     if (a.algo == GWAS_ALGO_CHOL) {
+      // Per trait, the split rows of [L^-1; (M^-1 X_L)^T; (M^-1 r)^T]: M^-1 X_L = L^-T (L^-1 X_L)
+      // and M^-1 r = L^-T (L^-1 r) are linear in the genotypes, so the whitening product also
+      // yields a_k and c (Algorithm 3 lines 8-9) in q + 1 extra accumulator columns.
+      st->rpad = (int)round_up(n + q + 1, 256);
       const size_t per = (size_t)2 * st->rpad * st->kpad;
       st->Lsplit = (__nv_bfloat16*)tc_alloc(st, per * t * 2);
       GW_CUDA(cudaMemsetAsync(st->Lsplit, 0, per * t * 2, s));
-      st->XLw32 = (float*)tc_alloc(st, (size_t)t * q * n * 4);
-      st->rw32 = (float*)tc_alloc(st, (size_t)t * n * 4);
-      convert_f64_to_f32(s, a.XLw, st->XLw32, (int64_t)t * q * n);
-      convert_f64_to_f32(s, a.rw, st->rw32, (int64_t)t * n);
+      double* Ut = (double*)tc_alloc(st, (size_t)(q + 1) * n * 8);
       for (int j = 0; j < t; ++j) {
+        const double* Li = a.Linv + (size_t)j * n * n;
         __nv_bfloat16* hi = st->Lsplit + per * j;
         __nv_bfloat16* lo = hi + (size_t)st->rpad * st->kpad;
-        split_bf16(s, a.Linv + (size_t)j * n * n, n, n, n, hi, lo, st->kpad);
-        st->lmap256.push_back(make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad, 256));
-        st->lmap128.push_back(make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad, 128));
+        split_bf16(s, Li, n, n, n, hi, lo, st->kpad);
+        gemm_f64(s, q, n, n, 1.0, a.XLw + (size_t)j * q * n, n, 1, Li, n, 1, 0.0, Ut, n, 1);
+        gemm_f64(s, 1, n, n, 1.0, a.rw + (size_t)j * n, n, 1, Li, n, 1, 0.0, Ut + (size_t)q * n,
+                 n, 1);
+        split_bf16(s, Ut, q + 1, n, n, hi + (size_t)n * st->kpad, lo + (size_t)n * st->kpad,
+                   st->kpad);
+        CholMaps mp;
+        for (int r = 0; r < 4; ++r)
+          mp.m[r] = make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad, 256 - 64 * r);
+        st->lmaps.push_back(mp);
       }
+      GW_CUDA(cudaStreamSynchronize(s));
+      cudaFree(Ut);
+      st->allocs.erase(std::find(st->allocs.begin(), st->allocs.end(), (void*)Ut));
       chol_tc_prepare();
       return st;
     }
@@ -199,6 +213,19 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
   const int rb = packed_row_bytes(st->n);
   if (st->algo == GWAS_ALGO_CHOL) {
     const CUtensorMap mapG = make_map_packed(a.G, a.m, rb);
+    if (st->intercept) {
+      if (st->mu_cap < a.m) {
+        if (st->mu) {
+          GW_CUDA(cudaStreamSynchronize(s));
+          cudaFree(st->mu);
+          st->allocs.erase(std::find(st->allocs.begin(), st->allocs.end(), (void*)st->mu));
+          st->mu = nullptr;
+        }
+        st->mu = (float*)tc_alloc(st, (size_t)a.m * 4);
+        st->mu_cap = a.m;
+      }
+      snp_centres_packed(s, a.G, a.m, st->n, st->mu);
+    }
     for (int j = 0; j < st->t; ++j) {
       CholTcParams p{};
       p.m = a.m;
@@ -208,14 +235,13 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
       p.j = j;
       p.kpad = st->kpad;
       p.rpad = st->rpad;
-      p.XLw = st->XLw32 + (size_t)j * st->q * st->n;
-      p.rw = st->rw32 + (size_t)j * st->n;
       p.P = st->P + (size_t)j * st->q * st->q;
       p.b0 = st->b0 + (size_t)j * st->q;
+      p.mu = st->intercept ? st->mu : nullptr;
       p.B = a.B;
       p.W = a.wald;
       p.flags = a.flags;
-      chol_tc_launch(s, st->lmap256[j], st->lmap128[j], mapG, p, st->num_sms);
+      chol_tc_launch(s, st->lmaps[j], mapG, p, st->num_sms);
     }
     return;
   }

@@ -118,3 +118,16 @@ def test_eig_split_singular_and_streamed(g):
     Bh, Wh, _ = run(g, c, "eig", "split_bf16", XR=XR, device=False, block_snps=256)
     ok = ~np.isnan(Bd)
     assert np.array_equal(np.isnan(Bd), np.isnan(Bh)) and np.array_equal(Bd[ok], Bh[ok])
+
+
+@pytest.mark.parametrize("algo,t", [("chol", 1), ("eig", 9)])
+def test_split_without_intercept(g, algo, t):
+    """X_L of zero-mean covariates and no all-ones column: the tensor-core path does not centre
+    the SNPs (centring is exact only when the intercept is in the model)."""
+    c = synth.small_problem(23, n=300, q=3, m=400, t=t)
+    c.XL = c.XL.copy()
+    c.XL[:, 0] = np.random.default_rng(5).standard_normal(c.n)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
+    B, W, _ = run(g, c, algo, "split_bf16")
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < TOL and ew < TOL, (eb, ew)
