@@ -161,11 +161,14 @@ def executed_flops(s, m):
     kpad = -(-n // 64) * 64
     rpad = -(-n // 256) * 256
     if s["algo"] == "chol":
+        # rows of L^-1 plus the q + 1 rows of M^-1 [X_L | r]; per block the live rows (16-row
+        # MMA granularity), and on the diagonal only the rows a K step meets
         macs = 0
-        for nb in range(rpad // 256):
+        for nb in range(-(-(n + q + 1) // 256)):
+            ncols = min(256, -(-(n + q + 1 - 256 * nb) // 16) * 16)
             nk = min(4 * (nb + 1), kpad // 64)
             for ks in range(nk):
-                macs += 64 * (256 - 64 * max(0, ks - 4 * nb))  # rows on/below the diagonal
+                macs += 64 * (ncols - 64 * max(0, ks - 4 * nb))
         return 2 * 2 * macs * m * t
     rot = 2 * 2 * rpad * kpad * m
     sq = 3 * 2 * kpad * t * m

@@ -58,7 +58,10 @@ def test_work_accounting():
     s = dict(synth.WORKLOADS[1])
     n, q = s["n"], s["q"]
     assert bench.algorithmic_flops(s, 10) == 10 * (n * (n + 1) + 2 * n * (q + 2))
-    # executed: 2 pieces x 2 flops x MACs of the 256/128-granular triangle over kpad = 1024
-    macs = sum(64 * (128 if ks >= 4 * nb + 2 else 256) for nb in range(4) for ks in range(min(4 * (nb + 1), 16)))
+    # executed: 2 pieces x 2 flops x MACs: 64-column K steps over kpad = 1024; blocks of 256 rows
+    # of the augmented L^-1 (1000 + q + 1 = 1004 rows: the last block has 240 live rows); on a
+    # block's diagonal, step 4 nb + j meets rows 64 j onwards
+    live = [256, 256, 256, 240]
+    macs = sum(64 * (live[nb] - 64 * max(0, ks - 4 * nb)) for nb in range(4) for ks in range(4 * (nb + 1)))
     assert bench.executed_flops(s, 1) == 4 * macs
     assert bench.executed_flops(s, 1) > 2 * bench.algorithmic_flops(s, 1)
