@@ -20,9 +20,9 @@
 //
 // Warp roles (448 threads):
 //   0-3  epilogue: one SNP per thread (TMEM lane 32*warp + lane)
-//   4    TMA producers: lane 0 the L^-1 tiles, lane 1 the 2-bit packed genotype slices
-//   5    MMA issuer (one elected lane); owns the 512 TMEM columns (two 256-column accumulators)
-//   6-13 genotype converters: packed slices (shared memory) -> BF16 tiles in the
+//   11   TMA producers: lane 0 the L^-1 tiles, lane 1 the 2-bit packed genotype slices
+//   7    MMA issuer (one elected lane); owns the 512 TMEM columns (two 256-column accumulators)
+//   4-6, 8-10, 12-13  genotype converters: packed slices (shared memory) -> BF16 tiles in the
 //        128-byte-swizzled K-major layout
 #include "tc_kernels.cuh"
 #include "tc_ptx.cuh"
@@ -43,7 +43,17 @@ constexpr int QMAX = 7;
 constexpr int PR = 8;                   // packed-genotype slice ring
 constexpr int PK_BYTES = BM * 16;       // 64 genotypes of 128 SNPs, 2-bit codes: 2 KB
 constexpr int NCONV = 8;                // genotype converter warps: 2 threads per row
+constexpr int CL = CHOL_TC_CLUSTER;     // CTAs per cluster; each fetches 1/CL of every L^-1 tile
+constexpr uint16_t CL_MASK = (1u << CL) - 1;
 constexpr int NUM_THREADS = 192 + 32 * NCONV;
+// Warp roles.  A warp issues on SMSP (warp % 4); the single-thread MMA issuer and TMA producers
+// share SMSP 3 with only an epilogue warp, so converter bursts never delay their issue.
+constexpr int MMA_WARP = 7;
+constexpr int TMA_WARP = 11;
+// converter warps 4, 5, 6, 8, 9, 10, 12, 13 -> 0 .. 7
+__device__ __forceinline__ int conv_index(int warp) {
+  return warp < MMA_WARP ? warp - 4 : warp < TMA_WARP ? warp - 5 : warp - 6;
+}
 constexpr int TMEM_COLS = 512;
 constexpr uint64_t WAIT_NS = 4000000000ull;
 
@@ -92,7 +102,7 @@ __device__ __forceinline__ void advance(Step& s, int nblocks, int kpad) {
 
 // QM: compile-time bound on q (3 or 7), so the epilogue's per-column arrays stay in registers.
 template <int QM>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     chol_tc_kernel(const __grid_constant__ CholMaps lmaps, const __grid_constant__ CUtensorMap mapG,
                    const CholTcParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -102,8 +112,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint8_t* sP = sB + SB * B_BYTES;
   Bars* bars = (Bars*)(sP + PR * PK_BYTES);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  // The CTAs of a cluster walk the same (block, k-step) sequence in lockstep, each on its own
+  // SNP tile; past the last tile a CTA runs on zero rows (TMA fills them) and writes nothing.
   const int64_t ntiles = (p.m + BM - 1) / BM;
+  const int64_t tiles_run = (ntiles + CL - 1) / CL * CL;
   const int nblocks = p.rpad / BN;
+  const uint32_t rank = CL > 1 ? cluster_ctarank() : 0;
   int* tflag = p.flags + FLAG_TIMEOUT;
 
   if (threadIdx.x == 0) {
@@ -113,7 +127,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     for (int i = 0; i < SB; ++i) {
       mbar_init(&bars->b_full[i], 1);
-      mbar_init(&bars->b_empty[i], 1);
+      mbar_init(&bars->b_empty[i], CL);  // released by the MMA issuer of every CTA
     }
     for (int i = 0; i < PR; ++i) {
       mbar_init(&bars->pk_full[i], 1);
@@ -127,45 +141,58 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     bars->abort = 0;
     fence_mbar_init();
   }
-  if (warp == 5) {
+  if (warp == MMA_WARP) {
     tmem_alloc(&bars->tmem_base, TMEM_COLS);
     tmem_relinquish();
   }
-  if (warp == 4 && lane == 0) {
+  if (warp == TMA_WARP && lane == 0) {
     for (int j = 0; j < 4; ++j) prefetch_tensormap(&lmaps.m[j]);
     prefetch_tensormap(&mapG);
   }
   tc_fence_before();
-  __syncthreads();
+  __syncwarp();
+  if (CL > 1)
+    cluster_sync();  // the peers' barriers are initialised before any multicast reaches them
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
   volatile int* abort = &bars->abort;
 
-  if (warp == 4) {
+  if (warp == TMA_WARP) {
     // ------------------------------------------------------------ L^-1 tiles via TMA
     if (lane == 0) {
       int bs = 0;
       uint32_t bph = 0;
-      for (Step st{blockIdx.x, 0, 0}; st.tile < ntiles; advance(st, nblocks, p.kpad)) {
+      bool ok = true;
+      for (Step st{blockIdx.x, 0, 0}; st.tile < tiles_run && ok; advance(st, nblocks, p.kpad)) {
         const int j = diag_skip(st.nb, st.ks);  // rows 64 j .. 255 of the block
-        bool ok = true;
+        const int h = (BN - 64 * j) / CL;       // this CTA's share of them
         for (int piece = 0; piece < 2; ++piece) {
+          // the slot is free once every CTA of the cluster has consumed it
           ok = mbar_wait(&bars->b_empty[bs], bph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
-          const int y = piece * p.rpad + st.nb * BN + 64 * j;
+          const int y = piece * p.rpad + st.nb * BN + 64 * j + (int)rank * h;
+          uint8_t* dst = sB + bs * B_BYTES + (B_BYTES / 4) * j + rank * h * 128;
           mbar_arrive_expect_tx(&bars->b_full[bs], (B_BYTES / 4) * (4 - j));
-          tma_load_2d(sB + bs * B_BYTES + (B_BYTES / 4) * j, &lmaps.m[j], &bars->b_full[bs],
-                      st.ks * BK, y);
+          if (CL > 1)
+            tma_load_2d_mc(dst, &lmaps.m[j], &bars->b_full[bs], st.ks * BK, y, CL_MASK);
+          else
+            tma_load_2d(dst, &lmaps.m[j], &bars->b_full[bs], st.ks * BK, y);
           if (++bs == SB) { bs = 0; bph ^= 1; }
         }
-        if (!ok) break;
+      }
+      // the peers' last releases of each slot land here before the CTA may exit
+      for (int i = 0; i < SB && ok; ++i) {
+        ok = mbar_wait(&bars->b_empty[bs], bph ^ 1, abort, tflag, WAIT_NS);
+        if (++bs == SB) { bs = 0; bph ^= 1; }
       }
     } else if (lane == 1) {
       // packed genotype slices (64 genotypes x 128 SNPs, 2 KB) via TMA, in the K-step order the
       // converters consume them; rows past m read as zero
       int ps = 0;
       uint32_t pph = 0;
-      for (Step st{blockIdx.x, 0, 0}; st.tile < ntiles; advance(st, nblocks, p.kpad)) {
+      for (Step st{blockIdx.x, 0, 0}; st.tile < tiles_run; advance(st, nblocks, p.kpad)) {
         if (!mbar_wait(&bars->pk_empty[ps], pph ^ 1, abort, tflag, WAIT_NS)) break;
         mbar_arrive_expect_tx(&bars->pk_full[ps], PK_BYTES);
         tma_load_2d(sP + ps * PK_BYTES, &mapG, &bars->pk_full[ps], st.ks * 16,
@@ -173,13 +200,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (++ps == PR) { ps = 0; pph ^= 1; }
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       int as = 0, bs = 0, buf = 0;
       uint32_t aph = 0, bph = 0, accph = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int64_t tile = blockIdx.x; tile < tiles_run && ok; tile += gridDim.x) {
         for (int nb = 0; nb < nblocks && ok; ++nb) {
           ok = mbar_wait(&bars->acc_empty[buf], accph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
@@ -201,7 +228,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk)
                 mma_bf16(dt + 64 * j, ad + 2 * kk, bd + 2 * kk, idesc, (ks | piece | kk) != 0);
-              mma_commit(&bars->b_empty[bs]);
+              if (CL > 1)
+                mma_commit_mc(&bars->b_empty[bs], CL_MASK);
+              else
+                mma_commit(&bars->b_empty[bs]);
               if (++bs == SB) { bs = 0; bph ^= 1; }
             }
             mma_commit(&bars->a_empty[as]);
@@ -214,11 +244,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mma_commit(&bars->done);  // TMEM is released only after every issued MMA retired
       mbar_wait(&bars->done, 0, abort, tflag, WAIT_NS);
     }
-  } else if (warp >= 6) {
+  } else if (warp >= 4) {
     // ------------------------------------------------------------ genotype converters
     // Thread ct converts half hh of row r of each K step: packed bytes 8 hh .. 8 hh + 7 (32
     // genotypes) into BF16 chunks 4 hh .. 4 hh + 3 of the row's swizzled 128-byte line.
-    const int ct = threadIdx.x - 192;
+    const int ct = conv_index(warp) * 32 + lane;
     const int r = ct >> 1, hh = ct & 1;
     const uint32_t line = (r >> 3) * 1024 + (r & 7) * 128;
     int per_tile = 0;
@@ -226,7 +256,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int as = 0, ps = 0;
     uint32_t aph = 0, pph = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (int64_t tile = blockIdx.x; tile < tiles_run && ok; tile += gridDim.x) {
       // byte tables of this row: g - mu (mu = 0 without centring)
       uint32_t lutlo = GENO_LO, luthi = GENO_HI;
       if (p.mu) {
@@ -268,7 +298,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int buf = 0;
     uint32_t accph = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int64_t tile = blockIdx.x; tile < tiles_run; tile += gridDim.x) {
       double S = 0.0;
       float A[QM], C = 0.f;
 #pragma unroll
@@ -353,8 +383,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   }
   tc_fence_before();
-  __syncthreads();
-  if (warp == 5) {
+  __syncwarp();
+  if (CL > 1)
+    cluster_sync();  // no CTA leaves while a peer may still write its shared memory
+  else
+    __syncthreads();
+  if (warp == MMA_WARP) {
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
@@ -362,19 +396,50 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 }  // namespace
 
+namespace {
+int g_max_ctas[2] = {0, 0};  // co-resident CTAs of each instantiation (whole clusters)
+
+template <int QM>
+int max_resident_ctas() {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  GW_CUDA(cudaOccupancyMaxActiveClusters(&clusters, chol_tc_kernel<QM>, &cfg));
+  GW_REQUIRE(clusters >= 1, GWAS_ERR_UNSUPPORTED, "no cluster of %d CTAs fits on this device", CL);
+  return clusters * CL;
+}
+}  // namespace
+
 void chol_tc_prepare() {
   GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)SMEM_BYTES));
   GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)SMEM_BYTES));
+  if (!g_max_ctas[0]) g_max_ctas[0] = max_resident_ctas<3>();
+  if (!g_max_ctas[1]) g_max_ctas[1] = max_resident_ctas<QMAX>();
 }
+
+int chol_tc_resident_ctas(int q) { return g_max_ctas[q <= 3 ? 0 : 1]; }
 
 void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& mapG,
                     const CholTcParams& p, int num_sms) {
   if (p.m <= 0) return;
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", p.q, QMAX);
+  // persistent: whole clusters, no more than fit at once (and no more than the tiles need)
   const int64_t tiles = (p.m + BM - 1) / BM;
-  const unsigned grid = (unsigned)(tiles < num_sms ? tiles : num_sms);
+  int64_t cap = g_max_ctas[p.q <= 3 ? 0 : 1];
+  if (cap <= 0 || cap > num_sms) cap = num_sms / CL * CL;
+  const int64_t want = (tiles + CL - 1) / CL * CL;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
   if (p.q <= 3)
     chol_tc_kernel<3><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
   else

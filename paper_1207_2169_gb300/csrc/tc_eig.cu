@@ -13,10 +13,10 @@
 // A persistent CTA walks (128-SNP tile, 256-column block) work items, eight SNP tiles per
 // column block at a time so that both operands are reused from L2.
 //
-// Warp roles (448 threads): 0-3 epilogue (one SNP per TMEM lane), 4 TMA producers (lane 0: the
-// B operand and SQ's A operand; lane 1: 2-bit packed genotype slices for ROT and AC), 5 MMA
-// issuer and TMEM owner (two 256-column FP32 accumulators), 6-13 genotype converters (packed
-// slices in shared memory -> centred BF16 tiles; ROT and AC).
+// Warp roles (448 threads): 0-3 epilogue (one SNP per TMEM lane), 11 TMA producers (lane 0: the
+// B operand and SQ's A operand; lane 1: 2-bit packed genotype slices for ROT and AC), 7 MMA
+// issuer and TMEM owner (two 256-column FP32 accumulators), 4-6, 8-10, 12-13 genotype converters
+// (packed slices in shared memory -> centred BF16 tiles; ROT and AC).
 #include "tc_kernels.cuh"
 #include "tc_ptx.cuh"
 
@@ -33,6 +33,14 @@ constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int NCONV = 8;                 // genotype converter warps (ROT, AC): 2 threads per row
 constexpr int NUM_THREADS = 192 + 32 * NCONV;
+// Warp roles.  A warp issues on SMSP (warp % 4); the single-thread MMA issuer and TMA producers
+// share SMSP 3 with only an epilogue warp, so converter bursts never delay their issue.
+constexpr int MMA_WARP = 7;
+constexpr int TMA_WARP = 11;
+// converter warps 4, 5, 6, 8, 9, 10, 12, 13 -> 0 .. 7
+__device__ __forceinline__ int conv_index(int warp) {
+  return warp < MMA_WARP ? warp - 4 : warp < TMA_WARP ? warp - 5 : warp - 6;
+}
 constexpr int PR = 8;                    // packed-genotype slice ring
 constexpr int PK_BYTES = BM * 16;        // 64 genotypes of 128 SNPs, 2-bit codes: 2 KB
 constexpr int TMEM_COLS = 512;
@@ -143,11 +151,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     bars->abort = 0;
     fence_mbar_init();
   }
-  if (warp == 5) {
+  if (warp == MMA_WARP) {
     tmem_alloc(&bars->tmem_base, TMEM_COLS);
     tmem_relinquish();
   }
-  if (warp == 4 && lane == 0) {
+  if (warp == TMA_WARP && lane == 0) {
     if (!CONV) prefetch_tensormap(&mapA);
     if (CONV) prefetch_tensormap(&mapG);
     prefetch_tensormap(&mapB);
@@ -158,7 +166,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const uint32_t tmem = bars->tmem_base;
   volatile int* abort = &bars->abort;
 
-  if (warp == 4) {
+  if (warp == TMA_WARP) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       int as = 0, bs = 0;
@@ -208,7 +216,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       int as = 0, bs = 0, buf = 0;
@@ -280,14 +288,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mma_commit(&bars->done);
       mbar_wait(&bars->done, 0, abort, tflag, WAIT_NS);
     }
-  } else if (warp >= 6) {
+  } else if (warp >= 4) {
     // ------------------------------------------------------------ genotype converters
     // Thread ct converts half hh of row r of each K step: packed bytes 8 hh .. 8 hh + 7 (32
     // genotypes) into BF16 chunks 4 hh .. 4 hh + 3 of the row's swizzled 128-byte line, through
     // the row's byte tables of g - mu (mu = 0 without centring).  Codes past n are 0 and map to
     // -mu; the B operand is zero there, so they add nothing.
     if (CONV) {
-      const int ct = threadIdx.x - 192;
+      const int ct = conv_index(warp) * 32 + lane;
       const int r = ct >> 1, hh = ct & 1;
       const uint32_t line = (r >> 3) * 1024 + (r & 7) * 128;
       const int64_t mine = blockIdx.x < nwork ? (nwork - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -537,7 +545,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) {
+  if (warp == MMA_WARP) {
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }

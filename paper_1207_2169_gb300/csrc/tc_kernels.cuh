@@ -24,8 +24,12 @@ struct CholTcParams {
   int* flags;
 };
 constexpr int CHOL_TC_BM = 128;  // SNPs per tile
-// Tensor maps of one trait's split augmented L^-1: rows = 2 * rpad (hi piece then lo piece), cols = kpad,
-// BF16, 128-byte swizzle, 64-column boxes of 256, 192, 128 and 64 rows (m[j]: 256 - 64 j rows).
+// CTAs per cluster of the CHOL kernel: they share every L^-1 tile, each fetching its part and
+// multicasting it to all.
+constexpr int CHOL_TC_CLUSTER = 2;
+// Tensor maps of one trait's split augmented L^-1: rows = 2 * rpad (hi piece then lo piece),
+// cols = kpad, BF16, 128-byte swizzle, 64-column boxes of (256 - 64 j) / CHOL_TC_CLUSTER rows
+// (m[j]: one CTA's part of the rows 64 j .. 255 of a block).
 struct CholMaps {
   CUtensorMap m[4];
 };
@@ -36,6 +40,8 @@ void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& ma
 // uint8 map over packed genotype rows (boxes 16 bytes x 128 rows).
 CUtensorMap make_map_packed(const void* base, int64_t rows, int row_bytes);
 void chol_tc_prepare();
+// CTAs of the CHOL kernel that fit on the device at once (after chol_tc_prepare).
+int chol_tc_resident_ctas(int q);
 
 // ------------------------------------------------------------------------------------------
 // EIG stages (tc_eig.cu): 0 = ROT (Xsq = (Z^T X_R)^2 split), 1 = SQ (s_ij), 2 = AC (a, c, Schur)

@@ -145,7 +145,8 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
                    st->kpad);
         CholMaps mp;
         for (int r = 0; r < 4; ++r)
-          mp.m[r] = make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad, 256 - 64 * r);
+          mp.m[r] = make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad,
+                                  (256 - 64 * r) / CHOL_TC_CLUSTER);
         st->lmaps.push_back(mp);
       }
       GW_CUDA(cudaStreamSynchronize(s));
