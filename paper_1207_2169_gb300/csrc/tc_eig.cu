@@ -347,6 +347,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     bool ok = true;
     // AC is compiled for one q, so the Schur loops below are fully unrolled
     const int q = EPI == EPI_AC ? QQ : p.q, q1 = q + 1;
+    // AC constants of trait block nb, flattened: per trait P_j (q x q) then b0_j (q); 0 past t
+    constexpr int PF_REGS = (eig_ac_traits(QQ > 0 ? QQ : 1) * (QQ * QQ + QQ) + 127) / 128;
+    static_assert(PF_REGS * 128 <= PB_FLOATS, "AC constants exceed their shared-memory area");
+    float pf[EPI == EPI_AC ? PF_REGS : 1];
+    bool have_pf = false;
+    auto const_at = [&](int nbk, int e) -> float {
+      const int per = q * q + q;
+      const int jl = e / per, u = e - jl * per, j = nbk * p.traits_per_blk + jl;
+      if (jl >= p.traits_per_blk || j >= p.t) return 0.f;
+      return u < q * q ? __ldg(&p.P[(int64_t)j * q * q + u]) : __ldg(&p.b0[(int64_t)j * q + u - q * q]);
+    };
     for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
       int64_t tile;
       int nb;
@@ -354,17 +365,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int64_t snp = tile * BM + 32 * warp + lane;
       const float mu_snp = (p.mu && snp < p.m) ? p.mu[snp] : 0.f;
       if (EPI == EPI_AC) {
-        // P_j and b0_j of this block's traits, FP32, into shared memory
+        // P_j and b0_j of this block's traits, FP32, into shared memory: from the registers
+        // loaded during the previous work item, then the next item's are loaded (their global
+        // latency hides behind this item)
         named_bar(1, 128);
-        const int j0 = nb * p.traits_per_blk;
-        const int per = q * q + q;
-        for (int e = threadIdx.x; e < p.traits_per_blk * per; e += 128) {
-          const int jl = e / per, u = e % per, j = j0 + jl;
-          float v = 0.f;
-          if (j < p.t) v = u < q * q ? p.P[(int64_t)j * q * q + u] : p.b0[(int64_t)j * q + u - q * q];
-          cst[e] = v;
+        if (have_pf) {
+#pragma unroll
+          for (int i = 0; i < PF_REGS; ++i) cst[threadIdx.x + 128 * i] = pf[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < PF_REGS; ++i) cst[threadIdx.x + 128 * i] = const_at(nb, threadIdx.x + 128 * i);
         }
         named_bar(1, 128);
+        const int64_t wn = w + gridDim.x;
+        have_pf = wn < nwork;
+        if (have_pf) {
+          int64_t tn;
+          int nbn;
+          work_coords(wn, mtiles, p.nblk, tn, nbn);
+#pragma unroll
+          for (int i = 0; i < PF_REGS; ++i) pf[i] = const_at(nbn, threadIdx.x + 128 * i);
+        }
       }
       if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full[buf], accph, abort, tflag, WAIT_NS));
       if (ok) {
@@ -449,6 +470,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
             for (int h = 0; h < QP / 4; ++h)
               tmem_wait32(*reinterpret_cast<uint32_t(*)[32]>(&r[4 * h][0]));
+            if (j8 + 8 >= T) {
+              // the block's last columns are in registers: hand the accumulator back to the
+              // MMA issuer before solving them
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
+            }
             const int nval = jend - (j0 + j8) < 8 ? jend - (j0 + j8) : 8;  // valid traits
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -536,9 +564,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
           if (nsing) atomicAdd(&p.flags[FLAG_SINGULAR], nsing);
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
+        if (EPI != EPI_AC) {  // AC hands the accumulator back inside its batch loop
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
+        }
       }
       if (++buf == 2) { buf = 0; accph ^= 1; }
     }

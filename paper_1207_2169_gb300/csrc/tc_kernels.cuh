@@ -64,6 +64,13 @@ struct EigTcParams {
   float* W;                // AC: m x t or NULL
   int* flags;
 };
+// Traits per AC column block: T (q+1) accumulator columns, with the last trait's load of
+// QP = (q+1 rounded up to 4 or 8) columns still inside the 256-column block.
+__host__ __device__ constexpr int eig_ac_traits(int q) {
+  return 256 / (q + 1) < (256 - (q + 1 <= 4 ? 4 : 8)) / (q + 1) + 1
+             ? 256 / (q + 1)
+             : (256 - (q + 1 <= 4 ? 4 : 8)) / (q + 1) + 1;
+}
 // mapA: the Xsq planes (SQ only; ignored otherwise).  mapB: Z^T split (ROT), d split (SQ),
 // U split (AC).  All BF16, 64-column boxes, 128-byte swizzle; mapA has 128-row boxes and mapB
 // 256-row boxes.  mapG: packed genotypes as for CHOL (ROT, AC; ignored by SQ).

@@ -180,9 +180,7 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     cudaFree(Uall);
     st->allocs.erase(std::find(st->allocs.begin(), st->allocs.end(), (void*)Uall));
     // traits per AC column block: T (q+1) columns, the last trait's load of QP columns in range
-    const int qp = q1 <= 4 ? 4 : 8;
-    const int ta = 256 / q1, tb = (256 - qp) / q1 + 1;
-    st->traits_ac = ta < tb ? ta : tb;
+    st->traits_ac = eig_ac_traits(q);
     // SNPs per internal chunk: at least the streaming block, up to 32 Ki while the s scratch
     // (t x chunk FP32) stays within 4 GB, so that many-trait scans keep every SM busy
     int64_t cap = (int64_t)(4e9 / (4.0 * t));
