@@ -59,9 +59,10 @@ constexpr uint64_t WAIT_NS = 4000000000ull;
 
 struct __align__(8) Bars {
   uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], pk_full[PR], pk_empty[PR];
-  uint64_t acc_full[2], acc_empty[2], done;
+  uint64_t acc_full[2], acc_empty[2], mu_full[2], mu_empty[2], done;
   uint32_t tmem_base;
   int abort;
+  float mu[2][BM];  // SNP centres of the tiles in flight (epilogue -> converters)
 };
 
 constexpr size_t SMEM_BYTES = 1024 + SA * A_BYTES + SB * B_BYTES + PR * PK_BYTES + sizeof(Bars);
@@ -136,6 +137,10 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bars->acc_full[i], 1);
       mbar_init(&bars->acc_empty[i], 4);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bars->mu_full[i], 128);            // every epilogue thread stores its SNP's centre
+      mbar_init(&bars->mu_empty[i], 32 * NCONV);    // every converter thread has read its row's
     }
     mbar_init(&bars->done, 1);
     bars->abort = 0;
@@ -256,12 +261,17 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     int as = 0, ps = 0;
     uint32_t aph = 0, pph = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < tiles_run && ok; tile += gridDim.x) {
+    int ti = 0;  // this CTA's tile counter (selects the centre buffer)
+    for (int64_t tile = blockIdx.x; tile < tiles_run && ok; tile += gridDim.x, ++ti) {
       // byte tables of this row: g - mu (mu = 0 without centring)
       uint32_t lutlo = GENO_LO, luthi = GENO_HI;
-      if (p.mu) {
-        const int64_t snp = tile * BM + r;
-        centred_lut(snp < p.m ? p.mu[snp] : 0.f, lutlo, luthi);
+      if (p.centre) {
+        const int mb = ti & 1;
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait(&bars->mu_full[mb], (ti >> 1) & 1, abort, tflag, WAIT_NS));
+        if (!ok) break;
+        centred_lut(bars->mu[mb][r], lutlo, luthi);
+        mbar_arrive(&bars->mu_empty[mb]);
       }
       for (int g = 0; g < per_tile; ++g) {
         // warp-uniform exits: every lane leaves together if any wait gave up
@@ -298,7 +308,45 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     int buf = 0;
     uint32_t accph = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < tiles_run; tile += gridDim.x) {
+    // With centring, this thread also finds the centre of its SNP one tile ahead (the
+    // converters build the tile's byte tables from it): the nearest multiple of 1/64 to the
+    // mean genotype, clamped to [0, 2] so that g - mu stays exact in BF16.  Rows past m get 0.
+    auto centre_of = [&](int64_t t) -> float {
+      const int64_t snp = t * BM + 32 * warp + lane;
+      if (snp >= p.m) return 0.f;
+      const uint4* row = reinterpret_cast<const uint4*>(p.G + snp * p.row_bytes);
+      int sum = 0;
+      for (int i = 0; i < p.row_bytes / 16; ++i) {
+        const uint4 v = __ldg(row + i);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sum += __popc(w[k] & 0x55555555u) + 2 * __popc(w[k] & 0xAAAAAAAAu);
+      }
+      const float c = rintf(64.f * (float)sum / (float)n) / 64.f;
+      return fminf(fmaxf(c, 0.f), 2.f);
+    };
+    auto publish_centre = [&](int ti, float c) -> bool {
+      const int mb = ti & 1;
+      // the converters have read this buffer's previous tile (two tiles back)
+      if (!__all_sync(0xffffffffu, mbar_wait(&bars->mu_empty[mb], ((ti >> 1) & 1) ^ 1, abort,
+                                             tflag, WAIT_NS)))
+        return false;
+      bars->mu[mb][32 * warp + lane] = c;
+      mbar_arrive(&bars->mu_full[mb]);
+      return true;
+    };
+    float mu_cur = 0.f;
+    if (p.centre && blockIdx.x < tiles_run) {
+      mu_cur = centre_of(blockIdx.x);
+      ok = publish_centre(0, mu_cur);
+    }
+    int ti = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles_run; tile += gridDim.x, ++ti) {
+      float mu_next = 0.f;
+      if (p.centre && ok && tile + gridDim.x < tiles_run) {
+        mu_next = centre_of(tile + gridDim.x);
+        ok = publish_centre(ti + 1, mu_next);
+      }
       double S = 0.0;
       float A[QM], C = 0.f;
 #pragma unroll
@@ -368,7 +416,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
           for (int k = 0; k < QM; ++k) bl[k] = k < q ? __ldg(&p.b0[k]) - v[k] * bs : 0.0;
           // centred SNP x - mu: the intercept (column 0 of X_L) absorbs mu * b_snp
-          if (p.mu) bl[0] -= (double)p.mu[snp] * bs;
+          if (p.centre) bl[0] -= (double)mu_cur * bs;
 #pragma unroll
           for (int k = 0; k < QM; ++k)
             if (k < q) Bo[k] = (float)bl[k];
@@ -380,6 +428,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
           atomicAdd(&p.flags[FLAG_SINGULAR], 1);
         }
       }
+      mu_cur = mu_next;
     }
   }
   tc_fence_before();

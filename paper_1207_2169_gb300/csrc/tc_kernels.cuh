@@ -18,7 +18,9 @@ struct CholTcParams {
                       // [L^-1; (M^-1 X_L)^T; (M^-1 r)^T] of trait j
   const double* P;    // q x q  (X_L^T M^-1 X_L)^-1
   const double* b0;   // q      null-model coefficients
-  const float* mu;    // m      per-SNP centres (multiples of 1/64), or NULL: no centring
+  int centre;         // nonzero: centre each SNP by the multiple of 1/64 nearest its mean
+  const uint8_t* G;   // the launch's packed genotype rows (also read through mapG)
+  int row_bytes;      // packed_row_bytes(n)
   float* B;           // m x t x p
   float* W;           // m x t or NULL
   int* flags;

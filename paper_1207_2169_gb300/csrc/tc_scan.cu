@@ -79,10 +79,9 @@ struct TcState {
   // EIG: split operands, FP32 null-model blocks, per-block scratch and tensor maps
   __nv_bfloat16 *Zsplit = nullptr, *Usplit = nullptr, *dsplit = nullptr, *xsq = nullptr;
   float *P32 = nullptr, *b032 = nullptr, *sbuf = nullptr;
-  // per-SNP centres (NULL: no intercept, no centring); EIG: of the current chunk (mcap SNPs),
-  // CHOL: of the current call (grown to the largest call, mu_cap SNPs)
+  // EIG: per-SNP centres of the current chunk (NULL: no intercept, no centring)
   float* mu = nullptr;
-  int64_t mcap = 0, mu_cap = 0;
+  int64_t mcap = 0;
   bool intercept = false;
   int traits_ac = 0;
   CUtensorMap mapZ, mapU, mapD, mapX;
@@ -212,19 +211,6 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
   const int rb = packed_row_bytes(st->n);
   if (st->algo == GWAS_ALGO_CHOL) {
     const CUtensorMap mapG = make_map_packed(a.G, a.m, rb);
-    if (st->intercept) {
-      if (st->mu_cap < a.m) {
-        if (st->mu) {
-          GW_CUDA(cudaStreamSynchronize(s));
-          cudaFree(st->mu);
-          st->allocs.erase(std::find(st->allocs.begin(), st->allocs.end(), (void*)st->mu));
-          st->mu = nullptr;
-        }
-        st->mu = (float*)tc_alloc(st, (size_t)a.m * 4);
-        st->mu_cap = a.m;
-      }
-      snp_centres_packed(s, a.G, a.m, st->n, st->mu);
-    }
     for (int j = 0; j < st->t; ++j) {
       CholTcParams p{};
       p.m = a.m;
@@ -236,7 +222,9 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
       p.rpad = st->rpad;
       p.P = st->P + (size_t)j * st->q * st->q;
       p.b0 = st->b0 + (size_t)j * st->q;
-      p.mu = st->intercept ? st->mu : nullptr;
+      p.centre = st->intercept ? 1 : 0;
+      p.G = a.G;
+      p.row_bytes = rb;
       p.B = a.B;
       p.W = a.wald;
       p.flags = a.flags;
