@@ -443,6 +443,113 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, ws, rank, local):
+    """Workload 4: 16 uneven cohorts scanned by one gwas_scan_batch (a CUDA graph whose launch
+    plan the library picked by timing), against the same scans issued cohort by cohort."""
+    import torch
+    import paper_1207_2169_gb300 as g
+    from oracle import gls
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    spec = synth.BATCH
+    m = spec["m"] if args.m is None else args.m
+    shapes = synth.batch_shapes()
+    cohorts = [synth.batch_cohort(i, n, q, t) for i, (n, q, t) in enumerate(shapes)]
+    t0 = time.perf_counter()
+    opt = g.gwas_default_options(precision="split_bf16", device=local)
+    b = g.gwas_setup_batch([(c.Phi, c.XL, c.Y, c.h2, c.s2) for c in cohorts], options=opt)
+    setup_s = time.perf_counter() - t0
+    try:
+        blocks, samples = [], []
+        rs = np.random.default_rng(4)
+        for i, ((n, q, t), c) in enumerate(zip(shapes, cohorts)):
+            X = synth.device_genotypes(i, n, m)
+            snps = np.sort(rs.choice(m, size=4, replace=False))
+            samples.append((snps, int(rs.integers(0, t)), X[torch.from_numpy(snps).cuda()].cpu().numpy()))
+            G = g.gwas_pack_genotypes(X)
+            del X
+            B = torch.empty((m, t, q + 1), dtype=torch.float32, device="cuda")
+            W = torch.empty((m, t), dtype=torch.float32, device="cuda")
+            blocks.append((G, B, W))
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        g.gwas_scan_batch(b, blocks, stream=stream.cuda_stream)  # picks the launch plan
+        plan, plan_ms = g.gwas_batch_plan(b)
+        for _ in range(args.warmup):
+            g.gwas_scan_batch(b, blocks, stream=stream.cuda_stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            _barrier(ws)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                g.gwas_scan_batch(b, blocks, stream=stream.cuda_stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            _barrier(ws)
+        ms = _max_over_ranks(ev0.elapsed_time(ev1) / args.steps, ws)
+        # the same work as separate per-cohort calls (each launch with every SM, one after another)
+        handles = [g.gwas_batch_handle(b, i) for i in range(len(cohorts))]
+        for _ in range(2):
+            for h, (G, B, W) in zip(handles, blocks):
+                g.gwas_scan_packed(h, G, B, W, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            for h, (G, B, W) in zip(handles, blocks):
+                g.gwas_scan_packed(h, G, B, W, stream=stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_seq = _max_over_ranks(ev0.elapsed_time(ev1) / args.steps, ws)
+        g.gwas_scan_batch(b, blocks, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        eb = ew = 0.0
+        for (snps, j, Xs), c, (G, B, W) in zip(samples, cohorts, blocks):
+            Bd = B[torch.from_numpy(snps).cuda(), j].cpu().numpy().astype(np.float64)
+            Wd = W[torch.from_numpy(snps).cuda(), j].cpu().numpy().astype(np.float64)
+            pairs = np.c_[np.arange(len(snps)), np.full(len(snps), j)]
+            Bref, Wref, Vref = gls.gls_pairs(c.Phi, c.XL, Xs, c.Y, c.h2, c.s2, pairs)
+            eb = max(eb, float(np.nanmax(gls.rel_err_b(Bd, Bref, Vref))))
+            ew = max(ew, float(np.nanmax(gls.rel_err_wald(Wd, Wref))))
+    finally:
+        g.gwas_destroy_batch(b)
+    if rank != 0:
+        return
+    pairs = m * sum(t for _, _, t in shapes)
+    flops = 0.0
+    for n, q, t in shapes:
+        kp, rp = -(-n // 64) * 64, -(-n // 256) * 256
+        flops += m * (4.0 * rp * kp + t * kp * (6.0 + 4.0 * (q + 1)))
+    peaks, kind = _peaks()
+    exe = flops / (ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": pairs * ws / (ms * 1e-3), "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2->f32", "data": "synthetic",
+        "config": {"workload": spec["name"], "cohorts": [dict(n=n, p=q + 1, t=t) for n, q, t in shapes],
+                   "m": m, "genotypes": "packed", "algo": "eig (t > 1)",
+                   "l2": "inputs (packed genotypes, %.2f GB) exceed the 129 MB L2; no flush" %
+                         (m * sum(-(-n // 64) * 16 for n, _, _ in shapes) / 1e9)},
+        "gpu_launches": args.steps * sum(launches_per_scan(dict(n=n, q=q, t=t, algo="eig", block=32768),
+                                                           "split_bf16", m, "packed")
+                                         for n, q, t in shapes),
+        "batch": {"plan": plan, "plan_ms": plan_ms,
+                  "plans": ["sequential", "concurrent, SM shares by work", "concurrent, all SMs",
+                            "two lanes of half the SMs"],
+                  "per_cohort_calls_ms": ms_seq, "speedup_vs_per_cohort_calls": ms_seq / ms},
+        "roofline": {"bound": "tensor", "achieved": None, "executed_tflops": exe,
+                     "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                     "executed_frac": exe / peaks["bf16_tflops_sustained"], "traffic": None,
+                     "kernel": "whole batched step", "peak_source": f"bf16_tflops_sustained, {kind}"},
+        "parity": {"max_rel_err_b": eb, "max_rel_err_wald": ew, "pairs_checked": 4 * len(shapes),
+                   "tolerance": 1e-4},
+        "setup_s": setup_s, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,6 +570,8 @@ def main():
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == 4:
+        run_batch(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

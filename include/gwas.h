@@ -146,6 +146,56 @@ gwas_status gwas_scan_packed(gwas_handle h, const uint8_t* G, int64_t m, int g_o
                              float* B, float* wald, int out_on_device, void* stream);
 
 /*
+ * Batched cohorts.  Several independent cohorts -- each its own kinship, covariates (q may
+ * differ), traits and sizes -- share one batch.  gwas_scan_batch scans one block of packed
+ * genotypes per cohort on the tensor cores as one CUDA graph: small cohorts cannot fill the GPU
+ * alone, so their persistent kernels share the SMs.  The launch plan (all cohorts one after
+ * another; all at once with SM shares proportional to their work; all at once with every SM; two
+ * lanes of half the SMs) is chosen by timing each candidate on the first call for a given set
+ * of block sizes.
+ */
+typedef struct gwas_batch_s* gwas_batch;
+
+typedef struct {          /* one cohort: the inputs of gwas_setup (host pointers, copied)    */
+  const double* Phi;
+  int n;
+  const double* XL;
+  int q;
+  const double* Y;
+  int t;
+  const double* h2;
+  const double* s2;
+} gwas_cohort;
+
+typedef struct {          /* one cohort's block: device pointers                              */
+  const uint8_t* G;       /* m packed genotype rows (gwas_packed_row_bytes(n) each), 16-byte
+                             aligned                                                         */
+  int64_t m;              /* SNPs of the block (0: this cohort is skipped)                   */
+  float* B;               /* m x t x p, as gwas_scan                                         */
+  float* wald;            /* m x t or NULL                                                   */
+} gwas_cohort_block;
+
+/* gwas_setup for every cohort (opt applies to all; precision must be SPLIT_BF16).  Fails with
+ * the first failing cohort's status (message names the cohort) and creates nothing then. */
+gwas_status gwas_setup_batch(int n_cohorts, const gwas_cohort* cohorts, const gwas_options* opt,
+                             gwas_batch* out);
+
+/* Scans blocks[i] of every cohort i, asynchronously on `stream` (cudaStream_t).  The first call
+ * for a given set of block sizes times the launch plans (it synchronises the stream) and keeps
+ * the fastest; later calls with the same sizes replay that plan's graph on the new buffers.
+ * Genotypes are not validated; use gwas_scan_packed with validate_genotypes for that. */
+gwas_status gwas_scan_batch(gwas_batch b, const gwas_cohort_block* blocks, void* stream);
+
+/* The chosen plan (0-3, -1 before the first scan) and the time of each plan (ms, 4 values). */
+gwas_status gwas_batch_plan(gwas_batch b, int* plan, double* plan_ms);
+
+/* The handle of cohort i (for gwas_info, gwas_singular_count; owned by the batch), or NULL. */
+gwas_handle gwas_batch_handle(gwas_batch b, int i);
+
+/* Frees the batch and every cohort's handle.  NULL is ignored. */
+void gwas_destroy_batch(gwas_batch b);
+
+/*
  * gwas_scan_static -- a scan that allocates no device memory.  (Not from the paper, which has
  * no counterpart: this is a deployment variant of gwas_scan.)
  *

@@ -25,6 +25,8 @@ STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ER
 # every symbol include/gwas.h declares
 EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_packed_row_bytes", "gwas_pack_genotypes", "gwas_scan_packed",
+           "gwas_setup_batch", "gwas_scan_batch", "gwas_batch_plan", "gwas_batch_handle",
+           "gwas_destroy_batch",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
            "gwas_last_error", "gwas_destroy"]
 
@@ -33,6 +35,17 @@ class GwasError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: {STATUS.get(status, status)}: {message}")
         self.status = status
+
+
+class gwas_cohort(ctypes.Structure):
+    _fields_ = [("Phi", ctypes.c_void_p), ("n", ctypes.c_int), ("XL", ctypes.c_void_p),
+                ("q", ctypes.c_int), ("Y", ctypes.c_void_p), ("t", ctypes.c_int),
+                ("h2", ctypes.c_void_p), ("s2", ctypes.c_void_p)]
+
+
+class gwas_cohort_block(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_void_p), ("m", ctypes.c_int64), ("B", ctypes.c_void_p),
+                ("wald", ctypes.c_void_p)]
 
 
 class gwas_options(ctypes.Structure):
@@ -58,6 +71,17 @@ def _load():
     lib.gwas_packed_row_bytes.restype = i32
     lib.gwas_pack_genotypes.argtypes = [vp, i64, i32, vp, i32, vp]
     lib.gwas_pack_genotypes.restype = i32
+    lib.gwas_setup_batch.argtypes = [i32, ctypes.POINTER(gwas_cohort), ctypes.POINTER(gwas_options),
+                                     ctypes.POINTER(vp)]
+    lib.gwas_setup_batch.restype = i32
+    lib.gwas_scan_batch.argtypes = [vp, ctypes.POINTER(gwas_cohort_block), vp]
+    lib.gwas_scan_batch.restype = i32
+    lib.gwas_batch_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp]
+    lib.gwas_batch_plan.restype = i32
+    lib.gwas_batch_handle.argtypes = [vp, i32]
+    lib.gwas_batch_handle.restype = vp
+    lib.gwas_destroy_batch.argtypes = [vp]
+    lib.gwas_destroy_batch.restype = None
     lib.gwas_scan_static.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.gwas_scan_static.restype = i32
     lib.gwas_setup_timing.argtypes = [vp, dp]
@@ -205,6 +229,64 @@ def gwas_scan_static(h, XR, B, wald=None, stream=None, m=None):
         stream = torch.cuda.current_stream().cuda_stream
     m = XR.shape[0] if m is None else m
     _check(lib.gwas_scan_static(h, xp, int(m), bp, wp or None, stream or None), "gwas_scan_static")
+
+
+def gwas_setup_batch(cohorts, options: gwas_options | None = None, **kw):
+    """cohorts: sequence of (Phi, XL, Y, h2, s2).  Returns an opaque batch (int)."""
+    keep, arr = [], (gwas_cohort * len(cohorts))()
+    for i, (Phi, XL, Y, h2, s2) in enumerate(cohorts):
+        Phi = np.asarray(Phi, dtype=np.float64)
+        n = Phi.shape[0]
+        XL = np.asarray(XL, dtype=np.float64)
+        Y = np.asarray(Y, dtype=np.float64)
+        if Y.ndim == 1:
+            Y = Y[:, None]
+        q, t = XL.shape[1], Y.shape[1]
+        Phi = _f64_fortran(Phi, (n, n), "Phi")
+        XL = _f64_fortran(XL, (n, q), "XL")
+        Y = _f64_fortran(Y, (n, t), "Y")
+        h2 = np.ascontiguousarray(np.broadcast_to(np.asarray(h2, dtype=np.float64), (t,)))
+        s2 = np.ascontiguousarray(np.broadcast_to(np.asarray(s2, dtype=np.float64), (t,)))
+        keep += [Phi, XL, Y, h2, s2]
+        arr[i] = gwas_cohort(Phi.ctypes.data, n, XL.ctypes.data, q, Y.ctypes.data, t,
+                             h2.ctypes.data, s2.ctypes.data)
+    o = options if options is not None else gwas_default_options(**kw)
+    b = ctypes.c_void_p()
+    _check(lib.gwas_setup_batch(len(cohorts), arr, ctypes.byref(o), ctypes.byref(b)),
+           "gwas_setup_batch")
+    return b.value
+
+
+def gwas_scan_batch(b, blocks, stream=None):
+    """blocks: sequence of (G, B, wald) CUDA tensors per cohort (G packed rows; wald may be
+    None; a G with 0 rows skips the cohort)."""
+    arr = (gwas_cohort_block * len(blocks))()
+    for i, (G, B, W) in enumerate(blocks):
+        gp, gdev = _ptr(G)
+        bp, bdev = _ptr(B)
+        wp = _ptr(W)[0] if W is not None else 0
+        if not (gdev and bdev):
+            raise ValueError("gwas_scan_batch takes device buffers only")
+        arr[i] = gwas_cohort_block(gp, int(G.shape[0]), bp, wp or None)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib.gwas_scan_batch(b, arr, stream or None), "gwas_scan_batch")
+
+
+def gwas_batch_plan(b):
+    plan = ctypes.c_int()
+    ms = (ctypes.c_double * 4)()
+    _check(lib.gwas_batch_plan(b, ctypes.byref(plan), ms), "gwas_batch_plan")
+    return plan.value, list(ms)
+
+
+def gwas_batch_handle(b, i):
+    return lib.gwas_batch_handle(b, int(i))
+
+
+def gwas_destroy_batch(b) -> None:
+    lib.gwas_destroy_batch(b)
 
 
 def gwas_setup_timing(h) -> float:

@@ -491,6 +491,16 @@ gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_d
 
 }  // namespace
 
+namespace gw {
+// Internals the batch API (batch.cu) builds on.
+TcState* handle_tc(gwas_handle h) { return h ? h->tc : nullptr; }
+int handle_device(gwas_handle h) { return h->dev; }
+int* handle_flags(gwas_handle h) { return h->flags; }
+int handle_n(gwas_handle h) { return h->n; }
+int handle_t(gwas_handle h) { return h->t; }
+int handle_p(gwas_handle h) { return h->p; }
+}  // namespace gw
+
 GW_API void gwas_default_options(gwas_options* opt) {
   if (!opt) return;
   opt->algo = GWAS_ALGO_AUTO;

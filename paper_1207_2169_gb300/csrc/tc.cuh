@@ -28,6 +28,7 @@ struct TcScanArgs {
   float* B;          // m x t x p device
   float* wald;       // m x t device or NULL
   int* flags;
+  int max_ctas;      // CTAs per kernel at most (0: one per SM); lets scans share the GPU
 };
 
 // Throws Fail{GWAS_ERR_UNSUPPORTED} for sizes the tensor-core kernels do not cover.
@@ -35,5 +36,7 @@ void tc_check_supported(int algo, int n, int q, int t);
 TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a);
 void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a);
 void tc_destroy(TcState* st);
+// Rough tensor-core work of scanning m SNPs (FLOPs issued), for planning concurrent scans.
+double tc_scan_work(const TcState* st, int64_t m);
 
 }  // namespace gw

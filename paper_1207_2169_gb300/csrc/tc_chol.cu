@@ -446,7 +446,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 }  // namespace
 
 namespace {
-int g_max_ctas[2] = {0, 0};  // co-resident CTAs of each instantiation (whole clusters)
+int g_max_ctas[64][2];  // per device: co-resident CTAs of each instantiation (whole clusters)
 
 template <int QM>
 int max_resident_ctas() {
@@ -466,18 +466,26 @@ int max_resident_ctas() {
   GW_REQUIRE(clusters >= 1, GWAS_ERR_UNSUPPORTED, "no cluster of %d CTAs fits on this device", CL);
   return clusters * CL;
 }
+
+int current_device() {
+  int dev = 0;
+  GW_CUDA(cudaGetDevice(&dev));
+  return dev & 63;
+}
 }  // namespace
 
 void chol_tc_prepare() {
+  int* mx = g_max_ctas[current_device()];
+  if (mx[0] && mx[1]) return;  // attributes and occupancy belong to the device: once per device
   GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)SMEM_BYTES));
   GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)SMEM_BYTES));
-  if (!g_max_ctas[0]) g_max_ctas[0] = max_resident_ctas<3>();
-  if (!g_max_ctas[1]) g_max_ctas[1] = max_resident_ctas<QMAX>();
+  mx[0] = max_resident_ctas<3>();
+  mx[1] = max_resident_ctas<QMAX>();
 }
 
-int chol_tc_resident_ctas(int q) { return g_max_ctas[q <= 3 ? 0 : 1]; }
+int chol_tc_resident_ctas(int q) { return g_max_ctas[current_device()][q <= 3 ? 0 : 1]; }
 
 void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& mapG,
                     const CholTcParams& p, int num_sms) {
@@ -485,7 +493,7 @@ void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& ma
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", p.q, QMAX);
   // persistent: whole clusters, no more than fit at once (and no more than the tiles need)
   const int64_t tiles = (p.m + BM - 1) / BM;
-  int64_t cap = g_max_ctas[p.q <= 3 ? 0 : 1];
+  int64_t cap = chol_tc_resident_ctas(p.q);
   if (cap <= 0 || cap > num_sms) cap = num_sms / CL * CL;
   const int64_t want = (tiles + CL - 1) / CL * CL;
   const unsigned grid = (unsigned)(want < cap ? want : cap);

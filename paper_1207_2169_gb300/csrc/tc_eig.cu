@@ -582,16 +582,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 }
 
 template <int EPI, int QQ>
+void prepare_one() {
+  constexpr size_t SMEM = smem_of(EPI, QQ);
+  static_assert(SMEM <= 232448, "shared memory over the sm_103 opt-in limit");
+  GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SMEM));
+}
+
+template <int EPI, int QQ>
 void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
                 const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {
   constexpr size_t SMEM = smem_of(EPI, QQ);
-  static_assert(SMEM <= 232448, "shared memory over the sm_103 opt-in limit");
-  static bool prepared = false;
-  if (!prepared) {
-    GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QQ>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
-    prepared = true;
-  }
   const int64_t work = ((p.m + BM - 1) / BM) * p.nblk;
   const unsigned grid = (unsigned)(work < num_sms ? work : num_sms);
   eig_tc_kernel<EPI, QQ><<<grid, NUM_THREADS, SMEM, s>>>(mapA, mapB, mapG, p);
@@ -599,6 +600,25 @@ void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB
 }
 
 }  // namespace
+
+void eig_tc_prepare() {
+  // attributes belong to the current device: set once per device
+  static uint64_t done_mask = 0;
+  int dev = 0;
+  GW_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done_mask & bit) return;
+  prepare_one<EPI_ROT, 0>();
+  prepare_one<EPI_SQ, 0>();
+  prepare_one<EPI_AC, 1>();
+  prepare_one<EPI_AC, 2>();
+  prepare_one<EPI_AC, 3>();
+  prepare_one<EPI_AC, 4>();
+  prepare_one<EPI_AC, 5>();
+  prepare_one<EPI_AC, 6>();
+  prepare_one<EPI_AC, 7>();
+  done_mask |= bit;
+}
 
 void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUtensorMap& mapB,
                    const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {

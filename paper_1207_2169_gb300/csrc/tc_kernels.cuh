@@ -78,5 +78,7 @@ __host__ __device__ constexpr int eig_ac_traits(int q) {
 // 256-row boxes.  mapG: packed genotypes as for CHOL (ROT, AC; ignored by SQ).
 void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUtensorMap& mapB,
                    const CUtensorMap& mapG, const EigTcParams& p, int num_sms);
+// Kernel attributes of every EIG stage (once per process; before any launch or graph capture).
+void eig_tc_prepare();
 
 }  // namespace gw

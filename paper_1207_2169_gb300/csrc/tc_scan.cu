@@ -197,7 +197,7 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     st->mapU = make_map_bf16(st->Usplit, 2 * (int64_t)t * q1, kp, 256);
     st->mapD = make_map_bf16(st->dsplit, 2 * (int64_t)t, kp, 256);
     st->mapX = make_map_bf16(st->xsq, 2 * st->mcap, kp, 128);
-    chol_tc_prepare();
+    eig_tc_prepare();
     return st;
   } catch (...) {
     tc_destroy(st);
@@ -205,9 +205,16 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
   }
 }
 
+double tc_scan_work(const TcState* st, int64_t m) {
+  const double kp = st->kpad, rp = st->rpad, t = st->t, q1 = st->q + 1;
+  if (st->algo == GWAS_ALGO_CHOL) return 2.0 * kp * rp * t * (double)m;  // ~ half the square x 2 pieces x 2 flops
+  return (4.0 * rp * kp + t * kp * (6.0 + 4.0 * q1)) * (double)m;
+}
+
 void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
   if (a.m <= 0) return;
   GW_REQUIRE(st != nullptr, GWAS_ERR_ARG, "no tensor-core state");
+  const int ctas = a.max_ctas > 0 && a.max_ctas < st->num_sms ? a.max_ctas : st->num_sms;
   const int rb = packed_row_bytes(st->n);
   if (st->algo == GWAS_ALGO_CHOL) {
     const CUtensorMap mapG = make_map_packed(a.G, a.m, rb);
@@ -228,7 +235,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
       p.B = a.B;
       p.W = a.wald;
       p.flags = a.flags;
-      chol_tc_launch(s, st->lmaps[j], mapG, p, st->num_sms);
+      chol_tc_launch(s, st->lmaps[j], mapG, p, ctas);
     }
     return;
   }
@@ -254,12 +261,12 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.nblk = st->rpad / 256;
     p.b_piece_rows = st->rpad;
     p.b_rows_per_blk = 256;
-    eig_tc_launch(s, 0, st->mapZ, st->mapZ, mapG, p, st->num_sms);
+    eig_tc_launch(s, 0, st->mapZ, st->mapZ, mapG, p, ctas);
     // SQ: s_ij = sum_r Xsq[i][r] d_j[r]
     p.nblk = (t + 255) / 256;
     p.b_piece_rows = t;
     p.b_rows_per_blk = 256;
-    eig_tc_launch(s, 1, st->mapX, st->mapD, mapG, p, st->num_sms);
+    eig_tc_launch(s, 1, st->mapX, st->mapD, mapG, p, ctas);
     // AC: a_ij, c_ij from the genotypes against U, then the bordered solve (lines 13-16)
     p.nblk = (t + st->traits_ac - 1) / st->traits_ac;
     p.b_piece_rows = t * q1;
@@ -269,7 +276,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.b0 = st->b032;
     p.B = a.B + (size_t)off * t * q1;
     p.W = a.wald ? a.wald + (size_t)off * t : nullptr;
-    eig_tc_launch(s, 2, st->mapU, st->mapU, mapG, p, st->num_sms);
+    eig_tc_launch(s, 2, st->mapU, st->mapU, mapG, p, ctas);
   }
 }
 

@@ -176,6 +176,51 @@ def snp_block(workload: int, n: int, m: int, block_index: int) -> np.ndarray:
     return genotypes(rng(workload, 1000 + block_index), n, m)
 
 
+# Workload 4: a batch of uneven cohorts, each with its own kinship (drawn as in workload 0),
+# n log-uniform in [500, 5000], p = q + 1 uniform in {3..8}, t log-uniform in [10, 2000],
+# h2 ~ U(0.05, 0.95), s2 ~ U(0.5, 2), m = 200,000 SNPs each.
+BATCH = dict(name="batch16_uneven_m200k", cohorts=16, n=(500, 5000), p=(3, 8), t=(10, 2000),
+             m=200_000, h2=(0.05, 0.95), s2=(0.5, 2.0))
+
+
+def batch_shapes(cohorts: int | None = None):
+    """(n, q, t) of each cohort of workload 4."""
+    spec = BATCH
+    k = spec["cohorts"] if cohorts is None else cohorts
+    g = rng(4, 0)
+    n = np.rint(np.exp(g.uniform(np.log(spec["n"][0]), np.log(spec["n"][1]), size=k))).astype(int)
+    p = g.integers(spec["p"][0], spec["p"][1] + 1, size=k)
+    t = np.rint(np.exp(g.uniform(np.log(spec["t"][0]), np.log(spec["t"][1]), size=k))).astype(int)
+    return [(int(a), int(b) - 1, int(c)) for a, b, c in zip(n, p, t)]
+
+
+def batch_cohort(i: int, n: int, q: int, t: int) -> Cohort:
+    """Cohort i of workload 4 without genotypes (they are drawn on the device, see
+    device_genotypes): its own kinship, covariates and traits."""
+    g = np.random.Generator(np.random.PCG64([SEED_BASE + 4, 100 + i]))
+    Gs = kinship_factor(g, n)
+    Phi = kinship(Gs)
+    XL = covariates(g, n, q)
+    h2 = g.uniform(*BATCH["h2"], size=t)
+    s2 = g.uniform(*BATCH["s2"], size=t)
+    Y, beta = traits(g, XL, Gs, h2, s2)
+    return Cohort(Phi=Phi, XL=XL, Y=Y, h2=h2, s2=s2, XR=None, beta=beta)
+
+
+def device_genotypes(seed: int, n: int, m: int, device="cuda"):
+    """m x n int8 hard calls drawn on a CUDA device (torch generator seeded by `seed`): per SNP
+    MAF ~ U(0.05, 0.5), each call Binomial(2, MAF) from one uniform -- the recipe of `genotypes`
+    with another generator, for batches too large to draw on the host."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(SEED_BASE * 1000 + seed)
+    f = torch.rand((m, 1), generator=gen, device=device) * 0.45 + 0.05
+    u = torch.rand((m, n), generator=gen, device=device)
+    x = (u >= (1.0 - f) ** 2).to(torch.int8)   # as `genotypes`: one uniform per call
+    x += (u >= 1.0 - f * f).to(torch.int8)
+    return x
+
+
 def workload_genotypes(workload: int, m: int | None = None) -> np.ndarray:
     """The first m SNPs (default: all) of workload `workload`'s genome, m x n int8, assembled
     from its per-block streams (snp_block) so that any prefix is the same at every m."""

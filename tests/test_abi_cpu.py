@@ -133,3 +133,20 @@ def test_host_packing_rejects_invalid_values(g):
 
 def test_scan_packed_null_handle(g):
     assert g.lib.gwas_scan_packed(None, None, 10, 1, None, None, 1, None) == -1
+
+
+def test_batch_argument_checks(g):
+    out = ctypes.c_void_p(7)
+    assert g.lib.gwas_setup_batch(0, None, None, ctypes.byref(out)) == -1 and out.value is None
+    Phi = np.eye(4, order="F"); XL = np.ones((4, 1), order="F"); Y = np.zeros((4, 1), order="F")
+    h2 = np.array([0.5]); s2 = np.array([1.0])
+    arr = (g.gwas_cohort * 1)()
+    arr[0] = g.gwas_cohort(Phi.ctypes.data, 4, XL.ctypes.data, 1, Y.ctypes.data, 1, h2.ctypes.data,
+                           s2.ctypes.data)
+    opt = g.gwas_default_options(precision="fp64")
+    assert g.lib.gwas_setup_batch(1, arr, ctypes.byref(opt), ctypes.byref(out)) == -5
+    assert g.lib.gwas_setup_batch(300, arr, None, ctypes.byref(out)) == -1
+    assert g.lib.gwas_scan_batch(None, None, None) == -1
+    assert g.lib.gwas_batch_plan(None, None, None) == -1
+    assert g.lib.gwas_batch_handle(None, 0) is None
+    g.lib.gwas_destroy_batch(None)
