@@ -115,9 +115,10 @@ gwas_status gwas_scan_f64(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_
                           double* B, double* wald, int out_on_device, void* stream);
 
 /*
- * Packed genotype format (a storage format; the paper's X_R is the same m x n matrix of hard
- * calls, Section 2 "Notation"): SNP i occupies gwas_packed_row_bytes(n) = ceil(n / 64) * 16
- * bytes starting at G + i * gwas_packed_row_bytes(n); the genotype of individual k sits in byte
+ * Packed genotype format (a storage format for the same genotype matrix X_R of "Sequences of
+ * GLS'", hard calls of m SNPs for n individuals): SNP i occupies gwas_packed_row_bytes(n) =
+ * ceil(n / 64) * 16 bytes starting at G + i * gwas_packed_row_bytes(n); the genotype of
+ * individual k sits in byte
  * k / 4 at bits 2 (k % 4) and 2 (k % 4) + 1 and holds the allele count 0, 1 or 2.  Code 3 is
  * invalid and every code past the n-th of a row is 0.  Four genotypes per byte: a quarter of the
  * int8 bytes to stream from host memory and HBM, and the tensor-core kernels read these rows
@@ -230,6 +231,23 @@ gwas_status gwas_info(gwas_handle h, int* n, int* q, int* t, int* algo, int* pre
 
 /* Number of singular pairs (written as NaN) seen by completed scans of this handle, or -1. */
 int64_t gwas_singular_count(gwas_handle h);
+
+/*
+ * gwas_sync -- waits for all work on the handle's device, then reports GWAS_ERR_TIMEOUT if a
+ * tensor-core kernel of this handle gave up one of its bounded waits since the last report
+ * (that call's outputs are incomplete; the flag is cleared and the handle stays usable).
+ * Synchronous scans (host buffers, or validate_genotypes) report it themselves.
+ */
+gwas_status gwas_sync(gwas_handle h);
+
+/*
+ * gwas_selftest_timeout -- checks the bounded-wait mechanism of the tensor-core kernels on
+ * `device` (not from the paper: a failure-detection self-test).  One GPU thread waits on a
+ * barrier phase that nothing completes; after limit_ms (1..10000) it must give up and record
+ * the timeout, and the GPU context stays usable.  Returns GWAS_ERR_TIMEOUT when that happened
+ * as designed, GWAS_ERR_CUDA otherwise.
+ */
+gwas_status gwas_selftest_timeout(int device, int limit_ms);
 
 /* Message of the last failure on the calling thread ("" if none).  Never NULL. */
 const char* gwas_last_error(void);

@@ -26,7 +26,7 @@ STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ER
 EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_packed_row_bytes", "gwas_pack_genotypes", "gwas_scan_packed",
            "gwas_setup_batch", "gwas_scan_batch", "gwas_batch_plan", "gwas_batch_handle",
-           "gwas_destroy_batch",
+           "gwas_destroy_batch", "gwas_sync", "gwas_selftest_timeout",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
            "gwas_last_error", "gwas_destroy"]
 
@@ -82,6 +82,10 @@ def _load():
     lib.gwas_batch_handle.restype = vp
     lib.gwas_destroy_batch.argtypes = [vp]
     lib.gwas_destroy_batch.restype = None
+    lib.gwas_sync.argtypes = [vp]
+    lib.gwas_sync.restype = i32
+    lib.gwas_selftest_timeout.argtypes = [i32, i32]
+    lib.gwas_selftest_timeout.restype = i32
     lib.gwas_scan_static.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.gwas_scan_static.restype = i32
     lib.gwas_setup_timing.argtypes = [vp, dp]
@@ -287,6 +291,15 @@ def gwas_batch_handle(b, i):
 
 def gwas_destroy_batch(b) -> None:
     lib.gwas_destroy_batch(b)
+
+
+def gwas_sync(h) -> None:
+    _check(lib.gwas_sync(h), "gwas_sync")
+
+
+def gwas_selftest_timeout(device: int = 0, limit_ms: int = 200) -> int:
+    """Status of the bounded-wait self-test: -7 (GWAS_ERR_TIMEOUT) when the wait gave up."""
+    return int(lib.gwas_selftest_timeout(int(device), int(limit_ms)))
 
 
 def gwas_setup_timing(h) -> float:

@@ -136,6 +136,18 @@ void read_flags(gwas_handle h, cudaStream_t s) {
   GW_CUDA(cudaStreamSynchronize(s));
 }
 
+// After a synchronisation: a kernel of this handle whose bounded wait gave up makes the call
+// fail with GWAS_ERR_TIMEOUT (the flag is cleared, so the handle stays usable).
+void check_timeout(gwas_handle h, cudaStream_t s) {
+  read_flags(h, s);
+  if (h->h_flags[FLAG_TIMEOUT]) {
+    GW_CUDA(cudaMemsetAsync(h->flags + FLAG_TIMEOUT, 0, sizeof(int), s));
+    GW_CUDA(cudaStreamSynchronize(s));
+    GW_REQUIRE(false, GWAS_ERR_TIMEOUT,
+               "a tensor-core kernel gave up waiting (its outputs for this call are incomplete)");
+  }
+}
+
 void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double* Y,
                 const double* h2, const double* s2) {
   const int n = h->n, q = h->q, t = h->t;
@@ -414,7 +426,7 @@ gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_d
     ensure_xt(h, m < h->block_snps ? m : h->block_snps);
     scan_block(h, X, fmt, m, B, wald, out_f64, s);
     if (h->validate) {
-      read_flags(h, s);
+      check_timeout(h, s);
       GW_REQUIRE(!h->h_flags[FLAG_GENOTYPE], GWAS_ERR_GENOTYPE, "genotype outside {0,1,2}");
     }
     return GWAS_OK;
@@ -482,10 +494,9 @@ gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_d
   GW_CUDA(cudaStreamSynchronize(s));
   GW_CUDA(cudaStreamSynchronize(h->st_h2d));
   GW_CUDA(cudaStreamSynchronize(h->st_d2h));
-  if (h->validate) {
-    read_flags(h, s);
+  check_timeout(h, s);
+  if (h->validate)
     GW_REQUIRE(!h->h_flags[FLAG_GENOTYPE], GWAS_ERR_GENOTYPE, "genotype outside {0,1,2}");
-  }
   return GWAS_OK;
 }
 
@@ -686,6 +697,32 @@ GW_API int64_t gwas_singular_count(gwas_handle h) {
     return h->h_flags[FLAG_SINGULAR];
   } catch (const Fail&) {
     return -1;
+  }
+}
+
+GW_API gwas_status gwas_sync(gwas_handle h) {
+  try {
+    GW_REQUIRE(h != nullptr, GWAS_ERR_ARG, "null handle");
+    DeviceGuard dg(h->dev);
+    GW_CUDA(cudaDeviceSynchronize());
+    check_timeout(h, h->st);
+    return GWAS_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+GW_API gwas_status gwas_selftest_timeout(int device, int limit_ms) {
+  try {
+    GW_REQUIRE(limit_ms >= 1 && limit_ms <= 10000, GWAS_ERR_ARG, "limit_ms=%d outside [1,10000]",
+               limit_ms);
+    int ndev = 0;
+    GW_CUDA(cudaGetDeviceCount(&ndev));
+    GW_REQUIRE(device >= 0 && device < ndev, GWAS_ERR_ARG, "device %d not present", device);
+    DeviceGuard dg(device);
+    return selftest_wait_timeout(limit_ms);
+  } catch (const Fail& f) {
+    return f.st;
   }
 }
 

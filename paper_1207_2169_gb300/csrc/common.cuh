@@ -141,6 +141,10 @@ struct EigScanArgs {
 };
 template <typename T> void eig_scan_simt(cudaStream_t s, const EigScanArgs<T>& a);
 
+// Launches one thread that waits, bounded by limit_ms, on a barrier nothing completes
+// (selftest.cu).  GWAS_ERR_TIMEOUT when the wait gave up as designed.
+gwas_status selftest_wait_timeout(int limit_ms);
+
 // Genotype check: flags[GENOTYPE] = 1 if any value is outside {0,1,2}.
 void validate_genotypes(cudaStream_t s, const int8_t* XR, int64_t count, int* flags);
 

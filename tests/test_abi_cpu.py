@@ -150,3 +150,9 @@ def test_batch_argument_checks(g):
     assert g.lib.gwas_batch_plan(None, None, None) == -1
     assert g.lib.gwas_batch_handle(None, 0) is None
     g.lib.gwas_destroy_batch(None)
+
+
+def test_sync_and_selftest_argument_checks(g):
+    assert g.lib.gwas_sync(None) == -1
+    assert g.lib.gwas_selftest_timeout(0, 0) == -1
+    assert g.lib.gwas_selftest_timeout(0, 20000) == -1
