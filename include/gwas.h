@@ -118,9 +118,8 @@ gwas_status gwas_scan_f64(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_
  * Packed genotype format (a storage format for the same genotype matrix X_R of "Sequences of
  * GLS'", hard calls of m SNPs for n individuals): SNP i occupies gwas_packed_row_bytes(n) =
  * ceil(n / 64) * 16 bytes starting at G + i * gwas_packed_row_bytes(n); the genotype of
- * individual k sits in byte
- * k / 4 at bits 2 (k % 4) and 2 (k % 4) + 1 and holds the allele count 0, 1 or 2.  Code 3 is
- * invalid and every code past the n-th of a row is 0.  Four genotypes per byte: a quarter of the
+ * individual k sits in byte k / 4 at bits 2 (k % 4) and 2 (k % 4) + 1 and holds the allele
+ * count 0, 1 or 2.  Code 3 is invalid and every code past the n-th of a row is 0.  Four genotypes per byte: a quarter of the
  * int8 bytes to stream from host memory and HBM, and the tensor-core kernels read these rows
  * directly (int8 input is packed on the device first).
  */
