@@ -28,18 +28,37 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int BK = 64;
-constexpr int SA = 4;
+constexpr int SA_MAX = 4;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int NCONV = 8;                 // genotype converter warps (ROT, AC): 2 threads per row
-constexpr int NUM_THREADS = 192 + 32 * NCONV;
-// Warp roles.  A warp issues on SMSP (warp % 4); the single-thread MMA issuer and TMA producers
-// share SMSP 3 with only an epilogue warp, so converter bursts never delay their issue.
+// Warp roles.  A warp issues on SMSP (warp % 4) and may read only TMEM lanes 32 (warp % 4) ..
+// +31.  The single-thread MMA issuer (7) and TMA producers (11) share SMSP 3 with epilogue warps
+// only, so converter bursts never delay their issue.  ROT and SQ: 14 warps, epilogue 0-3,
+// converters 4-6, 8-10, 12-13.  AC is epilogue-bound: 20 warps in five warpgroups, epilogue
+// warps 0-3 and 12-15 (each set takes half of a work item's traits), converters 4-6, 8-10,
+// 16-17, warps 18-19 idle.
 constexpr int MMA_WARP = 7;
 constexpr int TMA_WARP = 11;
-// converter warps 4, 5, 6, 8, 9, 10, 12, 13 -> 0 .. 7
+
+enum { EPI_ROT = 0, EPI_SQ = 1, EPI_AC = 2 };
+// the 20-warp layout: AC with q <= 3 (larger q would need more staging memory than fits)
+__host__ __device__ constexpr bool wide_of(int epi, int qq) { return epi == EPI_AC && qq <= 3; }
+__host__ __device__ constexpr int nwarps_of(int epi, int qq) { return wide_of(epi, qq) ? 20 : 14; }
+__host__ __device__ constexpr int nepi_of(int epi, int qq) { return wide_of(epi, qq) ? 8 : 4; }
+__host__ __device__ constexpr int sa_of(int epi, int qq) { return wide_of(epi, qq) ? 3 : 4; }
+// converter warps -> 0 .. 7
+template <bool WIDE>
 __device__ __forceinline__ int conv_index(int warp) {
-  return warp < MMA_WARP ? warp - 4 : warp < TMA_WARP ? warp - 5 : warp - 6;
+  return warp < MMA_WARP ? warp - 4 : warp < TMA_WARP ? warp - 5 : (WIDE ? warp - 10 : warp - 6);
+}
+template <bool WIDE>
+__device__ __forceinline__ bool is_epilogue(int warp) {
+  return warp < 4 || (WIDE && warp >= 12 && warp < 16);
+}
+template <bool WIDE>
+__device__ __forceinline__ bool is_idle(int warp) {
+  return WIDE && warp >= 18;
 }
 constexpr int PR = 8;                    // packed-genotype slice ring
 constexpr int PK_BYTES = BM * 16;        // 64 genotypes of 128 SNPs, 2-bit codes: 2 KB
@@ -47,8 +66,6 @@ constexpr int TMEM_COLS = 512;
 constexpr int GROUP_M = 8;
 constexpr int QMAX = 7;
 constexpr uint64_t WAIT_NS = 4000000000ull;
-
-enum { EPI_ROT = 0, EPI_SQ = 1, EPI_AC = 2 };
 
 // B-tile ring depth: AC gives one slot to the shared memory that stages its output rows.
 __host__ __device__ constexpr int sb_of(int epi) { return epi == EPI_AC ? 3 : 4; }
@@ -59,25 +76,25 @@ __host__ __device__ constexpr int qp_of(int qq) { return qq + 1 <= 4 ? 4 : 8; }
 // float4 and rows are 36 floats (16-byte aligned, conflict-free float4 access); otherwise rows
 // are 8 QP + 1 floats (odd: conflict-free scalar access).
 __host__ __device__ constexpr int stg_rb(int qq) { return qq == 3 ? 36 : 8 * qp_of(qq) + 1; }
-// AC shared floats: P_j, b0_j of a block (<= 2048), then per epilogue warp a staging area of
-// 32 rows of coefficients and 32 x 9 Wald values.
+// AC shared floats: P_j, b0_j of a block (<= 2048), then per epilogue warp (eight) a staging
+// area of 32 rows of coefficients and 32 x 9 Wald values.
 __host__ __device__ constexpr int stg_b(int qq) { return 32 * stg_rb(qq); }
 constexpr int STG_W = 32 * 9;
 constexpr int PB_FLOATS = 2048;
 __host__ __device__ constexpr int cst_of(int epi, int qq) {
-  return epi == EPI_AC ? PB_FLOATS + 4 * (stg_b(qq) + STG_W) : 0;
+  return epi == EPI_AC ? PB_FLOATS + nepi_of(epi, qq) * (stg_b(qq) + STG_W) : 0;
 }
 
 template <int NSB>
 struct __align__(8) BarsT {
-  uint64_t a_full[SA], a_empty[SA], b_full[NSB], b_empty[NSB], pk_full[PR], pk_empty[PR];
+  uint64_t a_full[SA_MAX], a_empty[SA_MAX], b_full[NSB], b_empty[NSB], pk_full[PR], pk_empty[PR];
   uint64_t acc_full[2], acc_empty[2], done;
   uint32_t tmem_base;
   int abort;
 };
 
 __host__ __device__ constexpr size_t smem_of(int epi, int qp) {
-  return 1024 + SA * A_BYTES + (size_t)sb_of(epi) * B_BYTES + PR * PK_BYTES +
+  return 1024 + (size_t)sa_of(epi, qp) * A_BYTES + (size_t)sb_of(epi) * B_BYTES + PR * PK_BYTES +
          (size_t)cst_of(epi, qp) * 4 + sizeof(BarsT<4>);
 }
 
@@ -110,12 +127,15 @@ __device__ __forceinline__ void tmem_ld_cols<8>(uint32_t taddr, uint32_t (&r)[8]
 }
 
 template <int EPI, int QQ>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+__global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
     eig_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapG, const EigTcParams p) {
   constexpr int QP = qp_of(QQ);
   constexpr bool CONV = EPI != EPI_SQ;  // A operand = genotypes through the converters
   constexpr int SB = sb_of(EPI);
+  constexpr bool WIDE = wide_of(EPI, QQ);
+  constexpr int SA = sa_of(EPI, QQ);
+  constexpr int NEPI = nepi_of(EPI, QQ);
   using Bars = BarsT<SB>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -145,7 +165,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bars->acc_full[i], 1);
-      mbar_init(&bars->acc_empty[i], 4);
+      mbar_init(&bars->acc_empty[i], NEPI);
     }
     mbar_init(&bars->done, 1);
     bars->abort = 0;
@@ -288,14 +308,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mma_commit(&bars->done);
       mbar_wait(&bars->done, 0, abort, tflag, WAIT_NS);
     }
-  } else if (warp >= 4) {
+  } else if (!is_epilogue<WIDE>(warp) && !is_idle<WIDE>(warp)) {
     // ------------------------------------------------------------ genotype converters
     // Thread ct converts half hh of row r of each K step: packed bytes 8 hh .. 8 hh + 7 (32
     // genotypes) into BF16 chunks 4 hh .. 4 hh + 3 of the row's swizzled 128-byte line, through
     // the row's byte tables of g - mu (mu = 0 without centring).  Codes past n are 0 and map to
     // -mu; the B operand is zero there, so they add nothing.
     if (CONV) {
-      const int ct = conv_index(warp) * 32 + lane;
+      const int ct = conv_index<WIDE>(warp) * 32 + lane;
       const int r = ct >> 1, hh = ct & 1;
       const uint32_t line = (r >> 3) * 1024 + (r & 7) * 128;
       const int64_t mine = blockIdx.x < nwork ? (nwork - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -340,16 +360,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
       }
     }
-  } else {
-    // ------------------------------------------------------------ epilogue (warps 0-3)
+  } else if (is_epilogue<WIDE>(warp)) {
+    // ------------------------------------------------------------ epilogue
+    // ew: epilogue warp 0 .. NEPI-1; it reads TMEM lanes (SNPs) 32 qd .. 32 qd + 31 and, in AC,
+    // the trait batches of its set (the two warpgroups take alternate batches of 8 traits)
+    const int ew = warp < 4 ? warp : warp - 8, qd = warp & 3, set = ew >> 2;
+    constexpr int NSETS = NEPI / 4;
     int buf = 0;
     uint32_t accph = 0;
     bool ok = true;
     // AC is compiled for one q, so the Schur loops below are fully unrolled
     const int q = EPI == EPI_AC ? QQ : p.q, q1 = q + 1;
     // AC constants of trait block nb, flattened: per trait P_j (q x q) then b0_j (q); 0 past t
-    constexpr int PF_REGS = (eig_ac_traits(QQ > 0 ? QQ : 1) * (QQ * QQ + QQ) + 127) / 128;
-    static_assert(PF_REGS * 128 <= PB_FLOATS, "AC constants exceed their shared-memory area");
+    constexpr int ET = 32 * NEPI;  // epilogue threads
+    constexpr int PF_REGS = (eig_ac_traits(QQ > 0 ? QQ : 1) * (QQ * QQ + QQ) + ET - 1) / ET;
+    static_assert(PF_REGS * ET <= PB_FLOATS, "AC constants exceed their shared-memory area");
+    const int et = 32 * ew + lane;
     float pf[EPI == EPI_AC ? PF_REGS : 1];
     bool have_pf = false;
     auto const_at = [&](int nbk, int e) -> float {
@@ -362,21 +388,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int64_t tile;
       int nb;
       work_coords(w, mtiles, p.nblk, tile, nb);
-      const int64_t snp = tile * BM + 32 * warp + lane;
+      const int64_t snp = tile * BM + 32 * qd + lane;
       const float mu_snp = (p.mu && snp < p.m) ? p.mu[snp] : 0.f;
       if (EPI == EPI_AC) {
         // P_j and b0_j of this block's traits, FP32, into shared memory: from the registers
         // loaded during the previous work item, then the next item's are loaded (their global
         // latency hides behind this item)
-        named_bar(1, 128);
+        named_bar(1, ET);
         if (have_pf) {
 #pragma unroll
-          for (int i = 0; i < PF_REGS; ++i) cst[threadIdx.x + 128 * i] = pf[i];
+          for (int i = 0; i < PF_REGS; ++i) cst[et + ET * i] = pf[i];
         } else {
 #pragma unroll
-          for (int i = 0; i < PF_REGS; ++i) cst[threadIdx.x + 128 * i] = const_at(nb, threadIdx.x + 128 * i);
+          for (int i = 0; i < PF_REGS; ++i) cst[et + ET * i] = const_at(nb, et + ET * i);
         }
-        named_bar(1, 128);
+        named_bar(1, ET);
         const int64_t wn = w + gridDim.x;
         have_pf = wn < nwork;
         if (have_pf) {
@@ -384,13 +410,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           int nbn;
           work_coords(wn, mtiles, p.nblk, tn, nbn);
 #pragma unroll
-          for (int i = 0; i < PF_REGS; ++i) pf[i] = const_at(nbn, threadIdx.x + 128 * i);
+          for (int i = 0; i < PF_REGS; ++i) pf[i] = const_at(nbn, et + ET * i);
         }
       }
       if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full[buf], accph, abort, tflag, WAIT_NS));
       if (ok) {
         tc_fence_after();
-        const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + buf * BN;
+        const uint32_t base = tmem + ((uint32_t)(32 * qd) << 16) + buf * BN;
         if (EPI == EPI_ROT) {
           for (int c = 0; c < BN / 32; ++c) {
             float v[32];
@@ -435,26 +461,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int T = p.traits_per_blk;
           const int j0 = nb * T;
           const int jend = (j0 + T < p.t ? j0 + T : p.t);
-          float* stgB = cst + PB_FLOATS + warp * (stg_b(QQ) + STG_W);
+          float* stgB = cst + PB_FLOATS + ew * (stg_b(QQ) + STG_W);
           float* stgW = stgB + stg_b(QQ);
           constexpr int RB = stg_rb(QQ);
           const bool live = snp < p.m;
+          constexpr int STEP = 8 * NSETS;  // this warp's batches: 8 set, 8 set + STEP, ...
           float snext[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const int j = j0 + u;
+            const int j = j0 + 8 * set + u;
             snext[u] = (live && j < jend) ? __ldg(&p.sbuf[(int64_t)j * p.lds + snp]) : 1.f;
           }
           int nsing = 0;
-          const int64_t row0 = tile * BM + 32 * warp;
-          for (int j8 = 0; j8 < T; j8 += 8) {
+          bool released = false;
+          const int64_t row0 = tile * BM + 32 * qd;
+          for (int j8 = 8 * set; j8 < T; j8 += STEP) {
             float scur[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) scur[u] = snext[u];
-            if (j8 + 8 < T) {
+            if (j8 + STEP < T) {
 #pragma unroll
               for (int u = 0; u < 8; ++u) {
-                const int j = j0 + j8 + 8 + u;
+                const int j = j0 + j8 + STEP + u;
                 snext[u] = (live && j < jend) ? __ldg(&p.sbuf[(int64_t)j * p.lds + snp]) : 1.f;
               }
             }
@@ -470,12 +498,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
             for (int h = 0; h < QP / 4; ++h)
               tmem_wait32(*reinterpret_cast<uint32_t(*)[32]>(&r[4 * h][0]));
-            if (j8 + 8 >= T) {
-              // the block's last columns are in registers: hand the accumulator back to the
+            if (j8 + STEP >= T) {
+              // this warp's last columns are in registers: hand the accumulator back to the
               // MMA issuer before solving them
               tc_fence_before();
               __syncwarp();
               if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
+              released = true;
             }
             const int nval = jend - (j0 + j8) < 8 ? jend - (j0 + j8) : 8;  // valid traits
 #pragma unroll
@@ -562,6 +591,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
             __syncwarp();
           }
+          if (!released) {  // a warp with no batch in this block (fewer than 9 traits)
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
+          }
           if (nsing) atomicAdd(&p.flags[FLAG_SINGULAR], nsing);
         }
         if (EPI != EPI_AC) {  // AC hands the accumulator back inside its batch loop
@@ -595,7 +629,7 @@ void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB
   constexpr size_t SMEM = smem_of(EPI, QQ);
   const int64_t work = ((p.m + BM - 1) / BM) * p.nblk;
   const unsigned grid = (unsigned)(work < num_sms ? work : num_sms);
-  eig_tc_kernel<EPI, QQ><<<grid, NUM_THREADS, SMEM, s>>>(mapA, mapB, mapG, p);
+  eig_tc_kernel<EPI, QQ><<<grid, 32 * nwarps_of(EPI, QQ), SMEM, s>>>(mapA, mapB, mapG, p);
   GW_CHECK_LAUNCH();
 }
 
