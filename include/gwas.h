@@ -67,15 +67,22 @@ enum { GWAS_ALGO_AUTO = 0, GWAS_ALGO_CHOL = 1, GWAS_ALGO_EIG = 2 };
  *               accumulation is FP32; the p x p Schur solve runs in FP32.                     */
 enum { GWAS_PREC_FP64 = 0, GWAS_PREC_FP32 = 1, GWAS_PREC_SPLIT_BF16 = 2 };
 
+/* What a scan writes per (SNP, trait) pair into B (wald is the same in both):
+ *   FULL  all p coefficients: B is m x t x p;
+ *   SNP   the SNP effect and its standard error, sqrt(Var(b)[p-1][p-1]) = 1 / sqrt(sigma):
+ *         B is m x t x 2 (GWAS summary statistics; with gwas_wald_pvalues, the p-values). */
+enum { GWAS_OUT_FULL = 0, GWAS_OUT_SNP = 1 };
+
 typedef struct {
   int algo;               /* GWAS_ALGO_*; AUTO = CHOL when t == 1, else EIG                   */
   int precision;          /* GWAS_PREC_*                                                      */
   int block_snps;         /* SNPs per device block when streaming host input; 0 = default     */
   int validate_genotypes; /* nonzero: scan checks every genotype is 0, 1 or 2                 */
   int device;             /* CUDA device ordinal                                              */
+  int out_mode;           /* GWAS_OUT_*                                                       */
 } gwas_options;
 
-/* Fills *opt with AUTO, SPLIT_BF16, block_snps 0, validation off, device 0. */
+/* Fills *opt with AUTO, SPLIT_BF16, block_snps 0, validation off, device 0, FULL outputs. */
 void gwas_default_options(gwas_options* opt);
 
 /*
@@ -113,6 +120,15 @@ gwas_status gwas_scan(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_devi
 /* gwas_scan_f64 -- as gwas_scan with FP64 outputs (meaningful for GWAS_PREC_FP64). */
 gwas_status gwas_scan_f64(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_device,
                           double* B, double* wald, int out_on_device, void* stream);
+
+/*
+ * gwas_wald_pvalues -- p-values of Wald statistics, the chi-square (1 degree of freedom) upper
+ * tail erfc(sqrt(wald / 2)) (Section "Mixed Models for GWAS": the test of each SNP effect).  NaN
+ * stays NaN.  on_device = 0: host arrays, synchronous; otherwise device arrays, asynchronous on
+ * `stream`.  wald and pval may be the same array.
+ */
+gwas_status gwas_wald_pvalues(const float* wald, int64_t count, float* pval, int on_device,
+                              void* stream);
 
 /*
  * Packed genotype format (a storage format for the same genotype matrix X_R of "Sequences of

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libgwasgb.so")
 
 ALGO = {"auto": 0, "chol": 1, "eig": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "split_bf16": 2}
+OUT_MODE = {"full": 0, "snp": 1}
 STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ERR_CUDA",
           -4: "GWAS_ERR_OOM", -5: "GWAS_ERR_UNSUPPORTED", -6: "GWAS_ERR_GENOTYPE",
           -7: "GWAS_ERR_TIMEOUT", -8: "GWAS_ERR_SINGULAR", -9: "GWAS_ERR_NOT_CONVERGED"}
@@ -26,7 +27,7 @@ STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ER
 EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_packed_row_bytes", "gwas_pack_genotypes", "gwas_scan_packed",
            "gwas_setup_batch", "gwas_scan_batch", "gwas_batch_plan", "gwas_batch_handle",
-           "gwas_destroy_batch", "gwas_sync", "gwas_selftest_timeout",
+           "gwas_destroy_batch", "gwas_sync", "gwas_selftest_timeout", "gwas_wald_pvalues",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
            "gwas_last_error", "gwas_destroy"]
 
@@ -50,7 +51,8 @@ class gwas_cohort_block(ctypes.Structure):
 
 class gwas_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("precision", ctypes.c_int), ("block_snps", ctypes.c_int),
-                ("validate_genotypes", ctypes.c_int), ("device", ctypes.c_int)]
+                ("validate_genotypes", ctypes.c_int), ("device", ctypes.c_int),
+                ("out_mode", ctypes.c_int)]
 
 
 def _load():
@@ -82,6 +84,8 @@ def _load():
     lib.gwas_batch_handle.restype = vp
     lib.gwas_destroy_batch.argtypes = [vp]
     lib.gwas_destroy_batch.restype = None
+    lib.gwas_wald_pvalues.argtypes = [vp, i64, vp, i32, vp]
+    lib.gwas_wald_pvalues.restype = i32
     lib.gwas_sync.argtypes = [vp]
     lib.gwas_sync.restype = i32
     lib.gwas_selftest_timeout.argtypes = [i32, i32]
@@ -138,6 +142,8 @@ def gwas_default_options(**kw) -> gwas_options:
             v = ALGO[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISION[v]
+        if k == "out_mode" and isinstance(v, str):
+            v = OUT_MODE[v]
         setattr(o, k, int(v))
     return o
 
@@ -291,6 +297,22 @@ def gwas_batch_handle(b, i):
 
 def gwas_destroy_batch(b) -> None:
     lib.gwas_destroy_batch(b)
+
+
+def gwas_wald_pvalues(wald, pval=None, stream=None):
+    """chi-square(1) upper-tail p-values of a float32 array or CUDA tensor of Wald statistics."""
+    wp, wdev = _ptr(wald)
+    if pval is None:
+        pval = wald.clone() if wdev else np.empty_like(wald)
+    pp, pdev = _ptr(pval)
+    if pdev != wdev:
+        raise ValueError("wald and pval must both be host or both be device arrays")
+    if wdev and stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    count = int(np.prod(wald.shape))
+    _check(lib.gwas_wald_pvalues(wp, count, pp, wdev, stream or None), "gwas_wald_pvalues")
+    return pval
 
 
 def gwas_sync(h) -> None:

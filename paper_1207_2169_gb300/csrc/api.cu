@@ -33,6 +33,8 @@ using namespace gw;
 
 struct gwas_handle_s {
   int dev = 0, n = 0, q = 0, p = 0, t = 0, algo = 0, prec = 0, validate = 0;
+  int out_snp = 0;  // GWAS_OUT_SNP: B holds (b_snp, se) per pair
+  int pw = 0;       // values per pair in B: p, or 2 with out_snp
   int block_snps = 0;
   int ldp = 0;  // n rounded up to 64: leading dimension of padded per-individual operands
   double setup_ms = 0.0;
@@ -241,6 +243,7 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     ta.Zt = h->Zt; ta.planes = h->planes; ta.ldp = h->ldp;
     ta.P = h->P; ta.b0 = h->b0;
     ta.block_snps = h->block_snps;
+    ta.out_snp = h->out_snp;
     ta.intercept = 1;
     for (int i = 0; i < n; ++i)
       if (XL[i] != 1.0) ta.intercept = 0;
@@ -325,11 +328,13 @@ void scan_block_simt(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* 
         CholScanArgs<double> a{n, q, t, j, h->Linv + (size_t)j * n * n, h->XLw + (size_t)j * q * n,
                                h->rw + (size_t)j * n, h->P + (size_t)j * q * q, h->b0 + (size_t)j * q,
                                XR, m, 0, B, wald, out_f64, 1e-12, h->flags};
+        a.out_snp = h->out_snp;
         chol_scan_simt<double>(s, a);
       } else {
         CholScanArgs<float> a{n, q, t, j, h->Linv32 + (size_t)j * n * n, h->XLw32 + (size_t)j * q * n,
                               h->rw32 + (size_t)j * n, h->P32 + (size_t)j * q * q, h->b032 + (size_t)j * q,
                               XR, m, 0, B, wald, out_f64, 1e-5f, h->flags};
+        a.out_snp = h->out_snp;
         chol_scan_simt<float>(s, a);
       }
     }
@@ -340,15 +345,17 @@ void scan_block_simt(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* 
   for (int64_t off = 0; off < m; off += cap) {
     const int64_t mm = m - off < cap ? m - off : cap;
     const size_t ob = out_f64 ? 8 : 4;
-    void* Bc = (char*)B + (size_t)off * t * (q + 1) * ob;
+    void* Bc = (char*)B + (size_t)off * t * h->pw * ob;
     void* Wc = wald ? (char*)wald + (size_t)off * t * ob : nullptr;
     if (h->prec == GWAS_PREC_FP64) {
       EigScanArgs<double> a{n, q, t, h->Zt, h->planes, h->ldp, h->P, h->b0, XR + off * n, mm, 0,
                             Bc, Wc, out_f64, 1e-12, (double*)h->xt, h->flags};
+      a.out_snp = h->out_snp;
       eig_scan_simt<double>(s, a);
     } else {
       EigScanArgs<float> a{n, q, t, h->Zt32, h->planes32, h->ldp, h->P32, h->b032, XR + off * n, mm,
                            0, Bc, Wc, out_f64, 1e-5f, (float*)h->xt, h->flags};
+      a.out_snp = h->out_snp;
       eig_scan_simt<float>(s, a);
     }
   }
@@ -359,7 +366,7 @@ void scan_block_simt(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* 
 // int8 rows: input in the other format is converted chunk by chunk into the handle's scratch.
 void scan_block(gwas_handle h, const void* X, int fmt, int64_t m, void* B, void* wald,
                 bool out_f64, cudaStream_t s) {
-  const int n = h->n, t = h->t, p = h->p;
+  const int n = h->n, t = h->t, p = h->pw;
   const size_t rbi = row_bytes_of(h, fmt);
   const size_t ob = out_f64 ? 8 : 4;
   if (h->prec == GWAS_PREC_SPLIT_BF16) {
@@ -417,7 +424,7 @@ gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_d
              "gwas_scan_f64 needs the FP64 or FP32 precision mode");
   DeviceGuard dg(h->dev);
   cudaStream_t s = (cudaStream_t)stream;
-  const int t = h->t, p = h->p;
+  const int t = h->t, p = h->pw;
   const size_t ob = out_f64 ? 8 : 4;
   const size_t rbi = row_bytes_of(h, fmt);
   if (h->validate)  // each call reports only its own genotypes
@@ -519,6 +526,7 @@ GW_API void gwas_default_options(gwas_options* opt) {
   opt->block_snps = 0;
   opt->validate_genotypes = 0;
   opt->device = 0;
+  opt->out_mode = GWAS_OUT_FULL;
 }
 
 GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q, const double* Y,
@@ -542,6 +550,8 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
     GW_REQUIRE(o.algo >= 0 && o.algo <= 2, GWAS_ERR_ARG, "bad algo %d", o.algo);
     GW_REQUIRE(o.precision >= 0 && o.precision <= 2, GWAS_ERR_ARG, "bad precision %d", o.precision);
     GW_REQUIRE(o.block_snps >= 0, GWAS_ERR_ARG, "block_snps < 0");
+    GW_REQUIRE(o.out_mode == GWAS_OUT_FULL || o.out_mode == GWAS_OUT_SNP, GWAS_ERR_ARG,
+               "bad out_mode %d", o.out_mode);
     h = new gwas_handle_s();
     h->dev = o.device;
     h->n = n;
@@ -551,6 +561,8 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
     h->algo = o.algo == GWAS_ALGO_AUTO ? (t == 1 ? GWAS_ALGO_CHOL : GWAS_ALGO_EIG) : o.algo;
     h->prec = o.precision;
     h->validate = o.validate_genotypes ? 1 : 0;
+    h->out_snp = o.out_mode == GWAS_OUT_SNP ? 1 : 0;
+    h->pw = h->out_snp ? 2 : h->p;
     h->ldp = (int)round_up(n, 64);
     if (h->algo == GWAS_ALGO_CHOL)
       GW_REQUIRE((double)t * n * n * 8.0 <= 64e9, GWAS_ERR_UNSUPPORTED,
@@ -627,6 +639,29 @@ GW_API gwas_status gwas_scan_packed(gwas_handle h, const uint8_t* G, int64_t m, 
 }
 
 GW_API int gwas_packed_row_bytes(int n) { return n >= 1 ? packed_row_bytes(n) : 0; }
+
+GW_API gwas_status gwas_wald_pvalues(const float* wald, int64_t count, float* pval, int on_device,
+                                     void* stream) {
+  try {
+    GW_REQUIRE(count >= 0, GWAS_ERR_ARG, "count < 0");
+    if (count == 0) return GWAS_OK;
+    GW_REQUIRE(wald != nullptr && pval != nullptr, GWAS_ERR_ARG, "null wald or pval");
+    if (on_device) {
+      wald_pvalues((cudaStream_t)stream, wald, count, pval);
+      return GWAS_OK;
+    }
+    for (int64_t e = 0; e < count; ++e) {
+      const double x = wald[e];
+      pval[e] = x >= 0.0 ? (float)erfc(sqrt(0.5 * x)) : (x == x ? 1.f : (float)x);
+    }
+    return GWAS_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  } catch (...) {
+    set_error("unexpected C++ exception in gwas_wald_pvalues");
+    return GWAS_ERR_CUDA;
+  }
+}
 
 GW_API gwas_status gwas_pack_genotypes(const int8_t* X, int64_t m, int n, uint8_t* G,
                                        int on_device, void* stream) {
@@ -784,10 +819,12 @@ GW_API gwas_status gwas_scan_static(gwas_handle h, const int8_t* XR, int64_t m, 
     if (h->prec == GWAS_PREC_FP64) {
       EigScanArgs<double> a{n, q, t, h->Zt, h->planes, h->ldp, h->P, h->b0, XR, m, 0,
                             B, wald, false, 1e-12, (double*)xt, h->flags};
+      a.out_snp = h->out_snp;
       eig_scan_simt<double>(s, a);
     } else {
       EigScanArgs<float> a{n, q, t, h->Zt32, h->planes32, h->ldp, h->P32, h->b032, XR, m, 0,
                            B, wald, false, 1e-5f, (float*)xt, h->flags};
+      a.out_snp = h->out_snp;
       eig_scan_simt<float>(s, a);
     }
     return GWAS_OK;

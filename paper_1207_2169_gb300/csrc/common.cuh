@@ -118,6 +118,7 @@ struct CholScanArgs {
   bool out_f64;
   T sing_tol;
   int* flags;
+  int out_snp = 0;           // B holds (b_snp, standard error) per pair instead of all p values
 };
 template <typename T> void chol_scan_simt(cudaStream_t s, const CholScanArgs<T>& a);
 
@@ -138,6 +139,7 @@ struct EigScanArgs {
   T sing_tol;
   T* xt;                     // scratch: m x ldp rotated genotypes
   int* flags;
+  int out_snp = 0;           // as CholScanArgs
 };
 template <typename T> void eig_scan_simt(cudaStream_t s, const EigScanArgs<T>& a);
 
@@ -159,5 +161,7 @@ void pack_genotypes(cudaStream_t s, const int8_t* x, int64_t m, int n, uint8_t* 
 void unpack_genotypes(cudaStream_t s, const uint8_t* in, int64_t m, int n, int8_t* out);
 void validate_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, int* flags);
 void snp_centres_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, float* mu);
+// pv[e] = erfc(sqrt(w[e] / 2)) (chi-square(1) upper tail); NaN stays NaN; in place allowed.
+void wald_pvalues(cudaStream_t s, const float* w, int64_t count, float* pv);
 
 }  // namespace gw

@@ -140,3 +140,24 @@ void snp_centres_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, flo
 }
 
 }  // namespace gw
+
+// ------------------------------------------------------------------------------------------
+// p-values of Wald statistics: the chi-square(1) upper tail erfc(sqrt(w / 2))
+// ------------------------------------------------------------------------------------------
+namespace gw {
+namespace {
+__global__ void pvalue_kernel(const float* __restrict__ w, int64_t count, float* __restrict__ pv) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float x = w[e];
+    pv[e] = x >= 0.f ? erfcf(sqrtf(0.5f * x)) : (x == x ? 1.f : x);
+  }
+}
+}  // namespace
+
+void wald_pvalues(cudaStream_t s, const float* w, int64_t count, float* pv) {
+  if (count <= 0) return;
+  pvalue_kernel<<<1184, 256, 0, s>>>(w, count, pv);
+  GW_CHECK_LAUNCH();
+}
+}  // namespace gw

@@ -27,7 +27,8 @@ constexpr int TK = 16;  // reduction chunk
 template <typename T>
 __device__ __forceinline__ void schur_store(int q, const T* __restrict__ P, const T* __restrict__ b0,
                                             const T* a, T c, T s, T tol, int64_t i, int j, int t,
-                                            void* B, void* wald, bool out_f64, int* flags) {
+                                            void* B, void* wald, bool out_f64, int* flags,
+                                            int out_snp) {
   const int p = q + 1;
   T v[QMAX];
   T aPa = 0;
@@ -59,18 +60,24 @@ __device__ __forceinline__ void schur_store(int q, const T* __restrict__ P, cons
     w = nanv;
     atomicAdd(&flags[FLAG_SINGULAR], 1);
   }
-  const int64_t o = (i * t + j) * p;
+  if (out_snp) {  // (b_snp, standard error 1 / sqrt(sigma)) per pair
+    const T se = sigma > tol * s ? (T)1 / sqrt(sigma) : (T)NAN;
+    out[0] = out[q];
+    out[1] = se;
+  }
+  const int pw = out_snp ? 2 : p;
+  const int64_t o = (i * t + j) * pw;
   if (out_f64) {
     double* Bd = (double*)B;
 #pragma unroll
     for (int k = 0; k <= QMAX; ++k)
-      if (k < p) Bd[o + k] = (double)out[k];
+      if (k < pw) Bd[o + k] = (double)out[k];
     if (wald) ((double*)wald)[i * t + j] = (double)w;
   } else {
     float* Bf = (float*)B;
 #pragma unroll
     for (int k = 0; k <= QMAX; ++k)
-      if (k < p) Bf[o + k] = (float)out[k];
+      if (k < pw) Bf[o + k] = (float)out[k];
     if (wald) ((float*)wald)[i * t + j] = (float)w;
   }
 }
@@ -166,7 +173,7 @@ __global__ void __launch_bounds__(256) chol_scan_kernel(CholScanArgs<T> a) {
 #pragma unroll
     for (int k = 0; k < QMAX; ++k) av[k] = k < q ? res[k][tid] : T(0);
     schur_store<T>(q, a.P, a.b0, av, res[q][tid], res[q + 1][tid], a.sing_tol,
-                   a.out_offset + s0 + tid, a.j, a.t, a.B, a.wald, a.out_f64, a.flags);
+                   a.out_offset + s0 + tid, a.j, a.t, a.B, a.wald, a.out_f64, a.flags, a.out_snp);
   }
 }
 
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(256) eig_reduce_kernel(EigScanArgs<T> a) {
     for (int k = 0; k < QMAX + 1; ++k)
       if (k == q) c = acc[u][k];
     schur_store<T>(q, P, b0, av, c, acc[u][QMAX + 1], a.sing_tol, a.out_offset + gs, j, t, a.B,
-                   a.wald, a.out_f64, a.flags);
+                   a.wald, a.out_f64, a.flags, a.out_snp);
   }
 }
 

@@ -19,13 +19,14 @@ struct TcSetupArgs {
   const double* b0;      // t x q
   int block_snps;        // EIG: SNPs per internal chunk (sizes the per-chunk scratch)
   int intercept;         // column 0 of X_L is all ones: SNPs are centred (CHOL, EIG)
+  int out_snp;           // B holds (b_snp, standard error) per pair instead of all p values
 };
 
 struct TcScanArgs {
   const uint8_t* G;  // m rows of packed_row_bytes(n) bytes, 2-bit genotype codes; device,
                      // 16-byte aligned
   int64_t m;
-  float* B;          // m x t x p device
+  float* B;          // m x t x p (or x 2 with out_snp) device
   float* wald;       // m x t device or NULL
   int* flags;
   int max_ctas;      // CTAs per kernel at most (0: one per SM); lets scans share the GPU

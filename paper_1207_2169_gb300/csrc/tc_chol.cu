@@ -407,9 +407,14 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
           v[k] = acc;
         }
         const double sigma = S - aPa;
-        const int pp = q + 1;
+        const int pp = p.out_snp ? 2 : q + 1;
         float* Bo = p.B + (snp * p.t + p.j) * pp;
-        if (sigma > 1e-5 * S) {
+        if (sigma > 1e-5 * S && p.out_snp) {
+          const double bs = (double)C / sigma;
+          Bo[0] = (float)bs;
+          Bo[1] = (float)(1.0 / sqrt(sigma));  // standard error: Var(b_snp) = 1 / sigma
+          if (p.W) p.W[snp * p.t + p.j] = (float)(bs * (double)C);
+        } else if (sigma > 1e-5 * S) {
           const double bs = (double)C / sigma;
 #pragma unroll
           double bl[QM];

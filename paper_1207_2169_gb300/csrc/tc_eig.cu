@@ -541,10 +541,16 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
                 wv = __int_as_float(0x7fc00000);
                 nsing += live;
               }
-              float* so = stgB + lane * RB + u * (QQ + 1);
-              if (QQ == 3) {
+              if (p.out_snp) {
+                // (b_snp, standard error 1 / sqrt(sigma)) per pair
+                float* so = stgB + lane * RB + 2 * u;
+                so[0] = o[QQ];
+                so[1] = sigma > 1e-5f * s ? rsqrtf(sigma) : __int_as_float(0x7fc00000);
+              } else if (QQ == 3) {
+                float* so = stgB + lane * RB + u * (QQ + 1);
                 *reinterpret_cast<float4*>(so) = make_float4(o[0], o[1], o[2], o[QQ]);
               } else {
+                float* so = stgB + lane * RB + u * (QQ + 1);
 #pragma unroll
                 for (int k = 0; k <= QQ; ++k) so[k] = o[k];
               }
@@ -554,7 +560,8 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
             // Write the warp's 32 SNP rows: each row holds nval (q+1) contiguous floats of B
             // and nval of wald; consecutive lanes take consecutive floats of a row.
             const int64_t jb = j0 + j8;
-            if (QQ == 3 && nval == 8) {
+            const int pw = p.out_snp ? 2 : q1;  // values per pair in B
+            if (QQ == 3 && nval == 8 && !p.out_snp) {
               // 8 float4 per row, 4 rows per instruction
 #pragma unroll
               for (int it = 0; it < 8; ++it) {
@@ -566,11 +573,11 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
                 }
               }
             } else {
-              const int nb_f = nval * q1;
+              const int nb_f = nval * pw;
               for (int e = lane; e < 32 * nb_f; e += 32) {
                 const int rr = e / nb_f, c = e - rr * nb_f;
                 const int64_t sn = row0 + rr;
-                if (sn < p.m) p.B[(sn * p.t + jb) * q1 + c] = stgB[rr * RB + c];
+                if (sn < p.m) p.B[(sn * p.t + jb) * pw + c] = stgB[rr * RB + c];
               }
             }
             if (p.W) {

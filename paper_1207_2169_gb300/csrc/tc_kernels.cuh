@@ -21,6 +21,7 @@ struct CholTcParams {
   int centre;         // nonzero: centre each SNP by the multiple of 1/64 nearest its mean
   const uint8_t* G;   // the launch's packed genotype rows (also read through mapG)
   int row_bytes;      // packed_row_bytes(n)
+  int out_snp;        // B holds (b_snp, standard error) per pair instead of all p values
   float* B;           // m x t x p
   float* W;           // m x t or NULL
   int* flags;
@@ -62,7 +63,8 @@ struct EigTcParams {
   const float* P;          // AC: t x q x q
   const float* b0;         // AC: t x q
   const float* mu;         // ROT, AC: per-SNP centring (multiples of 1/64) or NULL
-  float* B;                // AC: m x t x p
+  float* B;                // AC: m x t x p (or x 2 with out_snp)
+  int out_snp;             // AC: B holds (b_snp, standard error) per pair
   float* W;                // AC: m x t or NULL
   int* flags;
 };

@@ -6,15 +6,15 @@ from oracle import gls
 
 
 def run(g, c, algo, precision, XR=None, device=True, block_snps=0, f64=False, packed=False,
-        validate=False):
+        validate=False, out_mode="full"):
     """packed: pass the genotypes as packed rows (gwas_pack_genotypes on the host, then
     gwas_scan_packed) instead of int8 rows (gwas_scan)."""
     import torch
     XR = c.XR if XR is None else XR
     h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, algo=algo, precision=precision,
-                     block_snps=block_snps, validate_genotypes=int(validate))
+                     block_snps=block_snps, validate_genotypes=int(validate), out_mode=out_mode)
     try:
-        m, t, p = XR.shape[0], c.t, c.p
+        m, t, p = XR.shape[0], c.t, (2 if out_mode == "snp" else c.p)
         dt = torch.float64 if f64 else torch.float32
         dev = "cuda" if device else "cpu"
         X = np.ascontiguousarray(XR)

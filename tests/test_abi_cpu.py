@@ -156,3 +156,20 @@ def test_sync_and_selftest_argument_checks(g):
     assert g.lib.gwas_sync(None) == -1
     assert g.lib.gwas_selftest_timeout(0, 0) == -1
     assert g.lib.gwas_selftest_timeout(0, 20000) == -1
+
+
+def test_wald_pvalues_host(g):
+    from scipy.stats import chi2
+    w = np.array([0.0, 3.841458820694124, 6.634896601021214, 0.5, 25.0, np.nan], np.float32)
+    pv = g.gwas_wald_pvalues(w)
+    ref = chi2.sf(w.astype(np.float64), 1)
+    assert np.isnan(pv[-1])
+    assert np.allclose(pv[:-1], ref[:-1], rtol=1e-6, atol=0)
+    assert abs(pv[1] - 0.05) < 1e-7 and abs(pv[2] - 0.01) < 1e-7 and pv[0] == 1.0
+    assert g.lib.gwas_wald_pvalues(None, 3, None, 0, None) == -1
+    assert g.lib.gwas_wald_pvalues(None, 0, None, 0, None) == 0
+
+
+def test_out_mode_option(g):
+    o = g.gwas_default_options(out_mode="snp")
+    assert o.out_mode == 1 and g.gwas_default_options().out_mode == 0
