@@ -35,8 +35,6 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "(SNP x trait) GLS solves/s at <=1e-4 rel err vs FP64"
-KERNEL_SRC = {"chol": "paper_1207_2169_gb300/csrc/tc_chol.cu",
-              "eig": "paper_1207_2169_gb300/csrc/tc_eig.cu"}
 
 
 def _peaks():
@@ -191,13 +189,19 @@ def executed_flops(s, m):
     return rot + sq + ac
 
 
-def traffic_per_launch(algo, m):
-    """DRAM bytes of the dominant kernel from the committed ncu summary, scaled to m SNPs, or
-    None if the kernel source changed since the counters were taken."""
+def traffic_key(s):
+    """Entry of profiles/traffic.json for a workload: CHOL, or EIG at its trait count."""
+    return "chol" if s["algo"] == "chol" else f"eig_t{s['t']}"
+
+
+def traffic_per_launch(key, m):
+    """DRAM bytes of the dominant kernel (CHOL) or of the whole step (EIG) from the committed ncu
+    summary, scaled to m SNPs, or None if there is no capture for this workload or the kernel
+    source changed since the counters were taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            d = json.load(f)[algo]
-        with open(os.path.join(ROOT, KERNEL_SRC[algo]), "rb") as f:
+            d = json.load(f)[key]
+        with open(os.path.join(ROOT, d["source"]), "rb") as f:
             sha = hashlib.sha1(f.read()).hexdigest()
         if sha != d["source_sha1"]:
             return None
@@ -370,7 +374,7 @@ def roofline(res, precision):
     peak = peaks["bf16_tflops_sustained"]
     exe = executed_flops(s, m) / (ms * 1e-3) / 1e12
     return {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s",
-            "frac": alg / peak, "traffic": traffic_per_launch(s["algo"], m) if s["algo"] == "chol" else None,
+            "frac": alg / peak, "traffic": traffic_per_launch(traffic_key(s), m),
             "kernel": "chol_tc_kernel (whiten + reduce + Schur)" if s["algo"] == "chol"
             else "whole EIG step (rotation, s, a/c + Schur)",
             "peak_source": f"bf16_tflops_sustained, {kind} (MEASURED_PEAKS.json)",

@@ -215,10 +215,11 @@ void gwas_destroy_batch(gwas_batch b);
  * gwas_scan_static -- a scan that allocates no device memory.  (Not from the paper, which has
  * no counterpart: this is a deployment variant of gwas_scan.)
  *
- * Some callers cannot let a library call cudaMalloc during a scan: code that runs while a
- * stream is being captured into a CUDA graph (cudaMalloc is not a capturable operation),
- * latency-critical loops where cudaMalloc's implicit device synchronisation stalls other work,
- * and applications whose device memory is owned entirely by their own allocator or budget.
+ * Some callers cannot let a library call cudaMalloc during a scan: latency-critical loops,
+ * where cudaMalloc's implicit device synchronisation would stall work the caller has queued on
+ * other streams, and applications whose device memory is owned entirely by their own allocator
+ * or memory budget (a serving process that reserves HBM up front), where an allocation behind
+ * the allocator's back can fail or push another component out of memory.
  * gwas_scan may allocate on its first call (the EIG CUDA-core path's scratch for the rotated
  * genotypes Z^T X_R, and the host-streaming ring); this entry point never does.  It runs the
  * EIG CUDA-core scan (handles set up with algo EIG and precision FP64 or FP32) with that

@@ -1,6 +1,10 @@
 """gwas_scan_static: the scan entry point that allocates no device memory (its scratch is a
-fixed device array in the library).  Checked through the C ABI against gwas_scan on the same
-handle, on two calls in a row (the second finds the first call's data in the shared array).
+fixed 16 MiB device array in the library).  It exists for callers that cannot have a library
+call cudaMalloc in the middle of their work: latency-critical loops, which cudaMalloc's implicit
+device synchronisation would stall, and applications whose device memory belongs to their own
+allocator or budget.  Checked through the C ABI against gwas_scan on the same handle, on two
+calls in a row (the second finds the first call's data in the shared array), and for its
+rejection of blocks larger than the array.
 
 This file is collected last so that a failure here leaves every other test already run."""
 import ctypes
