@@ -111,8 +111,9 @@ gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q, const 
  *   stream: cudaStream_t (NULL = legacy default stream).
  * When XR and all outputs are on the device the call is asynchronous on `stream`.  Otherwise
  * XR is streamed through the handle's device ring in blocks of block_snps SNPs (host memory
- * pinned by the caller makes the copies asynchronous and overlapped) and the call returns when
- * the outputs are complete.
+ * pinned by the caller makes the copies asynchronous and overlapped; CHOL blocks alternate
+ * between `stream` and a second stream of the handle) and the call returns when the outputs
+ * are complete.
  */
 gwas_status gwas_scan(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_device, float* B,
                       float* wald, int out_on_device, void* stream);

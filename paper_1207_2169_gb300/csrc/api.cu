@@ -38,8 +38,12 @@ struct gwas_handle_s {
   int block_snps = 0;
   int ldp = 0;  // n rounded up to 64: leading dimension of padded per-individual operands
   double setup_ms = 0.0;
-  cudaStream_t st = nullptr, st_h2d = nullptr, st_d2h = nullptr;
-  cudaEvent_t ev_loaded[2] = {}, ev_computed[2] = {}, ev_drained[2] = {};
+  // st: setup and flag reads; st_lane: second compute stream of streamed scans; st_h2d /
+  // st_d2h: copies of streamed scans
+  cudaStream_t st = nullptr, st_lane = nullptr, st_h2d = nullptr, st_d2h = nullptr;
+  static constexpr int NRING = 4;  // streaming buffers at most (2, or 4 with two lanes)
+  cudaEvent_t ev_loaded[NRING] = {}, ev_computed[NRING] = {}, ev_drained[NRING] = {};
+  cudaEvent_t ev_begin = nullptr, ev_lane_done = nullptr;
   int* flags = nullptr;
   int* h_flags = nullptr;
   // per-trait null-model block (both algorithms)
@@ -54,10 +58,11 @@ struct gwas_handle_s {
   // scratch for the rotated block (EIG)
   void* xt = nullptr;
   int64_t xt_cap = 0;
-  // streaming ring (genotype bytes and outputs of one block per buffer)
-  uint8_t* ring[2] = {};
-  void* oring[2] = {};
+  // streaming ring (genotype bytes and outputs of one block per buffer); nring allocated
+  uint8_t* ring[NRING] = {};
+  void* oring[NRING] = {};
   size_t ring_bytes = 0, oring_bytes = 0;
+  int nring = 0;
   // format conversion scratch: packed rows for the tensor-core path (int8 input), int8 rows for
   // the CUDA-core paths (packed input)
   uint8_t* pk = nullptr;
@@ -105,17 +110,21 @@ void destroy_impl(gwas_handle h) {
   cudaGetDevice(&cur);
   cudaSetDevice(h->dev);
   if (h->st) cudaStreamSynchronize(h->st);
+  if (h->st_lane) cudaStreamSynchronize(h->st_lane);
   if (h->st_h2d) cudaStreamSynchronize(h->st_h2d);
   if (h->st_d2h) cudaStreamSynchronize(h->st_d2h);
   if (h->tc) tc_destroy(h->tc);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_flags) cudaFreeHost(h->h_flags);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < gwas_handle_s::NRING; ++i) {
     if (h->ev_loaded[i]) cudaEventDestroy(h->ev_loaded[i]);
     if (h->ev_computed[i]) cudaEventDestroy(h->ev_computed[i]);
     if (h->ev_drained[i]) cudaEventDestroy(h->ev_drained[i]);
   }
+  if (h->ev_begin) cudaEventDestroy(h->ev_begin);
+  if (h->ev_lane_done) cudaEventDestroy(h->ev_lane_done);
   if (h->st) cudaStreamDestroy(h->st);
+  if (h->st_lane) cudaStreamDestroy(h->st_lane);
   if (h->st_h2d) cudaStreamDestroy(h->st_h2d);
   if (h->st_d2h) cudaStreamDestroy(h->st_d2h);
   delete h;
@@ -438,33 +447,47 @@ gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_d
     }
     return GWAS_OK;
   }
-  // Streamed: double-buffered H2D of genotype blocks (copy stream), compute on `s`,
-  // D2H of each block's outputs (second copy stream).
+  // Streamed: H2D of genotype blocks through a ring of device buffers (copy stream), compute,
+  // D2H of each block's outputs (second copy stream).  A block whose scan uses no scratch of
+  // the handle (CHOL on the tensor cores from packed rows, or on CUDA cores from int8 rows)
+  // alternates between two compute streams: the next block's kernel then fills the SMs that
+  // the last wave of the current one leaves idle.  Other scans run their blocks in order on s.
+  const bool two = h->algo == GWAS_ALGO_CHOL &&
+                   (h->prec == GWAS_PREC_SPLIT_BF16 ? fmt == FMT_PACKED2 : fmt == FMT_INT8);
+  const int nring = two ? gwas_handle_s::NRING : 2;
   const int64_t blk = h->block_snps;
   const size_t gbytes = (size_t)blk * rbi, obytes = (size_t)blk * t * (p + 1) * 8;
-  if (h->ring_bytes < gbytes || h->oring_bytes < obytes) {
+  if (h->ring_bytes < gbytes || h->oring_bytes < obytes || h->nring < nring) {
     GW_CUDA(cudaStreamSynchronize(s));
+    GW_CUDA(cudaStreamSynchronize(h->st_lane));
     GW_CUDA(cudaStreamSynchronize(h->st_h2d));
     GW_CUDA(cudaStreamSynchronize(h->st_d2h));
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < gwas_handle_s::NRING; ++i) {
       dfree(h, h->ring[i]);
       dfree(h, h->oring[i]);
       h->ring[i] = nullptr;
       h->oring[i] = nullptr;
     }
+    h->nring = 0;
     const size_t gb = gbytes > h->ring_bytes ? gbytes : h->ring_bytes;
     const size_t obb = obytes > h->oring_bytes ? obytes : h->oring_bytes;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < nring; ++i) {
       h->ring[i] = (uint8_t*)dalloc(h, gb);
       h->oring[i] = dalloc(h, obb);
     }
+    h->nring = nring;
     h->ring_bytes = gb;
     h->oring_bytes = obb;
   }
   ensure_xt(h, blk);
+  if (two) {  // the second lane starts after the caller's prior work on s
+    GW_CUDA(cudaEventRecord(h->ev_begin, s));
+    GW_CUDA(cudaStreamWaitEvent(h->st_lane, h->ev_begin, 0));
+  }
   const int nblocks = ceil_div(m, blk);
   for (int b = 0; b < nblocks; ++b) {
-    const int buf = b & 1;
+    const int buf = b % nring;
+    cudaStream_t cs = two && (b & 1) ? h->st_lane : s;
     const int64_t off = (int64_t)b * blk;
     const int64_t mm = m - off < blk ? m - off : blk;
     const uint8_t* src = (const uint8_t*)X + off * rbi;
@@ -473,7 +496,7 @@ gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_d
       GW_CUDA(cudaMemcpyAsync(h->ring[buf], src, (size_t)mm * rbi, cudaMemcpyHostToDevice,
                               h->st_h2d));
       GW_CUDA(cudaEventRecord(h->ev_loaded[buf], h->st_h2d));
-      GW_CUDA(cudaStreamWaitEvent(s, h->ev_loaded[buf], 0));
+      GW_CUDA(cudaStreamWaitEvent(cs, h->ev_loaded[buf], 0));
       src = h->ring[buf];
     }
     void* Bo;
@@ -482,12 +505,12 @@ gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_d
       Bo = (char*)B + (size_t)off * t * p * ob;
       Wo = wald ? (char*)wald + (size_t)off * t * ob : nullptr;
     } else {
-      GW_CUDA(cudaStreamWaitEvent(s, h->ev_drained[buf], 0));
+      GW_CUDA(cudaStreamWaitEvent(cs, h->ev_drained[buf], 0));
       Bo = h->oring[buf];
       Wo = wald ? (char*)h->oring[buf] + (size_t)blk * t * p * ob : nullptr;
     }
-    scan_block(h, src, fmt, mm, Bo, Wo, out_f64, s);
-    GW_CUDA(cudaEventRecord(h->ev_computed[buf], s));
+    scan_block(h, src, fmt, mm, Bo, Wo, out_f64, cs);
+    GW_CUDA(cudaEventRecord(h->ev_computed[buf], cs));
     if (!out_dev) {
       GW_CUDA(cudaStreamWaitEvent(h->st_d2h, h->ev_computed[buf], 0));
       GW_CUDA(cudaMemcpyAsync((char*)B + (size_t)off * t * p * ob, Bo, (size_t)mm * t * p * ob,
@@ -497,6 +520,10 @@ gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_d
                                 cudaMemcpyDeviceToHost, h->st_d2h));
       GW_CUDA(cudaEventRecord(h->ev_drained[buf], h->st_d2h));
     }
+  }
+  if (two) {  // work after the call on s sees both lanes' results
+    GW_CUDA(cudaEventRecord(h->ev_lane_done, h->st_lane));
+    GW_CUDA(cudaStreamWaitEvent(s, h->ev_lane_done, 0));
   }
   GW_CUDA(cudaStreamSynchronize(s));
   GW_CUDA(cudaStreamSynchronize(h->st_h2d));
@@ -579,13 +606,16 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
     if (blk < 64) blk = 64;
     h->block_snps = (int)blk;
     GW_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    GW_CUDA(cudaStreamCreateWithFlags(&h->st_lane, cudaStreamNonBlocking));
     GW_CUDA(cudaStreamCreateWithFlags(&h->st_h2d, cudaStreamNonBlocking));
     GW_CUDA(cudaStreamCreateWithFlags(&h->st_d2h, cudaStreamNonBlocking));
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < gwas_handle_s::NRING; ++i) {
       GW_CUDA(cudaEventCreateWithFlags(&h->ev_loaded[i], cudaEventDisableTiming));
       GW_CUDA(cudaEventCreateWithFlags(&h->ev_computed[i], cudaEventDisableTiming));
       GW_CUDA(cudaEventCreateWithFlags(&h->ev_drained[i], cudaEventDisableTiming));
     }
+    GW_CUDA(cudaEventCreateWithFlags(&h->ev_begin, cudaEventDisableTiming));
+    GW_CUDA(cudaEventCreateWithFlags(&h->ev_lane_done, cudaEventDisableTiming));
     h->flags = (int*)dalloc(h, sizeof(int) * FLAG_COUNT);
     GW_CUDA(cudaMallocHost(&h->h_flags, sizeof(int) * FLAG_COUNT));
     setup_impl(h, Phi, XL, Y, h2, s2);

@@ -65,6 +65,19 @@ def test_packed_host_streamed(g, algo):
     assert _same(Bd, Bh) and _same(Wd, Wh)
 
 
+@pytest.mark.parametrize("prec,packed", [("split_bf16", True), ("fp64", False), ("fp32", False)])
+def test_chol_streamed_two_lanes_many_blocks(g, prec, packed):
+    """Host-streamed CHOL scans that use no scratch (tensor cores on packed rows, CUDA cores on
+    int8 rows) alternate their blocks between two compute streams through a ring of four device
+    buffers: 11 blocks of 256 SNPs (every buffer reused, a ragged last block) must give exactly
+    the results of one device-resident scan."""
+    c = synth.small_problem(33, n=257, q=2, m=2700, t=1)
+    f64 = prec == "fp64"
+    Bd, Wd, _ = run(g, c, "chol", prec, packed=packed, f64=f64)
+    Bh, Wh, _ = run(g, c, "chol", prec, packed=packed, f64=f64, device=False, block_snps=256)
+    assert _same(Bd, Bh) and _same(Wd, Wh)
+
+
 @pytest.mark.parametrize("algo,prec", [("chol", "split_bf16"), ("eig", "split_bf16"),
                                        ("eig", "fp32")])
 def test_packed_validation(g, algo, prec):
