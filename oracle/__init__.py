@@ -9,6 +9,8 @@ Modules:
            eigen algorithm (Algorithm 2), and the two sequence algorithms in the paper's
            order (Algorithm 3 CLAK-Chol, Algorithm 4 CLAK-Eig).
   exact -- the same definition in exact rational arithmetic (Fractions), for tiny problems.
+  estimate -- step 1 of the two-step method: per-trait (h^2, sigma^2) by maximum likelihood or
+           restricted maximum likelihood of the reduced model (Supplementary Note Section 1).
 """
 from .gls import (form_M, gls_chol, gls_eig, gls_grid, chol_sequence, eig_sequence,
                   wald_from, rel_err_b, rel_err_wald)
