@@ -22,8 +22,10 @@ Readings (also listed in the design doc):
   * Search interval h in [0, H2_MAX] (the model allows [0, 1]; setup of step 2 needs h < 1):
     the criterion on the grid h_g = (g / GRID) H2_MAX, g = 0..GRID, then a bounded scalar search
     between the best grid point's neighbours; the better of the two is the estimate.
-  * A trait fitted exactly by X_L (r^T H^-1 r <= 1e-20 y^T H^-1 y) has no finite estimate: NaN
-    for h and the criterion, 0 for sigma^2.
+  * A trait fitted exactly by X_L has no finite estimate: NaN for h and the criterion, 0 for
+    sigma^2.  "Exactly" is r^T H^-1 r <= 1e-12 y^T H^-1 y (R^2 within 1e-12 of 1), a margin
+    above the rounding of FP64 sums of n products, so that a computation of r^T H^-1 r as
+    y^T H^-1 y minus the fitted part reaches the same decision.
 """
 from __future__ import annotations
 
@@ -33,7 +35,7 @@ from scipy.optimize import minimize_scalar
 
 H2_MAX = 0.999
 GRID = 100
-EXACT_FIT = 1e-20  # r^T H^-1 r at most this fraction of y^T H^-1 y: y lies in the span of X_L
+EXACT_FIT = 1e-12  # r^T H^-1 r at most this fraction of y^T H^-1 y: y lies in the span of X_L
 ML, REML = 0, 1
 
 
