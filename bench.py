@@ -402,6 +402,48 @@ def launches_per_scan(s, precision, m, fmt):
     return sum(int(convert) + kernels(min(cc, m - off)) for off in range(0, m, cc))
 
 
+def measure_estimate(method="reml", sample=4):
+    """Step 1 (gwas_estimate) on the many-trait workload's cohort: n = 1,000, q = 3, t = 1,000
+    traits, h^2 and sigma^2 per trait by REML.  Device time from the call's own CUDA events: the
+    eigendecomposition of Phi with the rotation of X_L and Y (once per cohort), then the
+    per-trait search (168 evaluations of the criterion per trait).  The FP64 oracle runs on
+    `sample` evenly spaced traits for parity and as the CPU baseline."""
+    import paper_1207_2169_gb300 as g
+    from oracle import estimate as est
+    c = synth.make_cohort(2, m=0, with_genotypes=False)
+    n, q = c.XL.shape
+    t = c.Y.shape[1]
+    g.gwas_estimate(c.Phi, c.XL, c.Y[:, :8], method=method)  # warm-up
+    h2, s2, ll, ms = g.gwas_estimate(c.Phi, c.XL, c.Y, method=method)
+    sel = np.linspace(0, t - 1, sample).astype(int)
+    m = est.ML if method == "ml" else est.REML
+    t0 = time.perf_counter()
+    h2r, s2r, llr = est.estimate(c.Phi, c.XL, c.Y[:, sel], m)
+    cpu_s = time.perf_counter() - t0
+    total = float(ms[0] + ms[1])
+    # criterion evaluations: grid 101 + golden section 2 + 64 + final 1; per eigen-coordinate
+    # and evaluation q(q+1)/2 + q + 1 multiply-adds (2 flops each), one division, one logarithm
+    evals = 101 + 2 + 64 + 1
+    flops = t * evals * n * (2 * (q * (q + 1) // 2 + q + 1) + 2)
+    fp64_peak = 1250.0  # GFLOP/s, GB300 FP64 (nominal; no measured FP64 peak on this pool)
+    return {"config": {"workload": f"estimate_{method}_n{n}_t{t}", "n": n, "q": q, "t": t,
+                       "method": method, "grid": 101, "search": "golden section, 64 steps"},
+            "value": t / (total * 1e-3), "unit": "traits/s", "ms_per_step": total,
+            "ms_eigendecomposition": float(ms[0]), "ms_search": float(ms[1]),
+            "parity": {"max_rel_err_crit": float(np.max(np.abs(ll[sel] - llr) / np.abs(llr))),
+                       "max_abs_err_h2": float(np.max(np.abs(h2[sel] - h2r))),
+                       "max_rel_err_s2": float(np.max(np.abs(s2[sel] - s2r) / s2r)),
+                       "traits_checked": int(sample), "tolerance_crit": 1e-8},
+            "roofline": {"bound": "alu", "kernel": "estimate_kernel (per-trait search)",
+                         "achieved": flops / (ms[1] * 1e-3) / 1e9, "peak": fp64_peak,
+                         "unit": "GFLOP/s", "frac": flops / (ms[1] * 1e-3) / 1e9 / fp64_peak,
+                         "traffic": None, "peak_source": "nominal FP64 rate of GB300"},
+            "cpu_baseline": {"value": sample / cpu_s, "unit": "traits/s", "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{sample} of the {t} traits, FP64 oracle (H formed and "
+                                       f"factored per evaluation), {cpu_s:.1f} s"}}
+
+
 def run_ours(args, ws, rank, local):
     import torch
     torch.cuda.set_device(local)
@@ -427,6 +469,7 @@ def run_ours(args, ws, rank, local):
                           "roofline": roofline(o, args.precision),
                           "gpu_launches": k * launches_per_scan(o["s"], args.precision, o["m"],
                                                                 args.format)})
+        other.append(measure_estimate())
     if rank != 0:
         return
     line = {

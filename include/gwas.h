@@ -131,6 +131,32 @@ gwas_status gwas_scan_f64(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_
 gwas_status gwas_wald_pvalues(const float* wald, int64_t count, float* pval, int on_device,
                               void* stream);
 
+/* Criteria of gwas_estimate. */
+enum { GWAS_EST_ML = 0, GWAS_EST_REML = 1 };
+
+/*
+ * gwas_estimate -- step 1 of the two-step method (Supplementary Note Section 1, "Mixed Models
+ * for GWAS"; "Time complexity"): per trait, the variance components of the reduced model
+ * y_j = X_L beta + R, R ~ N(0, s2 (h2 Phi + (1 - h2) I)), that maximise its likelihood
+ * (GWAS_EST_ML) or restricted likelihood (GWAS_EST_REML), for gwas_setup's h2 and s2.
+ *   Phi, XL, Y, n, q, t: as in gwas_setup (host pointers, copied).  device: CUDA ordinal.
+ *   h2, s2: t outputs (host).  crit: t outputs or NULL, the maximised log-likelihood
+ *   (ML: -1/2 [n log(2 pi s2) + log|H| + n]; REML, the log-density of the error contrasts:
+ *   -1/2 [(n - q) log(2 pi s2) + log|H| + log|X_L^T H^-1 X_L| - log|X_L^T X_L| + (n - q)],
+ *   H = h2 Phi + (1 - h2) I).  ms: 2 outputs or NULL, device milliseconds of the
+ *   eigendecomposition of Phi with the rotation of X_L and Y, and of the search.
+ * Method (FP64 on the GPU): Phi = Z W Z^T; per trait the criterion, a weighted sum over the
+ * eigen-coordinates, on the grid h2 = (g / 100) 0.999, g = 0..100, then a golden-section search
+ * between the best grid point's neighbours.  h2 lies in [0, 0.999].  A trait that X_L fits
+ * exactly (r^T H^-1 r at most 1e-12 of y^T H^-1 y) gets h2 = NaN, s2 = 0, crit = NaN.  Returns GWAS_ERR_NOT_SPD if h Phi + (1 - h) I is
+ * not positive definite for some h in [0, 0.999], GWAS_ERR_SINGULAR for collinear covariates,
+ * GWAS_ERR_NOT_CONVERGED if the eigensolver fails.  Synchronous; allocates device memory for
+ * the duration of the call.
+ */
+gwas_status gwas_estimate(const double* Phi, int n, const double* XL, int q, const double* Y,
+                          int t, int method, int device, double* h2, double* s2, double* crit,
+                          double* ms);
+
 /*
  * Packed genotype format (a storage format for the same genotype matrix X_R of "Sequences of
  * GLS'", hard calls of m SNPs for n individuals): SNP i occupies gwas_packed_row_bytes(n) =

@@ -28,6 +28,7 @@ EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_packed_row_bytes", "gwas_pack_genotypes", "gwas_scan_packed",
            "gwas_setup_batch", "gwas_scan_batch", "gwas_batch_plan", "gwas_batch_handle",
            "gwas_destroy_batch", "gwas_sync", "gwas_selftest_timeout", "gwas_wald_pvalues",
+           "gwas_estimate",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
            "gwas_last_error", "gwas_destroy"]
 
@@ -69,6 +70,8 @@ def _load():
     for f in (lib.gwas_scan, lib.gwas_scan_f64, lib.gwas_scan_packed):
         f.argtypes = [vp, vp, i64, i32, vp, vp, i32, vp]
         f.restype = i32
+    lib.gwas_estimate.argtypes = [vp, i32, vp, i32, vp, i32, i32, i32, vp, vp, vp, vp]
+    lib.gwas_estimate.restype = i32
     lib.gwas_packed_row_bytes.argtypes = [i32]
     lib.gwas_packed_row_bytes.restype = i32
     lib.gwas_pack_genotypes.argtypes = [vp, i64, i32, vp, i32, vp]
@@ -191,6 +194,32 @@ def gwas_scan(h, XR, B, wald=None, stream=None, m=None):
 def gwas_scan_f64(h, XR, B, wald=None, stream=None, m=None):
     """As gwas_scan with float64 B and wald."""
     _scan(lib.gwas_scan_f64, "gwas_scan_f64", h, XR, XR.shape[0] if m is None else m, B, wald, stream)
+
+
+EST_METHOD = {"ml": 0, "reml": 1}
+
+
+def gwas_estimate(Phi, XL, Y, method="ml", device=0):
+    """Step 1: per trait, (h2, s2) maximising the ML or REML criterion of the reduced model.
+    Phi: n x n, XL: n x q, Y: n x t (or n).  Returns (h2, s2, crit, ms), ms = device
+    milliseconds of the eigendecomposition + rotation and of the search."""
+    Phi = np.asarray(Phi, dtype=np.float64)
+    n = Phi.shape[0]
+    XL = np.asarray(XL, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    if Y.ndim == 1:
+        Y = Y[:, None]
+    q, t = XL.shape[1], Y.shape[1]
+    Phi = _f64_fortran(Phi, (n, n), "Phi")
+    XL = _f64_fortran(XL, (n, q), "XL")
+    Y = _f64_fortran(Y, (n, t), "Y")
+    h2, s2, crit, ms = np.empty(t), np.empty(t), np.empty(t), np.empty(2)
+    m = EST_METHOD[method] if isinstance(method, str) else int(method)
+    st = lib.gwas_estimate(Phi.ctypes.data, n, XL.ctypes.data, q, Y.ctypes.data, t, m,
+                           int(device), h2.ctypes.data, s2.ctypes.data, crit.ctypes.data,
+                           ms.ctypes.data)
+    _check(st, "gwas_estimate")
+    return h2, s2, crit, ms
 
 
 def gwas_packed_row_bytes(n: int) -> int:

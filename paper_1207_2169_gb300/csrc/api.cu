@@ -693,6 +693,105 @@ GW_API gwas_status gwas_wald_pvalues(const float* wald, int64_t count, float* pv
   }
 }
 
+GW_API gwas_status gwas_estimate(const double* Phi, int n, const double* XL, int q,
+                                 const double* Y, int t, int method, int device, double* h2,
+                                 double* s2, double* crit, double* ms) {
+  std::vector<void*> mem;
+  auto alloc = [&](size_t bytes) -> double* {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+      throw Fail{GWAS_ERR_OOM};
+    }
+    mem.push_back(p);
+    return (double*)p;
+  };
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev[3] = {};
+  int prev = -1;
+  gwas_status st = GWAS_OK;
+  try {
+    GW_REQUIRE(Phi && XL && Y && h2 && s2, GWAS_ERR_ARG, "null input or output pointer");
+    GW_REQUIRE(n >= 2 && n <= 16384, GWAS_ERR_ARG, "n=%d outside [2,16384]", n);
+    GW_REQUIRE(q >= 1 && q <= 7 && q < n, GWAS_ERR_ARG, "q=%d outside [1,min(7,n-1)]", q);
+    GW_REQUIRE(t >= 1, GWAS_ERR_ARG, "t=%d < 1", t);
+    GW_REQUIRE(method == GWAS_EST_ML || method == GWAS_EST_REML, GWAS_ERR_ARG, "bad method %d",
+               method);
+    int ndev = 0;
+    GW_CUDA(cudaGetDeviceCount(&ndev));
+    GW_REQUIRE(device >= 0 && device < ndev, GWAS_ERR_ARG, "device %d not present", device);
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    GW_CUDA(cudaSetDevice(device));
+    GW_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    for (auto& e : ev) GW_CUDA(cudaEventCreate(&e));
+    const size_t nn = (size_t)n * n;
+    double* dPhi = alloc(nn * 8);
+    double* dXL = alloc((size_t)n * q * 8);
+    double* dY = alloc((size_t)n * t * 8);
+    double* Zt = alloc(nn * 8);
+    double* U = alloc(nn * 8);
+    double* w = alloc((size_t)n * 8);
+    double* XLt = alloc((size_t)q * n * 8);
+    double* Yt = alloc((size_t)t * n * 8);
+    double* out = alloc((size_t)3 * t * 8);
+    int* flags = (int*)alloc(sizeof(int) * FLAG_COUNT);
+    GW_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * FLAG_COUNT, s));
+    GW_CUDA(cudaMemcpyAsync(dPhi, Phi, nn * 8, cudaMemcpyHostToDevice, s));
+    GW_CUDA(cudaMemcpyAsync(dXL, XL, (size_t)n * q * 8, cudaMemcpyHostToDevice, s));
+    GW_CUDA(cudaMemcpyAsync(dY, Y, (size_t)n * t * 8, cudaMemcpyHostToDevice, s));
+    GW_CUDA(cudaEventRecord(ev[0], s));
+    // Phi = Z W Z^T; X~ = Z^T X_L (rows of XLt), y~_j = Z^T y_j (rows of Yt)
+    const int sweeps = jacobi_eig(s, n, dPhi, Zt, w, U, flags, 60);
+    GW_REQUIRE(sweeps >= 0, GWAS_ERR_NOT_CONVERGED, "Jacobi eigensolver did not converge in 60 sweeps");
+    gemm_f64(s, q, n, n, 1.0, dXL, n, 1, Zt, 1, n, 0.0, XLt, n, 1);
+    gemm_f64(s, t, n, n, 1.0, dY, n, 1, Zt, 1, n, 0.0, Yt, n, 1);
+    GW_CUDA(cudaEventRecord(ev[1], s));
+    // H(h) = h Phi + (1 - h) I must stay positive definite on the whole search interval
+    std::vector<double> hw(n);
+    GW_CUDA(cudaMemcpyAsync(hw.data(), w, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    GW_CUDA(cudaStreamSynchronize(s));
+    for (int r = 0; r < n; ++r)
+      GW_REQUIRE(0.999 * hw[r] + 0.001 > 0.0, GWAS_ERR_NOT_SPD,
+                 "h Phi + (1 - h) I is not positive definite for h up to 0.999 (eigenvalue %g)",
+                 hw[r]);
+    estimate_traits(s, n, q, t, method, w, XLt, Yt, out, out + t, out + 2 * t, flags);
+    GW_CUDA(cudaEventRecord(ev[2], s));
+    std::vector<double> hout((size_t)3 * t);
+    int hflags[FLAG_COUNT];
+    GW_CUDA(cudaMemcpyAsync(hout.data(), out, (size_t)3 * t * 8, cudaMemcpyDeviceToHost, s));
+    GW_CUDA(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+    GW_CUDA(cudaStreamSynchronize(s));
+    GW_REQUIRE(!hflags[FLAG_STL_SINGULAR], GWAS_ERR_SINGULAR,
+               "X_L^T H^-1 X_L is singular (collinear covariates)");
+    for (int j = 0; j < t; ++j) {
+      h2[j] = hout[j];
+      s2[j] = hout[t + j];
+      if (crit) crit[j] = hout[2 * t + j];
+    }
+    if (ms) {
+      float a = 0.f, b = 0.f;
+      GW_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+      GW_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
+      ms[0] = a;
+      ms[1] = b;
+    }
+  } catch (const Fail& f) {
+    st = f.st;
+  } catch (...) {
+    set_error("unexpected C++ exception in gwas_estimate");
+    st = GWAS_ERR_CUDA;
+  }
+  if (s) cudaStreamSynchronize(s);
+  for (void* p : mem) cudaFree(p);
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (s) cudaStreamDestroy(s);
+  if (prev >= 0) cudaSetDevice(prev);
+  return st;
+}
+
 GW_API gwas_status gwas_pack_genotypes(const int8_t* X, int64_t m, int n, uint8_t* G,
                                        int on_device, void* stream) {
   try {

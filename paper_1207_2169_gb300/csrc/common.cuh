@@ -65,6 +65,15 @@ void tri_inverse(cudaStream_t s, int n, const double* L, double* Linv, double* w
 int jacobi_eig(cudaStream_t s, int n, const double* Phi, double* Zt, double* w, double* U,
                int* flags, int max_sweeps);
 
+// Step 1 (estimate.cu): per trait j, the (h2, s2) maximising the ML (method 0) or REML (1)
+// criterion of the reduced model, from the eigenvalues w of Phi and the rotated covariates
+// XLt (q x n, row k = Z^T X_L[:, k]) and traits Yt (t x n, row j = Z^T y_j).  Writes h2, s2
+// and the criterion (t each, device).  Sets flags[FLAG_STL_SINGULAR] if X_L^T H^-1 X_L is
+// singular.
+void estimate_traits(cudaStream_t s, int n, int q, int t, int method, const double* w,
+                     const double* XLt, const double* Yt, double* h2, double* s2, double* crit,
+                     int* flags);
+
 // Per-trait null-model precompute shared by both algorithms (bordered-system top block).
 //   XLw (q x n, row k = k-th whitened covariate), yw (n) for each trait, weights d (n; all
 //   ones for CHOL, D_j for EIG).  Produces P = S_TL^-1 (q x q), b0 = P X_L^T D y, and the

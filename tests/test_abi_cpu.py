@@ -173,3 +173,23 @@ def test_wald_pvalues_host(g):
 def test_out_mode_option(g):
     o = g.gwas_default_options(out_mode="snp")
     assert o.out_mode == 1 and g.gwas_default_options().out_mode == 0
+
+
+def test_estimate_argument_checks(g):
+    """gwas_estimate rejects bad sizes, pointers and criteria before touching a device."""
+    n, q, t = 6, 2, 2
+    Phi = np.asfortranarray(np.eye(n))
+    XL = np.asfortranarray(np.ones((n, q)))
+    Y = np.asfortranarray(np.zeros((n, t)))
+    h2, s2 = np.zeros(t), np.zeros(t)
+    P, X, Yp, H, S = (a.ctypes.data for a in (Phi, XL, Y, h2, s2))
+    L = g.lib.gwas_estimate
+    assert L(None, n, X, q, Yp, t, 0, 0, H, S, None, None) == -1
+    assert L(P, n, X, q, Yp, t, 0, 0, None, S, None, None) == -1
+    assert L(P, 1, X, q, Yp, t, 0, 0, H, S, None, None) == -1
+    assert L(P, n, X, 0, Yp, t, 0, 0, H, S, None, None) == -1
+    assert L(P, n, X, n, Yp, t, 0, 0, H, S, None, None) == -1
+    assert L(P, n, X, 8, Yp, t, 0, 0, H, S, None, None) == -1
+    assert L(P, n, X, q, Yp, 0, 0, 0, H, S, None, None) == -1
+    assert L(P, n, X, q, Yp, t, 2, 0, H, S, None, None) == -1
+    assert g.EST_METHOD == {"ml": 0, "reml": 1}
