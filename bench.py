@@ -421,10 +421,12 @@ def measure_estimate(method="reml", sample=4):
     h2r, s2r, llr = est.estimate(c.Phi, c.XL, c.Y[:, sel], m)
     cpu_s = time.perf_counter() - t0
     total = float(ms[0] + ms[1])
-    # criterion evaluations: grid 101 + golden section 2 + 64 + final 1; per eigen-coordinate
-    # and evaluation q(q+1)/2 + q + 1 multiply-adds (2 flops each), one division, one logarithm
-    evals = 101 + 2 + 64 + 1
-    flops = t * evals * n * (2 * (q * (q + 1) // 2 + q + 1) + 2)
+    # algorithmic FP64 work of the search, per eigen-coordinate: the grid tables (101 points,
+    # once) q(q+1)/2 multiply-adds, a reciprocal and a logarithm; per trait, 101 grid points of
+    # q + 1 multiply-adds, then 2 + 64 + 1 search points of q(q+1)/2 + q + 1 multiply-adds, a
+    # reciprocal and a logarithm (a multiply-add counted as 2 flops)
+    full = 2 * (q * (q + 1) // 2 + q + 1) + 2
+    flops = 101 * n * (q * (q + 1) + 2) + t * n * (101 * 2 * (q + 1) + 67 * full)
     fp64_peak = 1250.0  # GFLOP/s, GB300 FP64 (nominal; no measured FP64 peak on this machine)
     return {"config": {"workload": f"estimate_{method}_n{n}_t{t}", "n": n, "q": q, "t": t,
                        "method": method, "grid": 101, "search": "golden section, 64 steps"},
@@ -612,9 +614,17 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip the EIG workload measurement")
+    ap.add_argument("--only-estimate", action="store_true",
+                    help="run only the step-1 (gwas_estimate) measurement and print its entry")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = _dist()
+    if args.only_estimate:
+        import torch
+        torch.cuda.set_device(local)
+        if rank == 0:
+            print(json.dumps(measure_estimate()), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
     elif args.workload == 4:

@@ -736,6 +736,7 @@ GW_API gwas_status gwas_estimate(const double* Phi, int n, const double* XL, int
     double* XLt = alloc((size_t)q * n * 8);
     double* Yt = alloc((size_t)t * n * 8);
     double* out = alloc((size_t)3 * t * 8);
+    double* tables = alloc(estimate_table_doubles(n) * 8);
     int* flags = (int*)alloc(sizeof(int) * FLAG_COUNT);
     GW_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * FLAG_COUNT, s));
     GW_CUDA(cudaMemcpyAsync(dPhi, Phi, nn * 8, cudaMemcpyHostToDevice, s));
@@ -756,7 +757,7 @@ GW_API gwas_status gwas_estimate(const double* Phi, int n, const double* XL, int
       GW_REQUIRE(0.999 * hw[r] + 0.001 > 0.0, GWAS_ERR_NOT_SPD,
                  "h Phi + (1 - h) I is not positive definite for h up to 0.999 (eigenvalue %g)",
                  hw[r]);
-    estimate_traits(s, n, q, t, method, w, XLt, Yt, out, out + t, out + 2 * t, flags);
+    estimate_traits(s, n, q, t, method, w, XLt, Yt, tables, out, out + t, out + 2 * t, flags);
     GW_CUDA(cudaEventRecord(ev[2], s));
     std::vector<double> hout((size_t)3 * t);
     int hflags[FLAG_COUNT];

@@ -68,11 +68,12 @@ int jacobi_eig(cudaStream_t s, int n, const double* Phi, double* Zt, double* w, 
 // Step 1 (estimate.cu): per trait j, the (h2, s2) maximising the ML (method 0) or REML (1)
 // criterion of the reduced model, from the eigenvalues w of Phi and the rotated covariates
 // XLt (q x n, row k = Z^T X_L[:, k]) and traits Yt (t x n, row j = Z^T y_j).  Writes h2, s2
-// and the criterion (t each, device).  Sets flags[FLAG_STL_SINGULAR] if X_L^T H^-1 X_L is
-// singular.
+// and the criterion (t each, device).  tables: device scratch of estimate_table_doubles(n)
+// doubles.  Sets flags[FLAG_STL_SINGULAR] if X_L^T H^-1 X_L is singular.
 void estimate_traits(cudaStream_t s, int n, int q, int t, int method, const double* w,
-                     const double* XLt, const double* Yt, double* h2, double* s2, double* crit,
-                     int* flags);
+                     const double* XLt, const double* Yt, double* tables, double* h2, double* s2,
+                     double* crit, int* flags);
+size_t estimate_table_doubles(int n);
 
 // Per-trait null-model precompute shared by both algorithms (bordered-system top block).
 //   XLw (q x n, row k = k-th whitened covariate), yw (n) for each trait, weights d (n; all
