@@ -79,6 +79,31 @@ def test_chol_streamed_two_lanes_many_blocks(g, prec, packed):
 
 
 @pytest.mark.parametrize("algo,prec", [("chol", "split_bf16"), ("eig", "split_bf16"),
+                                       ("eig", "fp32"), ("chol", "fp64")])
+def test_pinned_host_buffers_streamed(g, algo, prec):
+    """Page-locked host buffers (asynchronous copies through the handle's ring): with host input
+    and with device input, over several streamed blocks, the host outputs are exactly those of
+    the device-resident scan."""
+    import torch
+    c = synth.small_problem(35, n=200, q=3, m=1500, t=1 if algo == "chol" else 17)
+    f64 = prec == "fp64"
+    dt = torch.float64 if f64 else torch.float32
+    Bd, Wd, _ = run(g, c, algo, prec, f64=f64)
+    h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, algo=algo, precision=prec, block_snps=256)
+    try:
+        scan = g.gwas_scan_f64 if f64 else g.gwas_scan
+        X = torch.from_numpy(c.XR).pin_memory()
+        for xr in (X, X.cuda()):
+            B = torch.full((c.m, c.t, c.p), float("nan"), dtype=dt).pin_memory()
+            W = torch.full((c.m, c.t), float("nan"), dtype=dt).pin_memory()
+            scan(h, xr, B, W)
+            torch.cuda.synchronize()
+            assert _same(B.numpy().astype(np.float64), Bd) and _same(W.numpy().astype(np.float64), Wd)
+    finally:
+        g.gwas_destroy(h)
+
+
+@pytest.mark.parametrize("algo,prec", [("chol", "split_bf16"), ("eig", "split_bf16"),
                                        ("eig", "fp32")])
 def test_packed_validation(g, algo, prec):
     import torch
