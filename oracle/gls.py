@@ -109,14 +109,16 @@ def gls_eig(Phi, X, y, h2, s2, Z=None, w=None):
 # The 2-D problem (Eq. "probDef"), by definition
 # ---------------------------------------------------------------------------------------------
 
-def gls_grid(Phi, XL, XR, Y, h2, s2, snps=None, traits=None, chunk=512):
+def gls_grid(Phi, XL, XR, Y, h2, s2, snps=None, traits=None, chunk=512, full_var=False):
     """Eq. "probDef": for every (SNP i, trait j) solve b_ij = (X_i^T M_j^-1 X_i)^-1 X_i^T M_j^-1 y_j
     with X_i = [X_L | x_i], each problem by Algorithm 1.
 
     XR is (m, n) int8 (SNP-major), Y is (n, t).  The factor of M_j (Algorithm 1 lines 1-2) and
     L_j^-1 y_j (line 4) do not depend on i and are computed once per trait; line 3 whitens each
     X_i, solving for many SNPs' X_i in one triangular solve.  Returns
-    B (len(snps), len(traits), p), W (same, chi2) and Vd (same shape as B: diag of Var)."""
+    B (len(snps), len(traits), p), W (same, chi2) and Vd (same shape as B: diag of Var); with
+    full_var also V (len(snps), len(traits), p, p), the whole Var(b) = (X_i^T M_j^-1 X_i)^-1 of
+    Eq. "probDef"."""
     XL = np.asarray(XL, dtype=np.float64)
     n, q = XL.shape
     p = q + 1
@@ -124,6 +126,7 @@ def gls_grid(Phi, XL, XR, Y, h2, s2, snps=None, traits=None, chunk=512):
     traits = np.arange(Y.shape[1]) if traits is None else np.asarray(traits)
     B = np.empty((len(snps), len(traits), p))
     Vd = np.empty((len(snps), len(traits), p))
+    V = np.empty((len(snps), len(traits), p, p)) if full_var else None
     for jj, j in enumerate(traits):
         M = form_M(Phi, float(h2[j]), float(s2[j]))
         L = np.linalg.cholesky(M)
@@ -140,8 +143,10 @@ def gls_grid(Phi, XL, XR, Y, h2, s2, snps=None, traits=None, chunk=512):
             b, Var, _ = _small_spd_solve(S, r)
             B[s0:s0 + k, jj] = b
             Vd[s0:s0 + k, jj] = np.diagonal(Var, axis1=1, axis2=2)
+            if full_var:
+                V[s0:s0 + k, jj] = Var
     W = wald_from(B, Vd)
-    return B, W, Vd
+    return (B, W, Vd, V) if full_var else (B, W, Vd)
 
 
 def gls_pairs(Phi, XL, XR, Y, h2, s2, pairs):

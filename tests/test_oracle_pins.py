@@ -104,6 +104,38 @@ def test_ols_when_h2_is_zero():
             assert _rel(Vd[i, j], c.s2[j] * np.diag(XtXi)) < 1e-10
 
 
+def test_full_var_matches_exact_rational_and_ols():
+    """The whole Var(b) = (X^T M^-1 X)^-1 of every pair (Eq. "probDef"): equal to Gauss-Jordan in
+    rational arithmetic (oracle.exact) on a tiny problem, and to sigma^2 (X^T X)^-1 when h2 = 0."""
+    from fractions import Fraction
+    from oracle import exact
+    rs = np.random.default_rng(5)
+    n, q, m, t = 7, 2, 3, 2
+    A = rs.integers(-3, 4, size=(n, n))
+    Phi = [[Fraction(int(v), 9) for v in row] for row in (A @ A.T + 9 * np.eye(n, dtype=int))]
+    XL = [[1, int(rs.integers(-2, 3))] for _ in range(n)]
+    XR = [[int(v) for v in rs.integers(0, 3, size=n)] for _ in range(m)]
+    Y = [[int(v) for v in rs.integers(-5, 6, size=t)] for _ in range(n)]
+    h2, s2 = [Fraction(1, 3), Fraction(3, 5)], [Fraction(2), Fraction(1, 2)]
+    _, Ve, _ = exact.grid_exact(Phi, XL, XR, Y, h2, s2)
+    f = lambda x: np.array(x, dtype=np.float64)
+    B, W, Vd, V = gls.gls_grid(f([[float(v) for v in r] for r in Phi]), f(XL), np.array(XR, np.int8),
+                               f(Y), f([float(v) for v in h2]), f([float(v) for v in s2]),
+                               full_var=True)
+    for i in range(m):
+        for j in range(t):
+            ref = np.array([[float(v) for v in row] for row in Ve[i][j]])
+            assert np.max(np.abs(V[i, j] - ref)) <= 1e-12 * np.max(np.abs(ref))
+            assert np.allclose(np.diagonal(V[i, j]), Vd[i, j], rtol=0, atol=0)
+    c = _problem(t=2, h2=0.0, s2=[1.7, 0.6])
+    _, _, _, V = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, full_var=True)
+    for i in range(c.m):
+        X = np.c_[c.XL, c.XR[i].astype(float)]
+        XtXi = np.linalg.inv(X.T @ X)
+        for j in range(c.t):
+            assert np.max(np.abs(V[i, j] - c.s2[j] * XtXi)) <= 1e-10 * np.max(np.abs(c.s2[j] * XtXi))
+
+
 def test_ols_when_phi_is_identity():
     c = _problem(t=2)
     I = np.eye(c.n)
