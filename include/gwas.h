@@ -67,11 +67,14 @@ enum { GWAS_ALGO_AUTO = 0, GWAS_ALGO_CHOL = 1, GWAS_ALGO_EIG = 2 };
  *               accumulation is FP32; the p x p Schur solve runs in FP32.                     */
 enum { GWAS_PREC_FP64 = 0, GWAS_PREC_FP32 = 1, GWAS_PREC_SPLIT_BF16 = 2 };
 
-/* What a scan writes per (SNP, trait) pair into B (wald is the same in both):
+/* What a scan writes per (SNP, trait) pair into B (wald is the same in all modes):
  *   FULL  all p coefficients: B is m x t x p;
  *   SNP   the SNP effect and its standard error, sqrt(Var(b)[p-1][p-1]) = 1 / sqrt(sigma):
- *         B is m x t x 2 (GWAS summary statistics; with gwas_wald_pvalues, the p-values). */
-enum { GWAS_OUT_FULL = 0, GWAS_OUT_SNP = 1 };
+ *         B is m x t x 2 (GWAS summary statistics; with gwas_wald_pvalues, the p-values);
+ *   VAR   the p coefficients, then the whole Var(b) = (X_i^T M_j^-1 X_i)^-1 of Eq. "probDef"
+ *         as its upper triangle row by row, (0,0), (0,1), .., (0,p-1), (1,1), .., (p-1,p-1):
+ *         B is m x t x (p + p(p+1)/2).  A singular pair has NaN in all of them. */
+enum { GWAS_OUT_FULL = 0, GWAS_OUT_SNP = 1, GWAS_OUT_VAR = 2 };
 
 typedef struct {
   int algo;               /* GWAS_ALGO_*; AUTO = CHOL when t == 1, else EIG                   */

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libgwasgb.so")
 
 ALGO = {"auto": 0, "chol": 1, "eig": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "split_bf16": 2}
-OUT_MODE = {"full": 0, "snp": 1}
+OUT_MODE = {"full": 0, "snp": 1, "var": 2}
 STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ERR_CUDA",
           -4: "GWAS_ERR_OOM", -5: "GWAS_ERR_UNSUPPORTED", -6: "GWAS_ERR_GENOTYPE",
           -7: "GWAS_ERR_TIMEOUT", -8: "GWAS_ERR_SINGULAR", -9: "GWAS_ERR_NOT_CONVERGED"}

@@ -34,7 +34,8 @@ using namespace gw;
 struct gwas_handle_s {
   int dev = 0, n = 0, q = 0, p = 0, t = 0, algo = 0, prec = 0, validate = 0;
   int out_snp = 0;  // GWAS_OUT_SNP: B holds (b_snp, se) per pair
-  int pw = 0;       // values per pair in B: p, or 2 with out_snp
+  int out_var = 0;  // GWAS_OUT_VAR: B holds b, then Var(b) packed (p(p+1)/2) per pair
+  int pw = 0;       // values per pair in B: p, 2 with out_snp, p + p(p+1)/2 with out_var
   int block_snps = 0;
   int ldp = 0;  // n rounded up to 64: leading dimension of padded per-individual operands
   double setup_ms = 0.0;
@@ -253,6 +254,7 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     ta.P = h->P; ta.b0 = h->b0;
     ta.block_snps = h->block_snps;
     ta.out_snp = h->out_snp;
+    ta.out_var = h->out_var;
     ta.intercept = 1;
     for (int i = 0; i < n; ++i)
       if (XL[i] != 1.0) ta.intercept = 0;
@@ -338,12 +340,14 @@ void scan_block_simt(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* 
                                h->rw + (size_t)j * n, h->P + (size_t)j * q * q, h->b0 + (size_t)j * q,
                                XR, m, 0, B, wald, out_f64, 1e-12, h->flags};
         a.out_snp = h->out_snp;
+        a.out_var = h->out_var;
         chol_scan_simt<double>(s, a);
       } else {
         CholScanArgs<float> a{n, q, t, j, h->Linv32 + (size_t)j * n * n, h->XLw32 + (size_t)j * q * n,
                               h->rw32 + (size_t)j * n, h->P32 + (size_t)j * q * q, h->b032 + (size_t)j * q,
                               XR, m, 0, B, wald, out_f64, 1e-5f, h->flags};
         a.out_snp = h->out_snp;
+        a.out_var = h->out_var;
         chol_scan_simt<float>(s, a);
       }
     }
@@ -360,11 +364,13 @@ void scan_block_simt(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* 
       EigScanArgs<double> a{n, q, t, h->Zt, h->planes, h->ldp, h->P, h->b0, XR + off * n, mm, 0,
                             Bc, Wc, out_f64, 1e-12, (double*)h->xt, h->flags};
       a.out_snp = h->out_snp;
+      a.out_var = h->out_var;
       eig_scan_simt<double>(s, a);
     } else {
       EigScanArgs<float> a{n, q, t, h->Zt32, h->planes32, h->ldp, h->P32, h->b032, XR + off * n, mm,
                            0, Bc, Wc, out_f64, 1e-5f, (float*)h->xt, h->flags};
       a.out_snp = h->out_snp;
+      a.out_var = h->out_var;
       eig_scan_simt<float>(s, a);
     }
   }
@@ -577,8 +583,9 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
     GW_REQUIRE(o.algo >= 0 && o.algo <= 2, GWAS_ERR_ARG, "bad algo %d", o.algo);
     GW_REQUIRE(o.precision >= 0 && o.precision <= 2, GWAS_ERR_ARG, "bad precision %d", o.precision);
     GW_REQUIRE(o.block_snps >= 0, GWAS_ERR_ARG, "block_snps < 0");
-    GW_REQUIRE(o.out_mode == GWAS_OUT_FULL || o.out_mode == GWAS_OUT_SNP, GWAS_ERR_ARG,
-               "bad out_mode %d", o.out_mode);
+    GW_REQUIRE(o.out_mode == GWAS_OUT_FULL || o.out_mode == GWAS_OUT_SNP ||
+                   o.out_mode == GWAS_OUT_VAR,
+               GWAS_ERR_ARG, "bad out_mode %d", o.out_mode);
     h = new gwas_handle_s();
     h->dev = o.device;
     h->n = n;
@@ -589,7 +596,8 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
     h->prec = o.precision;
     h->validate = o.validate_genotypes ? 1 : 0;
     h->out_snp = o.out_mode == GWAS_OUT_SNP ? 1 : 0;
-    h->pw = h->out_snp ? 2 : h->p;
+    h->out_var = o.out_mode == GWAS_OUT_VAR ? 1 : 0;
+    h->pw = h->out_snp ? 2 : h->out_var ? h->p + h->p * (h->p + 1) / 2 : h->p;
     h->ldp = (int)round_up(n, 64);
     if (h->algo == GWAS_ALGO_CHOL)
       GW_REQUIRE((double)t * n * n * 8.0 <= 64e9, GWAS_ERR_UNSUPPORTED,
@@ -599,9 +607,10 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
     GW_CUDA(cudaGetDeviceCount(&ndev));
     GW_REQUIRE(h->dev >= 0 && h->dev < ndev, GWAS_ERR_ARG, "device %d not present", h->dev);
     DeviceGuard dg(h->dev);
-    // default block: CHOL 64 Ki SNPs; EIG bounded so a block's FP64 outputs stay <= 2 GB
+    // default block: CHOL 64 Ki SNPs; EIG bounded so a block's FP64 outputs (B and wald)
+    // stay <= 2 GB
     int64_t blk = o.block_snps > 0 ? o.block_snps : (h->algo == GWAS_ALGO_CHOL ? 65536 : 32768);
-    const int64_t out_cap = (int64_t)(2e9 / ((double)t * (q + 2) * 8));
+    const int64_t out_cap = (int64_t)(2e9 / ((double)t * (h->pw + 1) * 8));
     if (blk > out_cap) blk = out_cap;
     if (blk < 64) blk = 64;
     h->block_snps = (int)blk;
@@ -950,11 +959,13 @@ GW_API gwas_status gwas_scan_static(gwas_handle h, const int8_t* XR, int64_t m, 
       EigScanArgs<double> a{n, q, t, h->Zt, h->planes, h->ldp, h->P, h->b0, XR, m, 0,
                             B, wald, false, 1e-12, (double*)xt, h->flags};
       a.out_snp = h->out_snp;
+      a.out_var = h->out_var;
       eig_scan_simt<double>(s, a);
     } else {
       EigScanArgs<float> a{n, q, t, h->Zt32, h->planes32, h->ldp, h->P32, h->b032, XR, m, 0,
                            B, wald, false, 1e-5f, (float*)xt, h->flags};
       a.out_snp = h->out_snp;
+      a.out_var = h->out_var;
       eig_scan_simt<float>(s, a);
     }
     return GWAS_OK;

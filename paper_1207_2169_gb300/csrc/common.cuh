@@ -129,6 +129,7 @@ struct CholScanArgs {
   T sing_tol;
   int* flags;
   int out_snp = 0;           // B holds (b_snp, standard error) per pair instead of all p values
+  int out_var = 0;           // B holds the p values, then the p(p+1)/2 of Var(b) (packed upper)
 };
 template <typename T> void chol_scan_simt(cudaStream_t s, const CholScanArgs<T>& a);
 
@@ -150,6 +151,7 @@ struct EigScanArgs {
   T* xt;                     // scratch: m x ldp rotated genotypes
   int* flags;
   int out_snp = 0;           // as CholScanArgs
+  int out_var = 0;
 };
 template <typename T> void eig_scan_simt(cudaStream_t s, const EigScanArgs<T>& a);
 

@@ -28,7 +28,7 @@ template <typename T>
 __device__ __forceinline__ void schur_store(int q, const T* __restrict__ P, const T* __restrict__ b0,
                                             const T* a, T c, T s, T tol, int64_t i, int j, int t,
                                             void* B, void* wald, bool out_f64, int* flags,
-                                            int out_snp) {
+                                            int out_snp, int out_var) {
   const int p = q + 1;
   T v[QMAX];
   T aPa = 0;
@@ -65,20 +65,47 @@ __device__ __forceinline__ void schur_store(int q, const T* __restrict__ P, cons
     out[0] = out[q];
     out[1] = se;
   }
-  const int pw = out_snp ? 2 : p;
+  const int pw = out_snp ? 2 : out_var ? p + p * (p + 1) / 2 : p;
   const int64_t o = (i * t + j) * pw;
   if (out_f64) {
     double* Bd = (double*)B;
 #pragma unroll
     for (int k = 0; k <= QMAX; ++k)
-      if (k < pw) Bd[o + k] = (double)out[k];
+      if (k < (out_snp ? 2 : p)) Bd[o + k] = (double)out[k];
     if (wald) ((double*)wald)[i * t + j] = (double)w;
   } else {
     float* Bf = (float*)B;
 #pragma unroll
     for (int k = 0; k <= QMAX; ++k)
-      if (k < pw) Bf[o + k] = (float)out[k];
+      if (k < (out_snp ? 2 : p)) Bf[o + k] = (float)out[k];
     if (wald) ((float*)wald)[i * t + j] = (float)w;
+  }
+  if (out_var) {
+    // Var(b) = S^-1 of the bordered S = [[S_TL, a], [a^T, s]]: [[P + v v^T / sigma, -v / sigma],
+    // [-v^T / sigma, 1 / sigma]], packed upper triangle row by row after the p coefficients
+    // (constant loop bounds keep v[] in registers)
+    const bool ok = sigma > tol * s;
+    const T inv = ok ? (T)1 / sigma : (T)NAN;
+#pragma unroll
+    for (int r = 0; r <= QMAX; ++r)
+#pragma unroll
+      for (int cc = r; cc <= QMAX; ++cc) {
+        if (r >= p || cc >= p) continue;
+        const int e = p + r * p - r * (r - 1) / 2 + (cc - r);
+        const T vr = v[r < QMAX ? r : QMAX - 1], vcc = v[cc < QMAX ? cc : QMAX - 1];
+        T vrc;
+        if (cc < q)
+          vrc = P[r * q + cc] + vr * vcc * inv;
+        else if (r < q)
+          vrc = -vr * inv;
+        else
+          vrc = inv;
+        if (!ok) vrc = (T)NAN;
+        if (out_f64)
+          ((double*)B)[o + e] = (double)vrc;
+        else
+          ((float*)B)[o + e] = (float)vrc;
+      }
   }
 }
 
@@ -173,7 +200,8 @@ __global__ void __launch_bounds__(256) chol_scan_kernel(CholScanArgs<T> a) {
 #pragma unroll
     for (int k = 0; k < QMAX; ++k) av[k] = k < q ? res[k][tid] : T(0);
     schur_store<T>(q, a.P, a.b0, av, res[q][tid], res[q + 1][tid], a.sing_tol,
-                   a.out_offset + s0 + tid, a.j, a.t, a.B, a.wald, a.out_f64, a.flags, a.out_snp);
+                   a.out_offset + s0 + tid, a.j, a.t, a.B, a.wald, a.out_f64, a.flags, a.out_snp,
+                   a.out_var);
   }
 }
 
@@ -287,7 +315,7 @@ __global__ void __launch_bounds__(256) eig_reduce_kernel(EigScanArgs<T> a) {
     for (int k = 0; k < QMAX + 1; ++k)
       if (k == q) c = acc[u][k];
     schur_store<T>(q, P, b0, av, c, acc[u][QMAX + 1], a.sing_tol, a.out_offset + gs, j, t, a.B,
-                   a.wald, a.out_f64, a.flags, a.out_snp);
+                   a.wald, a.out_f64, a.flags, a.out_snp, a.out_var);
   }
 }
 

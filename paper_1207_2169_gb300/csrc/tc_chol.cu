@@ -407,7 +407,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
           v[k] = acc;
         }
         const double sigma = S - aPa;
-        const int pp = p.out_snp ? 2 : q + 1;
+        const int pp = p.out_snp ? 2 : p.out_var ? (q + 1) + (q + 1) * (q + 2) / 2 : q + 1;
         float* Bo = p.B + (snp * p.t + p.j) * pp;
         if (sigma > 1e-5 * S && p.out_snp) {
           const double bs = (double)C / sigma;
@@ -427,6 +427,28 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
             if (k < q) Bo[k] = (float)bl[k];
           Bo[q] = (float)bs;
           if (p.W) p.W[snp * p.t + p.j] = (float)(bs * (double)C);
+          if (p.out_var) {
+            // Var(b) of the centred design, [[P + v v^T / sigma, -v / sigma], [., 1 / sigma]],
+            // mapped back to the SNP x = (x - mu) + mu 1: b = T b_c with T = I - mu e_0 e_q^T,
+            // so Var(b) = T Var_c T^T changes only row and column 0 (the intercept).  Packed
+            // upper triangle, row by row, after the q + 1 coefficients.
+            const double inv = 1.0 / sigma, mu = p.centre ? (double)mu_cur : 0.0;
+            auto vk = [&](int k) { return v[k < QM ? k : QM - 1]; };  // every index in bounds
+            auto vc = [&](int r, int c) -> double {  // r <= c
+              if (c < q) return __ldg(&p.P[r * q + c]) + vk(r) * vk(c) * inv;
+              return r < q ? -vk(r) * inv : inv;
+            };
+#pragma unroll
+            for (int r = 0; r <= QM; ++r)
+#pragma unroll
+              for (int c = r; c <= QM; ++c) {
+                if (r > q || c > q) continue;
+                double x = vc(r, c);
+                if (r == 0) x -= mu * (c < q ? -vk(c) * inv : inv);  // - mu Var_c[q][c]
+                if (r == 0 && c == 0) x -= mu * vc(0, q) - mu * mu * inv;
+                Bo[(q + 1) + r * (q + 1) - r * (r - 1) / 2 + (c - r)] = (float)x;
+              }
+          }
         } else {
           for (int k = 0; k < pp; ++k) Bo[k] = __int_as_float(0x7fc00000);
           if (p.W) p.W[snp * p.t + p.j] = __int_as_float(0x7fc00000);

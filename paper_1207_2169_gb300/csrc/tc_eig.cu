@@ -126,7 +126,9 @@ __device__ __forceinline__ void tmem_ld_cols<8>(uint32_t taddr, uint32_t (&r)[8]
                : "r"(taddr));
 }
 
-template <int EPI, int QQ>
+// VAR (AC only): the epilogue writes b and the packed Var(b) per pair (GWAS_OUT_VAR), compiled
+// apart so that the other output modes keep their register allocation.
+template <int EPI, int QQ, bool VAR = false>
 __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
     eig_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapG, const EigTcParams p) {
@@ -541,6 +543,36 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
                 wv = __int_as_float(0x7fc00000);
                 nsing += live;
               }
+              if (VAR) {
+                // b, then Var(b) as a packed upper triangle, written by this thread straight to
+                // its SNP's row (no staging): [[P + v v^T / sigma, -v / sigma], [., 1 / sigma]]
+                // of the centred SNP, mapped back by b = T b_c, T = I - mu e_0 e_q^T, which
+                // changes only row and column 0 (the intercept)
+                if (live) {
+                  constexpr int PWV = (QQ + 1) + (QQ + 1) * (QQ + 2) / 2;
+                  float* dst = p.B + (snp * p.t + (j0 + j8 + u)) * PWV;
+                  const bool okp = sigma > 1e-5f * s;
+                  const float inv = 1.f / sigma, mu = p.mu ? mu_snp : 0.f;
+#pragma unroll
+                  for (int k = 0; k <= QQ; ++k) dst[k] = o[k];
+#pragma unroll
+                  for (int r = 0; r <= QQ; ++r)
+#pragma unroll
+                    for (int c = r; c <= QQ; ++c) {
+                      float x;
+                      if (c < QQ)
+                        x = Pj[r * QQ + c] + vq[r] * vq[c] * inv;
+                      else
+                        x = r < QQ ? -vq[r] * inv : inv;
+                      if (r == 0) x -= mu * (c < QQ ? -vq[c] * inv : inv);
+                      if (r == 0 && c == 0) x -= mu * (-vq[0] * inv) - mu * mu * inv;
+                      dst[(QQ + 1) + r * (QQ + 1) - r * (r - 1) / 2 + (c - r)] =
+                          okp ? x : __int_as_float(0x7fc00000);
+                    }
+                  if (p.W) p.W[snp * p.t + j0 + j8 + u] = wv;
+                }
+                continue;
+              }
               if (p.out_snp) {
                 // (b_snp, standard error 1 / sqrt(sigma)) per pair
                 float* so = stgB + lane * RB + 2 * u;
@@ -556,6 +588,7 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
               }
               stgW[lane * 9 + u] = wv;
             }
+            if (VAR) continue;  // written above, per thread
             __syncwarp();
             // Write the warp's 32 SNP rows: each row holds nval (q+1) contiguous floats of B
             // and nval of wald; consecutive lanes take consecutive floats of a row.
@@ -622,22 +655,36 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
   }
 }
 
-template <int EPI, int QQ>
+template <int EPI, int QQ, bool VAR = false>
 void prepare_one() {
   constexpr size_t SMEM = smem_of(EPI, QQ);
   static_assert(SMEM <= 232448, "shared memory over the sm_103 opt-in limit");
-  GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)SMEM));
+  GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QQ, VAR>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
 }
 
-template <int EPI, int QQ>
+template <int EPI, int QQ, bool VAR = false>
 void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
                 const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {
   constexpr size_t SMEM = smem_of(EPI, QQ);
   const int64_t work = ((p.m + BM - 1) / BM) * p.nblk;
   const unsigned grid = (unsigned)(work < num_sms ? work : num_sms);
-  eig_tc_kernel<EPI, QQ><<<grid, 32 * nwarps_of(EPI, QQ), SMEM, s>>>(mapA, mapB, mapG, p);
+  eig_tc_kernel<EPI, QQ, VAR><<<grid, 32 * nwarps_of(EPI, QQ), SMEM, s>>>(mapA, mapB, mapG, p);
   GW_CHECK_LAUNCH();
+}
+
+template <bool VAR>
+void launch_ac(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
+               const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {
+  switch (p.q) {
+    case 1: launch_one<EPI_AC, 1, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 2: launch_one<EPI_AC, 2, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 3: launch_one<EPI_AC, 3, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 4: launch_one<EPI_AC, 4, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 5: launch_one<EPI_AC, 5, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 6: launch_one<EPI_AC, 6, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
+    default: launch_one<EPI_AC, 7, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
+  }
 }
 
 }  // namespace
@@ -658,6 +705,13 @@ void eig_tc_prepare() {
   prepare_one<EPI_AC, 5>();
   prepare_one<EPI_AC, 6>();
   prepare_one<EPI_AC, 7>();
+  prepare_one<EPI_AC, 1, true>();
+  prepare_one<EPI_AC, 2, true>();
+  prepare_one<EPI_AC, 3, true>();
+  prepare_one<EPI_AC, 4, true>();
+  prepare_one<EPI_AC, 5, true>();
+  prepare_one<EPI_AC, 6, true>();
+  prepare_one<EPI_AC, 7, true>();
   done_mask |= bit;
 }
 
@@ -669,15 +723,10 @@ void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUt
     case 0: launch_one<EPI_ROT, 0>(s, mapA, mapB, mapG, p, num_sms); break;
     case 1: launch_one<EPI_SQ, 0>(s, mapA, mapB, mapG, p, num_sms); break;
     default:
-      switch (p.q) {
-        case 1: launch_one<EPI_AC, 1>(s, mapA, mapB, mapG, p, num_sms); break;
-        case 2: launch_one<EPI_AC, 2>(s, mapA, mapB, mapG, p, num_sms); break;
-        case 3: launch_one<EPI_AC, 3>(s, mapA, mapB, mapG, p, num_sms); break;
-        case 4: launch_one<EPI_AC, 4>(s, mapA, mapB, mapG, p, num_sms); break;
-        case 5: launch_one<EPI_AC, 5>(s, mapA, mapB, mapG, p, num_sms); break;
-        case 6: launch_one<EPI_AC, 6>(s, mapA, mapB, mapG, p, num_sms); break;
-        default: launch_one<EPI_AC, 7>(s, mapA, mapB, mapG, p, num_sms); break;
-      }
+      if (p.out_var)
+        launch_ac<true>(s, mapA, mapB, mapG, p, num_sms);
+      else
+        launch_ac<false>(s, mapA, mapB, mapG, p, num_sms);
   }
 }
 

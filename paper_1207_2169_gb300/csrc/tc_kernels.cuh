@@ -22,6 +22,7 @@ struct CholTcParams {
   const uint8_t* G;   // the launch's packed genotype rows (also read through mapG)
   int row_bytes;      // packed_row_bytes(n)
   int out_snp;        // B holds (b_snp, standard error) per pair instead of all p values
+  int out_var;        // B holds the p values, then the p(p+1)/2 of Var(b) (packed upper)
   float* B;           // m x t x p
   float* W;           // m x t or NULL
   int* flags;
@@ -65,6 +66,7 @@ struct EigTcParams {
   const float* mu;         // ROT, AC: per-SNP centring (multiples of 1/64) or NULL
   float* B;                // AC: m x t x p (or x 2 with out_snp)
   int out_snp;             // AC: B holds (b_snp, standard error) per pair
+  int out_var;             // AC: B holds the p values, then the p(p+1)/2 of Var(b)
   float* W;                // AC: m x t or NULL
   int* flags;
 };

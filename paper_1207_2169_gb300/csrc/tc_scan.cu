@@ -84,6 +84,7 @@ struct TcState {
   int64_t mcap = 0;
   bool intercept = false;
   int out_snp = 0;
+  int out_var = 0;
   int traits_ac = 0;
   CUtensorMap mapZ, mapU, mapD, mapX;
 };
@@ -119,6 +120,7 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     st->b0 = a.b0;
     st->intercept = a.intercept != 0;
     st->out_snp = a.out_snp;
+    st->out_var = a.out_var;
     int dev = 0;
     GW_CUDA(cudaGetDevice(&dev));
     GW_CUDA(cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -233,6 +235,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
       p.b0 = st->b0 + (size_t)j * st->q;
       p.centre = st->intercept ? 1 : 0;
       p.out_snp = st->out_snp;
+      p.out_var = st->out_var;
       p.G = a.G;
       p.row_bytes = rb;
       p.B = a.B;
@@ -277,8 +280,9 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.traits_per_blk = st->traits_ac;
     p.P = st->P32;
     p.b0 = st->b032;
-    p.B = a.B + (size_t)off * t * (st->out_snp ? 2 : q1);
+    p.B = a.B + (size_t)off * t * (st->out_snp ? 2 : st->out_var ? q1 + q1 * (q1 + 1) / 2 : q1);
     p.out_snp = st->out_snp;
+    p.out_var = st->out_var;
     p.W = a.wald ? a.wald + (size_t)off * t : nullptr;
     eig_tc_launch(s, 2, st->mapU, st->mapU, mapG, p, ctas);
   }

@@ -14,7 +14,8 @@ def run(g, c, algo, precision, XR=None, device=True, block_snps=0, f64=False, pa
     h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, algo=algo, precision=precision,
                      block_snps=block_snps, validate_genotypes=int(validate), out_mode=out_mode)
     try:
-        m, t, p = XR.shape[0], c.t, (2 if out_mode == "snp" else c.p)
+        pv = c.p + c.p * (c.p + 1) // 2
+        m, t, p = XR.shape[0], c.t, {"snp": 2, "var": pv}.get(out_mode, c.p)
         dt = torch.float64 if f64 else torch.float32
         dev = "cuda" if device else "cpu"
         X = np.ascontiguousarray(XR)

@@ -1,6 +1,7 @@
 """Output modes: GWAS_OUT_SNP writes (b_snp, standard error) per pair -- the SNP effect equal to
-the full scan's last coefficient, the standard error sqrt(Var(b)[p-1][p-1]) from the oracle --
-and p-values of the Wald statistics match the chi-square(1) upper tail."""
+the full scan's last coefficient, the standard error sqrt(Var(b)[p-1][p-1]) from the oracle --;
+GWAS_OUT_VAR writes the coefficients and the whole Var(b); p-values of the Wald statistics match
+the chi-square(1) upper tail."""
 import numpy as np
 import pytest
 
@@ -48,3 +49,50 @@ def test_snp_mode_streamed_and_pvalues(g):
     torch.cuda.synchronize()
     ref = chi2.sf(Wd, 1)
     assert np.allclose(pv.cpu().numpy(), ref, rtol=2e-5, atol=1e-30)
+
+
+def _unpack_upper(flat, p):
+    """(..., p(p+1)/2) packed upper triangle, row by row -> (..., p, p) symmetric."""
+    V = np.empty(flat.shape[:-1] + (p, p))
+    e = 0
+    for r in range(p):
+        for c in range(r, p):
+            V[..., r, c] = V[..., c, r] = flat[..., e]
+            e += 1
+    return V
+
+
+@pytest.mark.parametrize("algo,prec,n,q,m,t,packed", [
+    ("chol", "split_bf16", 200, 3, 300, 1, False), ("eig", "split_bf16", 300, 3, 257, 45, True),
+    ("eig", "split_bf16", 130, 6, 140, 12, False), ("eig", "split_bf16", 150, 1, 90, 9, True),
+    ("chol", "split_bf16", 256, 7, 160, 1, True), ("chol", "fp32", 97, 2, 131, 2, False),
+    ("eig", "fp64", 130, 3, 70, 5, False), ("chol", "fp64", 120, 4, 64, 1, False)])
+def test_var_mode(g, algo, prec, n, q, m, t, packed):
+    """GWAS_OUT_VAR: per pair the p coefficients (exactly those of the full scan), then the whole
+    Var(b) = (X_i^T M_j^-1 X_i)^-1 of Eq. "probDef" against the FP64 oracle, entry by entry on
+    the scale of sqrt(Var_rr Var_cc); a monomorphic SNP gives NaN throughout."""
+    c = synth.small_problem(181 + n + t, n=n, q=q, m=m, t=t)
+    c.XR[m // 2] = 1  # monomorphic: singular pair
+    p = q + 1
+    Bf, Wf, sf = run(g, c, algo, prec, packed=packed)
+    Bv, Wv, sv = run(g, c, algo, prec, packed=packed, out_mode="var")
+    assert Bv.shape == (m, t, p + p * (p + 1) // 2) and sv == sf
+    assert np.array_equal(Bv[:, :, :p], Bf, equal_nan=True) and np.array_equal(Wv, Wf, equal_nan=True)
+    _, _, _, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, full_var=True)
+    V = _unpack_upper(Bv[:, :, p:], p)
+    assert np.all(np.isnan(V[m // 2]))
+    ok = np.ones(m, bool)
+    ok[m // 2] = False
+    d = np.sqrt(np.diagonal(Vref[ok], axis1=2, axis2=3))
+    err = np.abs(V[ok] - Vref[ok]) / (d[..., :, None] * d[..., None, :])
+    tol = 1e-6 if prec == "fp64" else 1e-4
+    assert np.max(err) < tol, np.max(err)
+
+
+def test_var_mode_streamed(g):
+    """GWAS_OUT_VAR through the host-streaming path equals the device-resident scan."""
+    c = synth.small_problem(93, n=200, q=3, m=600, t=7)
+    Bd, Wd, _ = run(g, c, "eig", "split_bf16", out_mode="var", packed=True)
+    Bh, Wh, _ = run(g, c, "eig", "split_bf16", out_mode="var", packed=True, device=False,
+                    block_snps=256)
+    assert np.array_equal(Bd, Bh) and np.array_equal(Wd, Wh)
