@@ -9,6 +9,8 @@
 //   2  all at once, one stream each, every kernel with every SM (the hardware interleaves CTAs);
 //   3  two lanes of half the SMs each, cohorts assigned longest first to the less loaded lane.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -227,17 +229,32 @@ GW_API gwas_status gwas_setup_batch(int n_cohorts, const gwas_cohort* cohorts,
                "batched scans run the tensor-core path (precision SPLIT_BF16)");
     b = new gwas_batch_s();
     b->dev = o.device;
-    for (int i = 0; i < n_cohorts; ++i) {
-      const gwas_cohort& c = cohorts[i];
-      gwas_handle h = nullptr;
-      const gwas_status st = gwas_setup(c.Phi, c.n, c.XL, c.q, c.Y, c.t, c.h2, c.s2, &o, &h);
-      if (st != GWAS_OK) {
-        const std::string msg = gwas_last_error();
-        set_error("cohort %d: %s", i, msg.c_str());
-        throw Fail{st};
+    // The cohorts' setups (FP64 eigendecompositions and per-trait packs, each on its handle's
+    // own streams) run on up to 8 host threads at once: a small cohort alone leaves most of the
+    // GPU idle.  The first failure (lowest cohort index) is reported.
+    b->h.assign(n_cohorts, nullptr);
+    std::vector<gwas_status> sts(n_cohorts, GWAS_OK);
+    std::vector<std::string> msgs(n_cohorts);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+      for (int i = next++; i < n_cohorts; i = next++) {
+        const gwas_cohort& c = cohorts[i];
+        gwas_handle h = nullptr;
+        sts[i] = gwas_setup(c.Phi, c.n, c.XL, c.q, c.Y, c.t, c.h2, c.s2, &o, &h);
+        if (sts[i] != GWAS_OK) msgs[i] = gwas_last_error();
+        b->h[i] = h;
       }
-      b->h.push_back(h);
-    }
+    };
+    const int nthreads = n_cohorts < 8 ? n_cohorts : 8;
+    std::vector<std::thread> pool;
+    for (int k = 1; k < nthreads; ++k) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    for (int i = 0; i < n_cohorts; ++i)
+      if (sts[i] != GWAS_OK) {
+        set_error("cohort %d: %s", i, msgs[i].c_str());
+        throw Fail{sts[i]};
+      }
     int cur = 0;
     GW_CUDA(cudaGetDevice(&cur));
     GW_CUDA(cudaSetDevice(b->dev));

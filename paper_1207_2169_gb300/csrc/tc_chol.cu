@@ -24,6 +24,8 @@
 //   7    MMA issuer (one elected lane); owns the 512 TMEM columns (two 256-column accumulators)
 //   4-6, 8-10, 12-13  genotype converters: packed slices (shared memory) -> BF16 tiles in the
 //        128-byte-swizzled K-major layout
+#include <mutex>
+
 #include "tc_kernels.cuh"
 #include "tc_ptx.cuh"
 
@@ -502,6 +504,8 @@ int current_device() {
 }  // namespace
 
 void chol_tc_prepare() {
+  static std::mutex mu;  // setups may run on several host threads at once
+  std::lock_guard<std::mutex> lock(mu);
   int* mx = g_max_ctas[current_device()];
   if (mx[0] && mx[1]) return;  // attributes and occupancy belong to the device: once per device
   GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -17,6 +17,8 @@
 // B operand and SQ's A operand; lane 1: 2-bit packed genotype slices for ROT and AC), 7 MMA
 // issuer and TMEM owner (two 256-column FP32 accumulators), 4-6, 8-10, 12-13 genotype converters
 // (packed slices in shared memory -> centred BF16 tiles; ROT and AC).
+#include <mutex>
+
 #include "tc_kernels.cuh"
 #include "tc_ptx.cuh"
 
@@ -690,8 +692,11 @@ void launch_ac(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
 }  // namespace
 
 void eig_tc_prepare() {
-  // attributes belong to the current device: set once per device
+  // attributes belong to the current device: set once per device (setups may run on several
+  // host threads at once)
+  static std::mutex mu;
   static uint64_t done_mask = 0;
+  std::lock_guard<std::mutex> lock(mu);
   int dev = 0;
   GW_CUDA(cudaGetDevice(&dev));
   const uint64_t bit = 1ull << (dev & 63);

@@ -3,6 +3,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "tc.cuh"
@@ -15,7 +16,9 @@ namespace {
 constexpr int QMAX = 7;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::mutex mu;  // looked up once, possibly from several host threads
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
   if (!fn) {
     void* ptr = nullptr;
     cudaDriverEntryPointQueryResult q;
