@@ -237,10 +237,12 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config(s, "fp64", s["m"], "int8"),
+        # the same workload description as our arm's line (the oracle's own arithmetic is the
+        # line's dtype and its sample)
+        "data": "synthetic", "config": _config(s, args.precision, s["m"], args.format),
         "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"first {sample} SNPs x {c.t} trait(s) of the workload per step, "
-                                   "FP64 oracle (Algorithm 1 per GLS)"},
+                                   "FP64 oracle (Algorithm 1 per GLS on int8 genotypes)"},
         "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
