@@ -212,9 +212,9 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     h->Zt = dalloc_t<double>(h, nn);
     h->w = dalloc_t<double>(h, n);
     double* U = dalloc_t<double>(h, nn);
-    sweeps = jacobi_eig(s, n, dPhi, h->Zt, h->w, U, h->flags, 60);
+    sweeps = eigh_f64(s, n, dPhi, h->Zt, h->w, U, h->flags);
     dfree(h, U);
-    GW_REQUIRE(sweeps > 0, GWAS_ERR_NOT_CONVERGED, "Jacobi eigensolver did not converge in 60 sweeps");
+    GW_REQUIRE(sweeps >= 0, GWAS_ERR_NOT_CONVERGED, "the eigensolver did not converge");
     h->XLt = dalloc_t<double>(h, (size_t)q * n);
     gemm_f64(s, q, n, n, 1.0, dXL, n, 1, h->Zt, 1, n, 0.0, h->XLt, n, 1);
     gemm_f64(s, t, n, n, 1.0, dY, n, 1, h->Zt, 1, n, 0.0, yw, n, 1);
@@ -753,8 +753,8 @@ GW_API gwas_status gwas_estimate(const double* Phi, int n, const double* XL, int
     GW_CUDA(cudaMemcpyAsync(dY, Y, (size_t)n * t * 8, cudaMemcpyHostToDevice, s));
     GW_CUDA(cudaEventRecord(ev[0], s));
     // Phi = Z W Z^T; X~ = Z^T X_L (rows of XLt), y~_j = Z^T y_j (rows of Yt)
-    const int sweeps = jacobi_eig(s, n, dPhi, Zt, w, U, flags, 60);
-    GW_REQUIRE(sweeps >= 0, GWAS_ERR_NOT_CONVERGED, "Jacobi eigensolver did not converge in 60 sweeps");
+    const int sweeps = eigh_f64(s, n, dPhi, Zt, w, U, flags);
+    GW_REQUIRE(sweeps >= 0, GWAS_ERR_NOT_CONVERGED, "the eigensolver did not converge");
     gemm_f64(s, q, n, n, 1.0, dXL, n, 1, Zt, 1, n, 0.0, XLt, n, 1);
     gemm_f64(s, t, n, n, 1.0, dY, n, 1, Zt, 1, n, 0.0, Yt, n, 1);
     GW_CUDA(cudaEventRecord(ev[1], s));
