@@ -1,0 +1,69 @@
+"""The setup's FP64 eigendecomposition of the kinship matrix (Householder reduction, bisection,
+inverse iteration with cluster-separated shifts, Cholesky QR) on kinships whose spectra have large
+exactly degenerate eigenspaces -- a genomic kinship from fewer SNPs than individuals (the ridge
+eigenvalue repeated n - #SNPs times) and a pedigree of full sibships (two distinct eigenvalues) --
+seen through everything that uses it: the CLAK-Eig scans against the FP64 oracle and step 1's
+estimates against the step-1 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import estimate as est
+from oracle import gls
+from gpu_util import max_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1207_2169_gb300 as g
+    return g
+
+
+def _cohort(kind, n=300, q=3, m=200, t=6):
+    rs = np.random.default_rng(12072169 + (1 if kind == "few_snps" else 2))
+    if kind == "few_snps":
+        Phi = synth.kinship(synth.kinship_factor(rs, n, n_snps=40))
+    else:
+        Phi = np.eye(n)
+        for f in range(0, n, 4):  # families of four full sibs: relationship 1/2
+            blk = slice(f, min(f + 4, n))
+            Phi[blk, blk] = 0.5
+            np.fill_diagonal(Phi[blk, blk], 1.0)
+    XL = synth.covariates(rs, n, q)
+    Y = XL @ rs.standard_normal((q, t)) + rs.standard_normal((n, t))
+    h2 = rs.uniform(0.1, 0.9, t)
+    s2 = rs.uniform(0.5, 2.0, t)
+    XR = synth.genotypes(rs, n, m)
+    return Phi, XL, Y, h2, s2, XR
+
+
+@pytest.mark.parametrize("kind", ["few_snps", "sibships"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-6), ("split_bf16", 1e-4)])
+def test_eig_scan_on_degenerate_kinships(g, kind, prec, tol):
+    import torch
+    Phi, XL, Y, h2, s2, XR = _cohort(kind)
+    m, t, p = XR.shape[0], Y.shape[1], XL.shape[1] + 1
+    h = g.gwas_setup(Phi, XL, Y, h2, s2, algo="eig", precision=prec)
+    try:
+        B = torch.empty((m, t, p), dtype=torch.float32, device="cuda")
+        W = torch.empty((m, t), dtype=torch.float32, device="cuda")
+        g.gwas_scan(h, torch.from_numpy(XR).cuda(), B, W)
+        torch.cuda.synchronize()
+    finally:
+        g.gwas_destroy(h)
+    Bref, Wref, Vref = gls.gls_grid(Phi, XL, XR, Y, h2, s2)
+    eb, ew = max_errors(B.cpu().numpy().astype(np.float64), W.cpu().numpy().astype(np.float64),
+                        Bref, Wref, Vref)
+    assert eb < tol and ew < tol, (eb, ew)
+
+
+@pytest.mark.parametrize("kind", ["few_snps", "sibships"])
+def test_estimate_on_degenerate_kinships(g, kind):
+    Phi, XL, Y, _, _, _ = _cohort(kind, t=3)
+    h2, s2, ll, _ = g.gwas_estimate(Phi, XL, Y, method="reml")
+    _, _, llr = est.estimate(Phi, XL, Y, est.REML)
+    assert np.all(np.abs(ll - llr) <= 1e-8 * np.abs(llr)), (ll, llr)
