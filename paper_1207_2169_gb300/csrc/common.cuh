@@ -72,6 +72,17 @@ int eigh_tridiag(cudaStream_t s, int n, const double* Phi, double* Zt, double* w
 int eigh_f64(cudaStream_t s, int n, const double* Phi, double* Zt, double* w, double* U,
              int* flags);
 
+// 1 / e in FP64 for 1e-30 <= |e| <= 1e30: an FP32 reciprocal as the seed (relative error
+// ~2^-22), then two Newton-Raphson steps x <- x (2 - e x), each squaring the relative error
+// (2^-44, then below FP64 rounding).  Four FMAs instead of an FP64 division, whose throughput
+// on this GPU's FP64 units would dominate the loops that use it.
+__device__ __forceinline__ double recip_f64(double e) {
+  double x = (double)__frcp_rn((float)e);
+  x = fma(x, fma(-e, x, 1.0), x);
+  x = fma(x, fma(-e, x, 1.0), x);
+  return x;
+}
+
 // Step 1 (estimate.cu): per trait j, the (h2, s2) maximising the ML (method 0) or REML (1)
 // criterion of the reduced model, from the eigenvalues w of Phi and the rotated covariates
 // XLt (q x n, row k = Z^T X_L[:, k]) and traits Yt (t x n, row j = Z^T y_j).  Writes h2, s2

@@ -1,7 +1,7 @@
 // Symmetric FP64 eigendecomposition for the setup, Phi = Z W Z^T (Algorithm 4 line 1), by the
 // tridiagonal route the complexity count of the paper assumes (10/3 n^3):
 //   1. Householder reduction Q^T Phi Q = T (T tridiagonal: diagonal d, off-diagonal e);
-//   2. eigenvalues of T by bisection on Sturm counts, one thread per eigenvalue;
+//   2. eigenvalues of T by multisection on Sturm counts, one warp per eigenvalue;
 //   3. eigenvectors of T by inverse iteration, one thread per eigenvector (tridiagonal LU with
 //      partial pivoting).  Eigenvalues closer than 1e-12 ||T|| form a cluster; all of a
 //      cluster's members iterate with one shift placed just below the cluster (further than
@@ -130,31 +130,56 @@ __global__ void house_tail_kernel(int n, const double* A, double* d, double* e) 
   e[n - 2] = A[(int64_t)(n - 2) * n + n - 1];
 }
 
-// Eigenvalue i (ascending) of T by bisection on the Sturm count (the number of eigenvalues
-// below x is the number of negative pivots of T - x I).
+// Eigenvalue i (ascending) of T by multisection on the Sturm count (the number of eigenvalues
+// below x is the number of negative pivots of T - x I): one warp per eigenvalue, its lanes
+// counting at 31 interior points of the current interval, which then shrinks 32-fold per round
+// (a Sturm count is a chain of n dependent steps, so fewer rounds, not more threads per round,
+// shorten it).
+__device__ __forceinline__ int sturm_count(int n, const double* __restrict__ d,
+                                           const double* __restrict__ e2, double x,
+                                           double pivmin) {
+  // a pivot smaller than pivmin is replaced by -pivmin before it is counted, so that a shift
+  // landing exactly on a pivot counts it the way the rest of the recurrence uses it
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int cnt = q < 0.0;
+  for (int j = 1; j < n; ++j) {
+    // e2 / q by the Newton reciprocal where an FP32 seed exists, else by division
+    const double r = fabs(q) >= 1e-30 && fabs(q) <= 1e30 ? e2[j - 1] * recip_f64(q)
+                                                         : e2[j - 1] / q;
+    q = d[j] - x - r;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
 __global__ void bisect_kernel(int n, const double* __restrict__ d, const double* __restrict__ e2,
                               double gl, double gu, double pivmin, double* __restrict__ w) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (i >= n) return;  // warp-uniform
   double lo = gl, hi = gu;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (!(mid > lo && mid < hi)) break;  // no representable midpoint left
-    if (hi - lo <= 4.4e-16 * fmax(fabs(lo), fabs(hi)) + pivmin) break;
-    int cnt = 0;
-    double q = d[0] - mid;
-    cnt += q < 0.0;
-    for (int j = 1; j < n; ++j) {
-      if (fabs(q) < pivmin) q = -pivmin;
-      q = d[j] - mid - e2[j - 1] / q;
-      cnt += q < 0.0;
-    }
-    if (cnt > i)
-      hi = mid;
-    else
-      lo = mid;
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= 4.4e-16 * fmax(fabs(lo), fabs(hi)) + pivmin) break;  // warp-uniform
+    // the points rise with the lane; a point rounded onto or past an end takes that end's vote,
+    // so the votes stay monotone and the interval keeps eigenvalue i
+    const double x = lo + (hi - lo) * (double)(lane + 1) * (1.0 / 32.0);
+    bool above;
+    if (lane == 31 || x >= hi) above = true;
+    else if (x <= lo) above = false;
+    else above = sturm_count(n, d, e2, x, pivmin) > i;
+    // the first point with eigenvalue i below it bounds the interval from above
+    const unsigned bal = __ballot_sync(0xffffffffu, above);
+    const int f = __ffs(bal) - 1;  // 0..31 (lane 31 always votes)
+    const double xf = __shfl_sync(0xffffffffu, x, f);
+    const double xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+    const double nhi = f < 31 ? fmin(xf, hi) : hi;
+    const double nlo = f > 0 ? fmax(xp, lo) : lo;
+    if (!(nhi < hi || nlo > lo)) break;  // no progress left in floating point
+    hi = nhi;
+    lo = nlo;
   }
-  w[i] = 0.5 * (lo + hi);
+  if (lane == 0) w[i] = 0.5 * (lo + hi);
 }
 
 // Counter-based uniform in (-1, 1) for start vector i, component j (splitmix64 of (i, j)).
@@ -343,7 +368,8 @@ int eigh_tridiag(cudaStream_t s, int n, const double* Phi, double* Zt, double* w
   gu += 2.3e-16 * anorm * n + 1e-300;
   const double pivmin = 2.3e-308 * fmax(1.0, emax2);
   GW_CUDA(cudaMemcpyAsync(e2, he2.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  bisect_kernel<<<ceil_div(n, 128), 128, 0, s>>>(n, d, e2, gl, gu, pivmin, w);
+  // one warp per eigenvalue, four per CTA
+  bisect_kernel<<<ceil_div(n, 4), 128, 0, s>>>(n, d, e2, gl, gu, pivmin, w);
   GW_CHECK_LAUNCH();
   GW_CUDA(cudaMemcpyAsync(hw.data(), w, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   GW_CUDA(cudaStreamSynchronize(s));
@@ -365,8 +391,8 @@ int eigh_tridiag(cudaStream_t s, int n, const double* Phi, double* Zt, double* w
     i = j + 1;
   }
   GW_CUDA(cudaMemcpyAsync(sg, hs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  invit_kernel<<<ceil_div(n, 128), 128, 0, s>>>(n, d, e, sg, anorm, wk, wk + nn, wk + 2 * nn,
-                                                 wk + 3 * nn, S);
+  invit_kernel<<<ceil_div(n, 32), 32, 0, s>>>(n, d, e, sg, anorm, wk, wk + nn, wk + 2 * nn,
+                                               wk + 3 * nn, S);
   GW_CHECK_LAUNCH();
   // 4. Cholesky QR, twice: G = S^T S = L L^T, S := S L^-T
   double* Sc = S;

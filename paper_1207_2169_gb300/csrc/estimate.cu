@@ -43,17 +43,6 @@ struct EstArgs {
   int* flags;
 };
 
-// 1 / e for e > 0 in FP64: an FP32 reciprocal as the seed (relative error ~2^-22), then two
-// Newton-Raphson steps x <- x (2 - e x), each squaring the relative error (2^-44, then below
-// FP64 rounding).  Four FMAs instead of an FP64 division, whose throughput on this GPU's FP64
-// units would dominate the criterion.
-__device__ __forceinline__ double recip(double e) {
-  double x = (double)__frcp_rn((float)e);
-  x = fma(x, fma(-e, x, 1.0), x);
-  x = fma(x, fma(-e, x, 1.0), x);
-  return x;
-}
-
 template <int QM>
 struct Acc {
   static constexpr int NA = QM * (QM + 1) / 2;  // X~^T D X~, packed lower triangle
@@ -160,7 +149,7 @@ __device__ double criterion(const EstArgs& a, const double* __restrict__ y, doub
   int nprod = 0;
   for (int r = threadIdx.x; r < n; r += THREADS) {
     const double e = fma(h, a.w[r] - 1.0, 1.0);  // h w_r + 1 - h
-    const double d = recip(e);
+    const double d = recip_f64(e);
     prod *= e;
     if (++nprod == 16) {
       acc[NA + QM + 1] += log(prod);
@@ -234,7 +223,7 @@ __global__ void __launch_bounds__(THREADS) grid_tables_kernel(EstArgs a, double*
   int nprod = 0;
   for (int r = threadIdx.x; r < n; r += THREADS) {
     const double e = fma(h, a.w[r] - 1.0, 1.0);
-    const double d = recip(e);
+    const double d = recip_f64(e);
     Dtab[(int64_t)g * n + r] = d;
     prod *= e;
     if (++nprod == 16) {

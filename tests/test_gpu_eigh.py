@@ -3,7 +3,10 @@ inverse iteration with cluster-separated shifts, Cholesky QR) on kinships whose 
 exactly degenerate eigenspaces -- a genomic kinship from fewer SNPs than individuals (the ridge
 eigenvalue repeated n - #SNPs times) and a pedigree of full sibships (two distinct eigenvalues) --
 seen through everything that uses it: the CLAK-Eig scans against the FP64 oracle and step 1's
-estimates against the step-1 oracle."""
+estimates against the step-1 oracle.  Two more: unrelated individuals (Phi = I, one n-fold
+eigenvalue) and a weak chain of relatives (Phi = I + 1e-3 on the first off-diagonals, n even), whose
+spectrum is symmetric about 1 so that the Sturm count is taken at a shift equal to the diagonal --
+an exactly zero pivot, which has to be counted the way the rest of the recurrence uses it."""
 import numpy as np
 import pytest
 
@@ -23,10 +26,17 @@ def g():
     return g
 
 
+KINDS = ["few_snps", "sibships", "unrelated", "chain"]
+
+
 def _cohort(kind, n=300, q=3, m=200, t=6):
-    rs = np.random.default_rng(12072169 + (1 if kind == "few_snps" else 2))
+    rs = np.random.default_rng(12072169 + KINDS.index(kind) + 1)
     if kind == "few_snps":
         Phi = synth.kinship(synth.kinship_factor(rs, n, n_snps=40))
+    elif kind == "unrelated":
+        Phi = np.eye(n)
+    elif kind == "chain":
+        Phi = np.eye(n) + 1e-3 * (np.eye(n, k=1) + np.eye(n, k=-1))
     else:
         Phi = np.eye(n)
         for f in range(0, n, 4):  # families of four full sibs: relationship 1/2
@@ -41,7 +51,7 @@ def _cohort(kind, n=300, q=3, m=200, t=6):
     return Phi, XL, Y, h2, s2, XR
 
 
-@pytest.mark.parametrize("kind", ["few_snps", "sibships"])
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-6), ("split_bf16", 1e-4)])
 def test_eig_scan_on_degenerate_kinships(g, kind, prec, tol):
     import torch
@@ -61,7 +71,7 @@ def test_eig_scan_on_degenerate_kinships(g, kind, prec, tol):
     assert eb < tol and ew < tol, (eb, ew)
 
 
-@pytest.mark.parametrize("kind", ["few_snps", "sibships"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_estimate_on_degenerate_kinships(g, kind):
     Phi, XL, Y, _, _, _ = _cohort(kind, t=3)
     h2, s2, ll, _ = g.gwas_estimate(Phi, XL, Y, method="reml")
