@@ -51,9 +51,11 @@ enum { FLAG_GENOTYPE = 0, FLAG_SINGULAR = 1, FLAG_NOT_SPD = 2, FLAG_ROTATIONS = 
 // C = alpha * op(A) * op(B) + beta * C with arbitrary element strides:
 //   A(i,k) = A[i*sai + k*sak], B(k,j) = B[k*sbk + j*sbj], C(i,j) = C[i*sci + j*scj].
 // lower_only: skip 64x64 tiles of C that lie strictly above the diagonal.
+// b_tri: B is upper triangular (> 0: B(k,j) = 0 for k > j) or lower triangular (< 0: B(k,j) = 0
+// for k < j), and only the k range that can be non-zero is summed; 0 for a full B.
 void gemm_f64(cudaStream_t s, int M, int N, int K, double alpha, const double* A, int64_t sai,
               int64_t sak, const double* B, int64_t sbk, int64_t sbj, double beta, double* C,
-              int64_t sci, int64_t scj, bool lower_only = false);
+              int64_t sci, int64_t scj, bool lower_only = false, int b_tri = 0);
 // A (n x n, column-major, lower) := M = s2 (h2 Phi + (1-h2) I).
 void form_M(cudaStream_t s, int n, const double* Phi, double h2, double s2, double* A);
 // In-place lower Cholesky of A (column-major, ld n); upper part zeroed.  Sets flags[NOT_SPD].

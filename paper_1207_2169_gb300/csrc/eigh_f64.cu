@@ -394,14 +394,15 @@ int eigh_tridiag(cudaStream_t s, int n, const double* Phi, double* Zt, double* w
   invit_kernel<<<ceil_div(n, 32), 32, 0, s>>>(n, d, e, sg, anorm, wk, wk + nn, wk + 2 * nn,
                                                wk + 3 * nn, S);
   GW_CHECK_LAUNCH();
-  // 4. Cholesky QR, twice: G = S^T S = L L^T, S := S L^-T
+  // 4. Cholesky QR, twice: G = S^T S = L L^T, S := S L^-T (the Cholesky reads the lower triangle
+  //    of G only; L^-T is upper triangular)
   double* Sc = S;
   double* So = wk;
   for (int pass = 0; pass < 2; ++pass) {
-    gemm_f64(s, n, n, n, 1.0, Sc, n, 1, Sc, 1, n, 0.0, G, 1, n);
+    gemm_f64(s, n, n, n, 1.0, Sc, n, 1, Sc, 1, n, 0.0, G, 1, n, /*lower_only=*/true);
     cholesky(s, n, G, flags);
     tri_inverse(s, n, G, Li, W2);
-    gemm_f64(s, n, n, n, 1.0, Sc, 1, n, Li, 1, n, 0.0, So, 1, n);
+    gemm_f64(s, n, n, n, 1.0, Sc, 1, n, Li, 1, n, 0.0, So, 1, n, false, /*b_tri=*/1);
     std::swap(Sc, So);
   }
   int hflags[FLAG_COUNT];

@@ -29,15 +29,19 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int M, int N, int K, doub
                                                        int64_t sak, const double* __restrict__ B,
                                                        int64_t sbk, int64_t sbj, double beta,
                                                        double* __restrict__ C, int64_t sci,
-                                                       int64_t scj, int lower_only) {
+                                                       int64_t scj, int lower_only, int b_tri) {
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (lower_only && bj * GT > bi * GT + GT - 1) return;
+  // a triangular B has zeros outside k <= j (b_tri > 0) or k >= j (b_tri < 0): the tile's
+  // columns j0 .. j0 + GT - 1 need only the k range that can be non-zero
+  const int kbeg = b_tri < 0 ? min(bj * GT, K) : 0;
+  const int kend = b_tri > 0 ? min(bj * GT + GT, K) : K;
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int i0 = bi * GT, j0 = bj * GT;
   double acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += GK) {
+  for (int k0 = kbeg; k0 < kend; k0 += GK) {
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const int e = tid + 256 * l;
@@ -78,11 +82,11 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int M, int N, int K, doub
 
 void gemm_f64(cudaStream_t s, int M, int N, int K, double alpha, const double* A, int64_t sai,
               int64_t sak, const double* B, int64_t sbk, int64_t sbj, double beta, double* C,
-              int64_t sci, int64_t scj, bool lower_only) {
+              int64_t sci, int64_t scj, bool lower_only, int b_tri) {
   if (M <= 0 || N <= 0) return;
   dim3 grid(ceil_div(N, GT), ceil_div(M, GT));
   gemm_f64_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci,
-                                       scj, lower_only ? 1 : 0);
+                                       scj, lower_only ? 1 : 0, b_tri);
   GW_CHECK_LAUNCH();
 }
 
@@ -225,7 +229,8 @@ void tri_inverse(cudaStream_t s, int n, const double* L, double* Linv, double* w
     const int i0 = bi * NB;
     const int jb = n - i0 < NB ? n - i0 : NB;
     // work(jb x i0) = L[i0:i0+jb, 0:i0] * Linv[0:i0, 0:i0]
-    gemm_f64(s, jb, i0, i0, 1.0, L + i0, 1, n, Linv, n, 1, 0.0, work, n, 1);
+    // (Linv[0:i0, 0:i0] is lower triangular)
+    gemm_f64(s, jb, i0, i0, 1.0, L + i0, 1, n, Linv, n, 1, 0.0, work, n, 1, false, -1);
     // Linv[i0:i0+jb, 0:i0] = -Dinv * work
     gemm_f64(s, jb, i0, jb, -1.0, Linv + (int64_t)i0 * n + i0, n, 1, work, n, 1, 0.0,
              Linv + (int64_t)i0 * n, n, 1);
