@@ -29,9 +29,21 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int M, int N, int K, doub
                                                        int64_t sak, const double* __restrict__ B,
                                                        int64_t sbk, int64_t sbj, double beta,
                                                        double* __restrict__ C, int64_t sci,
-                                                       int64_t scj, int lower_only, int b_tri) {
-  const int bi = blockIdx.y, bj = blockIdx.x;
+                                                       int64_t scj, int lower_only, int b_tri,
+                                                       int64_t bsa, int64_t bsb, int64_t bsc,
+                                                       int M_last, int K_last) {
+  const int bi = blockIdx.y, bj = blockIdx.x, z = blockIdx.z;
   if (lower_only && bj * GT > bi * GT + GT - 1) return;
+  // batch member z: operands offset by z times their batch strides; the last member may have
+  // fewer rows and a shorter inner dimension
+  if (z == (int)gridDim.z - 1) {
+    M = M_last;
+    K = K_last;
+  }
+  if (bi * GT >= M) return;
+  A += z * bsa;
+  B += z * bsb;
+  C += z * bsc;
   // a triangular B has zeros outside k <= j (b_tri > 0) or k >= j (b_tri < 0): the tile's
   // columns j0 .. j0 + GT - 1 need only the k range that can be non-zero
   const int kbeg = b_tri < 0 ? min(bj * GT, K) : 0;
@@ -86,7 +98,22 @@ void gemm_f64(cudaStream_t s, int M, int N, int K, double alpha, const double* A
   if (M <= 0 || N <= 0) return;
   dim3 grid(ceil_div(N, GT), ceil_div(M, GT));
   gemm_f64_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci,
-                                       scj, lower_only ? 1 : 0, b_tri);
+                                       scj, lower_only ? 1 : 0, b_tri, 0, 0, 0, M, K);
+  GW_CHECK_LAUNCH();
+}
+
+// batch GEMMs in one launch: member z (0 <= z < batch) is the product above with A, B and C
+// offset by z * bsa, z * bsb, z * bsc elements; the last member has M_last rows and inner
+// dimension K_last (<= M, K), every other member M rows and K.
+static void gemm_f64_batched(cudaStream_t s, int batch, int M, int N, int K, double alpha,
+                             const double* A, int64_t sai, int64_t sak, int64_t bsa,
+                             const double* B, int64_t sbk, int64_t sbj, int64_t bsb, double beta,
+                             double* C, int64_t sci, int64_t scj, int64_t bsc, int M_last,
+                             int K_last, int b_tri) {
+  if (batch <= 0 || M <= 0 || N <= 0) return;
+  dim3 grid(ceil_div(N, GT), ceil_div(M, GT), batch);
+  gemm_f64_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci,
+                                       scj, 0, b_tri, bsa, bsb, bsc, M_last, K_last);
   GW_CHECK_LAUNCH();
 }
 
@@ -220,20 +247,28 @@ __global__ void diag_inv_kernel(int n, const double* __restrict__ L, double* __r
 }
 }  // namespace
 
+// Recursive doubling: with the inverses of the diagonal blocks [o, o + b) and [o + b, o + b + b2)
+// known, the inverse of [[L11, 0], [L21, L22]] has the lower-left block -L22^-1 L21 L11^-1.  Level
+// b = 32, 64, ... joins every aligned pair of b-blocks at once (one batched launch per product),
+// so each level's products run side by side instead of one 32-row panel at a time.  work (n x n)
+// holds T = L21 L11^-1 at the position of the block it becomes.
 void tri_inverse(cudaStream_t s, int n, const double* L, double* Linv, double* work) {
   GW_CUDA(cudaMemsetAsync(Linv, 0, sizeof(double) * (size_t)n * n, s));
   const int nblk = ceil_div(n, NB);
   diag_inv_kernel<<<nblk, NB, 0, s>>>(n, L, Linv);
   GW_CHECK_LAUNCH();
-  for (int bi = 1; bi < nblk; ++bi) {
-    const int i0 = bi * NB;
-    const int jb = n - i0 < NB ? n - i0 : NB;
-    // work(jb x i0) = L[i0:i0+jb, 0:i0] * Linv[0:i0, 0:i0]
-    // (Linv[0:i0, 0:i0] is lower triangular)
-    gemm_f64(s, jb, i0, i0, 1.0, L + i0, 1, n, Linv, n, 1, 0.0, work, n, 1, false, -1);
-    // Linv[i0:i0+jb, 0:i0] = -Dinv * work
-    gemm_f64(s, jb, i0, jb, -1.0, Linv + (int64_t)i0 * n + i0, n, 1, work, n, 1, 0.0,
-             Linv + (int64_t)i0 * n, n, 1);
+  for (int b = NB; b < n; b *= 2) {
+    const int pairs = ceil_div(n - b, 2 * b);  // pairs at o = 2 b p with o + b < n
+    const int o_last = 2 * b * (pairs - 1);
+    const int b2_last = n - o_last - b < b ? n - o_last - b : b;
+    const int64_t bs = 2 * (int64_t)b * (n + 1);  // from one pair's blocks to the next
+    // T (b2 x b, row-major in work) = L21 (column-major in L) * L11^-1 (lower triangular)
+    gemm_f64_batched(s, pairs, b, b, b, 1.0, L + b, 1, n, bs, Linv, n, 1, bs, 0.0,
+                     work + (int64_t)b * n, n, 1, bs, b2_last, b, /*b_tri=*/-1);
+    // Linv21 (b2 x b) = -L22^-1 (b2 x b2) * T
+    gemm_f64_batched(s, pairs, b, b, b, -1.0, Linv + (int64_t)b * n + b, n, 1, bs,
+                     work + (int64_t)b * n, n, 1, bs, 0.0, Linv + (int64_t)b * n, n, 1, bs,
+                     b2_last, b2_last, 0);
   }
 }
 
