@@ -12,7 +12,7 @@ out; the ones below are the standard Gaussian (restricted) log-likelihoods of th
 
 Notation: h stands for h^2 and H(h) = h Phi + (1 - h) I, so M = sigma^2 H(h).
 
-Readings (also listed in the design doc):
+Readings where the paper leaves a choice open:
   * ML: sigma^2 and beta are profiled out; the criterion is the log-likelihood maximised over them,
       l(h) = -1/2 [ n log(2 pi s2(h)) + log|H(h)| + n ],  s2(h) = r^T H^-1 r / n,
     with r = y - X_L beta(h) the GLS residual.

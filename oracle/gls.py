@@ -9,7 +9,7 @@ Notation (Supplementary Note Section 1): n individuals, X_i = [X_L | x_i] with X
 (q = p - 1 columns, intercept first) and the SNP column last, y_j the j-th trait,
 M_j = sigma_j^2 (h_j^2 Phi + (1 - h_j^2) I).
 
-Readings where the paper is silent or garbled (each one is also listed in the design doc):
+Readings where the paper is silent or garbled:
   * Var(b) = (X^T M^-1 X)^-1.  Eq. "probDef" multiplies by sigma^2 again although M already
     contains sigma^2; we take the standard GLS covariance (both coincide when sigma^2 = 1).
   * Wald statistic for the SNP effect: chi2 = b_snp^2 / Var(b)_snp,snp (the paper only says
