@@ -89,8 +89,9 @@ typedef struct {
 void gwas_default_options(gwas_options* opt);
 
 /*
- * gwas_setup -- the per-cohort precomputation (Algorithm 3 lines 1-3 and 5-7; Algorithm 4
- * lines 1-2 and 4, plus the per-trait lines 6-11), in FP64 on the GPU.
+ * gwas_setup -- the per-cohort precomputation, in FP64 on the GPU: for Algorithm 3, M_j, its
+ * Cholesky factor and inverse, the whitened covariates and trait, S_TL and b_T; for Algorithm 4,
+ * the eigendecomposition of Phi, the rotated covariates and traits, and per trait D_j, S_TL, b_T.
  *   Phi  n x n kinship, symmetric; only the lower triangle is read.        (host pointer)
  *   XL   n x q covariates, column 0 is normally the intercept (all ones).   (host pointer)
  *   Y    n x t traits.                                                      (host pointer)
@@ -105,8 +106,9 @@ gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q, const 
                        gwas_handle* out);
 
 /*
- * gwas_scan -- the GLS sequence over one block of m SNPs (Algorithm 3 lines 4 and 8-11, or
- * Algorithm 4 lines 3 and 12-16), every trait.
+ * gwas_scan -- the GLS sequence over one block of m SNPs, every trait: the whitening of the
+ * block and the per-SNP bordered solve of Algorithm 3, or the rotation of the block and the
+ * per-pair bordered solve of Algorithm 4.
  *   XR    m x n genotypes, int8 hard calls, SNP-major (SNP i's n calls at XR + i*n).
  *   B     m x t x p results, B[(i*t + j)*p + k]; k = p-1 is the SNP effect, k < q follow XL.
  *   wald  m x t Wald statistics, wald[i*t + j].  May be NULL (not written).

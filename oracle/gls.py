@@ -28,7 +28,7 @@ SINGULAR_TOL = 1e-12
 
 
 def form_M(Phi: np.ndarray, h2: float, s2: float) -> np.ndarray:
-    """Variance-components covariance, Supplementary Note Section 1 / Algorithm 1 line 1:
+    """Variance-components covariance, Supplementary Note Section 1 / Algorithm 1:
     M = sigma^2 (h^2 Phi + (1 - h^2) I)."""
     n = Phi.shape[0]
     return s2 * (h2 * Phi + (1.0 - h2) * np.eye(n))
@@ -113,9 +113,9 @@ def gls_grid(Phi, XL, XR, Y, h2, s2, snps=None, traits=None, chunk=512, full_var
     """Eq. "probDef": for every (SNP i, trait j) solve b_ij = (X_i^T M_j^-1 X_i)^-1 X_i^T M_j^-1 y_j
     with X_i = [X_L | x_i], each problem by Algorithm 1.
 
-    XR is (m, n) int8 (SNP-major), Y is (n, t).  The factor of M_j (Algorithm 1 lines 1-2) and
-    L_j^-1 y_j (line 4) do not depend on i and are computed once per trait; line 3 whitens each
-    X_i, solving for many SNPs' X_i in one triangular solve.  Returns
+    XR is (m, n) int8 (SNP-major), Y is (n, t).  Forming and factoring M_j (Algorithm 1) and
+    L_j^-1 y_j do not depend on i and are computed once per trait; Algorithm 1's whitening of
+    X_i is one triangular solve for many SNPs' X_i.  Returns
     B (len(snps), len(traits), p), W (same, chi2) and Vd (same shape as B: diag of Var); with
     full_var also V (len(snps), len(traits), p, p), the whole Var(b) = (X_i^T M_j^-1 X_i)^-1 of
     Eq. "probDef"."""

@@ -187,7 +187,7 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
   double* yw = dalloc_t<double>(h, (size_t)t * n);
   int sweeps = 0;
   if (h->algo == GWAS_ALGO_CHOL) {
-    // Algorithm 3 lines 1-3 and 5 for every trait: M_j, L_j, L_j^-1, L_j^-1 X_L, L_j^-1 y_j
+    // Algorithm 3's setup for every trait: M_j, L_j, L_j^-1, L_j^-1 X_L, L_j^-1 y_j
     h->Linv = dalloc_t<double>(h, (size_t)t * nn);
     h->XLw = dalloc_t<double>(h, (size_t)t * q * n);
     double* A = dalloc_t<double>(h, nn);
@@ -207,8 +207,8 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     TraitPackArgs ta{n, q, t, h->XLw, (int64_t)q * n, yw, nullptr, h->P, h->b0, h->rw, h->flags};
     trait_pack(s, ta);
   } else {
-    // Algorithm 4 lines 1, 2 and 4: Phi = Z W Z^T, X~_L = Z^T X_L, Y~ = Z^T Y; then per trait
-    // D_j, S_TL, b_T (lines 6-11) and the operand planes of the pair reduction.
+    // Algorithm 4's setup: Phi = Z W Z^T, X~_L = Z^T X_L, Y~ = Z^T Y; then per trait
+    // D_j, S_TL, b_T and the operand planes of the pair reduction.
     h->Zt = dalloc_t<double>(h, nn);
     h->w = dalloc_t<double>(h, n);
     double* U = dalloc_t<double>(h, nn);

@@ -1,4 +1,4 @@
-// Symmetric FP64 eigendecomposition for the setup, Phi = Z W Z^T (Algorithm 4 line 1), by the
+// Symmetric FP64 eigendecomposition for the setup, Phi = Z W Z^T (Algorithm 4), by the
 // tridiagonal route the complexity count of the paper assumes (10/3 n^3):
 //   1. Householder reduction Q^T Phi Q = T (T tridiagonal: diagonal d, off-diagonal e);
 //   2. eigenvalues of T by multisection on Sturm counts, one warp per eigenvalue;

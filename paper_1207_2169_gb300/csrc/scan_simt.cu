@@ -1,10 +1,10 @@
 // Plain CUDA-core forms (FP64 and FP32) of the per-SNP scan.
 //
-// CHOL (Algorithm 3 lines 4 and 8-11): for a block of SNPs, X' = L^-1 X_R is formed tile by
+// CHOL (Algorithm 3, per SNP block): for a block of SNPs, X' = L^-1 X_R is formed tile by
 // tile (lower-triangular tiles of L^-1 only) and immediately reduced to the bordered-system
 // entries a = X_L'^T x', c = r'^T x', s = x'^T x' of each SNP; X' never reaches memory.
 //
-// EIG (Algorithm 4 lines 3 and 12-16): X~ = Z^T X_R is written to scratch, then every
+// EIG (Algorithm 4, per SNP block): X~ = Z^T X_R is written to scratch, then every
 // (SNP, trait) pair reduces X~ against the trait planes E_k = d_j o X~_L[:,k], F = d_j o r~_j,
 // Dm = d_j:  a_k = <x~, E_k>, c = <x~, F>, s = <x~ o x~, Dm>.
 //

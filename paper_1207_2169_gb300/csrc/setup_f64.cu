@@ -1,10 +1,10 @@
 // FP64 setup kernels: the once-per-cohort and once-per-trait work of Algorithms 3 and 4.
 //
-//   form_M       Supplementary Note Section 1 / Algorithm 3 line 1: M = s2 (h2 Phi + (1-h2) I)
-//   cholesky     Algorithm 3 line 2: L L^T = M (blocked right-looking, 32-wide panels)
-//   tri_inverse  L^-1, so that the per-block whitening of Algorithm 3 line 4 is one product
-//   jacobi_eig   Algorithm 4 line 1: Phi = Z W Z^T (one-sided Jacobi, FP64)
-//   trait_pack   Algorithm 3 lines 6-7 / Algorithm 4 lines 6-11: S_TL, b_T, P = S_TL^-1,
+//   form_M       Supplementary Note Section 1 / Algorithm 3: M = s2 (h2 Phi + (1-h2) I)
+//   cholesky     Algorithm 3: L L^T = M (blocked right-looking, 32-wide panels)
+//   tri_inverse  L^-1, so that the per-block whitening of Algorithm 3 is one product
+//   jacobi_eig   Algorithm 4: Phi = Z W Z^T (one-sided Jacobi, FP64)
+//   trait_pack   Algorithms 3 and 4, per trait: S_TL, b_T, P = S_TL^-1,
 //                b0 = P b_T and the weighted null residual used by the bordered solve
 //
 // All of it runs on CUDA cores in FP64; none of it is on the per-SNP path.

@@ -1,6 +1,6 @@
 // CHOL fused whiten-and-reduce on the tensor cores (tcgen05 / TMEM / TMA, sm_103a).
 //
-// Algorithm 3 lines 4 and 8-11 for one trait.  A persistent CTA walks 128-SNP tiles.  The B
+// Algorithm 3's per-SNP work (whitening, bordered solve) for one trait.  A persistent CTA walks 128-SNP tiles.  The B
 // operand is L^-1 augmented with q + 1 rows: u_k = M^-1 X_L[:,k] (k < q) and M^-1 r (r the
 // null residual), so one product gives, per SNP, the whitened genotypes x' = L^-1 x (columns
 // < n) and, being linear in x, a_k = x^T M^-1 X_L[:,k] and c = x^T M^-1 r (columns n .. n+q).

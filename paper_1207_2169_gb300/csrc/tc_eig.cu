@@ -1,4 +1,4 @@
-// EIG on the tensor cores (tcgen05 / TMEM / TMA, sm_103a): Algorithm 4 lines 3 and 12-16.
+// EIG on the tensor cores (tcgen05 / TMEM / TMA, sm_103a): Algorithm 4's per-SNP work.
 //
 // Per SNP i and trait j the bordered system needs three reductions over the n individuals:
 //     a_ij[k] = x_i^T M_j^-1 X_L[:,k],   c_ij = x_i^T M_j^-1 r_j,   s_ij = x_i^T M_j^-1 x_i,

@@ -133,7 +133,7 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     if (a.algo == GWAS_ALGO_CHOL) {
       // Per trait, the split rows of [L^-1; (M^-1 X_L)^T; (M^-1 r)^T]: M^-1 X_L = L^-T (L^-1 X_L)
       // and M^-1 r = L^-T (L^-1 r) are linear in the genotypes, so the whitening product also
-      // yields a_k and c (Algorithm 3 lines 8-9) in q + 1 extra accumulator columns.
+      // yields a_k and c (Algorithm 3) in q + 1 extra accumulator columns.
       st->rpad = (int)round_up(n + q + 1, 256);
       const size_t per = (size_t)2 * st->rpad * st->kpad;
       st->Lsplit = (__nv_bfloat16*)tc_alloc(st, per * t * 2);
@@ -262,7 +262,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.sbuf = st->sbuf;
     p.lds = st->mcap;
     p.flags = a.flags;
-    // ROT: Xsq = (Z^T x)^2 for this chunk (Algorithm 4 line 3, squared and split)
+    // ROT: Xsq = (Z^T x)^2 for this chunk (Algorithm 4's rotation, squared and split)
     const uint8_t* Gc = a.G + off * rb;
     const CUtensorMap mapG = make_map_packed(Gc, mm, rb);
     if (st->mu) snp_centres_packed(s, Gc, mm, n, st->mu);
@@ -276,7 +276,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.b_piece_rows = t;
     p.b_rows_per_blk = 256;
     eig_tc_launch(s, 1, st->mapX, st->mapD, mapG, p, ctas);
-    // AC: a_ij, c_ij from the genotypes against U, then the bordered solve (lines 13-16)
+    // AC: a_ij, c_ij from the genotypes against U, then the bordered solve (Algorithm 4)
     p.nblk = (t + st->traits_ac - 1) / st->traits_ac;
     p.b_piece_rows = t * q1;
     p.b_rows_per_blk = st->traits_ac * q1;
