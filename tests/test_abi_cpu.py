@@ -84,6 +84,10 @@ def test_setup_null_pointers(g):
 
 def test_null_handle_calls(g):
     assert g.lib.gwas_scan(None, None, 10, 1, None, None, 1, None) == -1
+    assert g.lib.gwas_scan_f64(None, None, 10, 1, None, None, 1, None) == -1
+    # the allocation-free entry point checks its handle before anything else, even for m = 0
+    assert g.lib.gwas_scan_static(None, None, 10, None, None, None) == -1
+    assert g.lib.gwas_scan_static(None, None, 0, None, None, None) == -1
     assert g.lib.gwas_singular_count(None) == -1
     ms = ctypes.c_double()
     assert g.lib.gwas_setup_timing(None, ctypes.byref(ms)) == -1
