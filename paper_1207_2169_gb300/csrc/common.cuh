@@ -66,7 +66,7 @@ void tri_inverse(cudaStream_t s, int n, const double* L, double* Linv, double* w
 // sweeps used, or -1 when not converged within max_sweeps.
 int jacobi_eig(cudaStream_t s, int n, const double* Phi, double* Zt, double* w, double* U,
                int* flags, int max_sweeps);
-// The setup's eigensolver (eigh_f64.cu): Householder tridiagonalisation, bisection, inverse
+// The setup's eigensolver (eigh_f64.cu): Householder tridiagonalisation, multisection, inverse
 // iteration, Cholesky QR and back-transformation (Zt row r = eigenvector r, w eigenvalues);
 // falls back to jacobi_eig if the orthonormalisation fails.  Returns >= 0 on success, -1 if
 // neither converged.  eigh_tridiag alone returns 0, or -1 without a result.

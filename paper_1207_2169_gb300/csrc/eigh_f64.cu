@@ -349,7 +349,7 @@ int eigh_tridiag(cudaStream_t s, int n, const double* Phi, double* Zt, double* w
   }
   house_tail_kernel<<<1, 32, 0, s>>>(n, A, d, e);
   GW_CHECK_LAUNCH();
-  // 2. eigenvalues by bisection within the Gershgorin interval
+  // 2. eigenvalues by multisection within the Gershgorin interval
   std::vector<double> hd(n), he(n), he2(n), hw(n), hs(n);
   GW_CUDA(cudaMemcpyAsync(hd.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   GW_CUDA(cudaMemcpyAsync(he.data(), e, sizeof(double) * n, cudaMemcpyDeviceToHost, s));

@@ -1,4 +1,4 @@
-"""The setup's FP64 eigendecomposition of the kinship matrix (Householder reduction, bisection,
+"""The setup's FP64 eigendecomposition of the kinship matrix (Householder reduction, multisection,
 inverse iteration with cluster-separated shifts, Cholesky QR) on kinships whose spectra have large
 exactly degenerate eigenspaces -- a genomic kinship from fewer SNPs than individuals (the ridge
 eigenvalue repeated n - #SNPs times) and a pedigree of full sibships (two distinct eigenvalues) --
