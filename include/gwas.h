@@ -261,7 +261,10 @@ void gwas_destroy_batch(gwas_batch b);
  *   Limit: m * ldp * e <= 16 MiB, where ldp = n rounded up to 64 and e = 8 (FP64) or 4 (FP32)
  *   bytes; larger m returns GWAS_ERR_ARG (scan such genotypes in several calls).  Other
  *   handles return GWAS_ERR_UNSUPPORTED.
- * Asynchronous on `stream`.  The first call on a device looks up the array's device address
+ * Asynchronous on `stream`, except on a handle set up with validate_genotypes: then every
+ * genotype is checked first (a value outside {0, 1, 2} returns GWAS_ERR_GENOTYPE, and that
+ * call's outputs are not meaningful) and the call returns when the scan is complete.
+ * The first call on a device looks up the array's device address
  * (once per device; a cudaGetSymbolAddress, not an allocation): make that first call before
  * any stream capture.  Every call shares the one array and finds it holding the previous
  * call's data (the scan overwrites everything it reads), so calls whose work overlaps on the
@@ -296,6 +299,27 @@ gwas_status gwas_sync(gwas_handle h);
  * as designed, GWAS_ERR_CUDA otherwise.
  */
 gwas_status gwas_selftest_timeout(int device, int limit_ms);
+
+/*
+ * Per-stage device time of a handle's scans (not from the paper: instrumentation for the
+ * roofline of each kernel).  While enabled, every stage launch of a gwas_scan /
+ * gwas_scan_packed on this handle is bracketed by two CUDA events on the stream it runs on;
+ * gwas_stage_times waits for the recorded events, writes per stage the summed milliseconds
+ * (ms[GWAS_NSTAGES]) and the number of timed launches (launches[GWAS_NSTAGES], may be NULL),
+ * and starts a new tally.  A "launch" is one stage call for one chunk of SNPs (CHOL: one per
+ * trait).  gwas_stage_timing(h, 0 or 1) switches it off or on (waiting for the device first)
+ * and clears the tally.  Events are created on first use and kept by the handle.
+ */
+enum { GWAS_STAGE_PACK = 0,    /* int8 -> packed rows (tensor cores) or back (CUDA cores)      */
+       GWAS_STAGE_CENTRES = 1, /* per-SNP centres of the EIG tensor-core path                  */
+       GWAS_STAGE_CHOL = 2,    /* CHOL tensor-core whiten + reduce + Schur                      */
+       GWAS_STAGE_ROT = 3,     /* EIG rotation (Z^T X_R)^2                                      */
+       GWAS_STAGE_SQ = 4,      /* EIG s_ij                                                      */
+       GWAS_STAGE_AC = 5,      /* EIG a_ij, c_ij + Schur                                        */
+       GWAS_STAGE_SIMT = 6,    /* a whole CUDA-core (FP64 / FP32) scan of a block              */
+       GWAS_NSTAGES = 8 };
+gwas_status gwas_stage_timing(gwas_handle h, int enable);
+gwas_status gwas_stage_times(gwas_handle h, double* ms, int64_t* launches);
 
 /* Message of the last failure on the calling thread ("" if none).  Never NULL. */
 const char* gwas_last_error(void);

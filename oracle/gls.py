@@ -247,3 +247,23 @@ def rel_err_b(b, b_ref, vd_ref):
 def rel_err_wald(w, w_ref):
     """|chi2 - chi2_ref| / max(chi2_ref, 1)."""
     return np.abs(w - w_ref) / np.maximum(np.abs(w_ref), 1.0)
+
+
+def max_rel_errors(b, w, b_ref, w_ref, vd_ref):
+    """Largest rel_err_b and rel_err_wald over the checked pairs, for parity checks.
+
+    A singular GLS is NaN on both sides, so NaN must sit exactly where the reference has it: an
+    output that is NaN where the reference is finite (or finite where it is NaN) -- e.g. a pair
+    a kernel never wrote into a NaN-filled buffer -- makes both errors infinite instead of being
+    skipped.  Pairs NaN on both sides are left out of the maxima."""
+    b, w = np.asarray(b, dtype=np.float64), np.asarray(w, dtype=np.float64)
+    nb, nbr = np.isnan(b), np.isnan(b_ref)
+    nw, nwr = np.isnan(w), np.isnan(w_ref)
+    if nb.shape != nbr.shape or nw.shape != nwr.shape:
+        raise ValueError("output and reference shapes differ")
+    if not (np.array_equal(nb, nbr) and np.array_equal(nw, nwr)):
+        return float("inf"), float("inf")
+    eb = rel_err_b(b, b_ref, vd_ref)[~nbr]
+    ew = rel_err_wald(w, w_ref)[~nwr]
+    return (float(eb.max()) if eb.size else 0.0, float(ew.max()) if ew.size else 0.0)
+

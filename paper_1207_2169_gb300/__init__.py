@@ -30,7 +30,10 @@ EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_destroy_batch", "gwas_sync", "gwas_selftest_timeout", "gwas_wald_pvalues",
            "gwas_estimate",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
-           "gwas_last_error", "gwas_destroy"]
+           "gwas_stage_timing", "gwas_stage_times", "gwas_last_error", "gwas_destroy"]
+
+STAGES = ["pack", "centres", "chol", "rot", "sq", "ac", "simt"]
+NSTAGES = 8
 
 
 class GwasError(RuntimeError):
@@ -102,6 +105,10 @@ def _load():
     lib.gwas_info.restype = i32
     lib.gwas_singular_count.argtypes = [vp]
     lib.gwas_singular_count.restype = i64
+    lib.gwas_stage_timing.argtypes = [vp, i32]
+    lib.gwas_stage_timing.restype = i32
+    lib.gwas_stage_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
+    lib.gwas_stage_times.restype = i32
     lib.gwas_last_error.argtypes = []
     lib.gwas_last_error.restype = ctypes.c_char_p
     lib.gwas_destroy.argtypes = [vp]
@@ -368,6 +375,18 @@ def gwas_info(h) -> dict:
 
 def gwas_singular_count(h) -> int:
     return int(lib.gwas_singular_count(h))
+
+
+def gwas_stage_timing(h, enable=True) -> None:
+    _check(lib.gwas_stage_timing(h, int(bool(enable))), "gwas_stage_timing")
+
+
+def gwas_stage_times(h) -> dict:
+    """{stage name: (milliseconds, timed launches)} since the last read, stages with launches."""
+    ms = (ctypes.c_double * NSTAGES)()
+    n = (ctypes.c_int64 * NSTAGES)()
+    _check(lib.gwas_stage_times(h, ms, n), "gwas_stage_times")
+    return {name: (ms[i], int(n[i])) for i, name in enumerate(STAGES) if n[i]}
 
 
 def gwas_last_error() -> str:

@@ -73,6 +73,7 @@ struct gwas_handle_s {
   // tensor-core state
   TcState* tc = nullptr;
   std::vector<void*> allocs;
+  StageTimer timer;  // per-stage events (gwas_stage_timing)
 };
 
 namespace {
@@ -115,6 +116,7 @@ void destroy_impl(gwas_handle h) {
   if (h->st_h2d) cudaStreamSynchronize(h->st_h2d);
   if (h->st_d2h) cudaStreamSynchronize(h->st_d2h);
   if (h->tc) tc_destroy(h->tc);
+  h->timer.destroy();
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   for (int i = 0; i < gwas_handle_s::NRING; ++i) {
@@ -387,6 +389,7 @@ void scan_block(gwas_handle h, const void* X, int fmt, int64_t m, void* B, void*
   if (h->prec == GWAS_PREC_SPLIT_BF16) {
     TcScanArgs a{};
     a.flags = h->flags;
+    a.timer = &h->timer;
     if (fmt == FMT_PACKED2) {
       GW_REQUIRE(((uintptr_t)X & 15) == 0, GWAS_ERR_ARG,
                  "packed genotypes on the device must start on a 16-byte boundary");
@@ -403,7 +406,9 @@ void scan_block(gwas_handle h, const void* X, int fmt, int64_t m, void* B, void*
     ensure_rows(h, h->pk, h->pk_cap, chunk, rb);
     for (int64_t off = 0; off < m; off += chunk) {
       const int64_t mm = m - off < chunk ? m - off : chunk;
+      cudaEvent_t ev = h->timer.begin(s, STAGE_PACK);
       pack_genotypes(s, (const int8_t*)X + off * n, mm, n, h->pk, h->flags, h->validate != 0);
+      h->timer.end(s, ev);
       a.G = h->pk;
       a.m = mm;
       a.B = (float*)B + (size_t)off * t * p;
@@ -414,7 +419,9 @@ void scan_block(gwas_handle h, const void* X, int fmt, int64_t m, void* B, void*
   }
   if (fmt == FMT_INT8) {
     if (h->validate) validate_genotypes(s, (const int8_t*)X, m * n, h->flags);
+    cudaEvent_t ev = h->timer.begin(s, STAGE_SIMT);
     scan_block_simt(h, (const int8_t*)X, m, B, wald, out_f64, s);
+    h->timer.end(s, ev);
     return;
   }
   const int64_t chunk = convert_chunk(h, m, (size_t)n);
@@ -423,9 +430,13 @@ void scan_block(gwas_handle h, const void* X, int fmt, int64_t m, void* B, void*
     const int64_t mm = m - off < chunk ? m - off : chunk;
     const uint8_t* src = (const uint8_t*)X + off * rbi;
     if (h->validate) validate_packed(s, src, mm, n, h->flags);
+    cudaEvent_t ev = h->timer.begin(s, STAGE_PACK);
     unpack_genotypes(s, src, mm, n, h->u8);
+    h->timer.end(s, ev);
+    ev = h->timer.begin(s, STAGE_SIMT);
     scan_block_simt(h, h->u8, mm, (char*)B + (size_t)off * t * p * ob,
                     wald ? (char*)wald + (size_t)off * t * ob : nullptr, out_f64, s);
+    h->timer.end(s, ev);
   }
 }
 
@@ -900,6 +911,48 @@ GW_API gwas_status gwas_selftest_timeout(int device, int limit_ms) {
   }
 }
 
+GW_API gwas_status gwas_stage_timing(gwas_handle h, int enable) {
+  try {
+    GW_REQUIRE(h != nullptr, GWAS_ERR_ARG, "null handle");
+    DeviceGuard dg(h->dev);
+    GW_CUDA(cudaDeviceSynchronize());  // no recorded event is still pending
+    h->timer.on = enable != 0;
+    h->timer.stage.clear();
+    h->timer.used = 0;
+    return GWAS_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+GW_API gwas_status gwas_stage_times(gwas_handle h, double* ms, int64_t* launches) {
+  try {
+    GW_REQUIRE(h != nullptr && ms != nullptr, GWAS_ERR_ARG, "null handle or ms");
+    DeviceGuard dg(h->dev);
+    for (int i = 0; i < GWAS_NSTAGES; ++i) {
+      ms[i] = 0.0;
+      if (launches) launches[i] = 0;
+    }
+    StageTimer& tm = h->timer;
+    for (size_t k = 0; k < tm.stage.size(); ++k) {
+      cudaEvent_t e0 = tm.pool[2 * k], e1 = tm.pool[2 * k + 1];
+      GW_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      GW_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      const int st = tm.stage[k];
+      if (st >= 0 && st < GWAS_NSTAGES) {
+        ms[st] += t;
+        if (launches) launches[st] += 1;
+      }
+    }
+    tm.stage.clear();
+    tm.used = 0;
+    return GWAS_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
 GW_API const char* gwas_last_error(void) { return gw::g_err.c_str(); }
 
 GW_API void gwas_destroy(gwas_handle h) { destroy_impl(h); }
@@ -955,6 +1008,10 @@ GW_API gwas_status gwas_scan_static(gwas_handle h, const int8_t* XR, int64_t m, 
     void* xt = static_scratch(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
     const int n = h->n, q = h->q, t = h->t;
+    if (h->validate) {  // as gwas_scan: each call reports only its own genotypes
+      GW_CUDA(cudaMemsetAsync(h->flags + FLAG_GENOTYPE, 0, sizeof(int), s));
+      validate_genotypes(s, XR, m * n, h->flags);
+    }
     if (h->prec == GWAS_PREC_FP64) {
       EigScanArgs<double> a{n, q, t, h->Zt, h->planes, h->ldp, h->P, h->b0, XR, m, 0,
                             B, wald, false, 1e-12, (double*)xt, h->flags};
@@ -967,6 +1024,10 @@ GW_API gwas_status gwas_scan_static(gwas_handle h, const int8_t* XR, int64_t m, 
       a.out_snp = h->out_snp;
       a.out_var = h->out_var;
       eig_scan_simt<float>(s, a);
+    }
+    if (h->validate) {  // synchronous then: the flag is read back into pinned host memory
+      read_flags(h, s);
+      GW_REQUIRE(!h->h_flags[FLAG_GENOTYPE], GWAS_ERR_GENOTYPE, "genotype outside {0,1,2}");
     }
     return GWAS_OK;
   } catch (const Fail& f) {

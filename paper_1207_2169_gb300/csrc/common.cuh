@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/gwas.h"
 
@@ -40,6 +41,40 @@ struct Fail {
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Per-stage device time of a handle's scans (gwas_stage_timing): CUDA events recorded on the
+// launching stream around each stage's kernels, read back by gwas_stage_times.
+struct StageTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;        // created on first use, reused after each read
+  std::vector<int> stage;               // stage of each recorded (start, end) pair
+  size_t used = 0;                      // events in use: 2 per recorded pair
+  cudaEvent_t begin(cudaStream_t s, int st) {
+    if (!on) return nullptr;
+    while (pool.size() < used + 2) {
+      cudaEvent_t e;
+      GW_CUDA(cudaEventCreate(&e));
+      pool.push_back(e);
+    }
+    GW_CUDA(cudaEventRecord(pool[used], s));
+    stage.push_back(st);
+    used += 2;
+    return pool[used - 1];
+  }
+  void end(cudaStream_t s, cudaEvent_t e) {
+    if (e) GW_CUDA(cudaEventRecord(e, s));
+  }
+  void destroy() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+    stage.clear();
+    used = 0;
+  }
+};
+
+// Stages a timer tells apart (the GWAS_STAGE_* values of gwas.h).
+enum { STAGE_PACK = 0, STAGE_CENTRES = 1, STAGE_CHOL = 2, STAGE_ROT = 3, STAGE_SQ = 4,
+       STAGE_AC = 5, STAGE_SIMT = 6, STAGE_COUNT = 8 };
 
 // Device flags word layout (int32 array in the handle).
 enum { FLAG_GENOTYPE = 0, FLAG_SINGULAR = 1, FLAG_NOT_SPD = 2, FLAG_ROTATIONS = 3,

@@ -144,10 +144,9 @@ __device__ __forceinline__ int sturm_count(int n, const double* __restrict__ d,
   if (fabs(q) < pivmin) q = -pivmin;
   int cnt = q < 0.0;
   for (int j = 1; j < n; ++j) {
-    // e2 / q by the Newton reciprocal where an FP32 seed exists, else by division
-    const double r = fabs(q) >= 1e-30 && fabs(q) <= 1e30 ? e2[j - 1] * recip_f64(q)
-                                                         : e2[j - 1] / q;
-    q = d[j] - x - r;
+    // correctly rounded division: with every step correctly rounded the count cannot fall as
+    // x rises (the monotonicity the multisection's interval update relies on)
+    q = d[j] - x - e2[j - 1] / q;
     if (fabs(q) < pivmin) q = -pivmin;
     cnt += q < 0.0;
   }

@@ -31,6 +31,7 @@ struct TcScanArgs {
   float* wald;       // m x t device or NULL
   int* flags;
   int max_ctas;      // CTAs per kernel at most (0: one per SM); lets scans share the GPU
+  StageTimer* timer; // per-stage events (NULL or off: none)
 };
 
 // Throws Fail{GWAS_ERR_UNSUPPORTED} for sizes the tensor-core kernels do not cover.

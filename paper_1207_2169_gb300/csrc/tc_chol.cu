@@ -45,8 +45,6 @@ constexpr int QMAX = 7;
 constexpr int PR = 8;                   // packed-genotype slice ring
 constexpr int PK_BYTES = BM * 16;       // 64 genotypes of 128 SNPs, 2-bit codes: 2 KB
 constexpr int NCONV = 8;                // genotype converter warps: 2 threads per row
-constexpr int CL = CHOL_TC_CLUSTER;     // CTAs per cluster; each fetches 1/CL of every L^-1 tile
-constexpr uint16_t CL_MASK = (1u << CL) - 1;
 constexpr int NUM_THREADS = 192 + 32 * NCONV;
 // Warp roles.  A warp issues on SMSP (warp % 4); the single-thread MMA issuer and TMA producers
 // share SMSP 3 with only an epilogue warp, so converter bursts never delay their issue.
@@ -105,7 +103,7 @@ __device__ __forceinline__ void advance(Step& s, int nblocks, int kpad) {
 
 // QM: compile-time bound on q (3 or 7), so the epilogue's per-column arrays stay in registers.
 template <int QM>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
+__global__ void __launch_bounds__(NUM_THREADS, 1)
     chol_tc_kernel(const __grid_constant__ CholMaps lmaps, const __grid_constant__ CUtensorMap mapG,
                    const CholTcParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -115,12 +113,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   uint8_t* sP = sB + SB * B_BYTES;
   Bars* bars = (Bars*)(sP + PR * PK_BYTES);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  // The CTAs of a cluster walk the same (block, k-step) sequence in lockstep, each on its own
-  // SNP tile; past the last tile a CTA runs on zero rows (TMA fills them) and writes nothing.
-  const int64_t ntiles = (p.m + BM - 1) / BM;
-  const int64_t tiles_run = (ntiles + CL - 1) / CL * CL;
+  const int64_t tiles_run = (p.m + BM - 1) / BM;
   const int nblocks = p.rpad / BN;
-  const uint32_t rank = CL > 1 ? cluster_ctarank() : 0;
   int* tflag = p.flags + FLAG_TIMEOUT;
 
   if (threadIdx.x == 0) {
@@ -130,7 +124,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     }
     for (int i = 0; i < SB; ++i) {
       mbar_init(&bars->b_full[i], 1);
-      mbar_init(&bars->b_empty[i], CL);  // released by the MMA issuer of every CTA
+      mbar_init(&bars->b_empty[i], 1);
     }
     for (int i = 0; i < PR; ++i) {
       mbar_init(&bars->pk_full[i], 1);
@@ -157,11 +151,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     prefetch_tensormap(&mapG);
   }
   tc_fence_before();
-  __syncwarp();
-  if (CL > 1)
-    cluster_sync();  // the peers' barriers are initialised before any multicast reaches them
-  else
-    __syncthreads();
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
   volatile int* abort = &bars->abort;
@@ -174,25 +164,15 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       bool ok = true;
       for (Step st{blockIdx.x, 0, 0}; st.tile < tiles_run && ok; advance(st, nblocks, p.kpad)) {
         const int j = diag_skip(st.nb, st.ks);  // rows 64 j .. 255 of the block
-        const int h = (BN - 64 * j) / CL;       // this CTA's share of them
         for (int piece = 0; piece < 2; ++piece) {
-          // the slot is free once every CTA of the cluster has consumed it
           ok = mbar_wait(&bars->b_empty[bs], bph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
-          const int y = piece * p.rpad + st.nb * BN + 64 * j + (int)rank * h;
-          uint8_t* dst = sB + bs * B_BYTES + (B_BYTES / 4) * j + rank * h * 128;
+          const int y = piece * p.rpad + st.nb * BN + 64 * j;
+          uint8_t* dst = sB + bs * B_BYTES + (B_BYTES / 4) * j;
           mbar_arrive_expect_tx(&bars->b_full[bs], (B_BYTES / 4) * (4 - j));
-          if (CL > 1)
-            tma_load_2d_mc(dst, &lmaps.m[j], &bars->b_full[bs], st.ks * BK, y, CL_MASK);
-          else
-            tma_load_2d(dst, &lmaps.m[j], &bars->b_full[bs], st.ks * BK, y);
+          tma_load_2d(dst, &lmaps.m[j], &bars->b_full[bs], st.ks * BK, y);
           if (++bs == SB) { bs = 0; bph ^= 1; }
         }
-      }
-      // the peers' last releases of each slot land here before the CTA may exit
-      for (int i = 0; i < SB && ok; ++i) {
-        ok = mbar_wait(&bars->b_empty[bs], bph ^ 1, abort, tflag, WAIT_NS);
-        if (++bs == SB) { bs = 0; bph ^= 1; }
       }
     } else if (lane == 1) {
       // packed genotype slices (64 genotypes x 128 SNPs, 2 KB) via TMA, in the K-step order the
@@ -235,10 +215,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk)
                 mma_bf16(dt + 64 * j, ad + 2 * kk, bd + 2 * kk, idesc, (ks | piece | kk) != 0);
-              if (CL > 1)
-                mma_commit_mc(&bars->b_empty[bs], CL_MASK);
-              else
-                mma_commit(&bars->b_empty[bs]);
+              mma_commit(&bars->b_empty[bs]);
               if (++bs == SB) { bs = 0; bph ^= 1; }
             }
             mma_commit(&bars->a_empty[as]);
@@ -461,11 +438,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     }
   }
   tc_fence_before();
-  __syncwarp();
-  if (CL > 1)
-    cluster_sync();  // no CTA leaves while a peer may still write its shared memory
-  else
-    __syncthreads();
+  __syncthreads();
   if (warp == MMA_WARP) {
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
@@ -475,25 +448,17 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 }  // namespace
 
 namespace {
-int g_max_ctas[64][2];  // per device: co-resident CTAs of each instantiation (whole clusters)
+int g_max_ctas[64][2];  // per device: co-resident CTAs of each instantiation
 
 template <int QM>
 int max_resident_ctas() {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CL);
-  cfg.blockDim = dim3(NUM_THREADS);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int clusters = 0;
-  GW_CUDA(cudaOccupancyMaxActiveClusters(&clusters, chol_tc_kernel<QM>, &cfg));
-  GW_REQUIRE(clusters >= 1, GWAS_ERR_UNSUPPORTED, "no cluster of %d CTAs fits on this device", CL);
-  return clusters * CL;
+  int per_sm = 0, dev = 0, sms = 0;
+  GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_tc_kernel<QM>, NUM_THREADS,
+                                                        SMEM_BYTES));
+  GW_REQUIRE(per_sm >= 1, GWAS_ERR_UNSUPPORTED, "the CHOL tensor-core kernel does not fit on an SM");
+  GW_CUDA(cudaGetDevice(&dev));
+  GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  return per_sm * sms;
 }
 
 int current_device() {
@@ -522,12 +487,11 @@ void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& ma
                     const CholTcParams& p, int num_sms) {
   if (p.m <= 0) return;
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", p.q, QMAX);
-  // persistent: whole clusters, no more than fit at once (and no more than the tiles need)
+  // persistent: no more CTAs than fit at once (and no more than the tiles need)
   const int64_t tiles = (p.m + BM - 1) / BM;
   int64_t cap = chol_tc_resident_ctas(p.q);
-  if (cap <= 0 || cap > num_sms) cap = num_sms / CL * CL;
-  const int64_t want = (tiles + CL - 1) / CL * CL;
-  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  if (cap <= 0 || cap > num_sms) cap = num_sms;
+  const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
   if (p.q <= 3)
     chol_tc_kernel<3><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
   else

@@ -28,12 +28,9 @@ struct CholTcParams {
   int* flags;
 };
 constexpr int CHOL_TC_BM = 128;  // SNPs per tile
-// CTAs per cluster of the CHOL kernel: they share every L^-1 tile, each fetching its part and
-// multicasting it to all.
-constexpr int CHOL_TC_CLUSTER = 2;
 // Tensor maps of one trait's split augmented L^-1: rows = 2 * rpad (hi piece then lo piece),
-// cols = kpad, BF16, 128-byte swizzle, 64-column boxes of (256 - 64 j) / CHOL_TC_CLUSTER rows
-// (m[j]: one CTA's part of the rows 64 j .. 255 of a block).
+// cols = kpad, BF16, 128-byte swizzle, 64-column boxes of 256 - 64 j rows (m[j]: the rows
+// 64 j .. 255 of a block, which a K step on the block's diagonal meets).
 struct CholMaps {
   CUtensorMap m[4];
 };

@@ -151,8 +151,7 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
                    st->kpad);
         CholMaps mp;
         for (int r = 0; r < 4; ++r)
-          mp.m[r] = make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad,
-                                  (256 - 64 * r) / CHOL_TC_CLUSTER);
+          mp.m[r] = make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad, 256 - 64 * r);
         st->lmaps.push_back(mp);
       }
       GW_CUDA(cudaStreamSynchronize(s));
@@ -244,7 +243,9 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
       p.B = a.B;
       p.W = a.wald;
       p.flags = a.flags;
+      cudaEvent_t ev = a.timer ? a.timer->begin(s, STAGE_CHOL) : nullptr;
       chol_tc_launch(s, st->lmaps[j], mapG, p, ctas);
+      if (ev) a.timer->end(s, ev);
     }
     return;
   }
@@ -265,17 +266,27 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     // ROT: Xsq = (Z^T x)^2 for this chunk (Algorithm 4's rotation, squared and split)
     const uint8_t* Gc = a.G + off * rb;
     const CUtensorMap mapG = make_map_packed(Gc, mm, rb);
-    if (st->mu) snp_centres_packed(s, Gc, mm, n, st->mu);
+    StageTimer* tm = a.timer;
+    cudaEvent_t ev = nullptr;
+    if (st->mu) {
+      ev = tm ? tm->begin(s, STAGE_CENTRES) : nullptr;
+      snp_centres_packed(s, Gc, mm, n, st->mu);
+      if (ev) tm->end(s, ev);
+    }
     p.mu = st->mu;
     p.nblk = st->rpad / 256;
     p.b_piece_rows = st->rpad;
     p.b_rows_per_blk = 256;
+    ev = tm ? tm->begin(s, STAGE_ROT) : nullptr;
     eig_tc_launch(s, 0, st->mapZ, st->mapZ, mapG, p, ctas);
+    if (ev) tm->end(s, ev);
     // SQ: s_ij = sum_r Xsq[i][r] d_j[r]
     p.nblk = (t + 255) / 256;
     p.b_piece_rows = t;
     p.b_rows_per_blk = 256;
+    ev = tm ? tm->begin(s, STAGE_SQ) : nullptr;
     eig_tc_launch(s, 1, st->mapX, st->mapD, mapG, p, ctas);
+    if (ev) tm->end(s, ev);
     // AC: a_ij, c_ij from the genotypes against U, then the bordered solve (Algorithm 4)
     p.nblk = (t + st->traits_ac - 1) / st->traits_ac;
     p.b_piece_rows = t * q1;
@@ -287,7 +298,9 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.out_snp = st->out_snp;
     p.out_var = st->out_var;
     p.W = a.wald ? a.wald + (size_t)off * t : nullptr;
+    ev = tm ? tm->begin(s, STAGE_AC) : nullptr;
     eig_tc_launch(s, 2, st->mapU, st->mapU, mapG, p, ctas);
+    if (ev) tm->end(s, ev);
   }
 }
 

@@ -6,7 +6,11 @@ seen through everything that uses it: the CLAK-Eig scans against the FP64 oracle
 estimates against the step-1 oracle.  Two more: unrelated individuals (Phi = I, one n-fold
 eigenvalue) and a weak chain of relatives (Phi = I + 1e-3 on the first off-diagonals, n even), whose
 spectrum is symmetric about 1 so that the Sturm count is taken at a shift equal to the diagonal --
-an exactly zero pivot, which has to be counted the way the rest of the recurrence uses it."""
+an exactly zero pivot, which has to be counted the way the rest of the recurrence uses it.  Last,
+a Wilkinson-type kinship (tridiagonal, diagonal |k - i| for n = 2k + 1, off-diagonals 1, shifted
+and scaled to be positive definite): its largest eigenvalues come in pairs that agree to about
+1e-13 relative without being equal, the close-but-distinct clusters on which a Sturm count that
+is not monotone in the shift would lose or repeat an eigenvalue."""
 import numpy as np
 import pytest
 
@@ -26,12 +30,18 @@ def g():
     return g
 
 
-KINDS = ["few_snps", "sibships", "unrelated", "chain"]
+KINDS = ["few_snps", "sibships", "unrelated", "chain", "wilkinson"]
 
 
 def _cohort(kind, n=300, q=3, m=200, t=6):
     rs = np.random.default_rng(12072169 + KINDS.index(kind) + 1)
-    if kind == "few_snps":
+    if kind == "wilkinson":
+        n = 301
+        k = n // 2
+        W = np.diag(np.abs(k - np.arange(n)).astype(np.float64))
+        W += np.eye(n, k=1) + np.eye(n, k=-1)
+        Phi = (W + 2.0 * np.eye(n)) / (k + 3.0)
+    elif kind == "few_snps":
         Phi = synth.kinship(synth.kinship_factor(rs, n, n_snps=40))
     elif kind == "unrelated":
         Phi = np.eye(n)

@@ -76,6 +76,21 @@ def test_estimate_identity_kinship_and_exact_fit(g):
     assert np.isnan(h2[2]) and s2[2] == 0.0 and np.isnan(ll[2])
 
 
+def test_estimate_near_exact_fit_is_finite(g):
+    """A trait with R^2 = 1 - 1e-10 is above the exact-fit threshold (1e-12): a finite estimate,
+    with Phi = I the OLS residual variance to the accuracy the small residual allows."""
+    c = synth.small_problem(10, n=120, q=3, m=1, t=1)
+    n = c.XL.shape[0]
+    rs = np.random.default_rng(12)
+    fit = c.XL @ np.array([1.0, 0.5, -2.0])
+    e = rs.standard_normal(n)
+    e -= c.XL @ np.linalg.lstsq(c.XL, e, rcond=None)[0]
+    e *= np.sqrt(1e-10 * (fit @ fit) / (e @ e))
+    h2, s2, ll, _ = g.gwas_estimate(np.eye(n), c.XL, (fit + e)[:, None], method="ml")
+    assert np.isfinite(h2[0]) and np.isfinite(ll[0])
+    assert abs(s2[0] - (e @ e) / n) <= 1e-4 * (e @ e) / n
+
+
 def test_estimate_feeds_setup(g):
     """The estimates are valid gwas_setup parameters (h^2 < 1, sigma^2 > 0)."""
     c = synth.small_problem(12, n=128, q=3, m=64, t=3)

@@ -114,6 +114,29 @@ def test_exact_fit_is_nan():
     assert np.isnan(h2[0]) and s2[0] == 0.0 and np.isnan(ll[0])
 
 
+def test_near_exact_fit_is_finite():
+    """The exact-fit threshold (r^T H^-1 r <= 1e-12 y^T H^-1 y) only catches traits X_L fits to
+    rounding: a trait with R^2 = 1 - 1e-10 (residual fraction 1e-10, two orders above the
+    threshold) still gets a finite estimate -- with Phi = I the OLS residual variance, RSS / n."""
+    c = _problem(seed=4, n=40, t=1)
+    n = c.XL.shape[0]
+    rs = np.random.default_rng(11)
+    fit = c.XL @ np.array([1.0, -2.0, 0.5])
+    e = rs.standard_normal(n)
+    e -= c.XL @ np.linalg.lstsq(c.XL, e, rcond=None)[0]  # residual orthogonal to X_L
+    e *= np.sqrt(1e-10 * (fit @ fit) / (e @ e))
+    y = fit + e
+    frac = float(e @ e) / float(y @ y)
+    assert 0.9e-10 < frac < 1.1e-10
+    for method in (est.ML, est.REML):
+        h2, s2, ll = est.estimate(np.eye(n), c.XL, y[:, None], method)
+        assert np.isfinite(h2[0]) and np.isfinite(ll[0])
+        dof = n if method == est.ML else n - c.XL.shape[1]
+        assert abs(s2[0] - (e @ e) / dof) <= 1e-6 * (e @ e) / dof
+    h2, s2, ll = est.estimate(c.Phi, c.XL, y[:, None], est.REML)
+    assert np.isfinite(h2[0]) and s2[0] > 0 and np.isfinite(ll[0])
+
+
 def _mutant(kind):
     """The oracle's criterion with one plausible mistake planted."""
     def profile(Phi, XL, y, h, method=est.ML):

@@ -269,3 +269,46 @@ def test_planted_mistakes_are_caught(name, golden_pedigree, monkeypatch):
     except AssertionError:
         failed.append("sigma2")
     assert failed, f"mutation {name!r} survived every pin"
+
+
+def test_error_measures_on_hand_computed_values():
+    """The error measures every parity check uses, against values worked out by hand: a large
+    coefficient is compared relatively, one near zero in units of its standard error sqrt(Var)
+    (not Var), and the Wald statistic relatively above 1 and absolutely below."""
+    b = np.array([[1.0, 0.002]])
+    b_ref = np.array([[1.1, 0.0]])
+    vd_ref = np.array([[0.04, 1e-4]])       # standard errors 0.2 and 0.01
+    eb = gls.rel_err_b(b, b_ref, vd_ref)
+    assert np.allclose(eb, [[0.1 / 1.1, 0.002 / 0.01]], rtol=1e-12, atol=0)
+    ew = gls.rel_err_wald(np.array([4.0, 0.3]), np.array([5.0, 0.1]))
+    assert np.allclose(ew, [1.0 / 5.0, 0.2 / 1.0], rtol=1e-12, atol=0)
+    assert gls.max_rel_errors(b, np.array([4.0]), b_ref, np.array([5.0]), vd_ref) == \
+        pytest.approx((0.2, 0.2), rel=1e-12)
+
+
+def test_max_rel_errors_rejects_nan_where_the_reference_is_finite():
+    """A pair left unwritten in a NaN-filled output buffer (or written as a spurious NaN) is an
+    infinite error; NaN on both sides (a singular GLS) is left out of the maxima."""
+    rs = np.random.default_rng(0)
+    b_ref = rs.standard_normal((6, 3, 4))
+    w_ref = rs.random((6, 3)) * 5
+    vd_ref = rs.random((6, 3, 4)) + 0.1
+    b, w = b_ref * (1 + 1e-6), w_ref * (1 + 1e-6)
+    eb, ew = gls.max_rel_errors(b, w, b_ref, w_ref, vd_ref)
+    assert eb < 2e-6 and ew < 2e-6
+    planted = b.copy()
+    planted[4, 1] = np.nan                      # one pair overwritten by NaN on the output side
+    assert gls.max_rel_errors(planted, w, b_ref, w_ref, vd_ref) == (np.inf, np.inf)
+    wp = w.copy()
+    wp[2, 2] = np.nan
+    assert gls.max_rel_errors(b, wp, b_ref, w_ref, vd_ref) == (np.inf, np.inf)
+    # a pair the reference calls singular must be NaN in the output too
+    b_ref2, w_ref2 = b_ref.copy(), w_ref.copy()
+    b_ref2[0, 0] = np.nan
+    w_ref2[0, 0] = np.nan
+    assert gls.max_rel_errors(b, w, b_ref2, w_ref2, vd_ref) == (np.inf, np.inf)
+    b2, w2 = b.copy(), w.copy()
+    b2[0, 0] = np.nan
+    w2[0, 0] = np.nan
+    eb, ew = gls.max_rel_errors(b2, w2, b_ref2, w_ref2, vd_ref)
+    assert eb < 2e-6 and ew < 2e-6
