@@ -63,5 +63,27 @@ def test_work_accounting():
     # block's diagonal, step 4 nb + j meets rows 64 j onwards
     live = [256, 256, 256, 240]
     macs = sum(64 * (live[nb] - 64 * max(0, ks - 4 * nb)) for nb in range(4) for ks in range(4 * (nb + 1)))
-    assert bench.executed_flops(s, 1) == 4 * macs
-    assert bench.executed_flops(s, 1) > 2 * bench.algorithmic_flops(s, 1)
+    assert bench.stage_executed(s, 1) == {"chol": 4 * macs}
+    assert bench.stage_executed(s, 1)["chol"] > 2 * bench.algorithmic_flops(s, 1)
+    # EIG, per kernel: rotation 2 n^2 per SNP, s 2n per pair, a and c 2n(q+1) per pair
+    e = dict(synth.WORKLOADS[2])
+    n, q, t = e["n"], e["q"], e["t"]
+    assert bench.stage_flops(e, 3) == {"rot": 3 * 2 * n * n, "sq": 3 * t * 2 * n,
+                                       "ac": 3 * t * 2 * n * (q + 1)}
+    # executed: rotation 2 pieces over 1024 x 1024 padded; s 3 products over 1024 traits (t
+    # rounded up to 256-column blocks); a, c 2 products over 16 blocks of 64 traits x 256 columns
+    assert bench.stage_executed(e, 1) == {"rot": 4 * 1024 * 1024, "sq": 6 * 1024 * 1024,
+                                          "ac": 4 * 1024 * 256 * 16}
+    assert bench.eig_ac_traits(3) == 64 and bench.eig_ac_traits(7) == 32
+
+
+def test_code_hash_ignores_comments(tmp_path):
+    """The DRAM counters of a kernel stay valid across comment-only edits of its source."""
+    import bench
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    a.write_text("int f(int x) {  // doubles\n  return 2 * x; /* twice */\n}\n")
+    b.write_text("// a header comment\nint f(int x) {\n  return 2 * x;\n}\n")
+    assert bench.code_sha1(a) == bench.code_sha1(b)
+    b.write_text("int f(int x) {\n  return 3 * x;\n}\n")
+    assert bench.code_sha1(a) != bench.code_sha1(b)
