@@ -13,7 +13,9 @@ Modules:
            restricted maximum likelihood of the reduced model (Supplementary Note Section 1).
 """
 from .gls import (form_M, gls_chol, gls_eig, gls_grid, chol_sequence, eig_sequence,
-                  wald_from, rel_err_b, rel_err_wald, max_rel_errors)
+                  wald_from, wald_block, genetic_columns, GENETIC_MODELS, rel_err_b,
+                  rel_err_wald, max_rel_errors)
 
 __all__ = ["form_M", "gls_chol", "gls_eig", "gls_grid", "chol_sequence", "eig_sequence",
-           "wald_from", "rel_err_b", "rel_err_wald", "max_rel_errors"]
+           "wald_from", "wald_block", "genetic_columns", "GENETIC_MODELS", "rel_err_b",
+           "rel_err_wald", "max_rel_errors"]

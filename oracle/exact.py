@@ -47,21 +47,31 @@ def gls_exact(Phi, X, y, h2, s2):
     return b, Var
 
 
-def grid_exact(Phi, XL, XR, Y, h2, s2):
-    """Eq. "probDef" exactly: XL n x q, XR m x n (ints), Y n x t, h2/s2 length t.
-    Returns B[i][j] (list of p Fractions), V[i][j] (p x p) and W[i][j] = b_snp^2 / Var_snp."""
+def wald_exact(b, var, p_r):
+    """b_R^T Var_RR^-1 b_R of the last p_r coefficients, exactly (p_r = 1: b^2 / Var)."""
+    bR = b[-p_r:]
+    VR = [row[-p_r:] for row in var[-p_r:]]
+    sol = _solve(VR, [[v] for v in bR])
+    return sum(bR[k] * sol[k][0] for k in range(p_r))
+
+
+def grid_exact(Phi, XL, XR, Y, h2, s2, codings=((0, 1, 2),)):
+    """Eq. "probDef" exactly: XL n x q, XR m x n (ints), Y n x t, h2/s2 length t.  The SNP's
+    block X_R,i has one column per coding (the column's values for hard calls 0, 1, 2; the
+    default is the genotype itself).  Returns B[i][j] (list of p Fractions), V[i][j] (p x p)
+    and W[i][j] = b_R^T Var_RR^-1 b_R over the genetic block (b_snp^2 / Var_snp for one column)."""
     n = len(Phi)
     m = len(XR)
     t = len(Y[0])
     B, V, W = [], [], []
     for i in range(m):
-        X = [list(XL[r]) + [XR[i][r]] for r in range(n)]
+        X = [list(XL[r]) + [cd[XR[i][r]] for cd in codings] for r in range(n)]
         Bi, Vi, Wi = [], [], []
         for j in range(t):
             b, var = gls_exact(Phi, X, [Y[r][j] for r in range(n)], h2[j], s2[j])
             Bi.append(b)
             Vi.append(var)
-            Wi.append(b[-1] * b[-1] / var[-1][-1])
+            Wi.append(wald_exact(b, var, len(codings)))
         B.append(Bi)
         V.append(Vi)
         W.append(Wi)

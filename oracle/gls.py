@@ -13,7 +13,8 @@ Readings where the paper is silent or garbled:
   * Var(b) = (X^T M^-1 X)^-1.  Eq. "probDef" multiplies by sigma^2 again although M already
     contains sigma^2; we take the standard GLS covariance (both coincide when sigma^2 = 1).
   * Wald statistic for the SNP effect: chi2 = b_snp^2 / Var(b)_snp,snp (the paper only says
-    "p-values").
+    "p-values"); for a genetic model of p_R > 1 columns (e.g. additive and dominance codes),
+    the joint statistic of the block, b_R^T Var(b)_RR^-1 b_R with p_R degrees of freedom.
   * Algorithm 2 / Eq. "Eig0": M^-1 = Z D Z^T with D = diag(1 / (sigma^2 (h^2 w_k + 1 - h^2))),
     K = D^(1/2) (the printed Z D^-1 Z^T double-inverts D).
   * A GLS whose p x p normal matrix S is numerically singular (a Cholesky pivot d_k with
@@ -73,6 +74,42 @@ def wald_from(b: np.ndarray, var_diag: np.ndarray) -> np.ndarray:
     return b[..., -1] ** 2 / var_diag[..., -1]
 
 
+# Genetic models.  Table 1's p, the width of X, is set by the covariates and by "the genetic
+# model assumed": the block X_R,i a SNP contributes has one column per coding, a coding being
+# the column's value for the hard calls x = 0, 1, 2.
+GENETIC_MODELS = {
+    "additive": ((0, 1, 2),),            # allele count
+    "dominant": ((0, 1, 1),),            # carries at least one copy
+    "recessive": ((0, 0, 1),),           # carries two copies
+    "add_dom": ((0, 1, 2), (0, 1, 0)),   # allele count and heterozygosity (2 columns)
+}
+
+
+def codings_of(model):
+    """The codings of a genetic model: a name of GENETIC_MODELS or a tuple of codings."""
+    return GENETIC_MODELS[model] if isinstance(model, str) else tuple(tuple(c) for c in model)
+
+
+def genetic_columns(XR_rows: np.ndarray, model="additive") -> np.ndarray:
+    """X_R,i of k SNPs: (k, n) hard calls -> (n, k, p_R) float64, column c = coding c of x."""
+    x = np.asarray(XR_rows).astype(np.int64)
+    cols = [np.asarray(cd, dtype=np.float64)[x] for cd in codings_of(model)]
+    return np.stack(cols, axis=-1).transpose(1, 0, 2)
+
+
+def wald_block(b: np.ndarray, Var: np.ndarray, p_r: int) -> np.ndarray:
+    """Wald statistic of the genetic block (the last p_r coefficients), b_R^T Var_RR^-1 b_R,
+    chi-square with p_r d.o.f. (p_r = 1: b_snp^2 / Var_snp,snp).  NaN where Var is NaN."""
+    bR = b[..., -p_r:]
+    VR = Var[..., -p_r:, -p_r:]
+    out = np.full(bR.shape[:-1], np.nan)
+    ok = np.all(np.isfinite(VR), axis=(-1, -2)) & np.all(np.isfinite(bR), axis=-1)
+    if np.any(ok):
+        sol = np.linalg.solve(VR[ok], bR[ok][..., None])[..., 0]
+        out[ok] = np.sum(bR[ok] * sol, axis=-1)
+    return out
+
+
 # ---------------------------------------------------------------------------------------------
 # Single GLS (Supplementary Note Section 2)
 # ---------------------------------------------------------------------------------------------
@@ -109,22 +146,27 @@ def gls_eig(Phi, X, y, h2, s2, Z=None, w=None):
 # The 2-D problem (Eq. "probDef"), by definition
 # ---------------------------------------------------------------------------------------------
 
-def gls_grid(Phi, XL, XR, Y, h2, s2, snps=None, traits=None, chunk=512, full_var=False):
+def gls_grid(Phi, XL, XR, Y, h2, s2, snps=None, traits=None, chunk=512, full_var=False,
+             model="additive"):
     """Eq. "probDef": for every (SNP i, trait j) solve b_ij = (X_i^T M_j^-1 X_i)^-1 X_i^T M_j^-1 y_j
-    with X_i = [X_L | x_i], each problem by Algorithm 1.
+    with X_i = [X_L | X_R,i], each problem by Algorithm 1.  X_R,i is the SNP's genotype column
+    (model "additive") or the p_R columns of another genetic model (genetic_columns).
 
     XR is (m, n) int8 (SNP-major), Y is (n, t).  Forming and factoring M_j (Algorithm 1) and
     L_j^-1 y_j do not depend on i and are computed once per trait; Algorithm 1's whitening of
     X_i is one triangular solve for many SNPs' X_i.  Returns
-    B (len(snps), len(traits), p), W (same, chi2) and Vd (same shape as B: diag of Var); with
-    full_var also V (len(snps), len(traits), p, p), the whole Var(b) = (X_i^T M_j^-1 X_i)^-1 of
+    B (len(snps), len(traits), p), W (same, the Wald statistic of the genetic block, p_R
+    d.o.f.) and Vd (same shape as B: diag of Var), p = q + p_R; with full_var also
+    V (len(snps), len(traits), p, p), the whole Var(b) = (X_i^T M_j^-1 X_i)^-1 of
     Eq. "probDef"."""
     XL = np.asarray(XL, dtype=np.float64)
     n, q = XL.shape
-    p = q + 1
+    p_r = len(codings_of(model))
+    p = q + p_r
     snps = np.arange(XR.shape[0]) if snps is None else np.asarray(snps)
     traits = np.arange(Y.shape[1]) if traits is None else np.asarray(traits)
     B = np.empty((len(snps), len(traits), p))
+    W = np.empty((len(snps), len(traits)))
     Vd = np.empty((len(snps), len(traits), p))
     V = np.empty((len(snps), len(traits), p, p)) if full_var else None
     for jj, j in enumerate(traits):
@@ -136,66 +178,70 @@ def gls_grid(Phi, XL, XR, Y, h2, s2, snps=None, traits=None, chunk=512, full_var
             k = len(idx)
             X = np.empty((n, k, p))
             X[:, :, :q] = XL[:, None, :]
-            X[:, :, q] = XR[idx].T.astype(np.float64)
+            X[:, :, q:] = genetic_columns(XR[idx], model)
             Xw = solve_triangular(L, X.reshape(n, k * p), lower=True).reshape(n, k, p)
             S = np.einsum("rki,rkj->kij", Xw, Xw)
             r = np.einsum("rki,r->ki", Xw, yw)
             b, Var, _ = _small_spd_solve(S, r)
             B[s0:s0 + k, jj] = b
+            W[s0:s0 + k, jj] = wald_block(b, Var, p_r)
             Vd[s0:s0 + k, jj] = np.diagonal(Var, axis1=1, axis2=2)
             if full_var:
                 V[s0:s0 + k, jj] = Var
-    W = wald_from(B, Vd)
     return (B, W, Vd, V) if full_var else (B, W, Vd)
 
 
-def gls_pairs(Phi, XL, XR, Y, h2, s2, pairs):
+def gls_pairs(Phi, XL, XR, Y, h2, s2, pairs, model="additive"):
     """Eq. "probDef" on a list of (i, j) pairs, grouped by trait so each M_j is factored once.
     Returns B (len(pairs), p), W, Vd in the order of `pairs`."""
     pairs = np.asarray(pairs).reshape(-1, 2)
-    q = XL.shape[1]
-    B = np.empty((len(pairs), q + 1))
-    Vd = np.empty((len(pairs), q + 1))
+    p = XL.shape[1] + len(codings_of(model))
+    B = np.empty((len(pairs), p))
+    W = np.empty(len(pairs))
+    Vd = np.empty((len(pairs), p))
     for j in np.unique(pairs[:, 1]):
         sel = np.flatnonzero(pairs[:, 1] == j)
-        b, _, v = gls_grid(Phi, XL, XR, Y, h2, s2, snps=pairs[sel, 0], traits=[j])
+        b, w, v = gls_grid(Phi, XL, XR, Y, h2, s2, snps=pairs[sel, 0], traits=[j], model=model)
         B[sel] = b[:, 0]
+        W[sel] = w[:, 0]
         Vd[sel] = v[:, 0]
-    return B, wald_from(B, Vd), Vd
+    return B, W, Vd
 
 
 # ---------------------------------------------------------------------------------------------
 # Sequence algorithms, in the paper's order (Supplementary Note Section 3)
 # ---------------------------------------------------------------------------------------------
 
-def chol_sequence(Phi, XL, XR, y, h2, s2):
+def chol_sequence(Phi, XL, XR, y, h2, s2, model="additive"):
     """Algorithm 3 (CLAK-Chol, single trait): M; L L^T = M; X_L := L^-1 X_L; X_R := L^-1 X_R;
     y := L^-1 y; S_TL := X_L^T X_L; b_T := X_L^T y; then for each SNP i the bordered system
-    S = [[S_TL, *], [X_Ri^T X_L, X_Ri^T X_Ri]], b_i = [b_T; X_Ri^T y], b_i := S^-1 b_i.
-    Returns B (m, p), W (m,), Vd (m, p)."""
+    S = [[S_TL, *], [X_Ri^T X_L, X_Ri^T X_Ri]], b_i = [b_T; X_Ri^T y], b_i := S^-1 b_i, with
+    X_Ri the SNP's p_R columns of the genetic model.  Returns B (m, p), W (m,), Vd (m, p)."""
     n, q = XL.shape
+    m = XR.shape[0]
+    p_r = len(codings_of(model))
     M = form_M(Phi, h2, s2)
     L = np.linalg.cholesky(M)
     XLw = solve_triangular(L, XL, lower=True)
-    XRw = solve_triangular(L, XR.T.astype(np.float64), lower=True)  # n x m
+    XRw = solve_triangular(L, genetic_columns(XR, model).reshape(n, m * p_r),
+                           lower=True).reshape(n, m, p_r)
     yw = solve_triangular(L, y, lower=True)
     S_TL = XLw.T @ XLw
     b_T = XLw.T @ yw
-    m = XR.shape[0]
-    S = np.empty((m, q + 1, q + 1))
+    S = np.empty((m, q + p_r, q + p_r))
     S[:, :q, :q] = S_TL
-    S[:, q, :q] = XRw.T @ XLw
-    S[:, :q, q] = S[:, q, :q]
-    S[:, q, q] = np.sum(XRw * XRw, axis=0)
-    rhs = np.empty((m, q + 1))
+    S[:, q:, :q] = np.einsum("rmc,rk->mck", XRw, XLw)
+    S[:, :q, q:] = np.transpose(S[:, q:, :q], (0, 2, 1))
+    S[:, q:, q:] = np.einsum("rmc,rmd->mcd", XRw, XRw)
+    rhs = np.empty((m, q + p_r))
     rhs[:, :q] = b_T
-    rhs[:, q] = XRw.T @ yw
+    rhs[:, q:] = np.einsum("rmc,r->mc", XRw, yw)
     b, Var, _ = _small_spd_solve(S, rhs)
     Vd = np.diagonal(Var, axis1=1, axis2=2).copy()
-    return b, wald_from(b, Vd), Vd
+    return b, wald_block(b, Var, p_r), Vd
 
 
-def eig_sequence(Phi, XL, XR, Y, h2, s2, Z=None, w=None):
+def eig_sequence(Phi, XL, XR, Y, h2, s2, Z=None, w=None, model="additive"):
     """Algorithm 4 (CLAK-Eig, many traits): Z W Z^T = Phi; X_L := Z^T X_L; X_R := Z^T X_R;
     Y := Z^T Y; for each trait j: D := (sigma_j^2 (h_j^2 W + (1-h_j^2) I))^-1, K K^T = D,
     Y_j := K^T Y_j, W_L := K^T X_L, S_TL := W_L^T W_L, b_T := W_L^T Y_j; for each SNP i:
@@ -206,11 +252,13 @@ def eig_sequence(Phi, XL, XR, Y, h2, s2, Z=None, w=None):
     n, q = XL.shape
     m = XR.shape[0]
     t = Y.shape[1]
+    p_r = len(codings_of(model))
     XLt = Z.T @ XL
-    XRt = Z.T @ XR.T.astype(np.float64)  # n x m
+    XRt = (Z.T @ genetic_columns(XR, model).reshape(n, m * p_r)).reshape(n, m, p_r)
     Yt = Z.T @ Y
-    B = np.empty((m, t, q + 1))
-    Vd = np.empty((m, t, q + 1))
+    B = np.empty((m, t, q + p_r))
+    W = np.empty((m, t))
+    Vd = np.empty((m, t, q + p_r))
     for j in range(t):
         D = 1.0 / (s2[j] * (h2[j] * w + (1.0 - h2[j])))
         K = np.sqrt(D)
@@ -218,19 +266,20 @@ def eig_sequence(Phi, XL, XR, Y, h2, s2, Z=None, w=None):
         WL = K[:, None] * XLt
         S_TL = WL.T @ WL
         b_T = WL.T @ yj
-        WR = K[:, None] * XRt  # n x m: all SNPs' W_R at once
-        S = np.empty((m, q + 1, q + 1))
+        WR = K[:, None, None] * XRt  # n x m x p_R: all SNPs' W_R at once
+        S = np.empty((m, q + p_r, q + p_r))
         S[:, :q, :q] = S_TL
-        S[:, q, :q] = WR.T @ WL
-        S[:, :q, q] = S[:, q, :q]
-        S[:, q, q] = np.sum(WR * WR, axis=0)
-        rhs = np.empty((m, q + 1))
+        S[:, q:, :q] = np.einsum("rmc,rk->mck", WR, WL)
+        S[:, :q, q:] = np.transpose(S[:, q:, :q], (0, 2, 1))
+        S[:, q:, q:] = np.einsum("rmc,rmd->mcd", WR, WR)
+        rhs = np.empty((m, q + p_r))
         rhs[:, :q] = b_T
-        rhs[:, q] = WR.T @ yj
+        rhs[:, q:] = np.einsum("rmc,r->mc", WR, yj)
         b, Var, _ = _small_spd_solve(S, rhs)
         B[:, j] = b
+        W[:, j] = wald_block(b, Var, p_r)
         Vd[:, j] = np.diagonal(Var, axis1=1, axis2=2)
-    return B, wald_from(B, Vd), Vd
+    return B, W, Vd
 
 
 # ---------------------------------------------------------------------------------------------
