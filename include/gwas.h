@@ -4,13 +4,16 @@
  *
  * The operation (Supplementary Note Section 1, Eq. "probDef"): for every SNP i and trait j
  *
- *     b_ij  = (X_i^T M_j^-1 X_i)^-1 X_i^T M_j^-1 y_j ,   X_i = [X_L | x_i],
+ *     b_ij  = (X_i^T M_j^-1 X_i)^-1 X_i^T M_j^-1 y_j ,   X_i = [X_L | X_R,i],
  *     M_j   = s2_j (h2_j Phi + (1 - h2_j) I),
- *     Var_ij = (X_i^T M_j^-1 X_i)^-1 ,   wald_ij = b_ij[p-1]^2 / Var_ij[p-1][p-1],
+ *     Var_ij = (X_i^T M_j^-1 X_i)^-1 ,   wald_ij = b_R^T Var_RR^-1 b_R,
  *
- * with n individuals, X_L = [1 | covariates] (q = p - 1 columns, shared by all problems), x_i the
- * i-th SNP's genotypes (hard calls 0/1/2) and y_j the j-th trait.  The output is the
- * m x t x p object B of Fig. 1 plus the m x t Wald statistics.
+ * with n individuals, X_L = [1 | covariates] (q columns, shared by all problems), X_R,i the
+ * p_R columns the i-th SNP's genotypes (hard calls 0/1/2) give under the genetic model (p_R = 1
+ * for the default additive model: X_R,i = x_i), y_j the j-th trait, p = q + p_R, and b_R, Var_RR
+ * the genetic block of b and Var (wald is chi-square with p_R degrees of freedom; for p_R = 1,
+ * b_snp^2 / Var_snp,snp).  The output is the m x t x p object B of Fig. 1 plus the m x t Wald
+ * statistics.
  *
  * Two algorithms, both exact rearrangements of the definition:
  *   CHOL (Algorithm 3): M = L L^T once per trait; each SNP block is whitened by L^-1
@@ -76,6 +79,19 @@ enum { GWAS_PREC_FP64 = 0, GWAS_PREC_FP32 = 1, GWAS_PREC_SPLIT_BF16 = 2 };
  *         B is m x t x (p + p(p+1)/2).  A singular pair has NaN in all of them. */
 enum { GWAS_OUT_FULL = 0, GWAS_OUT_SNP = 1, GWAS_OUT_VAR = 2 };
 
+/* Genetic models (Table 1: p is set by the covariates and "the genetic model assumed"): the
+ * columns X_R,i of a SNP with hard calls x, placed after X_L's q columns in b and Var.
+ *   ADDITIVE   x                  (p_R = 1; the default)
+ *   DOMINANT   [x >= 1]           (p_R = 1)
+ *   RECESSIVE  [x == 2]           (p_R = 1)
+ *   ADD_DOM    x, [x == 1]        (p_R = 2: allele count and heterozygosity; wald is their joint
+ *                                 2-d.o.f. test)
+ * With GWAS_OUT_SNP, B holds per pair the p_R genetic coefficients, then their p_R standard
+ * errors sqrt(Var_RR[k][k]) (2 p_R values).  The tensor-core scans (SPLIT_BF16) take ADDITIVE
+ * only; other models need FP64 or FP32 (GWAS_ERR_UNSUPPORTED otherwise). */
+enum { GWAS_MODEL_ADDITIVE = 0, GWAS_MODEL_DOMINANT = 1, GWAS_MODEL_RECESSIVE = 2,
+       GWAS_MODEL_ADD_DOM = 3 };
+
 typedef struct {
   int algo;               /* GWAS_ALGO_*; AUTO = CHOL when t == 1, else EIG                   */
   int precision;          /* GWAS_PREC_*                                                      */
@@ -83,9 +99,11 @@ typedef struct {
   int validate_genotypes; /* nonzero: scan checks every genotype is 0, 1 or 2                 */
   int device;             /* CUDA device ordinal                                              */
   int out_mode;           /* GWAS_OUT_*                                                       */
+  int genetic_model;      /* GWAS_MODEL_*                                                     */
 } gwas_options;
 
-/* Fills *opt with AUTO, SPLIT_BF16, block_snps 0, validation off, device 0, FULL outputs. */
+/* Fills *opt with AUTO, SPLIT_BF16, block_snps 0, validation off, device 0, FULL outputs,
+ * the additive genetic model. */
 void gwas_default_options(gwas_options* opt);
 
 /*
@@ -110,7 +128,8 @@ gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q, const 
  * block and the per-SNP bordered solve of Algorithm 3, or the rotation of the block and the
  * per-pair bordered solve of Algorithm 4.
  *   XR    m x n genotypes, int8 hard calls, SNP-major (SNP i's n calls at XR + i*n).
- *   B     m x t x p results, B[(i*t + j)*p + k]; k = p-1 is the SNP effect, k < q follow XL.
+ *   B     m x t x p results, B[(i*t + j)*p + k]; k < q follow XL, k = q .. p-1 are the genetic
+ *         columns (k = p-1 is the SNP effect of the additive model).
  *   wald  m x t Wald statistics, wald[i*t + j].  May be NULL (not written).
  *   xr_on_device / out_on_device: nonzero when the pointer is device memory.
  *   stream: cudaStream_t (NULL = legacy default stream).
@@ -279,6 +298,9 @@ gwas_status gwas_setup_timing(gwas_handle h, double* ms_setup);
 
 /* Sizes and resolved options of a handle (any pointer may be NULL). */
 gwas_status gwas_info(gwas_handle h, int* n, int* q, int* t, int* algo, int* precision);
+
+/* p_R, the genetic columns per SNP of the handle's model (p = q + p_R), or -1 for NULL. */
+int gwas_genetic_columns(gwas_handle h);
 
 /* Number of singular pairs (written as NaN) seen by completed scans of this handle, or -1. */
 int64_t gwas_singular_count(gwas_handle h);

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libgwasgb.so")
 ALGO = {"auto": 0, "chol": 1, "eig": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "split_bf16": 2}
 OUT_MODE = {"full": 0, "snp": 1, "var": 2}
+GENETIC_MODEL = {"additive": 0, "dominant": 1, "recessive": 2, "add_dom": 3}
 STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ERR_CUDA",
           -4: "GWAS_ERR_OOM", -5: "GWAS_ERR_UNSUPPORTED", -6: "GWAS_ERR_GENOTYPE",
           -7: "GWAS_ERR_TIMEOUT", -8: "GWAS_ERR_SINGULAR", -9: "GWAS_ERR_NOT_CONVERGED"}
@@ -30,6 +31,7 @@ EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_destroy_batch", "gwas_sync", "gwas_selftest_timeout", "gwas_wald_pvalues",
            "gwas_estimate",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
+           "gwas_genetic_columns",
            "gwas_stage_timing", "gwas_stage_times", "gwas_last_error", "gwas_destroy"]
 
 STAGES = ["pack", "centres", "chol", "rot", "sq", "ac", "simt"]
@@ -56,7 +58,7 @@ class gwas_cohort_block(ctypes.Structure):
 class gwas_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("precision", ctypes.c_int), ("block_snps", ctypes.c_int),
                 ("validate_genotypes", ctypes.c_int), ("device", ctypes.c_int),
-                ("out_mode", ctypes.c_int)]
+                ("out_mode", ctypes.c_int), ("genetic_model", ctypes.c_int)]
 
 
 def _load():
@@ -103,6 +105,8 @@ def _load():
     ip = ctypes.POINTER(ctypes.c_int)
     lib.gwas_info.argtypes = [vp, ip, ip, ip, ip, ip]
     lib.gwas_info.restype = i32
+    lib.gwas_genetic_columns.argtypes = [vp]
+    lib.gwas_genetic_columns.restype = i32
     lib.gwas_singular_count.argtypes = [vp]
     lib.gwas_singular_count.restype = i64
     lib.gwas_stage_timing.argtypes = [vp, i32]
@@ -154,6 +158,8 @@ def gwas_default_options(**kw) -> gwas_options:
             v = PRECISION[v]
         if k == "out_mode" and isinstance(v, str):
             v = OUT_MODE[v]
+        if k == "genetic_model" and isinstance(v, str):
+            v = GENETIC_MODEL[v]
         setattr(o, k, int(v))
     return o
 
@@ -370,7 +376,12 @@ def gwas_info(h) -> dict:
     v = [ctypes.c_int() for _ in range(5)]
     _check(lib.gwas_info(h, *[ctypes.byref(x) for x in v]), "gwas_info")
     n, q, t, algo, prec = (x.value for x in v)
-    return dict(n=n, q=q, t=t, p=q + 1, algo=algo, precision=prec)
+    pr = int(lib.gwas_genetic_columns(h))
+    return dict(n=n, q=q, t=t, p=q + pr, p_r=pr, algo=algo, precision=prec)
+
+
+def gwas_genetic_columns(h) -> int:
+    return int(lib.gwas_genetic_columns(h))
 
 
 def gwas_singular_count(h) -> int:

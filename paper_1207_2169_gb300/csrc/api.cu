@@ -33,9 +33,11 @@ using namespace gw;
 
 struct gwas_handle_s {
   int dev = 0, n = 0, q = 0, p = 0, t = 0, algo = 0, prec = 0, validate = 0;
-  int out_snp = 0;  // GWAS_OUT_SNP: B holds (b_snp, se) per pair
+  int model = GWAS_MODEL_ADDITIVE;  // genetic model: the SNP's pr columns, p = q + pr
+  GeneticModel gm;
+  int out_snp = 0;  // GWAS_OUT_SNP: B holds (b_R, se_R) per pair
   int out_var = 0;  // GWAS_OUT_VAR: B holds b, then Var(b) packed (p(p+1)/2) per pair
-  int pw = 0;       // values per pair in B: p, 2 with out_snp, p + p(p+1)/2 with out_var
+  int pw = 0;       // values per pair in B: p, 2 pr with out_snp, p + p(p+1)/2 with out_var
   int block_snps = 0;
   int ldp = 0;  // n rounded up to 64: leading dimension of padded per-individual operands
   double setup_ms = 0.0;
@@ -291,7 +293,7 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
   GW_CUDA(cudaStreamSynchronize(s));
 }
 
-// Scratch of the EIG CUDA-core path: the rotated genotypes of up to `snps` SNPs.
+// Scratch of the EIG CUDA-core path: the rotated genetic columns of up to `snps` SNPs.
 void ensure_xt(gwas_handle h, int64_t snps) {
   if (h->algo != GWAS_ALGO_EIG || h->prec == GWAS_PREC_SPLIT_BF16) return;
   if (snps <= h->xt_cap) return;
@@ -300,7 +302,7 @@ void ensure_xt(gwas_handle h, int64_t snps) {
     dfree(h, h->xt);
   }
   const size_t es = h->prec == GWAS_PREC_FP64 ? 8 : 4;
-  h->xt = dalloc(h, (size_t)snps * h->ldp * es);
+  h->xt = dalloc(h, (size_t)snps * h->gm.pr * h->ldp * es);
   h->xt_cap = snps;
 }
 
@@ -343,6 +345,7 @@ void scan_block_simt(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* 
                                XR, m, 0, B, wald, out_f64, 1e-12, h->flags};
         a.out_snp = h->out_snp;
         a.out_var = h->out_var;
+        a.gm = h->gm;
         chol_scan_simt<double>(s, a);
       } else {
         CholScanArgs<float> a{n, q, t, j, h->Linv32 + (size_t)j * n * n, h->XLw32 + (size_t)j * q * n,
@@ -350,6 +353,7 @@ void scan_block_simt(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* 
                               XR, m, 0, B, wald, out_f64, 1e-5f, h->flags};
         a.out_snp = h->out_snp;
         a.out_var = h->out_var;
+        a.gm = h->gm;
         chol_scan_simt<float>(s, a);
       }
     }
@@ -367,12 +371,14 @@ void scan_block_simt(gwas_handle h, const int8_t* XR, int64_t m, void* B, void* 
                             Bc, Wc, out_f64, 1e-12, (double*)h->xt, h->flags};
       a.out_snp = h->out_snp;
       a.out_var = h->out_var;
+      a.gm = h->gm;
       eig_scan_simt<double>(s, a);
     } else {
       EigScanArgs<float> a{n, q, t, h->Zt32, h->planes32, h->ldp, h->P32, h->b032, XR + off * n, mm,
                            0, Bc, Wc, out_f64, 1e-5f, (float*)h->xt, h->flags};
       a.out_snp = h->out_snp;
       a.out_var = h->out_var;
+      a.gm = h->gm;
       eig_scan_simt<float>(s, a);
     }
   }
@@ -571,7 +577,22 @@ GW_API void gwas_default_options(gwas_options* opt) {
   opt->validate_genotypes = 0;
   opt->device = 0;
   opt->out_mode = GWAS_OUT_FULL;
+  opt->genetic_model = GWAS_MODEL_ADDITIVE;
 }
+
+namespace gw {
+GeneticModel genetic_model(int model) {
+  GeneticModel g;
+  switch (model) {
+    case GWAS_MODEL_ADDITIVE: break;
+    case GWAS_MODEL_DOMINANT: g.code[0][2] = 1; break;
+    case GWAS_MODEL_RECESSIVE: g.code[0][1] = 0; g.code[0][2] = 1; break;
+    case GWAS_MODEL_ADD_DOM: g.pr = 2; g.code[1][1] = 1; break;
+    default: GW_REQUIRE(false, GWAS_ERR_ARG, "bad genetic_model %d", model);
+  }
+  return g;
+}
+}  // namespace gw
 
 GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q, const double* Y,
                               int t, const double* h2, const double* s2, const gwas_options* opt,
@@ -597,23 +618,30 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
     GW_REQUIRE(o.out_mode == GWAS_OUT_FULL || o.out_mode == GWAS_OUT_SNP ||
                    o.out_mode == GWAS_OUT_VAR,
                GWAS_ERR_ARG, "bad out_mode %d", o.out_mode);
+    const GeneticModel gm = genetic_model(o.genetic_model);
     h = new gwas_handle_s();
+    h->model = o.genetic_model;
+    h->gm = gm;
     h->dev = o.device;
     h->n = n;
     h->q = q;
-    h->p = q + 1;
+    h->p = q + gm.pr;
     h->t = t;
     h->algo = o.algo == GWAS_ALGO_AUTO ? (t == 1 ? GWAS_ALGO_CHOL : GWAS_ALGO_EIG) : o.algo;
     h->prec = o.precision;
     h->validate = o.validate_genotypes ? 1 : 0;
     h->out_snp = o.out_mode == GWAS_OUT_SNP ? 1 : 0;
     h->out_var = o.out_mode == GWAS_OUT_VAR ? 1 : 0;
-    h->pw = h->out_snp ? 2 : h->out_var ? h->p + h->p * (h->p + 1) / 2 : h->p;
+    h->pw = h->out_snp ? 2 * gm.pr : h->out_var ? h->p + h->p * (h->p + 1) / 2 : h->p;
     h->ldp = (int)round_up(n, 64);
     if (h->algo == GWAS_ALGO_CHOL)
       GW_REQUIRE((double)t * n * n * 8.0 <= 64e9, GWAS_ERR_UNSUPPORTED,
                  "CHOL keeps one n x n factor per trait: t=%d, n=%d is too large (use EIG)", t, n);
-    if (h->prec == GWAS_PREC_SPLIT_BF16) tc_check_supported(h->algo, n, q, t);
+    if (h->prec == GWAS_PREC_SPLIT_BF16) {
+      tc_check_supported(h->algo, n, q, t);
+      GW_REQUIRE(h->model == GWAS_MODEL_ADDITIVE, GWAS_ERR_UNSUPPORTED,
+                 "the tensor-core scans take the additive genetic model (use FP64 or FP32)");
+    }
     int ndev = 0;
     GW_CUDA(cudaGetDeviceCount(&ndev));
     GW_REQUIRE(h->dev >= 0 && h->dev < ndev, GWAS_ERR_ARG, "device %d not present", h->dev);
@@ -873,6 +901,8 @@ GW_API gwas_status gwas_info(gwas_handle h, int* n, int* q, int* t, int* algo, i
   return GWAS_OK;
 }
 
+GW_API int gwas_genetic_columns(gwas_handle h) { return h ? h->gm.pr : -1; }
+
 GW_API int64_t gwas_singular_count(gwas_handle h) {
   if (!h) return -1;
   try {
@@ -998,7 +1028,7 @@ GW_API gwas_status gwas_scan_static(gwas_handle h, const int8_t* XR, int64_t m, 
                GWAS_ERR_UNSUPPORTED,
                "gwas_scan_static needs an EIG handle with FP64 or FP32 precision");
     const size_t es = h->prec == GWAS_PREC_FP64 ? 8 : 4;
-    const size_t per_snp = (size_t)h->ldp * es;
+    const size_t per_snp = (size_t)h->gm.pr * h->ldp * es;
     GW_REQUIRE((size_t)m * per_snp <= STATIC_SCRATCH_BYTES, GWAS_ERR_ARG,
                "m=%lld SNPs need %zu bytes of scratch; the static scratch holds %zu bytes "
                "(at most %zu SNPs per call for this handle)",
@@ -1017,12 +1047,14 @@ GW_API gwas_status gwas_scan_static(gwas_handle h, const int8_t* XR, int64_t m, 
                             B, wald, false, 1e-12, (double*)xt, h->flags};
       a.out_snp = h->out_snp;
       a.out_var = h->out_var;
+      a.gm = h->gm;
       eig_scan_simt<double>(s, a);
     } else {
       EigScanArgs<float> a{n, q, t, h->Zt32, h->planes32, h->ldp, h->P32, h->b032, XR, m, 0,
                            B, wald, false, 1e-5f, (float*)xt, h->flags};
       a.out_snp = h->out_snp;
       a.out_var = h->out_var;
+      a.gm = h->gm;
       eig_scan_simt<float>(s, a);
     }
     if (h->validate) {  // synchronous then: the flag is read back into pinned host memory

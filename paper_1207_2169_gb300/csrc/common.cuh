@@ -165,6 +165,17 @@ void split_bf16_rows(cudaStream_t s, const double* x, int rows, int cols, int64_
                      int gout, int off, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo);
 
 // ------------------------------------------------------------------------------------------
+// Genetic models: the block X_R,i a SNP contributes to X_i = [X_L | X_R,i] has pr columns
+// (1 or 2); column k takes the value code[k][x] for the hard call x = 0, 1, 2.
+// ------------------------------------------------------------------------------------------
+struct GeneticModel {
+  int pr = 1;
+  int8_t code[2][3] = {{0, 1, 2}, {0, 0, 0}};
+};
+// GWAS_MODEL_* -> its columns (throws Fail{GWAS_ERR_ARG} for an unknown model).
+GeneticModel genetic_model(int model);
+
+// ------------------------------------------------------------------------------------------
 // Scan kernels, scan_simt.cu (plain FP64 / FP32 CUDA-core forms)
 // ------------------------------------------------------------------------------------------
 template <typename T>
@@ -183,8 +194,9 @@ struct CholScanArgs {
   bool out_f64;
   T sing_tol;
   int* flags;
-  int out_snp = 0;           // B holds (b_snp, standard error) per pair instead of all p values
+  int out_snp = 0;           // B holds (b_R, standard errors) per pair instead of all p values
   int out_var = 0;           // B holds the p values, then the p(p+1)/2 of Var(b) (packed upper)
+  GeneticModel gm;           // the SNP's columns (p = q + gm.pr)
 };
 template <typename T> void chol_scan_simt(cudaStream_t s, const CholScanArgs<T>& a);
 
@@ -203,10 +215,11 @@ struct EigScanArgs {
   void* wald;
   bool out_f64;
   T sing_tol;
-  T* xt;                     // scratch: m x ldp rotated genotypes
+  T* xt;                     // scratch: (m pr) x ldp rotated genetic columns
   int* flags;
   int out_snp = 0;           // as CholScanArgs
   int out_var = 0;
+  GeneticModel gm;
 };
 template <typename T> void eig_scan_simt(cudaStream_t s, const EigScanArgs<T>& a);
 

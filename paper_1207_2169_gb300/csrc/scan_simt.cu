@@ -13,7 +13,9 @@
 //   v = P a (P = S_TL^-1), sigma = s - a^T v, b_s = c / sigma, b_L = b0 - v b_s,
 //   wald = b_s^2 sigma  (= b_s^2 / Var(b_s) with Var(b_s) = 1 / sigma),
 // where c uses the null residual r = y - X_L b0, so that c = x^T M^-1 y - a^T b0 without the
-// cancellation of forming the two terms separately.
+// cancellation of forming the two terms separately.  A genetic model of two columns per SNP
+// (X_R,i = [x, x == 1], say) makes a, c and s a q x 2 block, a 2-vector and a 2 x 2 block, and
+// the solve a 2 x 2 Schur complement (schur_store).
 #include "common.cuh"
 
 namespace gw {
@@ -24,93 +26,152 @@ constexpr int TS = 64;  // SNPs per tile
 constexpr int TR = 64;  // rows (individuals) per tile
 constexpr int TK = 16;  // reduction chunk
 
+// The bordered solve of one pair for a genetic block of pr <= 2 columns:
+//   a[r][k] = X_R,r^T M^-1 X_L[:,k],  c[r] = X_R,r^T M^-1 r0,  S[0..2] = (S_00, S_01, S_11) of
+//   S_RR = X_R^T M^-1 X_R (S[1], S[2] unused when pr = 1);
+//   V = P A (q x pr), Sigma = S_RR - A^T V, b_R = Sigma^-1 c, b_L = b0 - V b_R,
+//   wald = c^T Sigma^-1 c = b_R . c (pr d.o.f.),  Var(b) = [[P + V Sigma^-1 V^T, -V Sigma^-1],
+//   [-Sigma^-1 V^T, Sigma^-1]].
+// Singular (NaN outputs, counted) when a pivot of Sigma's Cholesky falls to <= tol times the
+// matching diagonal entry of S_RR -- the pivots of the full p x p Cholesky for the last rows.
 template <typename T>
-__device__ __forceinline__ void schur_store(int q, const T* __restrict__ P, const T* __restrict__ b0,
-                                            const T* a, T c, T s, T tol, int64_t i, int j, int t,
+__device__ __forceinline__ void schur_store(int q, int pr, const T* __restrict__ P,
+                                            const T* __restrict__ b0, const T (*a)[QMAX],
+                                            const T* c, const T* S, T tol, int64_t i, int j, int t,
                                             void* B, void* wald, bool out_f64, int* flags,
                                             int out_snp, int out_var) {
-  const int p = q + 1;
-  T v[QMAX];
-  T aPa = 0;
+  const int p = q + pr;
+  T v[2][QMAX];
+  T sg[2][2];
 #pragma unroll
-  for (int k = 0; k < QMAX; ++k) {
-    T acc = 0;
-    if (k < q) {
+  for (int r = 0; r < 2; ++r) {
 #pragma unroll
-      for (int l = 0; l < QMAX; ++l)
-        if (l < q) acc += P[k * q + l] * a[l];
-      aPa += a[k] * acc;
+    for (int k = 0; k < QMAX; ++k) {
+      T acc = 0;
+      if (k < q && r < pr) {
+#pragma unroll
+        for (int l = 0; l < QMAX; ++l)
+          if (l < q) acc += P[k * q + l] * a[r][l];
+      }
+      v[r][k] = acc;
     }
-    v[k] = acc;
   }
-  const T sigma = s - aPa;
-  T out[QMAX + 1];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < QMAX; ++k)
+        if (k < q) acc += a[r][k] * v[u][k];
+      sg[r][u] = (r == 0 ? (u == 0 ? S[0] : S[1]) : (u == 0 ? S[1] : S[2])) - acc;
+    }
+  // Sigma^-1 (pr = 1: 1 / sigma; pr = 2: the 2 x 2 inverse) after the pivot test
+  T si[2][2] = {{0, 0}, {0, 0}};
+  bool ok;
+  if (pr == 1) {
+    ok = sg[0][0] > tol * S[0];
+    si[0][0] = (T)1 / sg[0][0];
+  } else {
+    const T piv1 = sg[1][1] - sg[0][1] * sg[0][1] / sg[0][0];
+    ok = sg[0][0] > tol * S[0] && piv1 > tol * S[2];
+    const T det = sg[0][0] * piv1;  // = sigma00 sigma11 - sigma01^2
+    si[0][0] = sg[1][1] / det;
+    si[1][1] = sg[0][0] / det;
+    si[0][1] = si[1][0] = -sg[0][1] / det;
+  }
+  T out[QMAX + 4];
   T w;
-  if (sigma > tol * s) {
-    const T bs = c / sigma;
+  T bR[2] = {0, 0};
+  if (ok) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      if (r < pr) bR[r] = si[r][0] * c[0] + (pr > 1 ? si[r][1] * c[1] : (T)0);
 #pragma unroll
     for (int k = 0; k < QMAX; ++k)
-      if (k < q) out[k] = b0[k] - v[k] * bs;
-    out[q] = bs;
-    w = bs * c;
+      if (k < q) out[k] = b0[k] - v[0][k] * bR[0] - (pr > 1 ? v[1][k] * bR[1] : (T)0);
+    out[q] = bR[0];
+    if (pr > 1) out[q + 1] = bR[1];
+    w = bR[0] * c[0] + (pr > 1 ? bR[1] * c[1] : (T)0);
   } else {
     const T nanv = (T)NAN;
 #pragma unroll
-    for (int k = 0; k <= QMAX; ++k) out[k] = nanv;
+    for (int k = 0; k < QMAX + 4; ++k) out[k] = nanv;
     w = nanv;
     atomicAdd(&flags[FLAG_SINGULAR], 1);
   }
-  if (out_snp) {  // (b_snp, standard error 1 / sqrt(sigma)) per pair
-    const T se = sigma > tol * s ? (T)1 / sqrt(sigma) : (T)NAN;
-    out[0] = out[q];
-    out[1] = se;
+  if (out_snp) {  // (b_R, standard errors sqrt(diag Sigma^-1)) per pair
+    const T b0v = out[q], b1v = out[q + 1 < QMAX + 4 ? q + 1 : 0];
+    out[0] = b0v;
+    if (pr > 1) out[1] = b1v;
+    out[pr] = ok ? sqrt(si[0][0]) : (T)NAN;
+    if (pr > 1) out[pr + 1] = ok ? sqrt(si[1][1]) : (T)NAN;
   }
-  const int pw = out_snp ? 2 : out_var ? p + p * (p + 1) / 2 : p;
+  const int nb = out_snp ? 2 * pr : p;
+  const int pw = out_snp ? 2 * pr : out_var ? p + p * (p + 1) / 2 : p;
   const int64_t o = (i * t + j) * pw;
   if (out_f64) {
     double* Bd = (double*)B;
 #pragma unroll
-    for (int k = 0; k <= QMAX; ++k)
-      if (k < (out_snp ? 2 : p)) Bd[o + k] = (double)out[k];
+    for (int k = 0; k < QMAX + 2; ++k)
+      if (k < nb) Bd[o + k] = (double)out[k];
     if (wald) ((double*)wald)[i * t + j] = (double)w;
   } else {
     float* Bf = (float*)B;
 #pragma unroll
-    for (int k = 0; k <= QMAX; ++k)
-      if (k < (out_snp ? 2 : p)) Bf[o + k] = (float)out[k];
+    for (int k = 0; k < QMAX + 2; ++k)
+      if (k < nb) Bf[o + k] = (float)out[k];
     if (wald) ((float*)wald)[i * t + j] = (float)w;
   }
   if (out_var) {
-    // Var(b) = S^-1 of the bordered S = [[S_TL, a], [a^T, s]]: [[P + v v^T / sigma, -v / sigma],
-    // [-v^T / sigma, 1 / sigma]], packed upper triangle row by row after the p coefficients
-    // (constant loop bounds keep v[] in registers)
-    const bool ok = sigma > tol * s;
-    const T inv = ok ? (T)1 / sigma : (T)NAN;
+    // packed upper triangle row by row after the p coefficients; rows/cols < q are X_L's,
+    // q + r the genetic column r (constant loop bounds keep v[] in registers)
 #pragma unroll
-    for (int r = 0; r <= QMAX; ++r)
+    for (int r = 0; r < QMAX + 2; ++r)
 #pragma unroll
-      for (int cc = r; cc <= QMAX; ++cc) {
+      for (int cc = r; cc < QMAX + 2; ++cc) {
         if (r >= p || cc >= p) continue;
         const int e = p + r * p - r * (r - 1) / 2 + (cc - r);
-        const T vr = v[r < QMAX ? r : QMAX - 1], vcc = v[cc < QMAX ? cc : QMAX - 1];
-        T vrc;
-        if (cc < q)
-          vrc = P[r * q + cc] + vr * vcc * inv;
-        else if (r < q)
-          vrc = -vr * inv;
-        else
-          vrc = inv;
-        if (!ok) vrc = (T)NAN;
+        T x;
+        if (cc < q) {  // both covariates: P + V Sigma^-1 V^T
+          const int rr = r < QMAX ? r : 0, c2 = cc < QMAX ? cc : 0;
+          x = P[rr * q + c2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int z = 0; z < 2; ++z)
+              if (u < pr && z < pr) x += v[u][rr] * si[u][z] * v[z][c2];
+        } else if (r < q) {  // covariate r, genetic cc - q: -(V Sigma^-1)[r][cc - q]
+          const int g = cc - q;
+          x = 0;
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (u < pr) x -= v[u][r < QMAX ? r : 0] * si[u][g < 2 ? g : 0];
+        } else {  // both genetic
+          x = si[(r - q) < 2 ? r - q : 0][(cc - q) < 2 ? cc - q : 0];
+        }
+        if (!ok) x = (T)NAN;
         if (out_f64)
-          ((double*)B)[o + e] = (double)vrc;
+          ((double*)B)[o + e] = (double)x;
         else
-          ((float*)B)[o + e] = (float)vrc;
+          ((float*)B)[o + e] = (float)x;
       }
   }
 }
 
+// Virtual columns of a tile of 64: with pr = 1 column i is SNP i; with pr = 2 the SNPs' two
+// genetic columns sit 16 apart (column i: SNP (i / 32) 16 + i % 16, genetic column (i / 16) % 2),
+// so that a thread holding columns tx + 16 u holds both columns of SNPs tx and 16 + tx.
+__device__ __forceinline__ int vcol_snp(int i, int pr) { return pr == 1 ? i : (i >> 5) * 16 + (i & 15); }
+__device__ __forceinline__ int vcol_k(int i, int pr) { return pr == 1 ? 0 : (i >> 4) & 1; }
+
+// Coded value of hard call x for genetic column k (0 outside {0, 1, 2}: validation reports it).
+__device__ __forceinline__ int code_of(const GeneticModel& gm, int k, int8_t x) {
+  return (uint8_t)x <= 2 ? gm.code[k][x] : 0;
+}
+
 // ------------------------------------------------------------------------------------------
-// CHOL: fused whiten-and-reduce, one CTA per 64 SNPs
+// CHOL: fused whiten-and-reduce, one CTA per 64 genetic columns (64 SNPs, or 32 with pr = 2)
 // ------------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) chol_scan_kernel(CholScanArgs<T> a) {
@@ -118,11 +179,11 @@ __global__ void __launch_bounds__(256) chol_scan_kernel(CholScanArgs<T> a) {
   __shared__ T Xs[TK][TS + 1];
   __shared__ T Rs[QMAX + 1][TR];
   __shared__ T red[16][TS + 1];
-  __shared__ T res[QMAX + 2][TS];
-  const int n = a.n, q = a.q;
+  __shared__ T res[QMAX + 3][TS];
+  const int n = a.n, q = a.q, pr = a.gm.pr;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int64_t s0 = (int64_t)blockIdx.x * TS;
-  T ps[4] = {}, pc[4] = {}, pa[4][QMAX] = {};
+  const int64_t s0 = (int64_t)blockIdx.x * (TS / pr);  // first SNP of the tile
+  T ps[4] = {}, pc[4] = {}, pa[4][QMAX] = {}, px[2] = {};
   for (int r0 = 0; r0 < n; r0 += TR) {
     const int kend = min(n, r0 + TR);
     T acc[4][4] = {};
@@ -132,8 +193,8 @@ __global__ void __launch_bounds__(256) chol_scan_kernel(CholScanArgs<T> a) {
         const int e = tid + 256 * l, k = e % TK, i = e / TK;
         const int gr = r0 + i, gk = k0 + k;
         Ls[k][i] = (gr < n && gk < n) ? a.Linv[(int64_t)gr * n + gk] : T(0);
-        const int64_t gs = s0 + i;
-        Xs[k][i] = (gs < a.m && gk < n) ? (T)a.XR[gs * n + gk] : T(0);
+        const int64_t gs = s0 + vcol_snp(i, pr);
+        Xs[k][i] = (gs < a.m && gk < n) ? (T)code_of(a.gm, vcol_k(i, pr), a.XR[gs * n + gk]) : T(0);
       }
       __syncthreads();
 #pragma unroll
@@ -169,11 +230,16 @@ __global__ void __launch_bounds__(256) chol_scan_kernel(CholScanArgs<T> a) {
 #pragma unroll
         for (int k = 0; k < QMAX; ++k) pa[v][k] += xl[k] * x;
       }
+      // the cross product of a SNP's two genetic columns (columns tx and tx + 16 of this thread)
+      px[0] += acc[u][0] * acc[u][1];
+      px[1] += acc[u][2] * acc[u][3];
     }
     __syncthreads();
   }
-  // reduce the 16 row-groups of each SNP
-  for (int slot = 0; slot < q + 2; ++slot) {
+  // reduce the 16 row-groups of each column: a (q), c, s, and with pr = 2 the cross product
+  // (held at the SNP's first column)
+  const int nslot = q + 2 + (pr > 1);
+  for (int slot = 0; slot < nslot; ++slot) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       T val;
@@ -182,8 +248,12 @@ __global__ void __launch_bounds__(256) chol_scan_kernel(CholScanArgs<T> a) {
 #pragma unroll
         for (int k = 0; k < QMAX; ++k)
           if (k == slot) val = pa[v][k];
+      } else if (slot == q) {
+        val = pc[v];
+      } else if (slot == q + 1) {
+        val = ps[v];
       } else {
-        val = slot == q ? pc[v] : ps[v];
+        val = (v & 1) ? T(0) : px[v >> 1];
       }
       red[ty][tx + 16 * v] = val;
     }
@@ -195,23 +265,35 @@ __global__ void __launch_bounds__(256) chol_scan_kernel(CholScanArgs<T> a) {
     }
     __syncthreads();
   }
-  if (tid < TS && s0 + tid < a.m) {
-    T av[QMAX];
+  // one thread per SNP: its first column (and, with pr = 2, the second 16 columns on)
+  const int i0 = tid < TS / pr ? (pr == 1 ? tid : (tid / 16) * 32 + tid % 16) : 0;
+  const int64_t snp = s0 + vcol_snp(i0, pr);
+  if (tid < TS / pr && snp < a.m) {
+    T av[2][QMAX], cv[2], S[3];
 #pragma unroll
-    for (int k = 0; k < QMAX; ++k) av[k] = k < q ? res[k][tid] : T(0);
-    schur_store<T>(q, a.P, a.b0, av, res[q][tid], res[q + 1][tid], a.sing_tol,
-                   a.out_offset + s0 + tid, a.j, a.t, a.B, a.wald, a.out_f64, a.flags, a.out_snp,
-                   a.out_var);
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int k = 0; k < QMAX; ++k) av[r][k] = (k < q && r < pr) ? res[k][i0 + 16 * r] : T(0);
+    cv[0] = res[q][i0];
+    cv[1] = pr > 1 ? res[q][i0 + 16] : T(0);
+    S[0] = res[q + 1][i0];
+    S[1] = pr > 1 ? res[q + 2][i0] : T(0);
+    S[2] = pr > 1 ? res[q + 1][i0 + 16] : T(0);
+    schur_store<T>(q, pr, a.P, a.b0, av, cv, S, a.sing_tol, a.out_offset + snp, a.j, a.t, a.B,
+                   a.wald, a.out_f64, a.flags, a.out_snp, a.out_var);
   }
 }
 
 // ------------------------------------------------------------------------------------------
 // EIG stage 1: X~ = Z^T X_R into scratch (SNP-major, leading dimension ldp)
 // ------------------------------------------------------------------------------------------
+// xt row v = snp * pr + k holds Z^T of genetic column k of the SNP (m pr rows).
 template <typename T>
 __global__ void __launch_bounds__(256) eig_rotate_kernel(int n, int ldp, const T* __restrict__ Zt,
                                                          const int8_t* __restrict__ XR, int64_t m,
-                                                         T* __restrict__ xt) {
+                                                         T* __restrict__ xt, GeneticModel gm) {
+  const int pr = gm.pr;
+  const int64_t mv = m * pr;  // rows of xt
   __shared__ T Zs[TK][TR + 1];
   __shared__ T Xs[TK][TS + 1];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
@@ -224,8 +306,8 @@ __global__ void __launch_bounds__(256) eig_rotate_kernel(int n, int ldp, const T
       const int e = tid + 256 * l, k = e % TK, i = e / TK;
       const int gr = r0 + i, gk = k0 + k;
       Zs[k][i] = (gr < n && gk < n) ? Zt[(int64_t)gr * n + gk] : T(0);
-      const int64_t gs = s0 + i;
-      Xs[k][i] = (gs < m && gk < n) ? (T)XR[gs * n + gk] : T(0);
+      const int64_t gv = s0 + i;
+      Xs[k][i] = (gv < mv && gk < n) ? (T)code_of(gm, (int)(gv % pr), XR[(gv / pr) * n + gk]) : T(0);
     }
     __syncthreads();
 #pragma unroll
@@ -243,7 +325,7 @@ __global__ void __launch_bounds__(256) eig_rotate_kernel(int n, int ldp, const T
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int64_t gs = s0 + ty + 16 * u;
-    if (gs >= m) continue;
+    if (gs >= mv) continue;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int gr = r0 + tx + 16 * v;
@@ -253,7 +335,8 @@ __global__ void __launch_bounds__(256) eig_rotate_kernel(int n, int ldp, const T
 }
 
 // ------------------------------------------------------------------------------------------
-// EIG stage 2: trait-batched reduction + Schur, one CTA per 64 SNPs x 16 traits
+// EIG stage 2: trait-batched reduction + Schur, one CTA per 64 genetic columns (64 SNPs, or
+// 32 with pr = 2, in the column order of vcol_snp / vcol_k) x 16 traits
 // ------------------------------------------------------------------------------------------
 constexpr int TT = 16;
 
@@ -261,18 +344,19 @@ template <typename T>
 __global__ void __launch_bounds__(256) eig_reduce_kernel(EigScanArgs<T> a) {
   __shared__ T Xs[TK][TS + 1];
   __shared__ T Ps[TK][TT * (QMAX + 2) + 1];
-  const int n = a.n, q = a.q, qc = q + 2, t = a.t;
+  const int n = a.n, q = a.q, qc = q + 2, t = a.t, pr = a.gm.pr;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int64_t s0 = (int64_t)blockIdx.x * TS;
+  const int64_t s0 = (int64_t)blockIdx.x * (TS / pr);  // first SNP of the tile
   const int j0 = blockIdx.y * TT;
   const int j = j0 + ty;
   T acc[4][QMAX + 2] = {};
+  T ax[2] = {};  // cross products of a SNP's two genetic columns (columns u = 0, 1 and 2, 3)
   for (int k0 = 0; k0 < n; k0 += TK) {
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const int e = tid + 256 * l, k = e % TK, i = e / TK;
-      const int64_t gs = s0 + i;
-      Xs[k][i] = (gs < a.m && k0 + k < n) ? a.xt[gs * a.ldp + k0 + k] : T(0);
+      const int64_t gs = s0 + vcol_snp(i, pr);
+      Xs[k][i] = (gs < a.m && k0 + k < n) ? a.xt[(gs * pr + vcol_k(i, pr)) * a.ldp + k0 + k] : T(0);
     }
     for (int e = tid; e < TK * TT * qc; e += 256) {
       const int k = e % TK, row = e / TK;
@@ -285,37 +369,51 @@ __global__ void __launch_bounds__(256) eig_reduce_kernel(EigScanArgs<T> a) {
       T xv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) xv[u] = Xs[k][tx + 16 * u];
-      const T* pr = &Ps[k][ty * qc];
+      const T* pl = &Ps[k][ty * qc];
 #pragma unroll
       for (int c = 0; c < QMAX + 1; ++c) {
         if (c < q + 1) {
-          const T pv = pr[c];
+          const T pv = pl[c];
 #pragma unroll
           for (int u = 0; u < 4; ++u) acc[u][c] += xv[u] * pv;
         }
       }
-      const T dm = pr[q + 1];
+      const T dm = pl[q + 1];
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc[u][QMAX + 1] += xv[u] * xv[u] * dm;
+      ax[0] += xv[0] * xv[1] * dm;
+      ax[1] += xv[2] * xv[3] * dm;
     }
     __syncthreads();
   }
   if (j >= t) return;
   const T* P = a.P + (int64_t)j * q * q;
   const T* b0 = a.b0 + (int64_t)j * q;
+  // this thread's SNPs: u = 0..3 (pr = 1), or the pairs (0, 1) and (2, 3) (pr = 2)
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int64_t gs = s0 + tx + 16 * u;
+  for (int w = 0; w < 4; ++w) {
+    if (pr > 1 && w >= 2) break;
+    const int u0 = pr > 1 ? 2 * w : w;
+    const int64_t gs = s0 + vcol_snp(tx + 16 * u0, pr);
     if (gs >= a.m) continue;
-    T av[QMAX];
+    T av[2][QMAX], cv[2] = {0, 0}, S[3] = {0, 0, 0};
 #pragma unroll
-    for (int k = 0; k < QMAX; ++k) av[k] = k < q ? acc[u][k] : T(0);
-    T c = 0;
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int k = 0; k < QMAX; ++k) av[r][k] = (k < q && r < pr) ? acc[u0 + r < 4 ? u0 + r : 0][k] : T(0);
 #pragma unroll
     for (int k = 0; k < QMAX + 1; ++k)
-      if (k == q) c = acc[u][k];
-    schur_store<T>(q, P, b0, av, c, acc[u][QMAX + 1], a.sing_tol, a.out_offset + gs, j, t, a.B,
-                   a.wald, a.out_f64, a.flags, a.out_snp, a.out_var);
+      if (k == q) {
+        cv[0] = acc[u0][k];
+        if (pr > 1) cv[1] = acc[u0 + 1 < 4 ? u0 + 1 : 0][k];
+      }
+    S[0] = acc[u0][QMAX + 1];
+    if (pr > 1) {
+      S[1] = ax[w < 2 ? w : 0];
+      S[2] = acc[u0 + 1 < 4 ? u0 + 1 : 0][QMAX + 1];
+    }
+    schur_store<T>(q, pr, P, b0, av, cv, S, a.sing_tol, a.out_offset + gs, j, t, a.B, a.wald,
+                   a.out_f64, a.flags, a.out_snp, a.out_var);
   }
 }
 
@@ -333,7 +431,8 @@ template <typename T>
 void chol_scan_simt(cudaStream_t s, const CholScanArgs<T>& a) {
   if (a.m <= 0) return;
   GW_REQUIRE(a.q >= 1 && a.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", a.q, QMAX);
-  chol_scan_kernel<T><<<ceil_div(a.m, TS), 256, 0, s>>>(a);
+  GW_REQUIRE(a.gm.pr == 1 || a.gm.pr == 2, GWAS_ERR_ARG, "pr=%d outside [1,2]", a.gm.pr);
+  chol_scan_kernel<T><<<ceil_div(a.m, TS / a.gm.pr), 256, 0, s>>>(a);
   GW_CHECK_LAUNCH();
 }
 
@@ -341,12 +440,14 @@ template <typename T>
 void eig_scan_simt(cudaStream_t s, const EigScanArgs<T>& a) {
   if (a.m <= 0) return;
   GW_REQUIRE(a.q >= 1 && a.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", a.q, QMAX);
-  GW_REQUIRE(a.m <= (int64_t)65535 * TS, GWAS_ERR_ARG, "block of %lld SNPs too large", (long long)a.m);
-  dim3 g1(ceil_div(a.ldp, TR), ceil_div(a.m, TS));
-  eig_rotate_kernel<T><<<g1, 256, 0, s>>>(a.n, a.ldp, a.Zt, a.XR, a.m, a.xt);
+  GW_REQUIRE(a.gm.pr == 1 || a.gm.pr == 2, GWAS_ERR_ARG, "pr=%d outside [1,2]", a.gm.pr);
+  const int64_t mv = a.m * a.gm.pr;  // rotated genetic columns
+  GW_REQUIRE(mv <= (int64_t)65535 * TS, GWAS_ERR_ARG, "block of %lld SNPs too large", (long long)a.m);
+  dim3 g1(ceil_div(a.ldp, TR), ceil_div(mv, TS));
+  eig_rotate_kernel<T><<<g1, 256, 0, s>>>(a.n, a.ldp, a.Zt, a.XR, a.m, a.xt, a.gm);
   GW_CHECK_LAUNCH();
   GW_REQUIRE(ceil_div(a.t, TT) <= 65535, GWAS_ERR_ARG, "t=%d too large", a.t);
-  dim3 g2(ceil_div(a.m, TS), ceil_div(a.t, TT));
+  dim3 g2(ceil_div(a.m, TS / a.gm.pr), ceil_div(a.t, TT));
   eig_reduce_kernel<T><<<g2, 256, 0, s>>>(a);
   GW_CHECK_LAUNCH();
 }

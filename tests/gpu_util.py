@@ -6,16 +6,20 @@ from oracle import gls
 
 
 def run(g, c, algo, precision, XR=None, device=True, block_snps=0, f64=False, packed=False,
-        validate=False, out_mode="full"):
+        validate=False, out_mode="full", model="additive"):
     """packed: pass the genotypes as packed rows (gwas_pack_genotypes on the host, then
-    gwas_scan_packed) instead of int8 rows (gwas_scan)."""
+    gwas_scan_packed) instead of int8 rows (gwas_scan).  model: the genetic model (p_R columns
+    per SNP, p = q + p_R)."""
     import torch
     XR = c.XR if XR is None else XR
     h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, algo=algo, precision=precision,
-                     block_snps=block_snps, validate_genotypes=int(validate), out_mode=out_mode)
+                     block_snps=block_snps, validate_genotypes=int(validate), out_mode=out_mode,
+                     genetic_model=model)
     try:
-        pv = c.p + c.p * (c.p + 1) // 2
-        m, t, p = XR.shape[0], c.t, {"snp": 2, "var": pv}.get(out_mode, c.p)
+        pr = g.gwas_genetic_columns(h)
+        pp = c.q + pr
+        pv = pp + pp * (pp + 1) // 2
+        m, t, p = XR.shape[0], c.t, {"snp": 2 * pr, "var": pv}.get(out_mode, pp)
         dt = torch.float64 if f64 else torch.float32
         dev = "cuda" if device else "cpu"
         X = np.ascontiguousarray(XR)

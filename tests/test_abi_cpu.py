@@ -45,13 +45,15 @@ def test_every_declared_symbol_is_exported(g):
 def test_default_options(g):
     o = g.gwas_default_options()
     assert (o.algo, o.precision, o.block_snps, o.validate_genotypes, o.device) == (0, 2, 0, 0, 0)
+    assert (o.out_mode, o.genetic_model) == (0, 0)
 
 
 def test_destroy_null_is_noop(g):
     g.lib.gwas_destroy(None)
 
 
-@pytest.mark.parametrize("case", ["n0", "q0", "q8", "t0", "h2_one", "h2_neg", "s2_zero", "algo", "prec"])
+@pytest.mark.parametrize("case", ["n0", "q0", "q8", "t0", "h2_one", "h2_neg", "s2_zero", "algo", "prec",
+                                  "model"])
 def test_setup_rejects_bad_arguments(g, case):
     n, q, t = 6, 2, 2
     Phi = np.eye(n); XL = np.ones((n, q)); Y = np.zeros((n, t))
@@ -67,6 +69,7 @@ def test_setup_rejects_bad_arguments(g, case):
     if case == "s2_zero": s2[0] = 0.0
     if case == "algo": opt.algo = 7
     if case == "prec": opt.precision = 9
+    if case == "model": opt.genetic_model = 7
     XLb = np.ones((n, 8))
     out = ctypes.c_void_p(123)
     st = g.lib.gwas_setup(Phi.ctypes.data, nn, XLb.ctypes.data, qq, Y.ctypes.data, tt,
@@ -92,6 +95,7 @@ def test_null_handle_calls(g):
     ms = ctypes.c_double()
     assert g.lib.gwas_setup_timing(None, ctypes.byref(ms)) == -1
     assert g.lib.gwas_info(None, None, None, None, None, None) == -1
+    assert g.lib.gwas_genetic_columns(None) == -1
     assert g.lib.gwas_stage_timing(None, 1) == -1
     ms8 = (ctypes.c_double * 8)()
     assert g.lib.gwas_stage_times(None, ms8, None) == -1

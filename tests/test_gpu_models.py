@@ -1,0 +1,103 @@
+"""Parity of the genetic models (p_R genetic columns per SNP; Table 1's "genetic model assumed")
+with the FP64 oracle: additive, dominant, recessive and the two-column additive + dominance
+model, whose test is the joint 2-d.o.f. Wald statistic of the block.
+
+Every scan path that takes them -- CHOL and EIG on the CUDA cores in FP64 (1e-6) and FP32 (2e-3),
+the tensor-core paths once they do -- is compared element by element with oracle.gls.gls_grid(model)
+on ragged shapes (SNP counts that leave partial 32- and 64-column tiles, n off every tile size,
+q from 1 to 7, several traits), in all three output modes, through the host-streaming ring, and
+with SNPs whose block is singular (no heterozygote: an all-zero dominance column)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gls
+from gpu_util import run, max_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-6, "fp32": 2e-3}
+MODELS = ["dominant", "recessive", "add_dom"]
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1207_2169_gb300 as g
+    return g
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("algo,n,q,m,t", [("chol", 97, 1, 131, 1), ("chol", 200, 3, 300, 2),
+                                          ("eig", 97, 1, 131, 5), ("eig", 130, 7, 70, 17),
+                                          ("eig", 200, 3, 300, 37)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_models_ragged(g, model, algo, n, q, m, t, prec):
+    c = synth.small_problem(11 * n + q + m + t, n=n, q=q, m=m, t=t)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, model=model)
+    B, W, nsing = run(g, c, algo, prec, f64=(prec == "fp64"), model=model)
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < TOL[prec] and ew < TOL[prec], (eb, ew)
+    assert nsing == int(np.isnan(Wref).sum())
+
+
+@pytest.mark.parametrize("algo,t", [("chol", 1), ("eig", 9)])
+def test_add_dom_singular_snps(g, algo, t):
+    """SNPs with no heterozygote (all-zero dominance column) or no homozygote of one kind: NaN in
+    every output of the pair and counted, exactly where the oracle's Cholesky fails."""
+    c = synth.small_problem(31, n=150, q=3, m=100, t=t)
+    XR = c.XR.copy()
+    XR[5] = np.where(XR[5] == 1, 0, XR[5])
+    XR[77] = np.where(XR[77] == 1, 2, XR[77])
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, XR, c.Y, c.h2, c.s2, model="add_dom")
+    assert np.all(np.isnan(Wref[[5, 77]]))
+    B, W, nsing = run(g, c, algo, "fp64", XR=XR, f64=True, model="add_dom")
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < 1e-6 and ew < 1e-6, (eb, ew)
+    assert nsing == int(np.isnan(Wref).sum()) >= 2 * t
+
+
+@pytest.mark.parametrize("algo,t", [("chol", 1), ("eig", 11)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_add_dom_output_modes(g, algo, t, prec):
+    """SNP mode: (b_x, b_d, se_x, se_d) per pair; VAR mode: the p coefficients, then the whole
+    Var(b) = (X_i^T M_j^-1 X_i)^-1 (p = q + 2) against the oracle entry by entry."""
+    c = synth.small_problem(32, n=140, q=2, m=90, t=t)
+    p = c.q + 2
+    _, _, Vd, V = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, full_var=True, model="add_dom")
+    Bref, Wref, _ = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, model="add_dom")
+    tol = TOL[prec]
+    Bs, Ws, _ = run(g, c, algo, prec, model="add_dom", out_mode="snp")
+    assert Bs.shape == (c.m, t, 4)
+    eb, ew = max_errors(Bs[..., :2], Ws, Bref[..., c.q:], Wref, Vd[..., c.q:])
+    assert eb < tol and ew < tol, (eb, ew)
+    se = np.sqrt(Vd[..., c.q:])
+    ok = np.isfinite(se)
+    assert np.array_equal(np.isnan(Bs[..., 2:]), ~ok)
+    assert np.max(np.abs(Bs[..., 2:][ok] - se[ok]) / se[ok]) < tol
+    Bv, Wv, _ = run(g, c, algo, prec, model="add_dom", out_mode="var")
+    assert Bv.shape == (c.m, t, p + p * (p + 1) // 2)
+    eb, ew = max_errors(Bv[..., :p], Wv, Bref, Wref, Vd)
+    assert eb < tol and ew < tol, (eb, ew)
+    Vg = np.empty(Bv.shape[:2] + (p, p))
+    e = p
+    for r in range(p):
+        for cc in range(r, p):
+            Vg[..., r, cc] = Vg[..., cc, r] = Bv[..., e]
+            e += 1
+    fin = np.all(np.isfinite(V), axis=(-1, -2))
+    assert np.array_equal(np.all(np.isnan(Vg), axis=(-1, -2)), ~fin)
+    d = np.sqrt(np.diagonal(V[fin], axis1=-2, axis2=-1))
+    err = np.abs(Vg[fin] - V[fin]) / (d[..., :, None] * d[..., None, :])
+    assert np.max(err) < tol, np.max(err)
+
+
+@pytest.mark.parametrize("algo,t", [("chol", 2), ("eig", 13)])
+def test_add_dom_streamed_equals_device(g, algo, t):
+    """Host buffers through the streaming ring give the device-resident scan's outputs bit for
+    bit (blocks of 96 SNPs: partial tiles at every block end)."""
+    c = synth.small_problem(33, n=120, q=3, m=500, t=t)
+    Bd, Wd, _ = run(g, c, algo, "fp64", f64=True, model="add_dom")
+    Bh, Wh, _ = run(g, c, algo, "fp64", f64=True, model="add_dom", device=False, block_snps=96)
+    assert np.array_equal(Bd, Bh, equal_nan=True) and np.array_equal(Wd, Wh, equal_nan=True)

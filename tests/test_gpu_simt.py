@@ -151,7 +151,7 @@ def test_setup_timing_and_info(g):
     try:
         assert g.gwas_setup_timing(h) > 0
         info = g.gwas_info(h)
-        assert info == dict(n=64, q=2, t=3, p=3, algo=2, precision=0)
+        assert info == dict(n=64, q=2, t=3, p=3, p_r=1, algo=2, precision=0)
     finally:
         g.gwas_destroy(h)
 
