@@ -259,6 +259,7 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     ta.block_snps = h->block_snps;
     ta.out_snp = h->out_snp;
     ta.out_var = h->out_var;
+    ta.gm = h->gm;
     ta.intercept = 1;
     for (int i = 0; i < n; ++i)
       if (XL[i] != 1.0) ta.intercept = 0;
@@ -587,7 +588,17 @@ GeneticModel genetic_model(int model) {
     case GWAS_MODEL_ADDITIVE: break;
     case GWAS_MODEL_DOMINANT: g.code[0][2] = 1; break;
     case GWAS_MODEL_RECESSIVE: g.code[0][1] = 0; g.code[0][2] = 1; break;
-    case GWAS_MODEL_ADD_DOM: g.pr = 2; g.code[1][1] = 1; break;
+    case GWAS_MODEL_ADD_DOM:
+      // working basis: the genotype indicators [x == 1, x == 2], which span the same columns
+      // as (x, [x == 1]) but stay well conditioned when one homozygote class is rare (x and
+      // [x == 1] then differ in a few individuals only); x = I1 + 2 I2 and [x == 1] = I1 give
+      // b_additive = b_I2 / 2, b_dominance = b_I1 - b_I2 / 2
+      g.pr = 2;
+      g.code[0][1] = 1; g.code[0][2] = 0;
+      g.code[1][1] = 0; g.code[1][2] = 1;
+      g.tm[0][0] = 0.f; g.tm[0][1] = 0.5f;
+      g.tm[1][0] = 1.f; g.tm[1][1] = -0.5f;
+      break;
     default: GW_REQUIRE(false, GWAS_ERR_ARG, "bad genetic_model %d", model);
   }
   return g;
@@ -639,8 +650,8 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
                  "CHOL keeps one n x n factor per trait: t=%d, n=%d is too large (use EIG)", t, n);
     if (h->prec == GWAS_PREC_SPLIT_BF16) {
       tc_check_supported(h->algo, n, q, t);
-      GW_REQUIRE(h->model == GWAS_MODEL_ADDITIVE, GWAS_ERR_UNSUPPORTED,
-                 "the tensor-core scans take the additive genetic model (use FP64 or FP32)");
+      GW_REQUIRE(h->gm.pr == 1 || h->algo == GWAS_ALGO_CHOL, GWAS_ERR_UNSUPPORTED,
+                 "the EIG tensor-core scan takes one genetic column per SNP (use FP64 or FP32)");
     }
     int ndev = 0;
     GW_CUDA(cudaGetDeviceCount(&ndev));

@@ -166,11 +166,20 @@ void split_bf16_rows(cudaStream_t s, const double* x, int rows, int cols, int64_
 
 // ------------------------------------------------------------------------------------------
 // Genetic models: the block X_R,i a SNP contributes to X_i = [X_L | X_R,i] has pr columns
-// (1 or 2); column k takes the value code[k][x] for the hard call x = 0, 1, 2.
+// (1 or 2).  The kernels build the block in a working basis, column k taking the value
+// code[k][x] for the hard call x = 0, 1, 2, and report the model's own coefficients
+// b_model = tm b_work (tm: pr x pr, identity unless the model's columns are a different basis
+// of the same span).  The fit, b_L and the joint Wald statistic do not depend on the basis.
 // ------------------------------------------------------------------------------------------
 struct GeneticModel {
   int pr = 1;
   int8_t code[2][3] = {{0, 1, 2}, {0, 0, 0}};
+  float tm[2][2] = {{1.f, 0.f}, {0.f, 1.f}};
+  // column k's coding as bytes cd(0) | cd(1) << 8 | cd(2) << 16 (the tensor-core converters' form)
+  uint32_t code_word(int k) const {
+    return (uint32_t)(uint8_t)code[k][0] | (uint32_t)(uint8_t)code[k][1] << 8 |
+           (uint32_t)(uint8_t)code[k][2] << 16;
+  }
 };
 // GWAS_MODEL_* -> its columns (throws Fail{GWAS_ERR_ARG} for an unknown model).
 GeneticModel genetic_model(int model);
@@ -240,7 +249,10 @@ void pack_genotypes(cudaStream_t s, const int8_t* x, int64_t m, int n, uint8_t* 
                     bool validate);
 void unpack_genotypes(cudaStream_t s, const uint8_t* in, int64_t m, int n, int8_t* out);
 void validate_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, int* flags);
-void snp_centres_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, float* mu);
+// mu[i pr + k] = centre of SNP i's genetic column k (coding code[k]): the multiple of 1/64 nearest
+// the column's mean over the n individuals, clamped to [0, 2].
+void snp_centres_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, float* mu, int pr,
+                        const uint32_t* code);
 // pv[e] = erfc(sqrt(w[e] / 2)) (chi-square(1) upper tail); NaN stays NaN; in place allowed.
 void wald_pvalues(cudaStream_t s, const float* w, int64_t count, float* pv);
 

@@ -87,23 +87,34 @@ __global__ void validate_packed_kernel(const uint32_t* __restrict__ in, int64_t 
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&flags[FLAG_GENOTYPE], 1);
 }
 
-// mu[i] = nearest multiple of 1/64 to SNP i's mean genotype, from packed codes (one warp per SNP).
+// mu[i pr + k] = nearest multiple of 1/64 to the mean of SNP i's coded column k (coding word
+// code_k: the values of genotypes 0, 1, 2 in bytes 0, 1, 2), clamped to [0, 2], from packed
+// codes (one warp per SNP).
 __global__ void centres_packed_kernel(const uint32_t* __restrict__ in, int64_t m, int n,
-                                      int row_bytes, float* __restrict__ mu) {
+                                      int row_bytes, float* __restrict__ mu, int pr,
+                                      uint32_t code0, uint32_t code1) {
   const int64_t snp = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (snp >= m) return;
   const int words = row_bytes / 4;
   const uint32_t* row = in + snp * words;
-  int sum = 0;
+  int n1 = 0, n2 = 0;  // genotypes 1 and 2 (padding codes past n are 0)
   for (int w = lane; w < words; w += 32) {
     const uint32_t v = row[w];
-    sum += __popc(v & 0x55555555u) + 2 * __popc(v & 0xAAAAAAAAu);
+    const uint32_t lo = v & 0x55555555u, hi = (v >> 1) & 0x55555555u;
+    n1 += __popc(lo & ~hi);
+    n2 += __popc(hi & ~lo);
   }
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if (lane == 0) {
-    const float c = rintf(64.f * (float)sum / (float)n) / 64.f;
-    mu[snp] = fminf(fmaxf(c, 0.f), 2.f);
+  for (int o = 16; o > 0; o >>= 1) {
+    n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+    n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  }
+  if (lane < pr) {
+    const uint32_t code = lane == 0 ? code0 : code1;
+    const float sum = (float)(code & 0xFFu) * (float)(n - n1 - n2) +
+                      (float)((code >> 8) & 0xFFu) * (float)n1 + (float)((code >> 16) & 0xFFu) * (float)n2;
+    const float c = rintf(64.f * sum / (float)n) / 64.f;
+    mu[snp * pr + lane] = fminf(fmaxf(c, 0.f), 2.f);
   }
 }
 
@@ -132,10 +143,11 @@ void validate_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, int* f
   GW_CHECK_LAUNCH();
 }
 
-void snp_centres_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, float* mu) {
+void snp_centres_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, float* mu, int pr,
+                        const uint32_t* code) {
   if (m <= 0) return;
-  centres_packed_kernel<<<(unsigned)((m + 7) / 8), 256, 0, s>>>((const uint32_t*)in, m, n,
-                                                               packed_row_bytes(n), mu);
+  centres_packed_kernel<<<(unsigned)((m + 7) / 8), 256, 0, s>>>(
+      (const uint32_t*)in, m, n, packed_row_bytes(n), mu, pr, code[0], pr > 1 ? code[1] : 0u);
   GW_CHECK_LAUNCH();
 }
 

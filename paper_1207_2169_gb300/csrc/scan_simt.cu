@@ -26,20 +26,24 @@ constexpr int TS = 64;  // SNPs per tile
 constexpr int TR = 64;  // rows (individuals) per tile
 constexpr int TK = 16;  // reduction chunk
 
-// The bordered solve of one pair for a genetic block of pr <= 2 columns:
+// The bordered solve of one pair for a genetic block of pr <= 2 columns (in the model's working
+// basis, see GeneticModel):
 //   a[r][k] = X_R,r^T M^-1 X_L[:,k],  c[r] = X_R,r^T M^-1 r0,  S[0..2] = (S_00, S_01, S_11) of
 //   S_RR = X_R^T M^-1 X_R (S[1], S[2] unused when pr = 1);
-//   V = P A (q x pr), Sigma = S_RR - A^T V, b_R = Sigma^-1 c, b_L = b0 - V b_R,
-//   wald = c^T Sigma^-1 c = b_R . c (pr d.o.f.),  Var(b) = [[P + V Sigma^-1 V^T, -V Sigma^-1],
-//   [-Sigma^-1 V^T, Sigma^-1]].
+//   V = P A (q x pr), Sigma = S_RR - A^T V, b_w = Sigma^-1 c, b_L = b0 - V b_w,
+//   wald = c^T Sigma^-1 c = b_w . c (pr d.o.f.),  Var(b) = [[P + V Sigma^-1 V^T, -V Sigma^-1],
+//   [-Sigma^-1 V^T, Sigma^-1]];
+// the genetic coefficients and their rows and columns of Var are reported as b_R = tm b_w,
+// Var_RR = tm Sigma^-1 tm^T, Var_LR = -V Sigma^-1 tm^T.
 // Singular (NaN outputs, counted) when a pivot of Sigma's Cholesky falls to <= tol times the
 // matching diagonal entry of S_RR -- the pivots of the full p x p Cholesky for the last rows.
 template <typename T>
-__device__ __forceinline__ void schur_store(int q, int pr, const T* __restrict__ P,
+__device__ __forceinline__ void schur_store(int q, const GeneticModel& gm, const T* __restrict__ P,
                                             const T* __restrict__ b0, const T (*a)[QMAX],
                                             const T* c, const T* S, T tol, int64_t i, int j, int t,
                                             void* B, void* wald, bool out_f64, int* flags,
                                             int out_snp, int out_var) {
+  const int pr = gm.pr;
   const int p = q + pr;
   T v[2][QMAX];
   T sg[2][2];
@@ -80,19 +84,25 @@ __device__ __forceinline__ void schur_store(int q, int pr, const T* __restrict__
     si[1][1] = sg[0][0] / det;
     si[0][1] = si[1][0] = -sg[0][1] / det;
   }
+  // the map to the reported basis (identity for one column)
+  const T tm[2][2] = {{(T)gm.tm[0][0], (T)gm.tm[0][1]}, {(T)gm.tm[1][0], (T)gm.tm[1][1]}};
   T out[QMAX + 4];
   T w;
-  T bR[2] = {0, 0};
+  T bw[2] = {0, 0};
   if (ok) {
 #pragma unroll
     for (int r = 0; r < 2; ++r)
-      if (r < pr) bR[r] = si[r][0] * c[0] + (pr > 1 ? si[r][1] * c[1] : (T)0);
+      if (r < pr) bw[r] = si[r][0] * c[0] + (pr > 1 ? si[r][1] * c[1] : (T)0);
 #pragma unroll
     for (int k = 0; k < QMAX; ++k)
-      if (k < q) out[k] = b0[k] - v[0][k] * bR[0] - (pr > 1 ? v[1][k] * bR[1] : (T)0);
-    out[q] = bR[0];
-    if (pr > 1) out[q + 1] = bR[1];
-    w = bR[0] * c[0] + (pr > 1 ? bR[1] * c[1] : (T)0);
+      if (k < q) out[k] = b0[k] - v[0][k] * bw[0] - (pr > 1 ? v[1][k] * bw[1] : (T)0);
+    if (pr == 1) {
+      out[q] = bw[0];
+    } else {
+      out[q] = tm[0][0] * bw[0] + tm[0][1] * bw[1];
+      out[q + 1] = tm[1][0] * bw[0] + tm[1][1] * bw[1];
+    }
+    w = bw[0] * c[0] + (pr > 1 ? bw[1] * c[1] : (T)0);
   } else {
     const T nanv = (T)NAN;
 #pragma unroll
@@ -100,12 +110,26 @@ __device__ __forceinline__ void schur_store(int q, int pr, const T* __restrict__
     w = nanv;
     atomicAdd(&flags[FLAG_SINGULAR], 1);
   }
-  if (out_snp) {  // (b_R, standard errors sqrt(diag Sigma^-1)) per pair
+  // Var_RR in the reported basis: vr[g][h] = (tm Sigma^-1 tm^T)[g][h]
+  T vr[2][2];
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      T acc = 0;
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+          if (u < pr && z < pr) acc += (pr == 1 ? (T)1 : tm[g][u]) * si[u][z] * (pr == 1 ? (T)1 : tm[hh][z]);
+      vr[g][hh] = acc;
+    }
+  if (out_snp) {  // (b_R, standard errors sqrt(diag Var_RR)) per pair
     const T b0v = out[q], b1v = out[q + 1 < QMAX + 4 ? q + 1 : 0];
     out[0] = b0v;
     if (pr > 1) out[1] = b1v;
-    out[pr] = ok ? sqrt(si[0][0]) : (T)NAN;
-    if (pr > 1) out[pr + 1] = ok ? sqrt(si[1][1]) : (T)NAN;
+    out[pr] = ok ? sqrt(vr[0][0]) : (T)NAN;
+    if (pr > 1) out[pr + 1] = ok ? sqrt(vr[1][1]) : (T)NAN;
   }
   const int nb = out_snp ? 2 * pr : p;
   const int pw = out_snp ? 2 * pr : out_var ? p + p * (p + 1) / 2 : p;
@@ -125,7 +149,7 @@ __device__ __forceinline__ void schur_store(int q, int pr, const T* __restrict__
   }
   if (out_var) {
     // packed upper triangle row by row after the p coefficients; rows/cols < q are X_L's,
-    // q + r the genetic column r (constant loop bounds keep v[] in registers)
+    // q + g the reported genetic column g (constant loop bounds keep v[] in registers)
 #pragma unroll
     for (int r = 0; r < QMAX + 2; ++r)
 #pragma unroll
@@ -141,14 +165,16 @@ __device__ __forceinline__ void schur_store(int q, int pr, const T* __restrict__
 #pragma unroll
             for (int z = 0; z < 2; ++z)
               if (u < pr && z < pr) x += v[u][rr] * si[u][z] * v[z][c2];
-        } else if (r < q) {  // covariate r, genetic cc - q: -(V Sigma^-1)[r][cc - q]
-          const int g = cc - q;
+        } else if (r < q) {  // covariate r, genetic g: -(V Sigma^-1 tm^T)[r][g]
+          const int g = (cc - q) < 2 ? cc - q : 0, rr = r < QMAX ? r : 0;
           x = 0;
 #pragma unroll
           for (int u = 0; u < 2; ++u)
-            if (u < pr) x -= v[u][r < QMAX ? r : 0] * si[u][g < 2 ? g : 0];
+#pragma unroll
+            for (int z = 0; z < 2; ++z)
+              if (u < pr && z < pr) x -= v[z][rr] * si[z][u] * (pr == 1 ? (T)1 : tm[g][u]);
         } else {  // both genetic
-          x = si[(r - q) < 2 ? r - q : 0][(cc - q) < 2 ? cc - q : 0];
+          x = vr[(r - q) < 2 ? r - q : 0][(cc - q) < 2 ? cc - q : 0];
         }
         if (!ok) x = (T)NAN;
         if (out_f64)
@@ -279,7 +305,7 @@ __global__ void __launch_bounds__(256) chol_scan_kernel(CholScanArgs<T> a) {
     S[0] = res[q + 1][i0];
     S[1] = pr > 1 ? res[q + 2][i0] : T(0);
     S[2] = pr > 1 ? res[q + 1][i0 + 16] : T(0);
-    schur_store<T>(q, pr, a.P, a.b0, av, cv, S, a.sing_tol, a.out_offset + snp, a.j, a.t, a.B,
+    schur_store<T>(q, a.gm, a.P, a.b0, av, cv, S, a.sing_tol, a.out_offset + snp, a.j, a.t, a.B,
                    a.wald, a.out_f64, a.flags, a.out_snp, a.out_var);
   }
 }
@@ -412,7 +438,7 @@ __global__ void __launch_bounds__(256) eig_reduce_kernel(EigScanArgs<T> a) {
       S[1] = ax[w < 2 ? w : 0];
       S[2] = acc[u0 + 1 < 4 ? u0 + 1 : 0][QMAX + 1];
     }
-    schur_store<T>(q, pr, P, b0, av, cv, S, a.sing_tol, a.out_offset + gs, j, t, a.B, a.wald,
+    schur_store<T>(q, a.gm, P, b0, av, cv, S, a.sing_tol, a.out_offset + gs, j, t, a.B, a.wald,
                    a.out_f64, a.flags, a.out_snp, a.out_var);
   }
 }

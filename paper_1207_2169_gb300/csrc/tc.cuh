@@ -21,6 +21,7 @@ struct TcSetupArgs {
   int intercept;         // column 0 of X_L is all ones: SNPs are centred (CHOL, EIG)
   int out_snp;           // B holds (b_snp, standard error) per pair instead of all p values
   int out_var;           // B holds the p values, then the p(p+1)/2 of Var(b) (packed upper)
+  GeneticModel gm;       // the SNP's genetic columns (p = q + gm.pr)
 };
 
 struct TcScanArgs {

@@ -88,6 +88,13 @@ __device__ __forceinline__ int block_cols(int nb, int n, int q) {
   return c < BN ? c : BN;
 }
 
+// With GP = 2 genetic columns per SNP a tile holds 64 SNPs: A row r is column (r / 16) % 2 of SNP
+// (r / 32) 16 + r % 16, so that a SNP's two rows sit in lanes l and l + 16 of one epilogue warp.
+template <int GP>
+__device__ __forceinline__ int row_snp(int r) { return GP == 1 ? r : (r >> 5) * 16 + (r & 15); }
+template <int GP>
+__device__ __forceinline__ int row_col(int r) { return GP == 1 ? 0 : (r >> 4) & 1; }
+
 // (tile, block, k-step) sequence shared by every role of a CTA.
 struct Step {
   int64_t tile;
@@ -101,11 +108,138 @@ __device__ __forceinline__ void advance(Step& s, int nblocks, int kpad) {
   s.tile += gridDim.x;
 }
 
-// QM: compile-time bound on q (3 or 7), so the epilogue's per-column arrays stay in registers.
+// The bordered solve of one SNP with a two-column genetic block, in FP64 (Algorithm 3's per-SNP
+// solve with X_R,i = [g0 | g1], the working basis of the model): a0, a1 = X_L^T M^-1 g_k
+// (centred columns), c = g_k^T M^-1 r0, S00, S01, S11 = g_k^T M^-1 g_l.  V = P [a0 a1],
+// Sigma = S_RR - [a0 a1]^T V, b_w = Sigma^-1 c, b_L = b0 - V b_w, wald = b_w . c (2 d.o.f.),
+// singular when a pivot of Sigma's Cholesky is at most 1e-5 of the matching S_kk.  Centred
+// columns g_k - mu_k: the intercept absorbs sum_k mu_k b_w,k.  Reported: b_R = tm b_w and
+// Var(b) = R Var_c R^T, Var_c the centred working-basis Var, R the map b_c -> reported b
+// (row 0: e_0 - sum_k mu_k e_(q+k); rows q + g: sum_k tm[g][k] e_(q+k); other rows e_r).
 template <int QM>
+__device__ __noinline__ void solve_pair(const CholTcParams& p, const float* a0, const float* a1,
+                                        float c0, float c1, double S00, double S01, double S11,
+                                        float m0, float m1, int64_t snp) {
+  const int q = p.q;
+  double v[2][QM];
+#pragma unroll
+  for (int k = 0; k < QM; ++k) {
+    double x0 = 0.0, x1 = 0.0;
+    if (k < q) {
+#pragma unroll
+      for (int l = 0; l < QM; ++l)
+        if (l < q) {
+          const double pk = __ldg(&p.P[k * q + l]);
+          x0 += pk * (double)a0[l];
+          x1 += pk * (double)a1[l];
+        }
+    }
+    v[0][k] = x0;
+    v[1][k] = x1;
+  }
+  double g00 = S00, g01 = S01, g11 = S11;
+#pragma unroll
+  for (int k = 0; k < QM; ++k)
+    if (k < q) {
+      g00 -= (double)a0[k] * v[0][k];
+      g01 -= (double)a0[k] * v[1][k];
+      g11 -= (double)a1[k] * v[1][k];
+    }
+  const double piv1 = g11 - g01 * g01 / g00;
+  const bool ok = g00 > 1e-5 * S00 && piv1 > 1e-5 * S11;
+  const int p2 = q + 2;
+  const int pw = p.out_snp ? 4 : p.out_var ? p2 + p2 * (p2 + 1) / 2 : p2;
+  float* Bo = p.B + (snp * p.t + p.j) * pw;
+  const float nanv = __int_as_float(0x7fc00000);
+  if (!ok) {
+    for (int k = 0; k < pw; ++k) Bo[k] = nanv;
+    if (p.W) p.W[snp * p.t + p.j] = nanv;
+    atomicAdd(&p.flags[FLAG_SINGULAR], 1);
+    return;
+  }
+  const double det = g00 * piv1;
+  const double si[2][2] = {{g11 / det, -g01 / det}, {-g01 / det, g00 / det}};
+  const double bw[2] = {si[0][0] * c0 + si[0][1] * c1, si[1][0] * c0 + si[1][1] * c1};
+  const double mu[2] = {p.centre ? (double)m0 : 0.0, p.centre ? (double)m1 : 0.0};
+  const double tm[2][2] = {{p.tm[0], p.tm[1]}, {p.tm[2], p.tm[3]}};
+  if (p.W) p.W[snp * p.t + p.j] = (float)(bw[0] * c0 + bw[1] * c1);
+  const double bR[2] = {tm[0][0] * bw[0] + tm[0][1] * bw[1], tm[1][0] * bw[0] + tm[1][1] * bw[1]};
+  // reported Var_RR = tm Si tm^T
+  double vr[2][2];
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      double x = 0.0;
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int z = 0; z < 2; ++z) x += tm[g][u] * si[u][z] * tm[h][z];
+      vr[g][h] = x;
+    }
+  if (p.out_snp) {
+    Bo[0] = (float)bR[0];
+    Bo[1] = (float)bR[1];
+    Bo[2] = (float)sqrt(vr[0][0]);
+    Bo[3] = (float)sqrt(vr[1][1]);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < QM; ++k)
+    if (k < q) {
+      double b = __ldg(&p.b0[k]) - v[0][k] * bw[0] - v[1][k] * bw[1];
+      if (k == 0) b -= mu[0] * bw[0] + mu[1] * bw[1];
+      Bo[k] = (float)b;
+    }
+  Bo[q] = (float)bR[0];
+  Bo[q + 1] = (float)bR[1];
+  if (!p.out_var) return;
+  // Var_c (centred, working basis), entry (r, c) of [[P + V Si V^T, -V Si], [-Si V^T, Si]]
+  auto vk = [&](int u, int k) { return v[u][k < QM ? k : QM - 1]; };
+  auto vc = [&](int r, int c) -> double {
+    if (r >= q && c >= q) return si[r - q][c - q];
+    if (c >= q) return -(vk(0, r) * si[0][c - q] + vk(1, r) * si[1][c - q]);
+    if (r >= q) return -(vk(0, c) * si[0][r - q] + vk(1, c) * si[1][r - q]);
+    double x = __ldg(&p.P[r * q + c]);
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int z = 0; z < 2; ++z) x += vk(u, r) * si[u][z] * vk(z, c);
+    return x;
+  };
+  // row r of R as up to three (index, coefficient) terms
+  auto rterms = [&](int r, int* idx, double* cf) -> int {
+    if (r >= q) {
+      idx[0] = q; cf[0] = tm[r - q][0];
+      idx[1] = q + 1; cf[1] = tm[r - q][1];
+      return 2;
+    }
+    idx[0] = r; cf[0] = 1.0;
+    if (r != 0) return 1;
+    idx[1] = q; cf[1] = -mu[0];
+    idx[2] = q + 1; cf[2] = -mu[1];
+    return 3;
+  };
+  for (int r = 0; r < p2; ++r)
+    for (int c = r; c < p2; ++c) {
+      int ir[3], ic[3];
+      double fr[3], fc[3];
+      const int nr = rterms(r, ir, fr), nc = rterms(c, ic, fc);
+      double x = 0.0;
+      for (int u = 0; u < nr; ++u)
+        for (int z = 0; z < nc; ++z) x += fr[u] * fc[z] * vc(ir[u], ic[z]);
+      Bo[p2 + r * p2 - r * (r - 1) / 2 + (c - r)] = (float)x;
+    }
+}
+
+// QM: compile-time bound on q (3 or 7), so the epilogue's per-column arrays stay in registers.
+// GP: genetic columns per SNP (1, or 2 for a two-column genetic model).
+template <int QM, int GP>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     chol_tc_kernel(const __grid_constant__ CholMaps lmaps, const __grid_constant__ CUtensorMap mapG,
                    const CholTcParams p) {
+  constexpr int TS = BM / GP;        // SNPs per tile
+  constexpr int PKB = TS * 16;       // bytes of one packed slice (64 genotypes of TS SNPs)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -113,7 +247,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint8_t* sP = sB + SB * B_BYTES;
   Bars* bars = (Bars*)(sP + PR * PK_BYTES);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t tiles_run = (p.m + BM - 1) / BM;
+  const int64_t tiles_run = (p.m + TS - 1) / TS;
   const int nblocks = p.rpad / BN;
   int* tflag = p.flags + FLAG_TIMEOUT;
 
@@ -175,15 +309,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
       }
     } else if (lane == 1) {
-      // packed genotype slices (64 genotypes x 128 SNPs, 2 KB) via TMA, in the K-step order the
+      // packed genotype slices (64 genotypes x TS SNPs) via TMA, in the K-step order the
       // converters consume them; rows past m read as zero
       int ps = 0;
       uint32_t pph = 0;
       for (Step st{blockIdx.x, 0, 0}; st.tile < tiles_run; advance(st, nblocks, p.kpad)) {
         if (!mbar_wait(&bars->pk_empty[ps], pph ^ 1, abort, tflag, WAIT_NS)) break;
-        mbar_arrive_expect_tx(&bars->pk_full[ps], PK_BYTES);
+        mbar_arrive_expect_tx(&bars->pk_full[ps], PKB);
         tma_load_2d(sP + ps * PK_BYTES, &mapG, &bars->pk_full[ps], st.ks * 16,
-                    (int32_t)(st.tile * BM));
+                    (int32_t)(st.tile * TS));
         if (++ps == PR) { ps = 0; pph ^= 1; }
       }
     }
@@ -234,6 +368,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     // genotypes) into BF16 chunks 4 hh .. 4 hh + 3 of the row's swizzled 128-byte line.
     const int ct = conv_index(warp) * 32 + lane;
     const int r = ct >> 1, hh = ct & 1;
+    const int srow = row_snp<GP>(r);             // the row's SNP within the tile
+    const uint32_t code = p.code[row_col<GP>(r)];  // the row's genetic column
     const uint32_t line = (r >> 3) * 1024 + (r & 7) * 128;
     int per_tile = 0;
     for (int nb = 0; nb < nblocks; ++nb) per_tile += ksteps(nb, p.kpad);
@@ -242,21 +378,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     bool ok = true;
     int ti = 0;  // this CTA's tile counter (selects the centre buffer)
     for (int64_t tile = blockIdx.x; tile < tiles_run && ok; tile += gridDim.x, ++ti) {
-      // byte tables of this row: g - mu (mu = 0 without centring)
-      uint32_t lutlo = GENO_LO, luthi = GENO_HI;
+      // byte tables of this row: cd(g) - mu (mu = 0 without centring)
+      uint32_t lutlo, luthi;
       if (p.centre) {
         const int mb = ti & 1;
         ok = __all_sync(0xffffffffu,
                         mbar_wait(&bars->mu_full[mb], (ti >> 1) & 1, abort, tflag, WAIT_NS));
         if (!ok) break;
-        centred_lut(bars->mu[mb][r], lutlo, luthi);
+        coded_lut(bars->mu[mb][r], code, lutlo, luthi);
         mbar_arrive(&bars->mu_empty[mb]);
+      } else {
+        coded_lut(0.f, code, lutlo, luthi);
       }
       for (int g = 0; g < per_tile; ++g) {
         // warp-uniform exits: every lane leaves together if any wait gave up
         ok = __all_sync(0xffffffffu, mbar_wait(&bars->pk_full[ps], pph, abort, tflag, WAIT_NS));
         if (!ok) break;
-        const uint2 w = *reinterpret_cast<const uint2*>(sP + ps * PK_BYTES + r * 16 + hh * 8);
+        const uint2 w = *reinterpret_cast<const uint2*>(sP + ps * PK_BYTES + srow * 16 + hh * 8);
         // the slot is refilled by TMA (async proxy): order these generic reads before it
         fence_proxy_async_smem();
         __syncwarp();
@@ -287,22 +425,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int buf = 0;
     uint32_t accph = 0;
     bool ok = true;
-    // With centring, this thread also finds the centre of its SNP one tile ahead (the
+    // This thread's row: genetic column gcol of SNP row_snp(row) of each tile (GP = 2: lanes
+    // 0-15 hold the first column of the warp's 16 SNPs, lanes 16-31 the second).
+    const int row = 32 * warp + lane;
+    const int gcol = row_col<GP>(row);
+    // With centring, this thread also finds the centre of its row one tile ahead (the
     // converters build the tile's byte tables from it): the nearest multiple of 1/64 to the
-    // mean genotype, clamped to [0, 2] so that g - mu stays exact in BF16.  Rows past m get 0.
+    // mean of the coded column, clamped to [0, 2] so that cd(g) - mu stays exact in BF16.  Rows
+    // past m get 0.
     auto centre_of = [&](int64_t t) -> float {
-      const int64_t snp = t * BM + 32 * warp + lane;
+      const int64_t snp = t * TS + row_snp<GP>(row);
       if (snp >= p.m) return 0.f;
-      const uint4* row = reinterpret_cast<const uint4*>(p.G + snp * p.row_bytes);
-      int sum = 0;
+      const uint4* rw = reinterpret_cast<const uint4*>(p.G + snp * p.row_bytes);
+      int n1 = 0, n2 = 0;
       for (int i = 0; i < p.row_bytes / 16; ++i) {
-        const uint4 v = __ldg(row + i);
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sum += __popc(w[k] & 0x55555555u) + 2 * __popc(w[k] & 0xAAAAAAAAu);
+        const uint4 v = __ldg(rw + i);
+        count12(v.x, n1, n2);
+        count12(v.y, n1, n2);
+        count12(v.z, n1, n2);
+        count12(v.w, n1, n2);
       }
-      const float c = rintf(64.f * (float)sum / (float)n) / 64.f;
-      return fminf(fmaxf(c, 0.f), 2.f);
+      return coded_centre(n1, n2, n, p.code[gcol]);
     };
     auto publish_centre = [&](int ti, float c) -> bool {
       const int mb = ti & 1;
@@ -326,7 +469,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         mu_next = centre_of(tile + gridDim.x);
         ok = publish_centre(ti + 1, mu_next);
       }
-      double S = 0.0;
+      double S = 0.0, X = 0.0;  // s of this row; with GP = 2, the cross product with its partner
       float A[QM], C = 0.f;
 #pragma unroll
       for (int k = 0; k < QM; ++k) A[k] = 0.f;
@@ -336,18 +479,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           tc_fence_after();
           const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + buf * BN;
           const int c0 = nb * BN, ncols = block_cols(nb, n, q);
-          float bs_ = 0.f;
+          float bs_ = 0.f, bx_ = 0.f;
           uint32_t ra[32];
 #pragma unroll 1
           for (int c = 0; c < ncols; c += 32) {
             tmem_ld32_async(base + c, ra);
             tmem_wait32(ra);
-            float ss = 0.f;
+            float ss = 0.f, xs = 0.f;
             if (c0 + c + 32 <= n) {
 #pragma unroll
               for (int i = 0; i < 32; ++i) {
                 const float x = __uint_as_float(ra[i]);
                 ss = fmaf(x, x, ss);
+                // the partner row (the SNP's other genetic column) is 16 lanes away
+                if (GP == 2) xs = fmaf(x, __shfl_xor_sync(0xffffffffu, x, 16), xs);
               }
             } else {
               // the chunk holding row n: genotype columns, then a_0 .. a_{q-1}, c
@@ -355,6 +500,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               for (int i = 0; i < 32; ++i) {
                 const int col = c0 + c + i;
                 const float x = __uint_as_float(ra[i]);
+                if (GP == 2) {
+                  const float xp = __shfl_xor_sync(0xffffffffu, x, 16);
+                  if (col < n) xs = fmaf(x, xp, xs);
+                }
                 if (col < n) ss = fmaf(x, x, ss);
 #pragma unroll
                 for (int k = 0; k < QM; ++k)
@@ -363,16 +512,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               }
             }
             bs_ += ss;
+            bx_ += xs;
           }
           S += bs_;
+          X += bx_;
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
         }
         if (++buf == 2) { buf = 0; accph ^= 1; }
       }
-      const int64_t snp = tile * BM + 32 * warp + lane;
-      if (ok && snp < p.m) {
+      const int64_t snp = tile * TS + row_snp<GP>(row);
+      if (GP == 2) {
+        // the SNP's first-column lane (lanes 0-15) solves with its partner's s, a, c and centre
+        const double S1 = __shfl_down_sync(0xffffffffu, S, 16);
+        const float C1 = __shfl_down_sync(0xffffffffu, C, 16);
+        const float mu1 = __shfl_down_sync(0xffffffffu, mu_cur, 16);
+        float A1[QM];
+#pragma unroll
+        for (int k = 0; k < QM; ++k) A1[k] = __shfl_down_sync(0xffffffffu, A[k], 16);
+        if (ok && gcol == 0 && snp < p.m) solve_pair<QM>(p, A, A1, C, C1, S, X, S1, mu_cur, mu1, snp);
+      } else if (ok && snp < p.m) {
         double v[QM], aPa = 0.0;
 #pragma unroll
         for (int k = 0; k < QM; ++k) {
@@ -453,8 +613,8 @@ int g_max_ctas[64][2];  // per device: co-resident CTAs of each instantiation
 template <int QM>
 int max_resident_ctas() {
   int per_sm = 0, dev = 0, sms = 0;
-  GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_tc_kernel<QM>, NUM_THREADS,
-                                                        SMEM_BYTES));
+  GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_tc_kernel<QM, 1>,
+                                                        NUM_THREADS, SMEM_BYTES));
   GW_REQUIRE(per_sm >= 1, GWAS_ERR_UNSUPPORTED, "the CHOL tensor-core kernel does not fit on an SM");
   GW_CUDA(cudaGetDevice(&dev));
   GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -473,10 +633,14 @@ void chol_tc_prepare() {
   std::lock_guard<std::mutex> lock(mu);
   int* mx = g_max_ctas[current_device()];
   if (mx[0] && mx[1]) return;  // attributes and occupancy belong to the device: once per device
-  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)SMEM_BYTES));
-  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QMAX, 1>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)SMEM_BYTES));
+  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QMAX, 2>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
   mx[0] = max_resident_ctas<3>();
   mx[1] = max_resident_ctas<QMAX>();
 }
@@ -487,15 +651,20 @@ void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& ma
                     const CholTcParams& p, int num_sms) {
   if (p.m <= 0) return;
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", p.q, QMAX);
+  GW_REQUIRE(p.gp == 1 || p.gp == 2, GWAS_ERR_ARG, "genetic columns %d outside [1,2]", p.gp);
   // persistent: no more CTAs than fit at once (and no more than the tiles need)
-  const int64_t tiles = (p.m + BM - 1) / BM;
+  const int64_t tiles = (p.m + BM / p.gp - 1) / (BM / p.gp);
   int64_t cap = chol_tc_resident_ctas(p.q);
   if (cap <= 0 || cap > num_sms) cap = num_sms;
   const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
-  if (p.q <= 3)
-    chol_tc_kernel<3><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+  if (p.q <= 3 && p.gp == 1)
+    chol_tc_kernel<3, 1><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+  else if (p.gp == 1)
+    chol_tc_kernel<QMAX, 1><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+  else if (p.q <= 3)
+    chol_tc_kernel<3, 2><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
   else
-    chol_tc_kernel<QMAX><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+    chol_tc_kernel<QMAX, 2><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
   GW_CHECK_LAUNCH();
 }
 

@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
         if (tile != cur_tile) {
           cur_tile = tile;
           const int64_t snp = tile * BM + r;
-          centred_lut(p.mu && snp < p.m ? p.mu[snp] : 0.f, lutlo, luthi);
+          coded_lut(p.mu && snp < p.m ? p.mu[snp] : 0.f, p.code[0], lutlo, luthi);
         }
         for (int ks = 0; ks < nk; ++ks) {
           // warp-uniform exits: every lane leaves together if any wait gave up

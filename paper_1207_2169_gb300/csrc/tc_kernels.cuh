@@ -21,13 +21,16 @@ struct CholTcParams {
   int centre;         // nonzero: centre each SNP by the multiple of 1/64 nearest its mean
   const uint8_t* G;   // the launch's packed genotype rows (also read through mapG)
   int row_bytes;      // packed_row_bytes(n)
-  int out_snp;        // B holds (b_snp, standard error) per pair instead of all p values
+  int out_snp;        // B holds (b_R, standard errors) per pair instead of all p values
   int out_var;        // B holds the p values, then the p(p+1)/2 of Var(b) (packed upper)
-  float* B;           // m x t x p
+  float* B;           // m x t x p (p = q + gp)
   float* W;           // m x t or NULL
   int* flags;
+  int gp;             // genetic columns per SNP (1 or 2); a tile holds CHOL_TC_BM / gp SNPs
+  uint32_t code[2];   // coding of each genetic column: values of genotypes 0, 1, 2 in bytes 0-2
+  float tm[4];        // gp = 2: reported coefficients = tm (row-major 2 x 2) x working ones
 };
-constexpr int CHOL_TC_BM = 128;  // SNPs per tile
+constexpr int CHOL_TC_BM = 128;  // rows (SNP columns) per tile
 // Tensor maps of one trait's split augmented L^-1: rows = 2 * rpad (hi piece then lo piece),
 // cols = kpad, BF16, 128-byte swizzle, 64-column boxes of 256 - 64 j rows (m[j]: the rows
 // 64 j .. 255 of a block, which a K step on the block's diagonal meets).
@@ -35,11 +38,11 @@ struct CholMaps {
   CUtensorMap m[4];
 };
 // mapG: the 2-bit packed genotypes of the launch, uint8 [m][packed_row_bytes(n)], boxes of
-// 16 bytes x 128 rows, no swizzle.
+// 16 bytes x (128 / gp) rows, no swizzle.
 void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& mapG,
                     const CholTcParams& p, int num_sms);
-// uint8 map over packed genotype rows (boxes 16 bytes x 128 rows).
-CUtensorMap make_map_packed(const void* base, int64_t rows, int row_bytes);
+// uint8 map over packed genotype rows (boxes 16 bytes x box_rows rows).
+CUtensorMap make_map_packed(const void* base, int64_t rows, int row_bytes, int box_rows = 128);
 void chol_tc_prepare();
 // CTAs of the CHOL kernel that fit on the device at once (after chol_tc_prepare).
 int chol_tc_resident_ctas(int q);
@@ -66,6 +69,9 @@ struct EigTcParams {
   int out_var;             // AC: B holds the p values, then the p(p+1)/2 of Var(b)
   float* W;                // AC: m x t or NULL
   int* flags;
+  int gp;                  // genetic columns per SNP
+  uint32_t code[2];        // coding of each genetic column (bytes: values of genotypes 0, 1, 2)
+  float tm[4];             // gp = 2: reported coefficients = tm (row-major 2 x 2) x working ones
 };
 // Traits per AC column block: T (q+1) accumulator columns, with the last trait's load of
 // QP = (q+1 rounded up to 4 or 8) columns still inside the 256-column block.

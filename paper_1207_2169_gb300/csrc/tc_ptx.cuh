@@ -277,6 +277,38 @@ __device__ __forceinline__ void centred_lut(float mu, uint32_t& lo, uint32_t& hi
   }
 }
 
+// Byte tables for a coded, centred genotype cd(g) - mu (g = 0, 1, 2), cd(g) = byte g of `code`
+// (the genetic model's value for hard call g: 0, 1 or 2).  Exact when mu is a multiple of 1/64 in
+// [0, 2].  code = 0x020100 (the allele count) gives centred_lut.
+__device__ __forceinline__ void coded_lut(float mu, uint32_t code, uint32_t& lo, uint32_t& hi) {
+  lo = 0u;
+  hi = 0u;
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const float v = (float)((code >> (8 * g)) & 0xFFu) - mu;
+    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    lo |= (b & 0xFFu) << (8 * g);
+    hi |= (b >> 8) << (8 * g);
+  }
+}
+
+// Counts of codes 1 and 2 in a word of sixteen 2-bit genotype codes (code 3 counts as neither).
+__device__ __forceinline__ void count12(uint32_t w, int& n1, int& n2) {
+  const uint32_t lo = w & 0x55555555u, hi = (w >> 1) & 0x55555555u;
+  n1 += __popc(lo & ~hi);
+  n2 += __popc(hi & ~lo);
+}
+
+// The centre of a SNP's coded column from its counts of genotypes 1 and 2 among n: the multiple
+// of 1/64 nearest the column mean, clamped to [0, 2] (so that every cd(g) - mu is exact in BF16).
+__device__ __forceinline__ float coded_centre(int n1, int n2, int n, uint32_t code) {
+  const float c0 = (float)(code & 0xFFu), c1 = (float)((code >> 8) & 0xFFu),
+              c2 = (float)((code >> 16) & 0xFFu);
+  const float sum = c0 * (float)(n - n1 - n2) + c1 * (float)n1 + c2 * (float)n2;
+  const float c = rintf(64.f * sum / (float)n) / 64.f;
+  return fminf(fmaxf(c, 0.f), 2.f);
+}
+
 __device__ __forceinline__ uint4 geno8_to_bf16x8_lut(uint2 w, uint32_t LO, uint32_t HI) {
   const uint32_t s0 = (w.x & 0xFFFFu) * 17u + 0x4040u, s1 = (w.x >> 16) * 17u + 0x4040u;
   const uint32_t s2 = (w.y & 0xFFFFu) * 17u + 0x4040u, s3 = (w.y >> 16) * 17u + 0x4040u;

@@ -52,15 +52,15 @@ CUtensorMap make_map_bf16(const void* base, int64_t rows, int64_t cols, int box_
 }
 
 // 2-D uint8 map over packed genotype rows [rows][row_bytes] (row_bytes a multiple of 16, base
-// 16-byte aligned), boxes of 16 bytes x 128 rows, no swizzle; rows past the end read as zero.
-CUtensorMap make_map_packed(const void* base, int64_t rows, int row_bytes) {
+// 16-byte aligned), boxes of 16 bytes x box_rows rows, no swizzle; rows past the end read as zero.
+CUtensorMap make_map_packed(const void* base, int64_t rows, int row_bytes, int box_rows) {
   GW_REQUIRE(row_bytes % 16 == 0 && ((uintptr_t)base & 15) == 0 && rows >= 1 &&
-                 rows <= ((int64_t)1 << 32),
+                 rows <= ((int64_t)1 << 32) && box_rows >= 1 && box_rows <= 256,
              GWAS_ERR_ARG, "packed genotypes not TMA-aligned (base and rows need 16 bytes)");
   CUtensorMap m;
   cuuint64_t dims[2] = {(cuuint64_t)row_bytes, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
-  cuuint32_t box[2] = {16, 128};
+  cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims,
                            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -89,6 +89,7 @@ struct TcState {
   int out_snp = 0;
   int out_var = 0;
   int traits_ac = 0;
+  GeneticModel gm;
   CUtensorMap mapZ, mapU, mapD, mapX;
 };
 
@@ -124,6 +125,7 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     st->intercept = a.intercept != 0;
     st->out_snp = a.out_snp;
     st->out_var = a.out_var;
+    st->gm = a.gm;
     int dev = 0;
     GW_CUDA(cudaGetDevice(&dev));
     GW_CUDA(cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -223,7 +225,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
   const int ctas = a.max_ctas > 0 && a.max_ctas < st->num_sms ? a.max_ctas : st->num_sms;
   const int rb = packed_row_bytes(st->n);
   if (st->algo == GWAS_ALGO_CHOL) {
-    const CUtensorMap mapG = make_map_packed(a.G, a.m, rb);
+    const CUtensorMap mapG = make_map_packed(a.G, a.m, rb, CHOL_TC_BM / st->gm.pr);
     for (int j = 0; j < st->t; ++j) {
       CholTcParams p{};
       p.m = a.m;
@@ -240,6 +242,10 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
       p.out_var = st->out_var;
       p.G = a.G;
       p.row_bytes = rb;
+      p.gp = st->gm.pr;
+      p.code[0] = st->gm.code_word(0);
+      p.code[1] = st->gm.code_word(1);
+      for (int e = 0; e < 4; ++e) p.tm[e] = st->gm.tm[e / 2][e % 2];
       p.B = a.B;
       p.W = a.wald;
       p.flags = a.flags;
@@ -263,6 +269,10 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.sbuf = st->sbuf;
     p.lds = st->mcap;
     p.flags = a.flags;
+    p.gp = st->gm.pr;
+    p.code[0] = st->gm.code_word(0);
+    p.code[1] = st->gm.code_word(1);
+    for (int e = 0; e < 4; ++e) p.tm[e] = st->gm.tm[e / 2][e % 2];
     // ROT: Xsq = (Z^T x)^2 for this chunk (Algorithm 4's rotation, squared and split)
     const uint8_t* Gc = a.G + off * rb;
     const CUtensorMap mapG = make_map_packed(Gc, mm, rb);
@@ -270,7 +280,8 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     cudaEvent_t ev = nullptr;
     if (st->mu) {
       ev = tm ? tm->begin(s, STAGE_CENTRES) : nullptr;
-      snp_centres_packed(s, Gc, mm, n, st->mu);
+      const uint32_t codes[2] = {st->gm.code_word(0), st->gm.code_word(1)};
+      snp_centres_packed(s, Gc, mm, n, st->mu, st->gm.pr, codes);
       if (ev) tm->end(s, ev);
     }
     p.mu = st->mu;

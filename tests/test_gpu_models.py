@@ -16,7 +16,7 @@ from gpu_util import run, max_errors
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-6, "fp32": 2e-3}
+TOL = {"fp64": 1e-6, "fp32": 2e-3, "split_bf16": 1e-4}
 MODELS = ["dominant", "recessive", "add_dom"]
 
 
@@ -58,8 +58,9 @@ def test_add_dom_singular_snps(g, algo, t):
     assert nsing == int(np.isnan(Wref).sum()) >= 2 * t
 
 
-@pytest.mark.parametrize("algo,t", [("chol", 1), ("eig", 11)])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("algo,t,prec", [("chol", 1, "fp64"), ("chol", 1, "fp32"),
+                                         ("eig", 11, "fp64"), ("eig", 11, "fp32"),
+                                         ("chol", 1, "split_bf16")])
 def test_add_dom_output_modes(g, algo, t, prec):
     """SNP mode: (b_x, b_d, se_x, se_d) per pair; VAR mode: the p coefficients, then the whole
     Var(b) = (X_i^T M_j^-1 X_i)^-1 (p = q + 2) against the oracle entry by entry."""
@@ -101,3 +102,51 @@ def test_add_dom_streamed_equals_device(g, algo, t):
     Bd, Wd, _ = run(g, c, algo, "fp64", f64=True, model="add_dom")
     Bh, Wh, _ = run(g, c, algo, "fp64", f64=True, model="add_dom", device=False, block_snps=96)
     assert np.array_equal(Bd, Bh, equal_nan=True) and np.array_equal(Wd, Wh, equal_nan=True)
+
+
+# ------------------------------------------------------------------------------- tensor cores
+
+@pytest.mark.parametrize("model", ["dominant", "recessive"])
+@pytest.mark.parametrize("algo,n,q,m,t", [("chol", 97, 1, 131, 1), ("chol", 256, 3, 700, 1),
+                                          ("eig", 200, 3, 300, 37), ("eig", 130, 7, 70, 17)])
+@pytest.mark.parametrize("packed", [False, True])
+def test_split_single_column_models(g, model, algo, n, q, m, t, packed):
+    """One-column codings on the tensor cores: each row's byte table maps the hard calls to the
+    model's values (centred by the multiple of 1/64 nearest the coded column's mean)."""
+    c = synth.small_problem(13 * n + q + m + t, n=n, q=q, m=m, t=t)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, model=model)
+    B, W, nsing = run(g, c, algo, "split_bf16", model=model, packed=packed)
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < 1e-4 and ew < 1e-4, (eb, ew)
+    assert nsing == int(np.isnan(Wref).sum())
+
+
+@pytest.mark.parametrize("n,q,m,t", [(97, 1, 131, 1), (256, 3, 700, 1), (520, 7, 300, 2),
+                                     (64, 2, 1, 1), (1000, 3, 1500, 1)])
+def test_split_chol_add_dom(g, n, q, m, t):
+    """The two-column model on the CHOL tensor-core kernel: 64 SNPs per tile, a SNP's two working
+    columns 16 TMEM lanes apart, their cross product summed with a lane shuffle, the 2 x 2 Schur
+    solve in FP64; ragged tails, one SNP, q up to 7, the n = 1000 shape."""
+    c = synth.small_problem(17 * n + q + m, n=n, q=q, m=m, t=t, h2=0.5 if n == 1000 else None)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, model="add_dom")
+    for packed in (False, True):
+        B, W, nsing = run(g, c, "chol", "split_bf16", model="add_dom", packed=packed)
+        eb, ew = max_errors(B, W, Bref, Wref, Vref)
+        assert eb < 1e-4 and ew < 1e-4, (packed, eb, ew)
+        assert nsing == int(np.isnan(Wref).sum())
+
+
+def test_split_chol_add_dom_streamed_and_without_intercept(g):
+    """Host buffers through the streaming ring equal the device-resident scan; zero-mean
+    covariates without an intercept column (no centring) still meet the tolerance."""
+    c = synth.small_problem(35, n=300, q=3, m=700, t=1)
+    Bd, Wd, _ = run(g, c, "chol", "split_bf16", model="add_dom", packed=True)
+    Bh, Wh, _ = run(g, c, "chol", "split_bf16", model="add_dom", packed=True, device=False,
+                    block_snps=256)
+    assert np.array_equal(Bd, Bh, equal_nan=True) and np.array_equal(Wd, Wh, equal_nan=True)
+    c.XL = c.XL.copy()
+    c.XL[:, 0] = np.random.default_rng(6).standard_normal(c.n)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, model="add_dom")
+    B, W, _ = run(g, c, "chol", "split_bf16", model="add_dom")
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < 1e-4 and ew < 1e-4, (eb, ew)
