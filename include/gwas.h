@@ -87,8 +87,12 @@ enum { GWAS_OUT_FULL = 0, GWAS_OUT_SNP = 1, GWAS_OUT_VAR = 2 };
  *   ADD_DOM    x, [x == 1]        (p_R = 2: allele count and heterozygosity; wald is their joint
  *                                 2-d.o.f. test)
  * With GWAS_OUT_SNP, B holds per pair the p_R genetic coefficients, then their p_R standard
- * errors sqrt(Var_RR[k][k]) (2 p_R values).  The tensor-core scans (SPLIT_BF16) take ADDITIVE
- * only; other models need FP64 or FP32 (GWAS_ERR_UNSUPPORTED otherwise). */
+ * errors sqrt(Var_RR[k][k]) (2 p_R values).  ADD_DOM is solved in the basis of the genotype
+ * indicators [x == 1], [x == 2] (the same columns, well conditioned when one homozygote class is
+ * rare) and reported for (x, [x == 1]); the Wald statistic does not depend on the basis.  Every
+ * precision takes every model, except that the tensor-core scans (SPLIT_BF16) of ADD_DOM need
+ * column 0 of X_L to be the intercept (all ones), the paper's X = [1 | L | g]; without it gwas_setup
+ * returns GWAS_ERR_UNSUPPORTED (use FP64 or FP32). */
 enum { GWAS_MODEL_ADDITIVE = 0, GWAS_MODEL_DOMINANT = 1, GWAS_MODEL_RECESSIVE = 2,
        GWAS_MODEL_ADD_DOM = 3 };
 

@@ -650,8 +650,14 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
                  "CHOL keeps one n x n factor per trait: t=%d, n=%d is too large (use EIG)", t, n);
     if (h->prec == GWAS_PREC_SPLIT_BF16) {
       tc_check_supported(h->algo, n, q, t);
-      GW_REQUIRE(h->gm.pr == 1 || h->algo == GWAS_ALGO_CHOL, GWAS_ERR_UNSUPPORTED,
-                 "the EIG tensor-core scan takes one genetic column per SNP (use FP64 or FP32)");
+      // Two working columns on the tensor cores are centred by the intercept: without it their
+      // cross product g0^T M^-1 g1 is a large cancellation (both columns keep their means) that
+      // the split-BF16 operands cannot resolve to the 1e-4 bound.
+      bool ones = true;
+      for (int i = 0; i < n; ++i) ones = ones && XL[i] == 1.0;
+      GW_REQUIRE(gm.pr == 1 || ones, GWAS_ERR_UNSUPPORTED,
+                 "a two-column genetic model on the tensor cores needs the intercept as column 0 "
+                 "of X_L (use FP64 or FP32 without it)");
     }
     int ndev = 0;
     GW_CUDA(cudaGetDeviceCount(&ndev));

@@ -111,6 +111,127 @@ __device__ __forceinline__ void work_coords(int64_t w, int64_t mtiles, int nblk,
   tile = first + r % rows;
 }
 
+// With GP = 2 working columns per SNP (a two-column genetic model) a ROT or AC tile holds 64
+// SNPs: A row r is column (r / 16) % 2 of SNP (r / 32) 16 + r % 16, so that a SNP's two rows sit in
+// lanes l and l + 16 of one epilogue warp.
+template <int GP>
+__device__ __forceinline__ int row_snp(int r) { return GP == 1 ? r : (r >> 5) * 16 + (r & 15); }
+template <int GP>
+__device__ __forceinline__ int row_col(int r) { return GP == 1 ? 0 : (r >> 4) & 1; }
+
+// The bordered solve of one (SNP, trait) pair with a two-column genetic block, in FP32 (Algorithm
+// 4's per-pair solve in the model's working basis): a0, a1 = (a_k, c) of the two centred working
+// columns, S00, S01, S11 their s entries, Pj = P_j (q x q) then b0_j (q).  V = P [a0 a1],
+// Sigma = S_RR - [a0 a1]^T V, b_w = Sigma^-1 c, b_L = b0 - V b_w (the intercept absorbing
+// mu . b_w), wald = b_w . c; reported b_R = tm b_w, Var = R Var_c R^T as in the CHOL kernel's
+// pair solve.  Returns 1 for a singular pair (a pivot of Sigma's Cholesky at most 1e-5 of the
+// matching S_kk: NaN outputs), else 0.  Writes the pair's row of B (and W) directly.
+template <int QQ>
+__device__ __noinline__ int ac_pair(const EigTcParams& p, const float* Pj, const float* a0,
+                                    const float* a1, float S00, float S01, float S11, float m0,
+                                    float m1, int64_t snp, int j) {
+  constexpr int P2 = QQ + 2;
+  float v[2][QQ > 0 ? QQ : 1];
+#pragma unroll
+  for (int k = 0; k < QQ; ++k) {
+    float x0 = 0.f, x1 = 0.f;
+#pragma unroll
+    for (int l = 0; l < QQ; ++l) {
+      x0 = fmaf(Pj[k * QQ + l], a0[l], x0);
+      x1 = fmaf(Pj[k * QQ + l], a1[l], x1);
+    }
+    v[0][k] = x0;
+    v[1][k] = x1;
+  }
+  float g00 = S00, g01 = S01, g11 = S11;
+#pragma unroll
+  for (int k = 0; k < QQ; ++k) {
+    g00 = fmaf(-a0[k], v[0][k], g00);
+    g01 = fmaf(-a0[k], v[1][k], g01);
+    g11 = fmaf(-a1[k], v[1][k], g11);
+  }
+  const float piv1 = g11 - g01 * g01 / g00;
+  const bool ok = g00 > 1e-5f * S00 && piv1 > 1e-5f * S11;
+  const int pw = p.out_snp ? 4 : p.out_var ? P2 + P2 * (P2 + 1) / 2 : P2;
+  float* Bo = p.B + (snp * p.t + j) * pw;
+  const float nanv = __int_as_float(0x7fc00000);
+  if (!ok) {
+    for (int k = 0; k < pw; ++k) Bo[k] = nanv;
+    if (p.W) p.W[snp * p.t + j] = nanv;
+    return 1;
+  }
+  const float det = g00 * piv1;
+  const float si[2][2] = {{g11 / det, -g01 / det}, {-g01 / det, g00 / det}};
+  const float c0 = a0[QQ], c1 = a1[QQ];
+  const float bw[2] = {si[0][0] * c0 + si[0][1] * c1, si[1][0] * c0 + si[1][1] * c1};
+  const float mu[2] = {p.mu ? m0 : 0.f, p.mu ? m1 : 0.f};
+  const float tm[2][2] = {{p.tm[0], p.tm[1]}, {p.tm[2], p.tm[3]}};
+  if (p.W) p.W[snp * p.t + j] = bw[0] * c0 + bw[1] * c1;
+  const float bR[2] = {tm[0][0] * bw[0] + tm[0][1] * bw[1], tm[1][0] * bw[0] + tm[1][1] * bw[1]};
+  float vr[2][2];
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float x = 0.f;
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int z = 0; z < 2; ++z) x += tm[g][u] * si[u][z] * tm[h][z];
+      vr[g][h] = x;
+    }
+  if (p.out_snp) {
+    Bo[0] = bR[0];
+    Bo[1] = bR[1];
+    Bo[2] = sqrtf(vr[0][0]);
+    Bo[3] = sqrtf(vr[1][1]);
+    return 0;
+  }
+#pragma unroll
+  for (int k = 0; k < QQ; ++k) {
+    float b = Pj[QQ * QQ + k] - v[0][k] * bw[0] - v[1][k] * bw[1];
+    if (k == 0) b -= mu[0] * bw[0] + mu[1] * bw[1];
+    Bo[k] = b;
+  }
+  Bo[QQ] = bR[0];
+  Bo[QQ + 1] = bR[1];
+  if (!p.out_var) return 0;
+  auto vc = [&](int r, int c) -> float {
+    if (r >= QQ && c >= QQ) return si[r - QQ][c - QQ];
+    if (c >= QQ) return -(v[0][r] * si[0][c - QQ] + v[1][r] * si[1][c - QQ]);
+    if (r >= QQ) return -(v[0][c] * si[0][r - QQ] + v[1][c] * si[1][r - QQ]);
+    float x = Pj[r * QQ + c];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int z = 0; z < 2; ++z) x += v[u][r] * si[u][z] * v[z][c];
+    return x;
+  };
+  auto rterms = [&](int r, int* idx, float* cf) -> int {
+    if (r >= QQ) {
+      idx[0] = QQ; cf[0] = tm[r - QQ][0];
+      idx[1] = QQ + 1; cf[1] = tm[r - QQ][1];
+      return 2;
+    }
+    idx[0] = r; cf[0] = 1.f;
+    if (r != 0) return 1;
+    idx[1] = QQ; cf[1] = -mu[0];
+    idx[2] = QQ + 1; cf[2] = -mu[1];
+    return 3;
+  };
+  for (int r = 0; r < P2; ++r)
+    for (int c = r; c < P2; ++c) {
+      int ir[3], ic[3];
+      float fr[3], fc[3];
+      const int nr = rterms(r, ir, fr), nc = rterms(c, ic, fc);
+      float x = 0.f;
+      for (int u = 0; u < nr; ++u)
+        for (int z = 0; z < nc; ++z) x += fr[u] * fc[z] * vc(ir[u], ic[z]);
+      Bo[P2 + r * P2 - r * (r - 1) / 2 + (c - r)] = x;
+    }
+  return 0;
+}
+
 // 4 or 8 consecutive FP32 TMEM columns of this warp's lanes (no wait).
 template <int QP>
 __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[QP]);
@@ -130,10 +251,13 @@ __device__ __forceinline__ void tmem_ld_cols<8>(uint32_t taddr, uint32_t (&r)[8]
 
 // VAR (AC only): the epilogue writes b and the packed Var(b) per pair (GWAS_OUT_VAR), compiled
 // apart so that the other output modes keep their register allocation.
-template <int EPI, int QQ, bool VAR = false>
+template <int EPI, int QQ, bool VAR = false, int GP = 1>
 __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
     eig_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapG, const EigTcParams p) {
+  // rows of a tile are SNPs (SQ: rows of the squared planes); ROT and AC with GP = 2 hold 64 SNPs
+  constexpr int TS = EPI == EPI_SQ ? BM : BM / GP;
+  constexpr int PKB = TS * 16;  // bytes of one packed slice (64 genotypes of TS SNPs)
   constexpr int QP = qp_of(QQ);
   constexpr bool CONV = EPI != EPI_SQ;  // A operand = genotypes through the converters
   constexpr int SB = sb_of(EPI);
@@ -149,7 +273,7 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
   float* cst = (float*)(sP + PR * PK_BYTES);
   Bars* bars = (Bars*)(cst + cst_of(EPI, QQ));
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t mtiles = (p.m + BM - 1) / BM;
+  const int64_t mtiles = (p.m + TS - 1) / TS;
   const int64_t nwork = mtiles * p.nblk;
   const int nk = p.kpad / BK;
   int* tflag = p.flags + FLAG_TIMEOUT;
@@ -222,8 +346,8 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
         }
       }
     } else if (lane == 1 && CONV) {
-      // packed genotype slices (64 genotypes x 128 SNPs, 2 KB) via TMA, in the order the
-      // converters consume them; rows past m read as zero
+      // packed genotype slices (64 genotypes x TS SNPs) via TMA, in the order the converters
+      // consume them; rows past m read as zero
       int ps = 0;
       uint32_t pph = 0;
       bool ok = true;
@@ -234,8 +358,8 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
         for (int ks = 0; ks < nk; ++ks) {
           ok = mbar_wait(&bars->pk_empty[ps], pph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
-          mbar_arrive_expect_tx(&bars->pk_full[ps], PK_BYTES);
-          tma_load_2d(sP + ps * PK_BYTES, &mapG, &bars->pk_full[ps], ks * 16, (int32_t)(tile * BM));
+          mbar_arrive_expect_tx(&bars->pk_full[ps], PKB);
+          tma_load_2d(sP + ps * PK_BYTES, &mapG, &bars->pk_full[ps], ks * 16, (int32_t)(tile * TS));
           if (++ps == PR) { ps = 0; pph ^= 1; }
         }
       }
@@ -321,6 +445,7 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
     if (CONV) {
       const int ct = conv_index<WIDE>(warp) * 32 + lane;
       const int r = ct >> 1, hh = ct & 1;
+      const int srow = row_snp<GP>(r), gk = row_col<GP>(r);  // the row's SNP and working column
       const uint32_t line = (r >> 3) * 1024 + (r & 7) * 128;
       const int64_t mine = blockIdx.x < nwork ? (nwork - 1 - blockIdx.x) / gridDim.x + 1 : 0;
       int as = 0, ps = 0;
@@ -333,14 +458,14 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
         work_coords(blockIdx.x + i * gridDim.x, mtiles, p.nblk, tile, nb);
         if (tile != cur_tile) {
           cur_tile = tile;
-          const int64_t snp = tile * BM + r;
-          coded_lut(p.mu && snp < p.m ? p.mu[snp] : 0.f, p.code[0], lutlo, luthi);
+          const int64_t snp = tile * TS + srow;
+          coded_lut(p.mu && snp < p.m ? p.mu[snp * GP + gk] : 0.f, p.code[gk], lutlo, luthi);
         }
         for (int ks = 0; ks < nk; ++ks) {
           // warp-uniform exits: every lane leaves together if any wait gave up
           ok = __all_sync(0xffffffffu, mbar_wait(&bars->pk_full[ps], pph, abort, tflag, WAIT_NS));
           if (!ok) break;
-          const uint2 w = *reinterpret_cast<const uint2*>(sP + ps * PK_BYTES + r * 16 + hh * 8);
+          const uint2 w = *reinterpret_cast<const uint2*>(sP + ps * PK_BYTES + srow * 16 + hh * 8);
           // the slot is refilled by TMA (async proxy): order these generic reads before it
           fence_proxy_async_smem();
           __syncwarp();
@@ -392,8 +517,10 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
       int64_t tile;
       int nb;
       work_coords(w, mtiles, p.nblk, tile, nb);
-      const int64_t snp = tile * BM + 32 * qd + lane;
-      const float mu_snp = (p.mu && snp < p.m) ? p.mu[snp] : 0.f;
+      // this lane's row: working column egk of SNP snp (GP = 1: the SNP of TMEM lane 32 qd + lane)
+      const int erow = 32 * qd + lane, egk = row_col<GP>(erow);
+      const int64_t snp = tile * TS + row_snp<GP>(erow);
+      const float mu_snp = (p.mu && snp < p.m) ? p.mu[snp * GP + egk] : 0.f;
       if (EPI == EPI_AC) {
         // P_j and b0_j of this block's traits, FP32, into shared memory: from the registers
         // loaded during the previous work item, then the next item's are loaded (their global
@@ -422,28 +549,46 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
         tc_fence_after();
         const uint32_t base = tmem + ((uint32_t)(32 * qd) << 16) + buf * BN;
         if (EPI == EPI_ROT) {
+          // 32 products of rotated values, split hi + lo, into row `row` of the planes
+          auto store_split = [&](int64_t row, int col0, const float* x, const float* y) {
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float s0 = x[2 * i] * y[2 * i], s1 = x[2 * i + 1] * y[2 * i + 1];
+              const __nv_bfloat16 h0 = __float2bfloat16_rn(s0), h1 = __float2bfloat16_rn(s1);
+              const __nv_bfloat16 l0 = __float2bfloat16_rn(s0 - __bfloat162float(h0));
+              const __nv_bfloat16 l1 = __float2bfloat16_rn(s1 - __bfloat162float(h1));
+              hi[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+              lo[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            uint4* dh = reinterpret_cast<uint4*>(p.xsq + row * p.kpad + col0);
+            uint4* dl = reinterpret_cast<uint4*>(p.xsq + (p.a_piece_rows + row) * p.kpad + col0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              dh[u] = make_uint4(hi[4 * u], hi[4 * u + 1], hi[4 * u + 2], hi[4 * u + 3]);
+              dl[u] = make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]);
+            }
+          };
           for (int c = 0; c < BN / 32; ++c) {
             float v[32];
             tmem_ld32(base + 32 * c, v);
             const int col0 = nb * BN + 32 * c;
-            if (snp < p.m && col0 < p.kpad) {
-              uint32_t hi[16], lo[16];
+            if (GP == 2) {
+              // three planes per SNP (stride xplane rows): (Z^T g0)^2, (Z^T g0)(Z^T g1),
+              // (Z^T g1)^2; the partner row (the SNP's other working column) is 16 lanes away
+              float w2[32];
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                const float s0 = v[2 * i] * v[2 * i], s1 = v[2 * i + 1] * v[2 * i + 1];
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(s0), h1 = __float2bfloat16_rn(s1);
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(s0 - __bfloat162float(h0));
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(s1 - __bfloat162float(h1));
-                hi[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                lo[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+              for (int i = 0; i < 32; ++i) w2[i] = __shfl_xor_sync(0xffffffffu, v[i], 16);
+              if (snp < p.m && col0 < p.kpad) {
+                if (egk == 0) {
+                  store_split(snp, col0, v, v);
+                  store_split(p.xplane + snp, col0, v, w2);
+                } else {
+                  store_split(2 * p.xplane + snp, col0, v, v);
+                }
               }
-              uint4* dh = reinterpret_cast<uint4*>(p.xsq + snp * p.kpad + col0);
-              uint4* dl = reinterpret_cast<uint4*>(p.xsq + (p.a_piece_rows + snp) * p.kpad + col0);
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                dh[u] = make_uint4(hi[4 * u], hi[4 * u + 1], hi[4 * u + 2], hi[4 * u + 3]);
-                dl[u] = make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]);
-              }
+            } else if (snp < p.m && col0 < p.kpad) {
+              store_split(snp, col0, v, v);
             }
           }
         } else if (EPI == EPI_SQ) {
@@ -479,6 +624,8 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
           int nsing = 0;
           bool released = false;
           const int64_t row0 = tile * BM + 32 * qd;
+          // GP = 2: the centre of the SNP's second working column (held by the partner lane)
+          const float mu_pair = __shfl_down_sync(0xffffffffu, mu_snp, 16);
           for (int j8 = 8 * set; j8 < T; j8 += STEP) {
             float scur[8];
 #pragma unroll
@@ -511,6 +658,28 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
               released = true;
             }
             const int nval = jend - (j0 + j8) < 8 ? jend - (j0 + j8) : 8;  // valid traits
+            if (GP == 2) {
+              // a SNP's two working columns: the column-0 lanes (0-15) solve each pair with the
+              // partner lane's a and c and the SNP's three s planes, writing their rows directly
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                if (u >= nval) continue;
+                float a0[QQ + 1], a1[QQ + 1];
+#pragma unroll
+                for (int k = 0; k <= QQ; ++k) {
+                  a0[k] = __uint_as_float(r[u][k]);
+                  a1[k] = __shfl_down_sync(0xffffffffu, a0[k], 16);
+                }
+                const int j = j0 + j8 + u;
+                if (egk == 0 && live) {
+                  const float* sj = p.sbuf + (int64_t)j * p.lds;
+                  nsing += ac_pair<QQ>(p, cst + (j8 + u) * (QQ * QQ + QQ), a0, a1, __ldg(sj + snp),
+                                       __ldg(sj + p.xplane + snp), __ldg(sj + 2 * p.xplane + snp),
+                                       mu_snp, mu_pair, snp, j);
+                }
+              }
+              continue;
+            }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               if (u >= nval) continue;
@@ -657,36 +826,49 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
   }
 }
 
-template <int EPI, int QQ, bool VAR = false>
+template <int EPI, int QQ, bool VAR = false, int GP = 1>
 void prepare_one() {
   constexpr size_t SMEM = smem_of(EPI, QQ);
   static_assert(SMEM <= 232448, "shared memory over the sm_103 opt-in limit");
-  GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QQ, VAR>,
+  GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QQ, VAR, GP>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
 }
 
-template <int EPI, int QQ, bool VAR = false>
+template <int EPI, int QQ, bool VAR = false, int GP = 1>
 void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
                 const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {
   constexpr size_t SMEM = smem_of(EPI, QQ);
-  const int64_t work = ((p.m + BM - 1) / BM) * p.nblk;
+  constexpr int TS = EPI == EPI_SQ ? BM : BM / GP;
+  const int64_t work = ((p.m + TS - 1) / TS) * p.nblk;
   const unsigned grid = (unsigned)(work < num_sms ? work : num_sms);
-  eig_tc_kernel<EPI, QQ, VAR><<<grid, 32 * nwarps_of(EPI, QQ), SMEM, s>>>(mapA, mapB, mapG, p);
+  eig_tc_kernel<EPI, QQ, VAR, GP><<<grid, 32 * nwarps_of(EPI, QQ), SMEM, s>>>(mapA, mapB, mapG, p);
   GW_CHECK_LAUNCH();
 }
 
-template <bool VAR>
+// AC per q; two working columns solve each pair in ac_pair, which writes every output mode
+template <bool VAR, int GP>
 void launch_ac(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
                const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {
   switch (p.q) {
-    case 1: launch_one<EPI_AC, 1, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
-    case 2: launch_one<EPI_AC, 2, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
-    case 3: launch_one<EPI_AC, 3, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
-    case 4: launch_one<EPI_AC, 4, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
-    case 5: launch_one<EPI_AC, 5, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
-    case 6: launch_one<EPI_AC, 6, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
-    default: launch_one<EPI_AC, 7, VAR>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 1: launch_one<EPI_AC, 1, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 2: launch_one<EPI_AC, 2, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 3: launch_one<EPI_AC, 3, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 4: launch_one<EPI_AC, 4, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 5: launch_one<EPI_AC, 5, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 6: launch_one<EPI_AC, 6, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
+    default: launch_one<EPI_AC, 7, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
   }
+}
+
+template <bool VAR, int GP>
+void prepare_ac() {
+  prepare_one<EPI_AC, 1, VAR, GP>();
+  prepare_one<EPI_AC, 2, VAR, GP>();
+  prepare_one<EPI_AC, 3, VAR, GP>();
+  prepare_one<EPI_AC, 4, VAR, GP>();
+  prepare_one<EPI_AC, 5, VAR, GP>();
+  prepare_one<EPI_AC, 6, VAR, GP>();
+  prepare_one<EPI_AC, 7, VAR, GP>();
 }
 
 }  // namespace
@@ -702,21 +884,11 @@ void eig_tc_prepare() {
   const uint64_t bit = 1ull << (dev & 63);
   if (done_mask & bit) return;
   prepare_one<EPI_ROT, 0>();
+  prepare_one<EPI_ROT, 0, false, 2>();
   prepare_one<EPI_SQ, 0>();
-  prepare_one<EPI_AC, 1>();
-  prepare_one<EPI_AC, 2>();
-  prepare_one<EPI_AC, 3>();
-  prepare_one<EPI_AC, 4>();
-  prepare_one<EPI_AC, 5>();
-  prepare_one<EPI_AC, 6>();
-  prepare_one<EPI_AC, 7>();
-  prepare_one<EPI_AC, 1, true>();
-  prepare_one<EPI_AC, 2, true>();
-  prepare_one<EPI_AC, 3, true>();
-  prepare_one<EPI_AC, 4, true>();
-  prepare_one<EPI_AC, 5, true>();
-  prepare_one<EPI_AC, 6, true>();
-  prepare_one<EPI_AC, 7, true>();
+  prepare_ac<false, 1>();
+  prepare_ac<true, 1>();
+  prepare_ac<false, 2>();
   done_mask |= bit;
 }
 
@@ -724,14 +896,22 @@ void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUt
                    const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {
   if (p.m <= 0 || p.nblk <= 0) return;
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q out of range");
+  GW_REQUIRE(p.gp == 1 || p.gp == 2, GWAS_ERR_ARG, "genetic columns %d outside [1,2]", p.gp);
   switch (stage) {
-    case 0: launch_one<EPI_ROT, 0>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 0:
+      if (p.gp == 2)
+        launch_one<EPI_ROT, 0, false, 2>(s, mapA, mapB, mapG, p, num_sms);
+      else
+        launch_one<EPI_ROT, 0>(s, mapA, mapB, mapG, p, num_sms);
+      break;
     case 1: launch_one<EPI_SQ, 0>(s, mapA, mapB, mapG, p, num_sms); break;
     default:
-      if (p.out_var)
-        launch_ac<true>(s, mapA, mapB, mapG, p, num_sms);
+      if (p.gp == 2)
+        launch_ac<false, 2>(s, mapA, mapB, mapG, p, num_sms);
+      else if (p.out_var)
+        launch_ac<true, 1>(s, mapA, mapB, mapG, p, num_sms);
       else
-        launch_ac<false>(s, mapA, mapB, mapG, p, num_sms);
+        launch_ac<false, 1>(s, mapA, mapB, mapG, p, num_sms);
   }
 }
 

@@ -61,6 +61,8 @@ struct EigTcParams {
   __nv_bfloat16* xsq;      // ROT output: hi rows [0, cap), lo rows [cap, 2 cap), ld kpad
   float* sbuf;             // SQ output / AC input: s_ij at sbuf[j * lds + i]
   int64_t lds;
+  int64_t xplane;          // gp = 2: row stride of the three squared planes (x0 x0, x0 x1, x1 x1)
+                           // in xsq and of the three s planes in sbuf
   const float* P;          // AC: t x q x q
   const float* b0;         // AC: t x q
   const float* mu;         // ROT, AC: per-SNP centring (multiples of 1/64) or NULL

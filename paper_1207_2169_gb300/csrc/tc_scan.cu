@@ -190,21 +190,23 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     st->traits_ac = eig_ac_traits(q);
     // SNPs per internal chunk: at least the streaming block, up to 32 Ki while the s scratch
     // (t x chunk FP32) stays within 4 GB, so that many-trait scans keep every SM busy
-    int64_t cap = (int64_t)(4e9 / (4.0 * t));
+    // (a two-column genetic model has three squared planes per SNP: x0 x0, x0 x1, x1 x1)
+    const int np = a.gm.pr == 2 ? 3 : 1;
+    int64_t cap = (int64_t)(4e9 / (4.0 * t * np));
     cap = cap < 32768 ? cap : 32768;
     cap = cap > a.block_snps ? cap : a.block_snps;
     st->mcap = round_up(cap > 128 ? cap : 128, 128);
-    st->xsq = (__nv_bfloat16*)tc_alloc(st, (size_t)2 * st->mcap * kp * 2);
-    st->sbuf = (float*)tc_alloc(st, (size_t)t * st->mcap * 4);
+    st->xsq = (__nv_bfloat16*)tc_alloc(st, (size_t)2 * np * st->mcap * kp * 2);
+    st->sbuf = (float*)tc_alloc(st, (size_t)t * np * st->mcap * 4);
     // With an intercept in X_L, each SNP is centred by a multiple of 1/64 near its mean: the
     // estimates of b_snp and its Wald statistic are unchanged, the intercept is corrected
     // exactly, and the large intercept-direction component no longer cancels in
     // sigma = x^T M^-1 x - a^T S_TL^-1 a (which would amplify the BF16 splitting error).
-    if (a.intercept) st->mu = (float*)tc_alloc(st, (size_t)st->mcap * 4);
+    if (a.intercept) st->mu = (float*)tc_alloc(st, (size_t)st->mcap * a.gm.pr * 4);
     st->mapZ = make_map_bf16(st->Zsplit, 2 * (int64_t)zrows, kp, 256);
     st->mapU = make_map_bf16(st->Usplit, 2 * (int64_t)t * q1, kp, 256);
     st->mapD = make_map_bf16(st->dsplit, 2 * (int64_t)t, kp, 256);
-    st->mapX = make_map_bf16(st->xsq, 2 * st->mcap, kp, 128);
+    st->mapX = make_map_bf16(st->xsq, 2 * np * st->mcap, kp, 128);
     eig_tc_prepare();
     return st;
   } catch (...) {
@@ -264,10 +266,12 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.q = q;
     p.t = t;
     p.kpad = st->kpad;
-    p.a_piece_rows = (int)st->mcap;
+    const int gp = st->gm.pr, np = gp == 2 ? 3 : 1;
+    p.a_piece_rows = (int)(np * st->mcap);
     p.xsq = st->xsq;
     p.sbuf = st->sbuf;
-    p.lds = st->mcap;
+    p.lds = np * st->mcap;
+    p.xplane = round_up(mm, 128);  // gp = 2: rows of each squared plane of this chunk
     p.flags = a.flags;
     p.gp = st->gm.pr;
     p.code[0] = st->gm.code_word(0);
@@ -275,7 +279,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     for (int e = 0; e < 4; ++e) p.tm[e] = st->gm.tm[e / 2][e % 2];
     // ROT: Xsq = (Z^T x)^2 for this chunk (Algorithm 4's rotation, squared and split)
     const uint8_t* Gc = a.G + off * rb;
-    const CUtensorMap mapG = make_map_packed(Gc, mm, rb);
+    const CUtensorMap mapG = make_map_packed(Gc, mm, rb, 128 / gp);
     StageTimer* tm = a.timer;
     cudaEvent_t ev = nullptr;
     if (st->mu) {
@@ -291,7 +295,8 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     ev = tm ? tm->begin(s, STAGE_ROT) : nullptr;
     eig_tc_launch(s, 0, st->mapZ, st->mapZ, mapG, p, ctas);
     if (ev) tm->end(s, ev);
-    // SQ: s_ij = sum_r Xsq[i][r] d_j[r]
+    // SQ: s_ij = sum_r Xsq[i][r] d_j[r] (gp = 2: over the rows of all three planes)
+    p.m = gp == 2 ? 3 * p.xplane : mm;
     p.nblk = (t + 255) / 256;
     p.b_piece_rows = t;
     p.b_rows_per_blk = 256;
@@ -299,13 +304,15 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     eig_tc_launch(s, 1, st->mapX, st->mapD, mapG, p, ctas);
     if (ev) tm->end(s, ev);
     // AC: a_ij, c_ij from the genotypes against U, then the bordered solve (Algorithm 4)
+    p.m = mm;
     p.nblk = (t + st->traits_ac - 1) / st->traits_ac;
     p.b_piece_rows = t * q1;
     p.b_rows_per_blk = st->traits_ac * q1;
     p.traits_per_blk = st->traits_ac;
     p.P = st->P32;
     p.b0 = st->b032;
-    p.B = a.B + (size_t)off * t * (st->out_snp ? 2 : st->out_var ? q1 + q1 * (q1 + 1) / 2 : q1);
+    const int pp = q + gp;  // coefficients per pair
+    p.B = a.B + (size_t)off * t * (st->out_snp ? 2 * gp : st->out_var ? pp + pp * (pp + 1) / 2 : pp);
     p.out_snp = st->out_snp;
     p.out_var = st->out_var;
     p.W = a.wald ? a.wald + (size_t)off * t : nullptr;

@@ -2,8 +2,8 @@
 with the FP64 oracle: additive, dominant, recessive and the two-column additive + dominance
 model, whose test is the joint 2-d.o.f. Wald statistic of the block.
 
-Every scan path that takes them -- CHOL and EIG on the CUDA cores in FP64 (1e-6) and FP32 (2e-3),
-the tensor-core paths once they do -- is compared element by element with oracle.gls.gls_grid(model)
+Every scan path -- CHOL and EIG on the CUDA cores in FP64 (1e-6) and FP32 (2e-3), and on the
+tensor cores (split BF16, 1e-4) -- is compared element by element with oracle.gls.gls_grid(model)
 on ragged shapes (SNP counts that leave partial 32- and 64-column tiles, n off every tile size,
 q from 1 to 7, several traits), in all three output modes, through the host-streaming ring, and
 with SNPs whose block is singular (no heterozygote: an all-zero dominance column)."""
@@ -60,7 +60,7 @@ def test_add_dom_singular_snps(g, algo, t):
 
 @pytest.mark.parametrize("algo,t,prec", [("chol", 1, "fp64"), ("chol", 1, "fp32"),
                                          ("eig", 11, "fp64"), ("eig", 11, "fp32"),
-                                         ("chol", 1, "split_bf16")])
+                                         ("chol", 1, "split_bf16"), ("eig", 11, "split_bf16")])
 def test_add_dom_output_modes(g, algo, t, prec):
     """SNP mode: (b_x, b_d, se_x, se_d) per pair; VAR mode: the p coefficients, then the whole
     Var(b) = (X_i^T M_j^-1 X_i)^-1 (p = q + 2) against the oracle entry by entry."""
@@ -136,17 +136,49 @@ def test_split_chol_add_dom(g, n, q, m, t):
         assert nsing == int(np.isnan(Wref).sum())
 
 
-def test_split_chol_add_dom_streamed_and_without_intercept(g):
-    """Host buffers through the streaming ring equal the device-resident scan; zero-mean
-    covariates without an intercept column (no centring) still meet the tolerance."""
-    c = synth.small_problem(35, n=300, q=3, m=700, t=1)
-    Bd, Wd, _ = run(g, c, "chol", "split_bf16", model="add_dom", packed=True)
-    Bh, Wh, _ = run(g, c, "chol", "split_bf16", model="add_dom", packed=True, device=False,
+@pytest.mark.parametrize("algo,t", [("chol", 1), ("eig", 21)])
+def test_split_add_dom_streamed_and_without_intercept(g, algo, t):
+    """Host buffers through the streaming ring equal the device-resident scan.  Without an
+    intercept column the tensor-core setup refuses the two-column model (its working columns
+    are centred through the intercept), and the CUDA-core paths take it."""
+    c = synth.small_problem(35 if algo == "chol" else 36, n=300, q=3, m=700, t=t)
+    Bd, Wd, _ = run(g, c, algo, "split_bf16", model="add_dom", packed=True)
+    Bh, Wh, _ = run(g, c, algo, "split_bf16", model="add_dom", packed=True, device=False,
                     block_snps=256)
     assert np.array_equal(Bd, Bh, equal_nan=True) and np.array_equal(Wd, Wh, equal_nan=True)
     c.XL = c.XL.copy()
     c.XL[:, 0] = np.random.default_rng(6).standard_normal(c.n)
+    with pytest.raises(g.GwasError) as e:
+        run(g, c, algo, "split_bf16", model="add_dom")
+    assert e.value.status == -5 and "intercept" in str(e.value)
     Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, model="add_dom")
-    B, W, _ = run(g, c, "chol", "split_bf16", model="add_dom")
+    B, W, _ = run(g, c, algo, "fp32", model="add_dom")
     eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < TOL["fp32"] and ew < TOL["fp32"], (eb, ew)
+
+
+@pytest.mark.parametrize("n,q,m,t", [(97, 1, 131, 5), (200, 3, 300, 37), (130, 7, 70, 17),
+                                     (300, 3, 257, 300), (64, 2, 1, 3)])
+def test_split_eig_add_dom(g, n, q, m, t):
+    """The two-column model on the EIG tensor-core kernels: ROT writes three squared planes per
+    SNP (x0 x0, x0 x1, x1 x1; 64 SNPs per tile, a SNP's columns 16 lanes apart), SQ contracts
+    every plane row with d_j, and AC solves each pair's 2 x 2 Schur complement in FP32 from the
+    partner lane's a and c; several trait blocks, ragged tails, one SNP, q up to 7."""
+    c = synth.small_problem(19 * n + q + m + t, n=n, q=q, m=m, t=t)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, model="add_dom")
+    for packed in (False, True):
+        B, W, nsing = run(g, c, "eig", "split_bf16", model="add_dom", packed=packed)
+        eb, ew = max_errors(B, W, Bref, Wref, Vref)
+        assert eb < 1e-4 and ew < 1e-4, (packed, eb, ew)
+        assert nsing == int(np.isnan(Wref).sum())
+
+
+def test_split_eig_add_dom_workload2_shape(g):
+    """Workload 2's shape (n = 1000, t = 1000, h2 up to 0.95) on 700 SNPs; 300 sampled pairs."""
+    c = synth.make_cohort(2, m=700)
+    B, W, _ = run(g, c, "eig", "split_bf16", model="add_dom", packed=True)
+    rs = np.random.default_rng(8)
+    pairs = np.c_[rs.integers(0, c.m, 300), rs.integers(0, c.t, 300)]
+    Bref, Wref, Vref = gls.gls_pairs(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, pairs, model="add_dom")
+    eb, ew = max_errors(B[pairs[:, 0], pairs[:, 1]], W[pairs[:, 0], pairs[:, 1]], Bref, Wref, Vref)
     assert eb < 1e-4 and ew < 1e-4, (eb, ew)
