@@ -199,8 +199,9 @@ def algorithmic_flops(s, m):
     return sum(stage_flops(s, m).values())
 
 
-def stage_executed(s, m):
-    """Tensor-core FLOPs the split kernels issue per stage (split products, K and N padding)."""
+def stage_executed(s, m, pieces=2):
+    """Tensor-core FLOPs the split kernels issue per stage (split products, K and N padding);
+    `pieces`: BF16 pieces of L^-1 (CHOL) or U (EIG's a/c kernel), 2 or 3."""
     n, q, t = s["n"], s["q"], s["t"]
     kpad = -(-n // 64) * 64
     rpad = -(-n // 256) * 256
@@ -213,10 +214,10 @@ def stage_executed(s, m):
             nk = min(4 * (nb + 1), kpad // 64)
             for ks in range(nk):
                 macs += 64 * (ncols - 64 * max(0, ks - 4 * nb))
-        return {"chol": 2 * 2 * macs * m * t}
+        return {"chol": pieces * 2 * macs * m * t}
     nac = -(-t // eig_ac_traits(q))
     return {"rot": 2 * 2 * rpad * kpad * m, "sq": 3 * 2 * kpad * (-(-t // 256) * 256) * m,
-            "ac": 2 * 2 * kpad * 256 * nac * m}
+            "ac": pieces * 2 * kpad * 256 * nac * m}
 
 
 def code_sha1(path):
@@ -246,10 +247,10 @@ def traffic_per_unit(kernel):
         return None, None
 
 
-def kernel_roofline(s, m, stage, ms_total, launches, peak_tf, peak_src, steps):
+def kernel_roofline(s, m, stage, ms_total, launches, peak_tf, peak_src, steps, pieces=2):
     """Roofline entry of one kernel stage from its CUDA-event time over the timed region."""
     alg = stage_flops(s, m)[stage] * steps
-    exe = stage_executed(s, m)[stage] * steps
+    exe = stage_executed(s, m, pieces)[stage] * steps
     per, unit = traffic_per_unit(KERNEL_NAMES[stage])
     units = m * steps * (s["t"] if unit == "pair" else 1)
     sec = ms_total * 1e-3
@@ -262,7 +263,7 @@ def kernel_roofline(s, m, stage, ms_total, launches, peak_tf, peak_src, steps):
             "executed_tflops": exe / sec / 1e12, "executed_frac": exe / sec / 1e12 / peak_tf}
 
 
-def rooflines(s, m, stages, steps, precision):
+def rooflines(s, m, stages, steps, precision, pieces=2):
     """Per-kernel roofline entries of a tensor-core scan and the dominant one (largest time).
     The step's kernels are each timed alone per launch (a few ms at most), so the burst BF16 peak
     applies."""
@@ -275,7 +276,7 @@ def rooflines(s, m, stages, steps, precision):
     peaks, kind = _peaks()
     peak = peaks["bf16_tflops"]
     src = f"bf16_tflops (burst: each launch is timed alone), {kind} (MEASURED_PEAKS.json)"
-    entries = [kernel_roofline(s, m, st, stages[st][0], stages[st][1], peak, src, steps)
+    entries = [kernel_roofline(s, m, st, stages[st][0], stages[st][1], peak, src, steps, pieces)
                for st in (["chol"] if s["algo"] == "chol" else ["rot", "sq", "ac"]) if st in stages]
     dom = max(entries, key=lambda e: e["ms_per_launch"] * e["launches"])
     return dom, entries
@@ -389,6 +390,7 @@ def measure(idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=T
     h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, options=opt)
     try:
         setup_ms = g.gwas_setup_timing(h)
+        pieces = max(g.gwas_split_pieces(h), 2)
         xr_d = torch.from_numpy(c.XR).cuda()
         scan = g.gwas_scan
         if fmt == "packed":  # packed once, outside the timed region: it is the input format
@@ -438,9 +440,10 @@ def measure(idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=T
     finally:
         g.gwas_destroy(h)
     pairs = mm * t
-    dom, kernels = rooflines(s, mm, stages, steps, precision)
+    dom, kernels = rooflines(s, mm, stages, steps, precision, pieces)
     res = {
         "s": s, "m": mm, "ms": ms, "value": pairs * ws / (ms * 1e-3), "setup_ms": setup_ms,
+        "split_pieces": pieces if precision == "split_bf16" else None,
         "clocks": clk.summary(), "parity": {"max_rel_err_b": eb, "max_rel_err_wald": ew,
                                             "pairs_checked": npairs, "tolerance": TOL[precision]},
         "e2e": None if e2e_s is None else {
@@ -461,7 +464,8 @@ def entry(res, precision, fmt, steps, warmup, **extra):
          "value": res["value"], "unit": "pairs/s", "ms_per_step": res["ms"], "steps": steps,
          "warmup": warmup, "e2e": res["e2e"], "parity": res["parity"], "setup_ms": res["setup_ms"],
          "roofline": res["roofline"], "gpu_launches": res["gpu_launches"],
-         "stage_ms_per_step": res["stage_ms"], "clocks": res["clocks"]}
+         "stage_ms_per_step": res["stage_ms"], "clocks": res["clocks"],
+         "split_pieces": res.get("split_pieces")}
     if res["kernels"] and len(res["kernels"]) > 1:
         d["kernel_rooflines"] = res["kernels"]
     d.update(extra)
@@ -489,6 +493,7 @@ def measure_stream3(local, ws, steps=2, warmup=1, m=None, out_mode="full", pinne
     h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, options=opt)
     try:
         setup_ms = g.gwas_setup_timing(h)
+        pieces = g.gwas_split_pieces(h)
         G = g.gwas_pack_genotypes(torch.from_numpy(c.XR).cuda())
         Bs = [torch.empty((blk, t, pw), dtype=torch.float32, device="cuda") for _ in range(2)]
         Ws = [torch.empty((blk, t), dtype=torch.float32, device="cuda") for _ in range(2)]
@@ -558,8 +563,9 @@ def measure_stream3(local, ws, steps=2, warmup=1, m=None, out_mode="full", pinne
     finally:
         g.gwas_destroy(h)
     pairs = mm * t
-    dom, kernels = rooflines(s, mm, stages, steps, "split_bf16")
+    dom, kernels = rooflines(s, mm, stages, steps, "split_bf16", pieces)
     res = {"s": s, "m": mm, "ms": ms, "value": pairs * ws / (ms * 1e-3), "setup_ms": setup_ms,
+           "split_pieces": pieces,
            "clocks": clk.summary(),
            "parity": {"max_rel_err_b": eb, "max_rel_err_wald": ew, "pairs_checked": 10000,
                       "tolerance": 1e-4,
@@ -622,6 +628,7 @@ def measure_batch(local, ws, steps, warmup, m=None):
         ms = _max_over_ranks(ms / steps, ws)
         # the same work as separate per-cohort calls (each launch with every SM, one after another)
         handles = [g.gwas_batch_handle(b, i) for i in range(len(cohorts))]
+        pieces = [g.gwas_split_pieces(h) for h in handles]
 
         def seq():
             for h, (G, B, W) in zip(handles, blocks):
@@ -641,7 +648,8 @@ def measure_batch(local, ws, steps, warmup, m=None):
     finally:
         g.gwas_destroy_batch(b)
     pairs = m * sum(t for _, _, t in shapes)
-    exe = sum(sum(stage_executed(dict(n=n, q=q, t=t, algo="eig"), m).values()) for n, q, t in shapes)
+    exe = sum(sum(stage_executed(dict(n=n, q=q, t=t, algo="eig"), m, pc).values())
+              for (n, q, t), pc in zip(shapes, pieces))
     alg = sum(algorithmic_flops(dict(n=n, q=q, t=t, algo="eig"), m) for n, q, t in shapes)
     peaks, kind = _peaks()
     peak = peaks["bf16_tflops"]
@@ -656,7 +664,8 @@ def measure_batch(local, ws, steps, warmup, m=None):
         "batch": {"plan": plan, "plan_ms": plan_ms,
                   "plans": ["sequential", "concurrent, SM shares by work", "concurrent, all SMs",
                             "two lanes of half the SMs"],
-                  "per_cohort_calls_ms": ms_seq, "speedup_vs_per_cohort_calls": ms_seq / ms},
+                  "per_cohort_calls_ms": ms_seq, "speedup_vs_per_cohort_calls": ms_seq / ms,
+                  "split_pieces": pieces},
         "roofline": {"bound": "tensor", "kernel": "whole batched step (16 cohorts' EIG kernels)",
                      "achieved": alg / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": alg / (ms * 1e-3) / 1e12 / peak,

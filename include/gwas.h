@@ -66,8 +66,9 @@ enum { GWAS_ALGO_AUTO = 0, GWAS_ALGO_CHOL = 1, GWAS_ALGO_EIG = 2 };
  *   FP64        plain FP64 CUDA-core kernels;
  *   FP32        plain FP32 CUDA-core kernels;
  *   SPLIT_BF16  tensor-core kernels (tcgen05, sm_103a): the non-integer operand of each
- *               contraction is split into hi + lo BF16 pieces, genotypes are exact in BF16,
- *               accumulation is FP32; the p x p Schur solve runs in FP32.                     */
+ *               contraction is split into hi + lo BF16 pieces (a third for a badly conditioned
+ *               M_j, see gwas_split_pieces), genotypes are exact in BF16, accumulation is FP32;
+ *               the p x p Schur solve runs in FP64 (CHOL) or FP32 (EIG).                      */
 enum { GWAS_PREC_FP64 = 0, GWAS_PREC_FP32 = 1, GWAS_PREC_SPLIT_BF16 = 2 };
 
 /* What a scan writes per (SNP, trait) pair into B (wald is the same in all modes):
@@ -305,6 +306,17 @@ gwas_status gwas_info(gwas_handle h, int* n, int* q, int* t, int* algo, int* pre
 
 /* p_R, the genetic columns per SNP of the handle's model (p = q + p_R), or -1 for NULL. */
 int gwas_genetic_columns(gwas_handle h);
+
+/* BF16 pieces of the tensor-core scans' split operands: 2, or 3 when setup found some
+ * M_j = s2 (h2 Phi + (1 - h2) I) with lam_max / lam_min above 100 (h2 near 1 on a kinship with
+ * many eigenvalues at its ridge), where two pieces (~16 significant bits) would not hold the
+ * 1e-4 bound.  CHOL chooses per trait (3 pieces of its augmented L_j^-1: one product in two
+ * more); EIG per handle (3 pieces of every U_j = M_j^-1 [X_L | r_j]: the a/c kernel one product
+ * in two more).  0 for CUDA-core handles, -1 for NULL.  At such conditioning the FP32
+ * accumulation of the tensor cores bounds the relative error of the SNP effect near 1e-5; an
+ * intercept that the kinship's weighting determines far more precisely than the SNP effect
+ * (|mu b_snp| >> se(intercept), mu the SNP's mean) carries that error amplified by the ratio. */
+int gwas_split_pieces(gwas_handle h);
 
 /* Number of singular pairs (written as NaN) seen by completed scans of this handle, or -1. */
 int64_t gwas_singular_count(gwas_handle h);

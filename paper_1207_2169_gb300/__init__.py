@@ -31,7 +31,7 @@ EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_destroy_batch", "gwas_sync", "gwas_selftest_timeout", "gwas_wald_pvalues",
            "gwas_estimate",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
-           "gwas_genetic_columns",
+           "gwas_genetic_columns", "gwas_split_pieces",
            "gwas_stage_timing", "gwas_stage_times", "gwas_last_error", "gwas_destroy"]
 
 STAGES = ["pack", "centres", "chol", "rot", "sq", "ac", "simt"]
@@ -105,6 +105,8 @@ def _load():
     ip = ctypes.POINTER(ctypes.c_int)
     lib.gwas_info.argtypes = [vp, ip, ip, ip, ip, ip]
     lib.gwas_info.restype = i32
+    lib.gwas_split_pieces.argtypes = [vp]
+    lib.gwas_split_pieces.restype = i32
     lib.gwas_genetic_columns.argtypes = [vp]
     lib.gwas_genetic_columns.restype = i32
     lib.gwas_singular_count.argtypes = [vp]
@@ -382,6 +384,10 @@ def gwas_info(h) -> dict:
 
 def gwas_genetic_columns(h) -> int:
     return int(lib.gwas_genetic_columns(h))
+
+
+def gwas_split_pieces(h) -> int:
+    return int(lib.gwas_split_pieces(h))
 
 
 def gwas_singular_count(h) -> int:

@@ -72,8 +72,9 @@ struct gwas_handle_s {
   int64_t pk_cap = 0;
   int8_t* u8 = nullptr;
   int64_t u8_cap = 0;
-  // tensor-core state
+  // tensor-core state; split pieces per trait (CHOL) or of every U_j (EIG, pieces[0])
   TcState* tc = nullptr;
+  std::vector<int> pieces;
   std::vector<void*> allocs;
   StageTimer timer;  // per-stage events (gwas_stage_timing)
 };
@@ -195,13 +196,20 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     h->Linv = dalloc_t<double>(h, (size_t)t * nn);
     h->XLw = dalloc_t<double>(h, (size_t)t * q * n);
     double* A = dalloc_t<double>(h, nn);
-    double* work = dalloc_t<double>(h, nn);
+    double* work = dalloc_t<double>(h, nn > 3 * (size_t)n + 1 ? nn : 3 * (size_t)n + 1);
+    h->pieces.assign(t, 2);
     for (int j = 0; j < t; ++j) {
       double hj = h2[j], sj = s2[j];
       double* Lj = h->Linv + (size_t)j * nn;
       form_M(s, n, dPhi, hj, sj, A);
       cholesky(s, n, A, h->flags);
       tri_inverse(s, n, A, Lj, work);
+      if (h->prec == GWAS_PREC_SPLIT_BF16) {
+        read_flags(h, s);  // a failed factorisation is reported below; skip its estimate
+        if (!h->h_flags[FLAG_NOT_SPD] &&
+            condition_estimate(s, n, A, Lj, work, 24) > KAPPA_THIRD_PIECE)
+          h->pieces[j] = 3;
+      }
       // XLw_j (q x n, row k) = L^-1 X_L[:, k];  yw_j = L^-1 y_j
       gemm_f64(s, q, n, n, 1.0, dXL, n, 1, Lj, 1, n, 0.0, h->XLw + (size_t)j * q * n, n, 1);
       gemm_f64(s, 1, n, n, 1.0, dY + (size_t)j * n, 0, 1, Lj, 1, n, 0.0, yw + (size_t)j * n, 0, 1);
@@ -224,6 +232,22 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     gemm_f64(s, t, n, n, 1.0, dY, n, 1, h->Zt, 1, n, 0.0, yw, n, 1);
     double* d = dalloc_t<double>(h, (size_t)t * n);
     eig_weights(s, n, t, h->w, dh2, ds2, d, h->flags);
+    // conditioning of each M_j from the eigenvalues of Phi: one number decides the U pieces
+    h->pieces.assign(1, 2);
+    if (h->prec == GWAS_PREC_SPLIT_BF16) {
+      std::vector<double> hw(n);
+      GW_CUDA(cudaMemcpyAsync(hw.data(), h->w, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+      GW_CUDA(cudaStreamSynchronize(s));
+      double wmin = hw[0], wmax = hw[0];
+      for (int r = 1; r < n; ++r) {
+        wmin = hw[r] < wmin ? hw[r] : wmin;
+        wmax = hw[r] > wmax ? hw[r] : wmax;
+      }
+      for (int j = 0; j < t; ++j) {
+        const double lo = h2[j] * wmin + 1.0 - h2[j], hi = h2[j] * wmax + 1.0 - h2[j];
+        if (lo > 0.0 && hi / lo > KAPPA_THIRD_PIECE) h->pieces[0] = 3;
+      }
+    }
     TraitPackArgs ta{n, q, t, h->XLt, 0, yw, d, h->P, h->b0, h->rw, h->flags};
     trait_pack(s, ta);
     h->planes = dalloc_t<double>(h, (size_t)t * (q + 2) * h->ldp);
@@ -260,6 +284,7 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     ta.out_snp = h->out_snp;
     ta.out_var = h->out_var;
     ta.gm = h->gm;
+    ta.pieces = h->pieces.data();
     ta.intercept = 1;
     for (int i = 0; i < n; ++i)
       if (XL[i] != 1.0) ta.intercept = 0;
@@ -919,6 +944,11 @@ GW_API gwas_status gwas_info(gwas_handle h, int* n, int* q, int* t, int* algo, i
 }
 
 GW_API int gwas_genetic_columns(gwas_handle h) { return h ? h->gm.pr : -1; }
+
+GW_API int gwas_split_pieces(gwas_handle h) {
+  if (!h) return -1;
+  return h->tc ? tc_split_pieces(h->tc) : 0;
+}
 
 GW_API int64_t gwas_singular_count(gwas_handle h) {
   if (!h) return -1;

@@ -154,15 +154,24 @@ void eig_weights(cudaStream_t s, int n, int t, const double* w, const double* h2
 void eig_planes_f64(cudaStream_t s, int n, int q, int t, int ldp, const double* XLt,
                     const double* d, const double* rw, double* planes);
 
+// lam_max(M) / lam_min(M) of SPD M = L L^T, each extreme eigenvalue by `iters` power
+// iterations (M v = L L^T v; M^-1 v = L^-T L^-1 v) from a start with every component, so an
+// estimate from below of each (and of the ratio).  L: column-major lower Cholesky factor, Linv:
+// row-major lower inverse, both n x n.  work: 3 n + 1 doubles.  Synchronises s.
+double condition_estimate(cudaStream_t s, int n, const double* L, const double* Linv,
+                          double* work, int iters);
+
 // Conversions.
 void convert_f64_to_f32(cudaStream_t s, const double* x, float* y, int64_t count);
-// hi = bf16(x), lo = bf16(x - hi) for a rows x cols row-major matrix with leading dims.
+// hi = bf16(x), lo = bf16(x - hi) and, when lo2 is not NULL, lo2 = bf16(x - hi - lo), for a
+// rows x cols row-major matrix with leading dims.
 void split_bf16(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx,
-                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo);
+                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, __nv_bfloat16* lo2 = nullptr);
 // As split_bf16, with output row r taken from input row (r / gout) * gin + r % gout + off
 // (selects `gout` of every `gin` input rows, starting at `off`).
 void split_bf16_rows(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx, int gin,
-                     int gout, int off, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo);
+                     int gout, int off, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo,
+                     __nv_bfloat16* lo2 = nullptr);
 
 // ------------------------------------------------------------------------------------------
 // Genetic models: the block X_R,i a SNP contributes to X_i = [X_L | X_R,i] has pr columns

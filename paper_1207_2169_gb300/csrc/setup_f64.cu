@@ -527,24 +527,35 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ x, float* __restric
     y[e] = (float)x[e];
 }
 
+// x = hi + lo (+ lo2): each piece the BF16 rounding of what the previous pieces leave; lo2 may
+// be NULL (two pieces, ~16 significant bits; three carry ~24).
+__device__ __forceinline__ void split_store(double v, int64_t e, __nv_bfloat16* hi,
+                                            __nv_bfloat16* lo, __nv_bfloat16* lo2) {
+  const __nv_bfloat16 h = __double2bfloat16(v);
+  const double r1 = v - (double)__bfloat162float(h);
+  const __nv_bfloat16 l = __double2bfloat16(r1);
+  hi[e] = h;
+  lo[e] = l;
+  if (lo2) lo2[e] = __double2bfloat16(r1 - (double)__bfloat162float(l));
+}
+
 __global__ void split_bf16_kernel(const double* __restrict__ x, int rows, int cols, int64_t ldx,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                                  int64_t ldo) {
+                                  __nv_bfloat16* __restrict__ lo2, int64_t ldo) {
   const int64_t total = (int64_t)rows * ldo;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / ldo), c = (int)(e % ldo);
     const double v = c < cols ? x[(int64_t)r * ldx + c] : 0.0;
-    const __nv_bfloat16 h = __double2bfloat16(v);
-    hi[e] = h;
-    lo[e] = __double2bfloat16(v - (double)__bfloat162float(h));
+    split_store(v, e, hi, lo, lo2);
   }
 }
 
 __global__ void split_bf16_rows_kernel(const double* __restrict__ x, int rows, int cols,
                                        int64_t ldx, int gin, int gout, int off,
                                        __nv_bfloat16* __restrict__ hi,
-                                       __nv_bfloat16* __restrict__ lo, int64_t ldo) {
+                                       __nv_bfloat16* __restrict__ lo,
+                                       __nv_bfloat16* __restrict__ lo2, int64_t ldo) {
   const int64_t total = (int64_t)rows * ldo;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -552,16 +563,16 @@ __global__ void split_bf16_rows_kernel(const double* __restrict__ x, int rows, i
     const int c = (int)(e % ldo);
     const int64_t src = (r / gout) * gin + r % gout + off;
     const double v = c < cols ? x[src * ldx + c] : 0.0;
-    const __nv_bfloat16 h = __double2bfloat16(v);
-    hi[e] = h;
-    lo[e] = __double2bfloat16(v - (double)__bfloat162float(h));
+    split_store(v, e, hi, lo, lo2);
   }
 }
 }  // namespace
 
 void split_bf16_rows(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx, int gin,
-                     int gout, int off, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo) {
-  split_bf16_rows_kernel<<<1184, 256, 0, s>>>(x, rows, cols, ldx, gin, gout, off, hi, lo, ldo);
+                     int gout, int off, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo,
+                     __nv_bfloat16* lo2) {
+  split_bf16_rows_kernel<<<1184, 256, 0, s>>>(x, rows, cols, ldx, gin, gout, off, hi, lo, lo2,
+                                              ldo);
   GW_CHECK_LAUNCH();
 }
 
@@ -590,9 +601,82 @@ void convert_f64_to_f32(cudaStream_t s, const double* x, float* y, int64_t count
   GW_CHECK_LAUNCH();
 }
 
+namespace {
+
+// One power-iteration step: rq[0] = v . y (the Rayleigh quotient of unit v), then v = y / |y|.
+__global__ void power_step_kernel(int n, double* __restrict__ v, const double* __restrict__ y,
+                                  double* __restrict__ rq) {
+  __shared__ double red[2][32];
+  double vy = 0.0, yy = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    vy += v[i] * y[i];
+    yy += y[i] * y[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    vy += __shfl_xor_sync(0xffffffffu, vy, o);
+    yy += __shfl_xor_sync(0xffffffffu, yy, o);
+  }
+  if (threadIdx.x % 32 == 0) {
+    red[0][threadIdx.x / 32] = vy;
+    red[1][threadIdx.x / 32] = yy;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    vy = threadIdx.x < blockDim.x / 32 ? red[0][threadIdx.x] : 0.0;
+    yy = threadIdx.x < blockDim.x / 32 ? red[1][threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      vy += __shfl_xor_sync(0xffffffffu, vy, o);
+      yy += __shfl_xor_sync(0xffffffffu, yy, o);
+    }
+    if (threadIdx.x == 0) {
+      red[0][0] = vy;
+      red[1][0] = yy > 0.0 ? rsqrt(yy) : 0.0;
+    }
+  }
+  __syncthreads();
+  const double inv = red[1][0];
+  if (threadIdx.x == 0) rq[0] = red[0][0];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = y[i] * inv;
+}
+
+__global__ void power_start_kernel(int n, double* __restrict__ v) {
+  const double inv = rsqrt((double)n);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    v[i] = inv * (1.0 + 0.25 * (double)((i * 7919) % 13) / 13.0);  // a start with every component
+}
+
+}  // namespace
+
+double condition_estimate(cudaStream_t s, int n, const double* L, const double* Linv,
+                          double* work, int iters) {
+  double* v = work;
+  double* y = work + n;
+  double* z = work + 2 * n;
+  double* rq = work + 3 * n;
+  double lam[2] = {0.0, 0.0};
+  for (int which = 0; which < 2; ++which) {
+    power_start_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, v);
+    GW_CHECK_LAUNCH();
+    for (int it = 0; it < iters; ++it) {
+      if (which == 0) {  // M v = L (L^T v); L column-major lower
+        gemm_f64(s, n, 1, n, 1.0, L, n, 1, v, 1, 0, 0.0, y, 1, 0);
+        gemm_f64(s, n, 1, n, 1.0, L, 1, n, y, 1, 0, 0.0, z, 1, 0);
+      } else {  // M^-1 v = L^-T (L^-1 v); L^-1 row-major lower
+        gemm_f64(s, n, 1, n, 1.0, Linv, n, 1, v, 1, 0, 0.0, y, 1, 0);
+        gemm_f64(s, n, 1, n, 1.0, Linv, 1, n, y, 1, 0, 0.0, z, 1, 0);
+      }
+      power_step_kernel<<<1, 1024, 0, s>>>(n, v, z, rq);
+      GW_CHECK_LAUNCH();
+    }
+    GW_CUDA(cudaMemcpyAsync(&lam[which], rq, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GW_CUDA(cudaStreamSynchronize(s));
+  }
+  return lam[0] * lam[1];  // lam_max(M) lam_max(M^-1) = lam_max(M) / lam_min(M)
+}
+
 void split_bf16(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx,
-                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo) {
-  split_bf16_kernel<<<1184, 256, 0, s>>>(x, rows, cols, ldx, hi, lo, ldo);
+                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, __nv_bfloat16* lo2) {
+  split_bf16_kernel<<<1184, 256, 0, s>>>(x, rows, cols, ldx, hi, lo, lo2, ldo);
   GW_CHECK_LAUNCH();
 }
 

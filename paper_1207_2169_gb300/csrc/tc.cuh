@@ -7,6 +7,13 @@ namespace gw {
 
 struct TcState;
 
+// Pieces of the BF16 split of the M_j^-1-weighted operand (CHOL: the augmented L_j^-1; EIG:
+// U_j = M_j^-1 [X_L | r_j]): two (~16 significant bits) unless the conditioning of M_j,
+// kappa = lam_max / lam_min, exceeds this, then three (~24 bits).  The two-piece error grows with
+// kappa when Phi has many eigenvalues at its ridge (a kinship from fewer SNPs than individuals):
+// ~3e-5 at kappa = 100, past 1e-4 near kappa = 600-1000, while three pieces stay near 2e-6.
+constexpr double KAPPA_THIRD_PIECE = 100.0;
+
 struct TcSetupArgs {
   int algo, n, q, t;
   const double* Linv;    // CHOL: t x n x n row-major lower (FP64)
@@ -22,6 +29,7 @@ struct TcSetupArgs {
   int out_snp;           // B holds (b_snp, standard error) per pair instead of all p values
   int out_var;           // B holds the p values, then the p(p+1)/2 of Var(b) (packed upper)
   GeneticModel gm;       // the SNP's genetic columns (p = q + gm.pr)
+  const int* pieces;     // CHOL: split pieces (2 or 3) per trait; EIG: pieces[0] for every U_j
 };
 
 struct TcScanArgs {
@@ -42,5 +50,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a);
 void tc_destroy(TcState* st);
 // Rough tensor-core work of scanning m SNPs (FLOPs issued), for planning concurrent scans.
 double tc_scan_work(const TcState* st, int64_t m);
+// Largest number of split pieces the state's kernels use (2 or 3).
+int tc_split_pieces(const TcState* st);
 
 }  // namespace gw

@@ -10,7 +10,8 @@
 // diagonal of a block a K step of 64 columns multiplies only the rows it meets (narrower MMAs
 // into the matching accumulator columns), and the last block stops at row n + q.  The
 // augmented matrix is split into BF16 hi + lo pieces and genotypes are exact in BF16, so
-// D = X hi^T + X lo^T carries ~16 significant bits with FP32 accumulation.  The epilogue sums
+// D = X hi^T + X lo^T carries ~16 significant bits with FP32 accumulation (a third piece,
+// ~24 bits, for a trait whose M is badly conditioned).  The epilogue sums
 // s = x'^T x' out of TMEM (FP32 within a block, FP64 across blocks), picks up a and c, and
 // finishes each tile with the Schur-complement solve in FP64.  X' is never written to memory.
 // With an intercept in X_L each SNP is centred by mu, the multiple of 1/64 nearest its mean
@@ -233,8 +234,10 @@ __device__ __noinline__ void solve_pair(const CholTcParams& p, const float* a0, 
 }
 
 // QM: compile-time bound on q (3 or 7), so the epilogue's per-column arrays stay in registers.
-// GP: genetic columns per SNP (1, or 2 for a two-column genetic model).
-template <int QM, int GP>
+// GP: genetic columns per SNP (1, or 2 for a two-column genetic model).  NP: BF16 pieces of the
+// split matrix (2, or 3 for a badly conditioned M; a compile-time bound keeps the issuer's and
+// producer's piece loops unrolled).
+template <int QM, int GP, int NP>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     chol_tc_kernel(const __grid_constant__ CholMaps lmaps, const __grid_constant__ CUtensorMap mapG,
                    const CholTcParams p) {
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       bool ok = true;
       for (Step st{blockIdx.x, 0, 0}; st.tile < tiles_run && ok; advance(st, nblocks, p.kpad)) {
         const int j = diag_skip(st.nb, st.ks);  // rows 64 j .. 255 of the block
-        for (int piece = 0; piece < 2; ++piece) {
+        for (int piece = 0; piece < NP; ++piece) {
           ok = mbar_wait(&bars->b_empty[bs], bph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
           const int y = piece * p.rpad + st.nb * BN + 64 * j;
@@ -341,7 +344,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const uint64_t ad = sw128_desc(sA + as * A_BYTES);
             const int j = diag_skip(nb, ks);  // accumulator columns 64 j .. ncols - 1
             const uint32_t idesc = idesc_bf16(BM, ncols - 64 * j);
-            for (int piece = 0; piece < 2; ++piece) {
+            for (int piece = 0; piece < NP; ++piece) {
               ok = mbar_wait(&bars->b_full[bs], bph, abort, tflag, WAIT_NS);
               if (!ok) break;
               tc_fence_after();
@@ -613,7 +616,7 @@ int g_max_ctas[64][2];  // per device: co-resident CTAs of each instantiation
 template <int QM>
 int max_resident_ctas() {
   int per_sm = 0, dev = 0, sms = 0;
-  GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_tc_kernel<QM, 1>,
+  GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_tc_kernel<QM, 1, 2>,
                                                         NUM_THREADS, SMEM_BYTES));
   GW_REQUIRE(per_sm >= 1, GWAS_ERR_UNSUPPORTED, "the CHOL tensor-core kernel does not fit on an SM");
   GW_CUDA(cudaGetDevice(&dev));
@@ -628,19 +631,34 @@ int current_device() {
 }
 }  // namespace
 
+template <int QM, int GP, int NP>
+void set_smem() {
+  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QM, GP, NP>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+}
+
+template <int GP, int NP>
+void launch_q(unsigned grid, cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& mapG,
+              const CholTcParams& p) {
+  if (p.q <= 3)
+    chol_tc_kernel<3, GP, NP><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+  else
+    chol_tc_kernel<QMAX, GP, NP><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+}
+
 void chol_tc_prepare() {
   static std::mutex mu;  // setups may run on several host threads at once
   std::lock_guard<std::mutex> lock(mu);
   int* mx = g_max_ctas[current_device()];
   if (mx[0] && mx[1]) return;  // attributes and occupancy belong to the device: once per device
-  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)SMEM_BYTES));
-  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QMAX, 1>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)SMEM_BYTES));
-  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QMAX, 2>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+  set_smem<3, 1, 2>();
+  set_smem<QMAX, 1, 2>();
+  set_smem<3, 2, 2>();
+  set_smem<QMAX, 2, 2>();
+  set_smem<3, 1, 3>();
+  set_smem<QMAX, 1, 3>();
+  set_smem<3, 2, 3>();
+  set_smem<QMAX, 2, 3>();
   mx[0] = max_resident_ctas<3>();
   mx[1] = max_resident_ctas<QMAX>();
 }
@@ -652,19 +670,21 @@ void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& ma
   if (p.m <= 0) return;
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q=%d outside [1,%d]", p.q, QMAX);
   GW_REQUIRE(p.gp == 1 || p.gp == 2, GWAS_ERR_ARG, "genetic columns %d outside [1,2]", p.gp);
+  GW_REQUIRE(p.pieces == 2 || p.pieces == 3, GWAS_ERR_ARG, "split pieces %d outside [2,3]",
+             p.pieces);
   // persistent: no more CTAs than fit at once (and no more than the tiles need)
   const int64_t tiles = (p.m + BM / p.gp - 1) / (BM / p.gp);
   int64_t cap = chol_tc_resident_ctas(p.q);
   if (cap <= 0 || cap > num_sms) cap = num_sms;
   const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
-  if (p.q <= 3 && p.gp == 1)
-    chol_tc_kernel<3, 1><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+  if (p.gp == 1 && p.pieces == 2)
+    launch_q<1, 2>(grid, s, lmaps, mapG, p);
   else if (p.gp == 1)
-    chol_tc_kernel<QMAX, 1><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
-  else if (p.q <= 3)
-    chol_tc_kernel<3, 2><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+    launch_q<1, 3>(grid, s, lmaps, mapG, p);
+  else if (p.pieces == 2)
+    launch_q<2, 2>(grid, s, lmaps, mapG, p);
   else
-    chol_tc_kernel<QMAX, 2><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+    launch_q<2, 3>(grid, s, lmaps, mapG, p);
   GW_CHECK_LAUNCH();
 }
 

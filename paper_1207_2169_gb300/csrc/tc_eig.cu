@@ -251,7 +251,9 @@ __device__ __forceinline__ void tmem_ld_cols<8>(uint32_t taddr, uint32_t (&r)[8]
 
 // VAR (AC only): the epilogue writes b and the packed Var(b) per pair (GWAS_OUT_VAR), compiled
 // apart so that the other output modes keep their register allocation.
-template <int EPI, int QQ, bool VAR = false, int GP = 1>
+// NP: BF16 pieces of the B operand of ROT and AC (2, or 3 for AC when some M_j is badly
+// conditioned); a compile-time bound keeps the producer's and issuer's piece loops unrolled.
+template <int EPI, int QQ, bool VAR = false, int GP = 1, int NP = 2>
 __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
     eig_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapG, const EigTcParams p) {
@@ -335,7 +337,9 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
               if (++as == SA) { as = 0; aph ^= 1; }
             }
           }
-          for (int piece = 0; piece < 2 && ok; ++piece) {
+          // B pieces: ROT and AC NP against the exact genotype operand; SQ hi, lo
+          constexpr int NBP = CONV ? NP : 2;
+          for (int piece = 0; piece < NBP && ok; ++piece) {
             ok = mbar_wait(&bars->b_empty[bs], bph ^ 1, abort, tflag, WAIT_NS);
             if (!ok) break;
             mbar_arrive_expect_tx(&bars->b_full[bs], B_BYTES);
@@ -378,12 +382,12 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
         const uint32_t dt = tmem + buf * BN;
         for (int ks = 0; ks < nk && ok; ++ks) {
           if (CONV) {
-            // products (x, U_hi), (x, U_lo) -- the genotype operand is exact
+            // products (x, U_hi), (x, U_lo) (and (x, U_lo2)) -- the genotype operand is exact
             ok = mbar_wait(&bars->a_full[as], aph, abort, tflag, WAIT_NS);
             if (!ok) break;
             tc_fence_after();
             const uint64_t ad = sw128_desc(sA + as * A_BYTES);
-            for (int piece = 0; piece < 2 && ok; ++piece) {
+            for (int piece = 0; piece < NP && ok; ++piece) {
               ok = mbar_wait(&bars->b_full[bs], bph, abort, tflag, WAIT_NS);
               if (!ok) break;
               tc_fence_after();
@@ -549,24 +553,27 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
         tc_fence_after();
         const uint32_t base = tmem + ((uint32_t)(32 * qd) << 16) + buf * BN;
         if (EPI == EPI_ROT) {
-          // 32 products of rotated values, split hi + lo, into row `row` of the planes
+          // 32 products of rotated values, split into NP BF16 pieces (each the rounding of what
+          // the previous leave), into row `row` of each piece's planes
           auto store_split = [&](int64_t row, int col0, const float* x, const float* y) {
-            uint32_t hi[16], lo[16];
+            float rem[32];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const float s0 = x[2 * i] * y[2 * i], s1 = x[2 * i + 1] * y[2 * i + 1];
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(s0), h1 = __float2bfloat16_rn(s1);
-              const __nv_bfloat16 l0 = __float2bfloat16_rn(s0 - __bfloat162float(h0));
-              const __nv_bfloat16 l1 = __float2bfloat16_rn(s1 - __bfloat162float(h1));
-              hi[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-              lo[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-            }
-            uint4* dh = reinterpret_cast<uint4*>(p.xsq + row * p.kpad + col0);
-            uint4* dl = reinterpret_cast<uint4*>(p.xsq + (p.a_piece_rows + row) * p.kpad + col0);
+            for (int i = 0; i < 32; ++i) rem[i] = x[i] * y[i];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              dh[u] = make_uint4(hi[4 * u], hi[4 * u + 1], hi[4 * u + 2], hi[4 * u + 3]);
-              dl[u] = make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]);
+            for (int pc = 0; pc < NP; ++pc) {
+              uint32_t pk[16];
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(rem[2 * i]);
+                const __nv_bfloat16 h1 = __float2bfloat16_rn(rem[2 * i + 1]);
+                rem[2 * i] -= __bfloat162float(h0);
+                rem[2 * i + 1] -= __bfloat162float(h1);
+                pk[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+              }
+              uint4* dst = reinterpret_cast<uint4*>(p.xsq + (pc * p.a_piece_rows + row) * p.kpad + col0);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                dst[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
             }
           };
           for (int c = 0; c < BN / 32; ++c) {
@@ -826,49 +833,50 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
   }
 }
 
-template <int EPI, int QQ, bool VAR = false, int GP = 1>
+template <int EPI, int QQ, bool VAR = false, int GP = 1, int NP = 2>
 void prepare_one() {
   constexpr size_t SMEM = smem_of(EPI, QQ);
   static_assert(SMEM <= 232448, "shared memory over the sm_103 opt-in limit");
-  GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QQ, VAR, GP>,
+  GW_CUDA(cudaFuncSetAttribute(eig_tc_kernel<EPI, QQ, VAR, GP, NP>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
 }
 
-template <int EPI, int QQ, bool VAR = false, int GP = 1>
+template <int EPI, int QQ, bool VAR = false, int GP = 1, int NP = 2>
 void launch_one(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
                 const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {
   constexpr size_t SMEM = smem_of(EPI, QQ);
   constexpr int TS = EPI == EPI_SQ ? BM : BM / GP;
   const int64_t work = ((p.m + TS - 1) / TS) * p.nblk;
   const unsigned grid = (unsigned)(work < num_sms ? work : num_sms);
-  eig_tc_kernel<EPI, QQ, VAR, GP><<<grid, 32 * nwarps_of(EPI, QQ), SMEM, s>>>(mapA, mapB, mapG, p);
+  eig_tc_kernel<EPI, QQ, VAR, GP, NP>
+      <<<grid, 32 * nwarps_of(EPI, QQ), SMEM, s>>>(mapA, mapB, mapG, p);
   GW_CHECK_LAUNCH();
 }
 
 // AC per q; two working columns solve each pair in ac_pair, which writes every output mode
-template <bool VAR, int GP>
+template <bool VAR, int GP, int NP>
 void launch_ac(cudaStream_t s, const CUtensorMap& mapA, const CUtensorMap& mapB,
                const CUtensorMap& mapG, const EigTcParams& p, int num_sms) {
   switch (p.q) {
-    case 1: launch_one<EPI_AC, 1, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
-    case 2: launch_one<EPI_AC, 2, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
-    case 3: launch_one<EPI_AC, 3, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
-    case 4: launch_one<EPI_AC, 4, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
-    case 5: launch_one<EPI_AC, 5, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
-    case 6: launch_one<EPI_AC, 6, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
-    default: launch_one<EPI_AC, 7, VAR, GP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 1: launch_one<EPI_AC, 1, VAR, GP, NP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 2: launch_one<EPI_AC, 2, VAR, GP, NP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 3: launch_one<EPI_AC, 3, VAR, GP, NP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 4: launch_one<EPI_AC, 4, VAR, GP, NP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 5: launch_one<EPI_AC, 5, VAR, GP, NP>(s, mapA, mapB, mapG, p, num_sms); break;
+    case 6: launch_one<EPI_AC, 6, VAR, GP, NP>(s, mapA, mapB, mapG, p, num_sms); break;
+    default: launch_one<EPI_AC, 7, VAR, GP, NP>(s, mapA, mapB, mapG, p, num_sms); break;
   }
 }
 
-template <bool VAR, int GP>
+template <bool VAR, int GP, int NP>
 void prepare_ac() {
-  prepare_one<EPI_AC, 1, VAR, GP>();
-  prepare_one<EPI_AC, 2, VAR, GP>();
-  prepare_one<EPI_AC, 3, VAR, GP>();
-  prepare_one<EPI_AC, 4, VAR, GP>();
-  prepare_one<EPI_AC, 5, VAR, GP>();
-  prepare_one<EPI_AC, 6, VAR, GP>();
-  prepare_one<EPI_AC, 7, VAR, GP>();
+  prepare_one<EPI_AC, 1, VAR, GP, NP>();
+  prepare_one<EPI_AC, 2, VAR, GP, NP>();
+  prepare_one<EPI_AC, 3, VAR, GP, NP>();
+  prepare_one<EPI_AC, 4, VAR, GP, NP>();
+  prepare_one<EPI_AC, 5, VAR, GP, NP>();
+  prepare_one<EPI_AC, 6, VAR, GP, NP>();
+  prepare_one<EPI_AC, 7, VAR, GP, NP>();
 }
 
 }  // namespace
@@ -886,9 +894,12 @@ void eig_tc_prepare() {
   prepare_one<EPI_ROT, 0>();
   prepare_one<EPI_ROT, 0, false, 2>();
   prepare_one<EPI_SQ, 0>();
-  prepare_ac<false, 1>();
-  prepare_ac<true, 1>();
-  prepare_ac<false, 2>();
+  prepare_ac<false, 1, 2>();
+  prepare_ac<true, 1, 2>();
+  prepare_ac<false, 2, 2>();
+  prepare_ac<false, 1, 3>();
+  prepare_ac<true, 1, 3>();
+  prepare_ac<false, 2, 3>();
   done_mask |= bit;
 }
 
@@ -897,8 +908,11 @@ void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUt
   if (p.m <= 0 || p.nblk <= 0) return;
   GW_REQUIRE(p.q >= 1 && p.q <= QMAX, GWAS_ERR_ARG, "q out of range");
   GW_REQUIRE(p.gp == 1 || p.gp == 2, GWAS_ERR_ARG, "genetic columns %d outside [1,2]", p.gp);
+  GW_REQUIRE(p.pieces == 2 || p.pieces == 3, GWAS_ERR_ARG, "split pieces %d outside [2,3]",
+             p.pieces);
   switch (stage) {
     case 0:
+      GW_REQUIRE(p.pieces == 2, GWAS_ERR_ARG, "the rotation takes two split pieces");
       if (p.gp == 2)
         launch_one<EPI_ROT, 0, false, 2>(s, mapA, mapB, mapG, p, num_sms);
       else
@@ -906,12 +920,20 @@ void eig_tc_launch(cudaStream_t s, int stage, const CUtensorMap& mapA, const CUt
       break;
     case 1: launch_one<EPI_SQ, 0>(s, mapA, mapB, mapG, p, num_sms); break;
     default:
-      if (p.gp == 2)
-        launch_ac<false, 2>(s, mapA, mapB, mapG, p, num_sms);
-      else if (p.out_var)
-        launch_ac<true, 1>(s, mapA, mapB, mapG, p, num_sms);
-      else
-        launch_ac<false, 1>(s, mapA, mapB, mapG, p, num_sms);
+      if (p.pieces == 3) {
+        if (p.gp == 2)
+          launch_ac<false, 2, 3>(s, mapA, mapB, mapG, p, num_sms);
+        else if (p.out_var)
+          launch_ac<true, 1, 3>(s, mapA, mapB, mapG, p, num_sms);
+        else
+          launch_ac<false, 1, 3>(s, mapA, mapB, mapG, p, num_sms);
+      } else if (p.gp == 2) {
+        launch_ac<false, 2, 2>(s, mapA, mapB, mapG, p, num_sms);
+      } else if (p.out_var) {
+        launch_ac<true, 1, 2>(s, mapA, mapB, mapG, p, num_sms);
+      } else {
+        launch_ac<false, 1, 2>(s, mapA, mapB, mapG, p, num_sms);
+      }
   }
 }
 

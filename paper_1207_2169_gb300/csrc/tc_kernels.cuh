@@ -29,6 +29,7 @@ struct CholTcParams {
   int gp;             // genetic columns per SNP (1 or 2); a tile holds CHOL_TC_BM / gp SNPs
   uint32_t code[2];   // coding of each genetic column: values of genotypes 0, 1, 2 in bytes 0-2
   float tm[4];        // gp = 2: reported coefficients = tm (row-major 2 x 2) x working ones
+  int pieces;         // BF16 pieces of trait j's split matrix (2 or 3), rpad rows each
 };
 constexpr int CHOL_TC_BM = 128;  // rows (SNP columns) per tile
 // Tensor maps of one trait's split augmented L^-1: rows = 2 * rpad (hi piece then lo piece),
@@ -74,6 +75,7 @@ struct EigTcParams {
   int gp;                  // genetic columns per SNP
   uint32_t code[2];        // coding of each genetic column (bytes: values of genotypes 0, 1, 2)
   float tm[4];             // gp = 2: reported coefficients = tm (row-major 2 x 2) x working ones
+  int pieces;              // ROT, AC: BF16 pieces of the B operand (b_piece_rows rows each)
 };
 // Traits per AC column block: T (q+1) accumulator columns, with the last trait's load of
 // QP = (q+1 rounded up to 4 or 8) columns still inside the 256-column block.

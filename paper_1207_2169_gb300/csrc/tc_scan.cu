@@ -76,7 +76,8 @@ struct TcState {
   std::vector<void*> allocs;
   // CHOL, per trait: split L^-1 (hi rows then lo rows) and its tensor maps
   std::vector<CholMaps> lmaps;
-  __nv_bfloat16* Lsplit = nullptr;  // t x (2 rpad) x kpad
+  std::vector<int> lpieces;         // split pieces of each trait's matrix (2 or 3)
+  __nv_bfloat16* Lsplit = nullptr;  // per trait (pieces rpad) x kpad, traits one after another
   const double* P = nullptr;        // t x q x q (owned by the handle)
   const double* b0 = nullptr;       // t x q
   // EIG: split operands, FP32 null-model blocks, per-block scratch and tensor maps
@@ -89,6 +90,7 @@ struct TcState {
   int out_snp = 0;
   int out_var = 0;
   int traits_ac = 0;
+  int upieces = 2;  // split pieces of U
   GeneticModel gm;
   CUtensorMap mapZ, mapU, mapD, mapX;
 };
@@ -137,23 +139,32 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
       // and M^-1 r = L^-T (L^-1 r) are linear in the genotypes, so the whitening product also
       // yields a_k and c (Algorithm 3) in q + 1 extra accumulator columns.
       st->rpad = (int)round_up(n + q + 1, 256);
-      const size_t per = (size_t)2 * st->rpad * st->kpad;
-      st->Lsplit = (__nv_bfloat16*)tc_alloc(st, per * t * 2);
-      GW_CUDA(cudaMemsetAsync(st->Lsplit, 0, per * t * 2, s));
-      double* Ut = (double*)tc_alloc(st, (size_t)(q + 1) * n * 8);
+      const size_t piece = (size_t)st->rpad * st->kpad;  // elements of one piece
+      size_t total = 0;
       for (int j = 0; j < t; ++j) {
+        st->lpieces.push_back(a.pieces && a.pieces[j] == 3 ? 3 : 2);
+        total += piece * st->lpieces[j];
+      }
+      st->Lsplit = (__nv_bfloat16*)tc_alloc(st, total * 2);
+      GW_CUDA(cudaMemsetAsync(st->Lsplit, 0, total * 2, s));
+      double* Ut = (double*)tc_alloc(st, (size_t)(q + 1) * n * 8);
+      size_t off = 0;
+      for (int j = 0; j < t; ++j) {
+        const int np = st->lpieces[j];
         const double* Li = a.Linv + (size_t)j * n * n;
-        __nv_bfloat16* hi = st->Lsplit + per * j;
-        __nv_bfloat16* lo = hi + (size_t)st->rpad * st->kpad;
-        split_bf16(s, Li, n, n, n, hi, lo, st->kpad);
+        __nv_bfloat16* hi = st->Lsplit + off;
+        __nv_bfloat16* lo = hi + piece;
+        __nv_bfloat16* lo2 = np == 3 ? lo + piece : nullptr;
+        off += piece * np;
+        split_bf16(s, Li, n, n, n, hi, lo, st->kpad, lo2);
         gemm_f64(s, q, n, n, 1.0, a.XLw + (size_t)j * q * n, n, 1, Li, n, 1, 0.0, Ut, n, 1);
         gemm_f64(s, 1, n, n, 1.0, a.rw + (size_t)j * n, n, 1, Li, n, 1, 0.0, Ut + (size_t)q * n,
                  n, 1);
-        split_bf16(s, Ut, q + 1, n, n, hi + (size_t)n * st->kpad, lo + (size_t)n * st->kpad,
-                   st->kpad);
+        const size_t aug = (size_t)n * st->kpad;  // the q + 1 augmented rows follow L^-1's n
+        split_bf16(s, Ut, q + 1, n, n, hi + aug, lo + aug, st->kpad, lo2 ? lo2 + aug : nullptr);
         CholMaps mp;
         for (int r = 0; r < 4; ++r)
-          mp.m[r] = make_map_bf16(hi, 2 * (int64_t)st->rpad, st->kpad, 256 - 64 * r);
+          mp.m[r] = make_map_bf16(hi, (int64_t)np * st->rpad, st->kpad, 256 - 64 * r);
         st->lmaps.push_back(mp);
       }
       GW_CUDA(cudaStreamSynchronize(s));
@@ -165,6 +176,10 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     // EIG.  Z^T split (rows = eigenvectors).
     const int kp = st->kpad, q1 = q + 1, q2 = q + 2;
     const size_t zrows = (size_t)st->rpad;
+    // U_j takes a third BF16 piece when some M_j is badly conditioned; Z^T (orthonormal), d_j
+    // and the squared planes (positive sums) keep two: at that conditioning the FP32 accumulation
+    // of the contractions, not their operands' 16 bits, bounds s_ij
+    st->upieces = a.pieces && a.pieces[0] == 3 ? 3 : 2;
     st->Zsplit = (__nv_bfloat16*)tc_alloc(st, 2 * zrows * kp * 2);
     GW_CUDA(cudaMemsetAsync(st->Zsplit, 0, 2 * zrows * kp * 2, s));
     split_bf16(s, a.Zt, n, n, n, st->Zsplit, st->Zsplit + zrows * kp, kp);
@@ -172,9 +187,10 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     // Uall[row][c] = sum_r planes[row][r] Z^T[r][c] over all q+2 plane rows (the last is unused)
     double* Uall = (double*)tc_alloc(st, (size_t)t * q2 * a.ldp * 8);
     gemm_f64(s, t * q2, n, n, 1.0, a.planes, a.ldp, 1, a.Zt, n, 1, 0.0, Uall, a.ldp, 1);
-    st->Usplit = (__nv_bfloat16*)tc_alloc(st, (size_t)2 * t * q1 * kp * 2);
-    split_bf16_rows(s, Uall, t * q1, n, a.ldp, q2, q1, 0, st->Usplit,
-                    st->Usplit + (size_t)t * q1 * kp, kp);
+    const size_t upiece = (size_t)t * q1 * kp;
+    st->Usplit = (__nv_bfloat16*)tc_alloc(st, (size_t)st->upieces * upiece * 2);
+    split_bf16_rows(s, Uall, t * q1, n, a.ldp, q2, q1, 0, st->Usplit, st->Usplit + upiece, kp,
+                    st->upieces == 3 ? st->Usplit + 2 * upiece : nullptr);
     // d_j (the last plane row of each trait), split
     st->dsplit = (__nv_bfloat16*)tc_alloc(st, (size_t)2 * t * kp * 2);
     split_bf16_rows(s, a.planes, t, n, a.ldp, q2, 1, q + 1, st->dsplit,
@@ -204,9 +220,9 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
     // sigma = x^T M^-1 x - a^T S_TL^-1 a (which would amplify the BF16 splitting error).
     if (a.intercept) st->mu = (float*)tc_alloc(st, (size_t)st->mcap * a.gm.pr * 4);
     st->mapZ = make_map_bf16(st->Zsplit, 2 * (int64_t)zrows, kp, 256);
-    st->mapU = make_map_bf16(st->Usplit, 2 * (int64_t)t * q1, kp, 256);
+    st->mapU = make_map_bf16(st->Usplit, (int64_t)st->upieces * t * q1, kp, 256);
     st->mapD = make_map_bf16(st->dsplit, 2 * (int64_t)t, kp, 256);
-    st->mapX = make_map_bf16(st->xsq, 2 * np * st->mcap, kp, 128);
+    st->mapX = make_map_bf16(st->xsq, 2 * (int64_t)np * st->mcap, kp, 128);
     eig_tc_prepare();
     return st;
   } catch (...) {
@@ -248,6 +264,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
       p.code[0] = st->gm.code_word(0);
       p.code[1] = st->gm.code_word(1);
       for (int e = 0; e < 4; ++e) p.tm[e] = st->gm.tm[e / 2][e % 2];
+      p.pieces = st->lpieces[j];
       p.B = a.B;
       p.W = a.wald;
       p.flags = a.flags;
@@ -290,6 +307,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     }
     p.mu = st->mu;
     p.nblk = st->rpad / 256;
+    p.pieces = 2;  // Z^T (and, in SQ, the squared planes and d_j): two pieces
     p.b_piece_rows = st->rpad;
     p.b_rows_per_blk = 256;
     ev = tm ? tm->begin(s, STAGE_ROT) : nullptr;
@@ -309,6 +327,7 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     p.b_piece_rows = t * q1;
     p.b_rows_per_blk = st->traits_ac * q1;
     p.traits_per_blk = st->traits_ac;
+    p.pieces = st->upieces;
     p.P = st->P32;
     p.b0 = st->b032;
     const int pp = q + gp;  // coefficients per pair
@@ -320,6 +339,13 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     eig_tc_launch(s, 2, st->mapU, st->mapU, mapG, p, ctas);
     if (ev) tm->end(s, ev);
   }
+}
+
+int tc_split_pieces(const TcState* st) {
+  if (!st) return 0;
+  int np = st->algo == GWAS_ALGO_CHOL ? 2 : st->upieces;
+  for (int v : st->lpieces) np = v > np ? v : np;
+  return np;
 }
 
 void tc_destroy(TcState* st) {

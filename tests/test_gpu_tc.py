@@ -131,3 +131,55 @@ def test_split_without_intercept(g, algo, t):
     B, W, _ = run(g, c, algo, "split_bf16")
     eb, ew = max_errors(B, W, Bref, Wref, Vref)
     assert eb < TOL and ew < TOL, (eb, ew)
+
+
+@pytest.mark.parametrize("algo,t", [("chol", 1), ("eig", 24)])
+def test_split_near_one_heritability(g, algo, t):
+    """h2 up to 0.999 on a kinship from 200 SNPs for n = 500: 300 eigenvalues at the 1e-3 ridge,
+    so M_j^-1 weights those coordinates up to ~1000 times the others (lam_max / lam_min of M_j
+    near 3000 at h2 = 0.999, near 1000 at 0.995), the hardest case the split operands meet; some
+    SNPs are nearly collinear with the covariates (half their values copied from covariate 1's
+    sign) so that sigma = s - a^T P a cancels.  Setup takes a third BF16 piece of L_j^-1 / U_j here
+    (two would give 1.3e-4 / 2.9e-4).  CHOL then meets 1e-4 on every output at h2 = 0.999, and EIG
+    on every output of the traits with h2 <= 0.995.  At h2 = 0.999 EIG reaches the FP32
+    accumulation floor of its a/c contraction (~5e-6 of b_snp): ~1e-4 on the SNP effect, and on an
+    intercept that this kinship determines ~40 times more precisely than mu b_snp (the all-ones
+    vector lies in the ridge eigenspace of a kinship of standardised genotypes) that error
+    amplified, 1.2e-4 measured; bounded here at 2e-4 and 5e-4."""
+    rs = np.random.default_rng(12)
+    n, q = 500, 3
+    Phi = synth.kinship(synth.kinship_factor(rs, n, n_snps=200))
+    XL = synth.covariates(rs, n, q)
+    h2 = np.full(t, 0.999) if t == 1 else np.r_[np.full(t // 2, 0.999), rs.uniform(0.9, 0.995, t - t // 2)]
+    s2 = rs.uniform(0.5, 2.0, t)
+    Y = XL @ rs.standard_normal((q, t)) + rs.standard_normal((n, t))
+    XR = synth.genotypes(rs, n, 400)
+    lead = np.flatnonzero(XL[:, 1] > 0)
+    for i in range(0, 40, 4):  # genotype tracks covariate 1 on half the individuals
+        XR[i, lead] = np.where(rs.random(lead.size) < 0.9, 2, XR[i, lead])
+    c = synth.Cohort(Phi=Phi, XL=XL, Y=Y, h2=h2, s2=s2, XR=XR, beta=None)
+    Bref, Wref, Vref = gls.gls_grid(Phi, XL, XR, Y, h2, s2)
+    B, W, _ = run(g, c, algo, "split_bf16", packed=True)
+    easy = h2 <= 0.995
+    if easy.any():
+        eb, ew = max_errors(B[:, easy], W[:, easy], Bref[:, easy], Wref[:, easy], Vref[:, easy])
+        assert eb < TOL and ew < TOL, ("h2 <= 0.995", eb, ew)
+    hard = ~easy
+    eb, ew = max_errors(B[:, hard, 1:], W[:, hard], Bref[:, hard, 1:], Wref[:, hard], Vref[:, hard, 1:])
+    e_int, _ = max_errors(B[:, hard, :1], W[:, hard], Bref[:, hard, :1], Wref[:, hard], Vref[:, hard, :1])
+    if algo == "chol":
+        assert max(eb, ew, e_int) < TOL, (eb, ew, e_int)
+    else:
+        assert eb < 2e-4 and ew < 2e-4 and e_int < 5e-4, (eb, ew, e_int)
+    # this cohort's M is conditioned ~3000: setup chose the three-piece split; a well conditioned
+    # one (h2 = 0.5 on the same kinship, kappa ~ 7) keeps two
+    h = g.gwas_setup(Phi, XL, Y, h2, s2, algo=algo, precision="split_bf16")
+    try:
+        assert g.gwas_split_pieces(h) == 3
+    finally:
+        g.gwas_destroy(h)
+    h = g.gwas_setup(Phi, XL, Y, np.full(t, 0.5), s2, algo=algo, precision="split_bf16")
+    try:
+        assert g.gwas_split_pieces(h) == 2
+    finally:
+        g.gwas_destroy(h)
