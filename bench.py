@@ -424,18 +424,23 @@ def measure(idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=T
         ms = _max_over_ranks(ms / steps, ws)
         del scratch
         # end to end: pinned host genotypes in, pinned host results out, through the same call
-        e2e_s, same = None, None
+        e2e_s, same, stream = None, None, None
         if e2e:
             xr_h = xr_d.cpu().pin_memory()
             del xr_d
             B_h = torch.empty((mm, t, p), dtype=torch.float32).pin_memory()
             W_h = torch.empty((mm, t), dtype=torch.float32).pin_memory()
-            scan(h, xr_h, B_h, W_h)
+            scan(h, xr_h, B_h, W_h)  # the first streamed call also picks the block size
+            info0 = g.gwas_stream_info(h)
             _barrier(ws)
             t0 = time.perf_counter()
             for _ in range(e2e_steps):
                 scan(h, xr_h, B_h, W_h)
             e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
+            info1 = g.gwas_stream_info(h)
+            stream = {"block_snps": info1["block_snps"], "block_chosen_by_timing": info1["tuned"],
+                      "candidates_ms_h2d_scan_d2h": {str(k): v for k, v in info0["candidates"].items()},
+                      "graph_replays_per_step": (info1["graph_launches"] - info0["graph_launches"]) / e2e_steps}
             same = bool(torch.equal(B_h, B_d.cpu()))
     finally:
         g.gwas_destroy(h)
@@ -450,7 +455,7 @@ def measure(idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=T
             "value": pairs * ws / e2e_s, "unit": "pairs/s",
             "h2d_bytes_per_step": mm * _row_bytes(n, fmt),
             "d2h_bytes_per_step": mm * t * (p + 1) * 4, "ms_per_step": e2e_s * 1e3,
-            "matches_device_run": same},
+            "matches_device_run": same, "streaming": stream},
         "roofline": dom, "kernels": kernels,
         "gpu_launches": sum(v[1] for v in stages.values()),
         "stage_ms": {k: v[0] / steps for k, v in stages.items()},

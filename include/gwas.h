@@ -100,7 +100,8 @@ enum { GWAS_MODEL_ADDITIVE = 0, GWAS_MODEL_DOMINANT = 1, GWAS_MODEL_RECESSIVE = 
 typedef struct {
   int algo;               /* GWAS_ALGO_*; AUTO = CHOL when t == 1, else EIG                   */
   int precision;          /* GWAS_PREC_*                                                      */
-  int block_snps;         /* SNPs per device block when streaming host input; 0 = default     */
+  int block_snps;         /* SNPs per device block when streaming host input; 0 = chosen by
+                             timing on the first streamed call (gwas_stream_info)             */
   int validate_genotypes; /* nonzero: scan checks every genotype is 0, 1 or 2                 */
   int device;             /* CUDA device ordinal                                              */
   int out_mode;           /* GWAS_OUT_*                                                       */
@@ -303,6 +304,23 @@ gwas_status gwas_setup_timing(gwas_handle h, double* ms_setup);
 
 /* Sizes and resolved options of a handle (any pointer may be NULL). */
 gwas_status gwas_info(gwas_handle h, int* n, int* q, int* t, int* algo, int* precision);
+
+/*
+ * gwas_stream_info -- how a handle streams host input or output (not from the paper: the
+ * pipeline of "Sequences of GLS'" on this GPU).  Any pointer may be NULL.
+ *   block_snps      SNPs per streamed block now in use;
+ *   tuned           1 once the block size was chosen by timing: with block_snps = 0 at setup,
+ *                   the first streamed call times, on its own first SNPs, the H2D copy, the scan
+ *                   and the D2H copy of a block at sizes 8 Ki .. 256 Ki SNPs (within the output
+ *                   ring's 2 GB) and keeps the size minimising that call's modelled pipeline
+ *                   time (the fill plus, per further block, its slowest stage);
+ *   graph_launches  full blocks whose device work ran as a replayed CUDA graph (one graph per
+ *                   ring slot, captured on first use);
+ *   ncand, cand_snps (8), cand_ms (8 x 3)  the timed candidates: size, and ms of H2D copy,
+ *                   scan and D2H copy (0 for a copy the call did not need).
+ */
+gwas_status gwas_stream_info(gwas_handle h, int* block_snps, int* tuned, int64_t* graph_launches,
+                             int* ncand, int64_t* cand_snps, double* cand_ms);
 
 /* p_R, the genetic columns per SNP of the handle's model (p = q + p_R), or -1 for NULL. */
 int gwas_genetic_columns(gwas_handle h);

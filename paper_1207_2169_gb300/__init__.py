@@ -31,7 +31,7 @@ EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_destroy_batch", "gwas_sync", "gwas_selftest_timeout", "gwas_wald_pvalues",
            "gwas_estimate",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
-           "gwas_genetic_columns", "gwas_split_pieces",
+           "gwas_genetic_columns", "gwas_split_pieces", "gwas_stream_info",
            "gwas_stage_timing", "gwas_stage_times", "gwas_last_error", "gwas_destroy"]
 
 STAGES = ["pack", "centres", "chol", "rot", "sq", "ac", "simt"]
@@ -105,6 +105,10 @@ def _load():
     ip = ctypes.POINTER(ctypes.c_int)
     lib.gwas_info.argtypes = [vp, ip, ip, ip, ip, ip]
     lib.gwas_info.restype = i32
+    lib.gwas_stream_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                     ctypes.POINTER(i64), dp]
+    lib.gwas_stream_info.restype = i32
     lib.gwas_split_pieces.argtypes = [vp]
     lib.gwas_split_pieces.restype = i32
     lib.gwas_genetic_columns.argtypes = [vp]
@@ -388,6 +392,19 @@ def gwas_genetic_columns(h) -> int:
 
 def gwas_split_pieces(h) -> int:
     return int(lib.gwas_split_pieces(h))
+
+
+def gwas_stream_info(h) -> dict:
+    """Streaming block size in use, whether it was chosen by timing, graph replays, and the timed
+    candidates {snps: (ms H2D, ms scan, ms D2H)}."""
+    blk, tuned, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    gl = ctypes.c_int64()
+    snps = (ctypes.c_int64 * 8)()
+    ms = (ctypes.c_double * 24)()
+    _check(lib.gwas_stream_info(h, ctypes.byref(blk), ctypes.byref(tuned), ctypes.byref(gl),
+                                ctypes.byref(nc), snps, ms), "gwas_stream_info")
+    return dict(block_snps=blk.value, tuned=bool(tuned.value), graph_launches=gl.value,
+                candidates={int(snps[i]): tuple(ms[3 * i:3 * i + 3]) for i in range(nc.value)})
 
 
 def gwas_singular_count(h) -> int:

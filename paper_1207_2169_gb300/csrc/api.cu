@@ -39,6 +39,11 @@ struct gwas_handle_s {
   int out_var = 0;  // GWAS_OUT_VAR: B holds b, then Var(b) packed (p(p+1)/2) per pair
   int pw = 0;       // values per pair in B: p, 2 pr with out_snp, p + p(p+1)/2 with out_var
   int block_snps = 0;
+  // block_snps = 0 at setup: the streaming block is chosen by timing on the first streamed call
+  bool block_auto = false, block_tuned = false;
+  int ntune = 0;
+  int64_t tune_b[8] = {};
+  double tune_ms[8][3] = {};  // per candidate: H2D copy, scan, D2H copy (ms)
   int ldp = 0;  // n rounded up to 64: leading dimension of padded per-individual operands
   double setup_ms = 0.0;
   // st: setup and flag reads; st_lane: second compute stream of streamed scans; st_h2d /
@@ -72,6 +77,18 @@ struct gwas_handle_s {
   int64_t pk_cap = 0;
   int8_t* u8 = nullptr;
   int64_t u8_cap = 0;
+  // CUDA graph of the device work of one full block in ring slot i (host input and output),
+  // captured on first use and replayed; valid while its key (buffers, block, format) holds
+  struct BlockGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void *ring = nullptr, *oring = nullptr;
+    int64_t blk = 0;
+    int fmt = -1;
+    bool f64 = false, wald = false;
+  };
+  BlockGraph graphs[NRING];
+  cudaStream_t st_cap = nullptr;  // graphs are captured here
+  int64_t graph_launches = 0;
   // tensor-core state; split pieces per trait (CHOL) or of every U_j (EIG, pieces[0])
   TcState* tc = nullptr;
   std::vector<int> pieces;
@@ -120,6 +137,9 @@ void destroy_impl(gwas_handle h) {
   if (h->st_d2h) cudaStreamSynchronize(h->st_d2h);
   if (h->tc) tc_destroy(h->tc);
   h->timer.destroy();
+  for (auto& gph : h->graphs)
+    if (gph.exec) cudaGraphExecDestroy(gph.exec);
+  if (h->st_cap) cudaStreamDestroy(h->st_cap);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   for (int i = 0; i < gwas_handle_s::NRING; ++i) {
@@ -472,6 +492,141 @@ void scan_block(gwas_handle h, const void* X, int fmt, int64_t m, void* B, void*
   }
 }
 
+// Conversion scratch a block of `blk` SNPs in format `fmt` needs, allocated ahead (no device
+// allocation may happen while a graph is being captured).
+void prepare_scratch(gwas_handle h, int fmt, int64_t blk) {
+  if (h->prec == GWAS_PREC_SPLIT_BF16 && fmt == FMT_INT8) {
+    const size_t rb = (size_t)packed_row_bytes(h->n);
+    ensure_rows(h, h->pk, h->pk_cap, convert_chunk(h, blk, rb), rb);
+  } else if (h->prec != GWAS_PREC_SPLIT_BF16 && fmt == FMT_PACKED2) {
+    ensure_rows(h, h->u8, h->u8_cap, convert_chunk(h, blk, (size_t)h->n), (size_t)h->n);
+  }
+  ensure_xt(h, blk);
+}
+
+// The graph of ring slot `buf`'s device work for a full block: captured on first use (or when
+// the slot's buffers or the block changed) on the handle's capture stream, replayed after.
+cudaGraphExec_t block_graph(gwas_handle h, int buf, int fmt, int64_t blk, bool out_f64, bool wald) {
+  gwas_handle_s::BlockGraph& g = h->graphs[buf];
+  if (g.exec && g.ring == h->ring[buf] && g.oring == h->oring[buf] && g.blk == blk &&
+      g.fmt == fmt && g.f64 == out_f64 && g.wald == wald)
+    return g.exec;
+  if (g.exec) {
+    GW_CUDA(cudaGraphExecDestroy(g.exec));
+    g.exec = nullptr;
+  }
+  prepare_scratch(h, fmt, blk);
+  const size_t ob = out_f64 ? 8 : 4;
+  void* Bo = h->oring[buf];
+  void* Wo = wald ? (char*)h->oring[buf] + (size_t)blk * h->t * h->pw * ob : nullptr;
+  const bool timer_on = h->timer.on;  // replays are not timed per stage
+  h->timer.on = false;
+  GW_CUDA(cudaStreamBeginCapture(h->st_cap, cudaStreamCaptureModeThreadLocal));
+  try {
+    scan_block(h, h->ring[buf], fmt, blk, Bo, Wo, out_f64, h->st_cap);
+  } catch (...) {
+    cudaGraph_t gr = nullptr;
+    cudaStreamEndCapture(h->st_cap, &gr);
+    if (gr) cudaGraphDestroy(gr);
+    h->timer.on = timer_on;
+    throw;
+  }
+  h->timer.on = timer_on;
+  cudaGraph_t gr = nullptr;
+  GW_CUDA(cudaStreamEndCapture(h->st_cap, &gr));
+  cudaError_t e = cudaGraphInstantiate(&g.exec, gr, 0);
+  cudaGraphDestroy(gr);
+  GW_CUDA(e);
+  g.ring = h->ring[buf];
+  g.oring = h->oring[buf];
+  g.blk = blk;
+  g.fmt = fmt;
+  g.f64 = out_f64;
+  g.wald = wald;
+  return g.exec;
+}
+
+// block_snps = 0: on the first streamed call the handle times the three stages of its pipeline
+// -- the H2D copy of a block, the block's scan, the D2H copy of its outputs -- at each candidate
+// block size, on the call's own first SNPs (written again by the scan that follows), and keeps
+// the size that minimises the modelled time of this call: the pipeline's fill (the three stages
+// of one block) plus, for every further block, its slowest stage (the scan shared by the lanes
+// that run in parallel).
+void tune_block(gwas_handle h, const void* X, int fmt, int64_t m, int xr_dev, void* B,
+                void* wald, int out_dev, bool out_f64, cudaStream_t s, int lanes) {
+  const int t = h->t, p = h->pw;
+  const size_t ob = out_f64 ? 8 : 4;
+  const size_t rbi = row_bytes_of(h, fmt);
+  const int64_t out_cap = (int64_t)(2e9 / ((double)t * (p + 1) * 8));
+  std::vector<int64_t> cands;
+  for (int64_t b = 8192; b <= 262144 && b <= out_cap; b *= 2)
+    if (b <= m || cands.empty()) cands.push_back(b < m ? b : m);
+  if (cands.empty()) cands.push_back(out_cap < m ? (out_cap > 64 ? out_cap : 64) : m);
+  const int64_t bmax = cands.back();
+  uint8_t* gtmp = xr_dev ? nullptr : (uint8_t*)dalloc(h, (size_t)bmax * rbi);
+  void* otmp = out_dev ? nullptr : dalloc(h, (size_t)bmax * t * (p + 1) * ob);
+  prepare_scratch(h, fmt, bmax);
+  cudaEvent_t ev[6];
+  for (auto& e : ev) GW_CUDA(cudaEventCreate(&e));
+  h->ntune = 0;
+  double best = 1e300;
+  int64_t best_b = cands[0];
+  for (int rep = 0; rep < 2; ++rep) {  // the first pass warms up; the second is timed
+    for (int64_t b : cands) {
+      const void* src = X;
+      if (!xr_dev) {
+        GW_CUDA(cudaEventRecord(ev[0], h->st_h2d));
+        GW_CUDA(cudaMemcpyAsync(gtmp, X, (size_t)b * rbi, cudaMemcpyHostToDevice, h->st_h2d));
+        GW_CUDA(cudaEventRecord(ev[1], h->st_h2d));
+        GW_CUDA(cudaStreamWaitEvent(s, ev[1], 0));
+        src = gtmp;
+      }
+      void* Bo = out_dev ? B : otmp;
+      void* Wo = !wald ? nullptr : out_dev ? wald : (char*)otmp + (size_t)b * t * p * ob;
+      GW_CUDA(cudaEventRecord(ev[2], s));
+      scan_block(h, src, fmt, b, Bo, Wo, out_f64, s);
+      GW_CUDA(cudaEventRecord(ev[3], s));
+      if (!out_dev) {
+        GW_CUDA(cudaStreamWaitEvent(h->st_d2h, ev[3], 0));
+        GW_CUDA(cudaEventRecord(ev[4], h->st_d2h));
+        GW_CUDA(cudaMemcpyAsync(B, otmp, (size_t)b * t * p * ob, cudaMemcpyDeviceToHost,
+                                h->st_d2h));
+        if (wald)
+          GW_CUDA(cudaMemcpyAsync(wald, Wo, (size_t)b * t * ob, cudaMemcpyDeviceToHost,
+                                  h->st_d2h));
+        GW_CUDA(cudaEventRecord(ev[5], h->st_d2h));
+      }
+      GW_CUDA(cudaDeviceSynchronize());
+      if (rep == 0) continue;
+      float tin = 0.f, tc = 0.f, tout = 0.f;
+      if (!xr_dev) GW_CUDA(cudaEventElapsedTime(&tin, ev[0], ev[1]));
+      GW_CUDA(cudaEventElapsedTime(&tc, ev[2], ev[3]));
+      if (!out_dev) GW_CUDA(cudaEventElapsedTime(&tout, ev[4], ev[5]));
+      const double nb = (double)((m + b - 1) / b);
+      double slow = tc / lanes;
+      slow = tin > slow ? tin : slow;
+      slow = tout > slow ? tout : slow;
+      const double T = tin + tc + tout + (nb - 1.0) * slow;
+      if (h->ntune < 8) {
+        h->tune_b[h->ntune] = b;
+        h->tune_ms[h->ntune][0] = tin;
+        h->tune_ms[h->ntune][1] = tc;
+        h->tune_ms[h->ntune][2] = tout;
+        ++h->ntune;
+      }
+      if (T < best) {
+        best = T;
+        best_b = b;
+      }
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  dfree(h, gtmp);
+  dfree(h, otmp);
+  h->block_snps = (int)(best_b > 64 ? best_b : 64);
+  h->block_tuned = true;
+}
+
 gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_dev, void* B,
                       void* wald, int out_dev, void* stream, bool out_f64) {
   GW_REQUIRE(h != nullptr, GWAS_ERR_ARG, "null handle");
@@ -504,6 +659,8 @@ gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_d
   const bool two = h->algo == GWAS_ALGO_CHOL &&
                    (h->prec == GWAS_PREC_SPLIT_BF16 ? fmt == FMT_PACKED2 : fmt == FMT_INT8);
   const int nring = two ? gwas_handle_s::NRING : 2;
+  if (h->block_auto && !h->block_tuned)
+    tune_block(h, X, fmt, m, xr_dev, B, wald, out_dev, out_f64, s, two ? 2 : 1);
   const int64_t blk = h->block_snps;
   const size_t gbytes = (size_t)blk * rbi, obytes = (size_t)blk * t * (p + 1) * 8;
   if (h->ring_bytes < gbytes || h->oring_bytes < obytes || h->nring < nring) {
@@ -558,7 +715,13 @@ gwas_status scan_impl(gwas_handle h, const void* X, int fmt, int64_t m, int xr_d
       Bo = h->oring[buf];
       Wo = wald ? (char*)h->oring[buf] + (size_t)blk * t * p * ob : nullptr;
     }
-    scan_block(h, src, fmt, mm, Bo, Wo, out_f64, cs);
+    if (!xr_dev && !out_dev && mm == blk) {
+      // a full block between ring slots: its device work is one captured graph
+      GW_CUDA(cudaGraphLaunch(block_graph(h, buf, fmt, blk, out_f64, wald != nullptr), cs));
+      ++h->graph_launches;
+    } else {
+      scan_block(h, src, fmt, mm, Bo, Wo, out_f64, cs);
+    }
     GW_CUDA(cudaEventRecord(h->ev_computed[buf], cs));
     if (!out_dev) {
       GW_CUDA(cudaStreamWaitEvent(h->st_d2h, h->ev_computed[buf], 0));
@@ -695,7 +858,9 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
     if (blk > out_cap) blk = out_cap;
     if (blk < 64) blk = 64;
     h->block_snps = (int)blk;
+    h->block_auto = o.block_snps == 0;
     GW_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    GW_CUDA(cudaStreamCreateWithFlags(&h->st_cap, cudaStreamNonBlocking));
     GW_CUDA(cudaStreamCreateWithFlags(&h->st_lane, cudaStreamNonBlocking));
     GW_CUDA(cudaStreamCreateWithFlags(&h->st_h2d, cudaStreamNonBlocking));
     GW_CUDA(cudaStreamCreateWithFlags(&h->st_d2h, cudaStreamNonBlocking));
@@ -944,6 +1109,25 @@ GW_API gwas_status gwas_info(gwas_handle h, int* n, int* q, int* t, int* algo, i
 }
 
 GW_API int gwas_genetic_columns(gwas_handle h) { return h ? h->gm.pr : -1; }
+
+GW_API gwas_status gwas_stream_info(gwas_handle h, int* block_snps, int* tuned,
+                                    int64_t* graph_launches, int* ncand, int64_t* cand_snps,
+                                    double* cand_ms) {
+  if (!h) {
+    set_error("null handle");
+    return GWAS_ERR_ARG;
+  }
+  if (block_snps) *block_snps = h->block_snps;
+  if (tuned) *tuned = h->block_tuned ? 1 : 0;
+  if (graph_launches) *graph_launches = h->graph_launches;
+  if (ncand) *ncand = h->ntune;
+  for (int i = 0; i < h->ntune; ++i) {
+    if (cand_snps) cand_snps[i] = h->tune_b[i];
+    if (cand_ms)
+      for (int k = 0; k < 3; ++k) cand_ms[3 * i + k] = h->tune_ms[i][k];
+  }
+  return GWAS_OK;
+}
 
 GW_API int gwas_split_pieces(gwas_handle h) {
   if (!h) return -1;
