@@ -772,7 +772,21 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
             // and nval of wald; consecutive lanes take consecutive floats of a row.
             const int64_t jb = j0 + j8;
             const int pw = p.out_snp ? 2 : q1;  // values per pair in B
-            if (QQ == 3 && nval == 8 && !p.out_snp) {
+            // float4 stores need B 16-byte aligned (the ABI promises only float alignment) and,
+            // for SNP mode (2 floats per pair), an even t
+            const bool vec_ok = (reinterpret_cast<uintptr_t>(p.B) & 15) == 0;
+            if (QQ == 3 && nval == 8 && p.out_snp && vec_ok && (p.t & 1) == 0) {
+              // SNP mode: (b_snp, se) of 8 traits = 4 float4 per row, 8 rows per instruction
+#pragma unroll
+              for (int it = 0; it < 4; ++it) {
+                const int rr = it * 8 + (lane >> 2), c4 = lane & 3;
+                const int64_t sn = row0 + rr;
+                if (sn < p.m) {
+                  const float4 v = *reinterpret_cast<const float4*>(stgB + rr * RB + c4 * 4);
+                  *reinterpret_cast<float4*>(p.B + (sn * p.t + jb) * 2 + c4 * 4) = v;
+                }
+              }
+            } else if (QQ == 3 && nval == 8 && !p.out_snp && vec_ok) {
               // 8 float4 per row, 4 rows per instruction
 #pragma unroll
               for (int it = 0; it < 8; ++it) {

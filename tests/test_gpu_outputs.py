@@ -96,3 +96,31 @@ def test_var_mode_streamed(g):
     Bh, Wh, _ = run(g, c, "eig", "split_bf16", out_mode="var", packed=True, device=False,
                     block_snps=256)
     assert np.array_equal(Bd, Bh) and np.array_equal(Wd, Wh)
+
+
+@pytest.mark.parametrize("out_mode,t", [("full", 64), ("snp", 64), ("snp", 65)])
+def test_unaligned_outputs(g, out_mode, t):
+    """Output buffers the C ABI allows -- float-aligned, not 16-byte aligned -- and an odd trait
+    count in SNP mode get the same values as 16-byte-aligned ones (the kernel's vector stores
+    are used only where the alignment allows them)."""
+    import torch
+    c = synth.small_problem(95, n=200, q=3, m=300, t=t)
+    pw = 2 if out_mode == "snp" else c.p
+    h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, algo="eig", precision="split_bf16",
+                     out_mode=out_mode)
+    try:
+        xr = torch.from_numpy(c.XR).cuda()
+        outs = []
+        for shift in (0, 1):
+            Bbuf = torch.full((c.m * c.t * pw + 4,), float("nan"), device="cuda")
+            Wbuf = torch.full((c.m * c.t + 4,), float("nan"), device="cuda")
+            B = Bbuf[shift:shift + c.m * c.t * pw].view(c.m, c.t, pw)
+            W = Wbuf[shift:shift + c.m * c.t].view(c.m, c.t)
+            assert (B.data_ptr() % 16 == 0) == (shift == 0)
+            g.gwas_scan(h, xr, B, W)
+            torch.cuda.synchronize()
+            outs.append((B.cpu().numpy(), W.cpu().numpy()))
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+        assert not np.isnan(outs[0][0]).any()
+    finally:
+        g.gwas_destroy(h)
