@@ -639,6 +639,30 @@ __global__ void power_step_kernel(int n, double* __restrict__ v, const double* _
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = y[i] * inv;
 }
 
+// y = A x for an n x n matrix whose rows are contiguous (A(i, k) = A[i * n + k]): one warp per
+// output, coalesced along the row.
+__global__ void gemv_rows_kernel(int n, const double* __restrict__ A, const double* __restrict__ x,
+                                 double* __restrict__ y) {
+  const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (i >= n) return;  // warp-uniform
+  const double* row = A + (int64_t)i * n;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc += row[k] * x[k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[i] = acc;
+}
+
+// y = A x for an n x n matrix whose columns are contiguous (A(i, k) = A[i + k * n]): one thread
+// per output, consecutive threads reading consecutive elements of each column.
+__global__ void gemv_cols_kernel(int n, const double* __restrict__ A, const double* __restrict__ x,
+                                 double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int k = 0; k < n; ++k) acc += A[i + (int64_t)k * n] * x[k];
+  y[i] = acc;
+}
+
 __global__ void power_start_kernel(int n, double* __restrict__ v) {
   const double inv = rsqrt((double)n);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -658,13 +682,15 @@ double condition_estimate(cudaStream_t s, int n, const double* L, const double* 
     power_start_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, v);
     GW_CHECK_LAUNCH();
     for (int it = 0; it < iters; ++it) {
-      if (which == 0) {  // M v = L (L^T v); L column-major lower
-        gemm_f64(s, n, 1, n, 1.0, L, n, 1, v, 1, 0, 0.0, y, 1, 0);
-        gemm_f64(s, n, 1, n, 1.0, L, 1, n, y, 1, 0, 0.0, z, 1, 0);
-      } else {  // M^-1 v = L^-T (L^-1 v); L^-1 row-major lower
-        gemm_f64(s, n, 1, n, 1.0, Linv, n, 1, v, 1, 0, 0.0, y, 1, 0);
-        gemm_f64(s, n, 1, n, 1.0, Linv, 1, n, y, 1, 0, 0.0, z, 1, 0);
+      const unsigned gw = (unsigned)ceil_div(n, 8), gt = (unsigned)ceil_div(n, 256);
+      if (which == 0) {  // M v = L (L^T v); L column-major: L^T has contiguous rows
+        gemv_rows_kernel<<<gw, 256, 0, s>>>(n, L, v, y);
+        gemv_cols_kernel<<<gt, 256, 0, s>>>(n, L, y, z);
+      } else {  // M^-1 v = L^-T (L^-1 v); L^-1 row-major: L^-T has contiguous columns
+        gemv_rows_kernel<<<gw, 256, 0, s>>>(n, Linv, v, y);
+        gemv_cols_kernel<<<gt, 256, 0, s>>>(n, Linv, y, z);
       }
+      GW_CHECK_LAUNCH();
       power_step_kernel<<<1, 1024, 0, s>>>(n, v, z, rq);
       GW_CHECK_LAUNCH();
     }
