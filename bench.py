@@ -21,8 +21,9 @@ rooflines from CUDA events recorded around each kernel on its stream (gwas_stage
 the count of kernels launched.  `--impl reference` times the FP64 CPU oracle instead.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--workload 0|1|2|3|4] [--precision P]
-Under torchrun (N > 1) every rank scans its own replica of the workload (weak scaling, no
-collective on the data path); rank 0 prints the max-over-ranks time.
+Under torchrun (N > 1) every rank scans its own SNP range of a genome N times the workload's
+length (gwas_shard; weak scaling, the same cohort on every rank, no collective on the data
+path); rank 0 prints the max-over-ranks time and value = all ranks' pairs / that time.
 """
 from __future__ import annotations
 
@@ -134,14 +135,24 @@ def _barrier(ws):
 _INPUTS = {}
 
 
-def make_inputs(idx: int, m: int | None = None):
+def make_inputs(idx: int, m: int | None = None, shard: bool = False):
     """Workload `idx` with its genotypes drawn block by block (each block its own stream).  The
-    last workload drawn is kept, so that its variants (input format, precision) reuse it."""
-    key = (idx, m)
+    last workload drawn is kept, so that its variants (input format, precision) reuse it.
+    shard: under torchrun, this rank's own SNP range (gwas_shard) of a genome of WORLD_SIZE x m
+    SNPs -- every rank scans m SNPs (weak scaling), different ones, with the same cohort."""
+    ws, rank, _ = _dist()
+    spec = synth.WORKLOADS[idx]
+    m = spec["m"] if m is None else m
+    start = 0
+    if shard and ws > 1:
+        import paper_1207_2169_gb300 as g
+        start, m = g.gwas_shard(ws * m, rank, ws)
+    key = (idx, m, start)
     if key not in _INPUTS:
         _INPUTS.clear()
         c = synth.make_cohort(idx, m=0, with_genotypes=False)
-        c.XR = synth.workload_genotypes(idx, m)
+        c.XR = synth.workload_genotypes(idx, m, start=start)
+        c.snp_start = start
         _INPUTS[key] = c
     return _INPUTS[key]
 
@@ -355,6 +366,50 @@ def parity_sample(c, Bd, Wd, count=256, every=False):
     return eb, ew, len(pairs)
 
 
+_LINK = {}
+
+
+def host_link():
+    """Bandwidth of this GPU's host link, measured here: 256 MB copies between pinned host memory
+    and the device, each direction alone (GB/s).  Several streams, or an SM copy kernel reading
+    mapped host memory, reach the same rate on a GB300 machine, and the two directions share it
+    (both at once add up to about the one-direction figure), so the e2e floor of a step is
+    h2d_bytes / h2d_gbs + d2h_bytes / d2h_gbs."""
+    if not _LINK:
+        import torch
+        nb = 256 << 20
+        h = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        d = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        h.fill_(1)
+        d.fill_(2)
+        for key, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                dst.copy_(src, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            _LINK[key] = 5 * nb / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        del h, d
+    return dict(_LINK)
+
+
+def with_link_roof(e2e):
+    """Adds the host-link floor of an e2e entry: the time its copies take at the measured link
+    rate, and that floor over the measured e2e step (1.0 = the step runs at the link's rate)."""
+    if not e2e or not e2e.get("ms_per_step"):
+        return e2e
+    link = host_link()
+    floor = (e2e["h2d_bytes_per_step"] / link["h2d_gbs"] + e2e["d2h_bytes_per_step"] / link["d2h_gbs"]) / 1e6
+    e2e["host_link"] = {"h2d_gbs": link["h2d_gbs"], "d2h_gbs": link["d2h_gbs"],
+                        "copy_floor_ms_per_step": floor, "frac": floor / e2e["ms_per_step"],
+                        "note": "pinned cudaMemcpyAsync rate measured in this run; the two "
+                                "directions share the link"}
+    return e2e
+
+
 def _timed(stream, steps, step, flush, scratch):
     """Device milliseconds of `steps` calls of step(), from CUDA events on `stream`."""
     import torch
@@ -384,7 +439,7 @@ def measure(idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=T
     import torch
     import paper_1207_2169_gb300 as g
     s = dict(synth.WORKLOADS[idx])
-    c = make_inputs(idx, m=m) if c is None else c
+    c = make_inputs(idx, m=m, shard=True) if c is None else c
     mm, n, t, p = c.m, c.n, c.t, c.p
     opt = g.gwas_default_options(algo=s["algo"], precision=precision, device=local)
     h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, options=opt)
@@ -473,7 +528,8 @@ def entry(res, precision, fmt, steps, warmup, **extra):
     """A workload's entry under other_workloads."""
     d = {"config": _config(res["s"], precision, res["m"], fmt, **extra.pop("config", {})),
          "value": res["value"], "unit": "pairs/s", "ms_per_step": res["ms"], "steps": steps,
-         "warmup": warmup, "e2e": res["e2e"], "parity": res["parity"], "setup_ms": res["setup_ms"],
+         "warmup": warmup, "e2e": with_link_roof(res["e2e"]), "parity": res["parity"],
+         "setup_ms": res["setup_ms"],
          "roofline": res["roofline"], "gpu_launches": res["gpu_launches"],
          "stage_ms_per_step": res["stage_ms"], "clocks": res["clocks"],
          "split_pieces": res.get("split_pieces")}
@@ -495,7 +551,7 @@ def measure_stream3(local, ws, steps=2, warmup=1, m=None, out_mode="full", pinne
     from oracle import gls
     s = dict(synth.WORKLOADS[3])
     blk = s["block"]
-    c = make_inputs(3, m=m)
+    c = make_inputs(3, m=m, shard=True)
     mm, n, t, p = c.m, c.n, c.t, c.p
     pw = 2 if out_mode == "snp" else p
     nblk = -(-mm // blk)
@@ -863,8 +919,11 @@ def run_ours(args, ws, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"split_bf16": "bf16x2->f32", "fp32": "f32", "fp64": "f64"}[args.precision],
-        "data": "synthetic", "config": _config(s, args.precision, res["m"], fmt),
-        "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
+        "data": "synthetic",
+        "config": dict(_config(s, args.precision, res["m"], fmt),
+                       **({"sharding": f"rank r scans SNPs [r*{res['m']}, (r+1)*{res['m']}) of a "
+                                       f"{ws * res['m']}-SNP genome (gwas_shard)"} if ws > 1 else {})),
+        "e2e": with_link_roof(res["e2e"]), "gpu_launches": res["gpu_launches"],
         "roofline": res["roofline"], "parity": res["parity"], "setup_ms": res["setup_ms"],
         "clocks": res["clocks"], "stage_ms_per_step": res["stage_ms"],
     }

@@ -199,6 +199,20 @@ gwas_status gwas_estimate(const double* Phi, int n, const double* XL, int q, con
 int gwas_packed_row_bytes(int n); /* 0 for n < 1 */
 
 /*
+ * gwas_shard -- the SNP range [*start, *start + *count) that rank `rank` of `world` processes
+ * when a genome of m_total SNPs is split across processes (one per GPU).  Every (SNP, trait)
+ * pair of the grid of Eq. "probDef" is independent of the others given the setup state
+ * (Algorithms 3 and 4 loop over SNPs with nothing carried between iterations), so ranks need
+ * no exchange on the data path: each sets up its own handle and scans its own range.  The
+ * ranges are contiguous, disjoint, ordered by rank and cover [0, m_total); each holds a whole
+ * number of `align`-SNP units except where m_total ends, and the unit counts of two ranks differ
+ * by at most one.  Host only, no GPU needed.  GWAS_ERR_ARG if m_total < 0, world < 1,
+ * rank outside [0, world), align < 1 or an output pointer is NULL.
+ */
+gwas_status gwas_shard(int64_t m_total, int rank, int world, int64_t align, int64_t* start,
+                       int64_t* count);
+
+/*
  * gwas_pack_genotypes -- int8 m x n hard calls X -> packed rows G (m * gwas_packed_row_bytes(n)
  * bytes, caller-owned).  on_device = 0: both host pointers, synchronous; a value outside
  * {0,1,2} is written as code 3 and the call returns GWAS_ERR_GENOTYPE after packing every row.

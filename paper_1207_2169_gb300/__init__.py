@@ -26,7 +26,7 @@ STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ER
 
 # every symbol include/gwas.h declares
 EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
-           "gwas_packed_row_bytes", "gwas_pack_genotypes", "gwas_scan_packed",
+           "gwas_packed_row_bytes", "gwas_pack_genotypes", "gwas_scan_packed", "gwas_shard",
            "gwas_setup_batch", "gwas_scan_batch", "gwas_batch_plan", "gwas_batch_handle",
            "gwas_destroy_batch", "gwas_sync", "gwas_selftest_timeout", "gwas_wald_pvalues",
            "gwas_estimate",
@@ -79,6 +79,8 @@ def _load():
     lib.gwas_estimate.restype = i32
     lib.gwas_packed_row_bytes.argtypes = [i32]
     lib.gwas_packed_row_bytes.restype = i32
+    lib.gwas_shard.argtypes = [i64, i32, i32, i64, ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_int64)]
     lib.gwas_pack_genotypes.argtypes = [vp, i64, i32, vp, i32, vp]
     lib.gwas_pack_genotypes.restype = i32
     lib.gwas_setup_batch.argtypes = [i32, ctypes.POINTER(gwas_cohort), ctypes.POINTER(gwas_options),
@@ -243,6 +245,14 @@ def gwas_estimate(Phi, XL, Y, method="ml", device=0):
 
 def gwas_packed_row_bytes(n: int) -> int:
     return int(lib.gwas_packed_row_bytes(int(n)))
+
+
+def gwas_shard(m_total: int, rank: int, world: int, align: int = 1) -> tuple[int, int]:
+    """(start, count): the SNP range of rank `rank` of `world` in a genome of m_total SNPs."""
+    a, c = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.gwas_shard(int(m_total), int(rank), int(world), int(align), ctypes.byref(a),
+                          ctypes.byref(c)), "gwas_shard")
+    return a.value, c.value
 
 
 def gwas_pack_genotypes(X, G=None, stream=None):

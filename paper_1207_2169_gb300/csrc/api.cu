@@ -925,6 +925,23 @@ GW_API gwas_status gwas_scan_packed(gwas_handle h, const uint8_t* G, int64_t m, 
 
 GW_API int gwas_packed_row_bytes(int n) { return n >= 1 ? packed_row_bytes(n) : 0; }
 
+GW_API gwas_status gwas_shard(int64_t m_total, int rank, int world, int64_t align, int64_t* start,
+                              int64_t* count) {
+  try {
+    GW_REQUIRE(start != nullptr && count != nullptr, GWAS_ERR_ARG, "null start or count");
+    GW_REQUIRE(m_total >= 0 && world >= 1 && rank >= 0 && rank < world && align >= 1, GWAS_ERR_ARG,
+               "need m_total >= 0, world >= 1, 0 <= rank < world, align >= 1");
+    const int64_t units = m_total / align + (m_total % align != 0);
+    const int64_t u0 = units / world * rank + std::min<int64_t>(rank, units % world);
+    const int64_t u1 = u0 + units / world + (rank < units % world);
+    *start = std::min(u0 * align, m_total);
+    *count = std::min(u1 * align, m_total) - *start;
+    return GWAS_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
 GW_API gwas_status gwas_wald_pvalues(const float* wald, int64_t count, float* pval, int on_device,
                                      void* stream) {
   try {

@@ -221,16 +221,18 @@ def device_genotypes(seed: int, n: int, m: int, device="cuda"):
     return x
 
 
-def workload_genotypes(workload: int, m: int | None = None) -> np.ndarray:
-    """The first m SNPs (default: all) of workload `workload`'s genome, m x n int8, assembled
-    from its per-block streams (snp_block) so that any prefix is the same at every m."""
+def workload_genotypes(workload: int, m: int | None = None, start: int = 0) -> np.ndarray:
+    """SNPs [start, start + m) (default: the whole genome) of workload `workload`'s genome, m x n
+    int8, assembled from its per-block streams (snp_block), so that every SNP is the same
+    whatever range it is drawn in: any prefix, and any rank's shard of a longer genome."""
     spec = WORKLOADS[workload]
     n, blk = spec["n"], spec["block"]
     m = spec["m"] if m is None else m
     XR = np.empty((m, n), dtype=np.int8)
-    for b in range((m + blk - 1) // blk):
-        lo, hi = b * blk, min(m, (b + 1) * blk)
-        XR[lo:hi] = snp_block(workload, n, blk, b)[:hi - lo]
+    end = start + m
+    for b in range(start // blk, (end + blk - 1) // blk):
+        lo, hi = max(start, b * blk), min(end, (b + 1) * blk)
+        XR[lo - start:hi - start] = snp_block(workload, n, blk, b)[lo - b * blk:hi - b * blk]
     return XR
 
 

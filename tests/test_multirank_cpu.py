@@ -1,6 +1,9 @@
-"""The N > 1 host path of bench.py (weak scaling, barrier + max-over-ranks timing) on two gloo
-ranks on CPU.  The GPU work of each rank is an independent replica; only the timing reduction
-crosses ranks, so that is what is exercised here."""
+"""The N > 1 host path on two gloo ranks on CPU: the SNP-range split (gwas_shard, host-only in
+the C library) and bench.py's weak scaling with barrier + max-over-ranks timing.  No pair of
+the grid depends on another, so each rank scans its own SNP range with no exchange on the data
+path; here each rank solves its range with the FP64 oracle (the CPU stand-in for its GPU) and
+the gathered ranges must equal the whole grid bit for bit.  Only the timing reduction and this
+check cross ranks."""
 import os
 import socket
 
@@ -87,3 +90,70 @@ def test_code_hash_ignores_comments(tmp_path):
     assert bench.code_sha1(a) == bench.code_sha1(b)
     b.write_text("int f(int x) {\n  return 3 * x;\n}\n")
     assert bench.code_sha1(a) != bench.code_sha1(b)
+
+
+def test_shard_ranges_cover_the_genome():
+    """Contiguous, disjoint, ordered ranges covering [0, m); whole align-units except at the end;
+    unit counts differing by at most one; bad arguments rejected."""
+    import paper_1207_2169_gb300 as g
+    for m in (0, 1, 7, 1000, 65535, 2_000_000):
+        for world in (1, 2, 3, 8):
+            for align in (1, 64, 65536):
+                got = [g.gwas_shard(m, r, world, align) for r in range(world)]
+                pos = 0
+                units = []
+                for start, count in got:
+                    assert start == pos and count >= 0
+                    pos += count
+                    if start + count < m:
+                        assert count % align == 0
+                    units.append(-(-count // align))
+                assert pos == m
+                assert max(units) - min(units) <= 1
+    for bad in ((-1, 0, 2, 1), (10, 2, 2, 1), (10, -1, 2, 1), (10, 0, 0, 1), (10, 0, 2, 0)):
+        with pytest.raises(RuntimeError):
+            g.gwas_shard(*bad)
+
+
+def _shard_main(rank, world, port, out):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import paper_1207_2169_gb300 as g
+    import synth
+    from oracle import gls
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    c = synth.small_problem(81, n=40, q=2, m=37, t=3)
+    start, count = g.gwas_shard(c.m, rank, world)
+    B, W, _ = gls.gls_grid(c.Phi, c.XL, c.XR[start:start + count], c.Y, c.h2, c.s2)
+    parts = [None] * world
+    dist.all_gather_object(parts, (start, B, W))
+    if rank == 0:
+        parts.sort(key=lambda x: x[0])
+        Ball = np.concatenate([p[1] for p in parts])
+        Wall = np.concatenate([p[2] for p in parts])
+        Bref, Wref, _ = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
+        out["ok"] = bool(np.array_equal(Ball, Bref, equal_nan=True)
+                         and np.array_equal(Wall, Wref, equal_nan=True))
+    # bench.py's inputs on this rank: its own range of a genome of world x m SNPs
+    import bench
+    x = bench.make_inputs(0, m=3000, shard=True).XR
+    out[rank] = bool(np.array_equal(x, synth.workload_genotypes(0, 3000, start=3000 * rank)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_scan_their_own_snp_ranges():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_main, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    assert dict(out) == {"ok": True, 0: True, 1: True}
