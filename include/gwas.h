@@ -161,6 +161,15 @@ gwas_status gwas_scan_f64(gwas_handle h, const int8_t* XR, int64_t m, int xr_on_
 gwas_status gwas_wald_pvalues(const float* wald, int64_t count, float* pval, int on_device,
                               void* stream);
 
+/*
+ * gwas_wald_pvalues_dof -- as gwas_wald_pvalues for the joint test of a p_R-column genetic model
+ * (Eq. "probDef" with a block X_R; gwas_genetic_columns): the chi-square upper tail with `dof`
+ * degrees of freedom, dof = 1 (erfc(sqrt(wald / 2))) or dof = 2 (exp(-wald / 2), exact for two
+ * degrees of freedom).  Any other dof returns GWAS_ERR_ARG.
+ */
+gwas_status gwas_wald_pvalues_dof(const float* wald, int64_t count, int dof, float* pval,
+                                  int on_device, void* stream);
+
 /* Criteria of gwas_estimate. */
 enum { GWAS_EST_ML = 0, GWAS_EST_REML = 1 };
 

@@ -29,6 +29,7 @@ EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_packed_row_bytes", "gwas_pack_genotypes", "gwas_scan_packed", "gwas_shard",
            "gwas_setup_batch", "gwas_scan_batch", "gwas_batch_plan", "gwas_batch_handle",
            "gwas_destroy_batch", "gwas_sync", "gwas_selftest_timeout", "gwas_wald_pvalues",
+           "gwas_wald_pvalues_dof",
            "gwas_estimate",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
            "gwas_genetic_columns", "gwas_split_pieces", "gwas_stream_info",
@@ -96,6 +97,7 @@ def _load():
     lib.gwas_destroy_batch.restype = None
     lib.gwas_wald_pvalues.argtypes = [vp, i64, vp, i32, vp]
     lib.gwas_wald_pvalues.restype = i32
+    lib.gwas_wald_pvalues_dof.argtypes = [vp, i64, i32, vp, i32, vp]
     lib.gwas_sync.argtypes = [vp]
     lib.gwas_sync.restype = i32
     lib.gwas_selftest_timeout.argtypes = [i32, i32]
@@ -357,8 +359,7 @@ def gwas_destroy_batch(b) -> None:
     lib.gwas_destroy_batch(b)
 
 
-def gwas_wald_pvalues(wald, pval=None, stream=None):
-    """chi-square(1) upper-tail p-values of a float32 array or CUDA tensor of Wald statistics."""
+def _pvalues(wald, pval, stream, dof):
     wp, wdev = _ptr(wald)
     if pval is None:
         pval = wald.clone() if wdev else np.empty_like(wald)
@@ -369,8 +370,22 @@ def gwas_wald_pvalues(wald, pval=None, stream=None):
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     count = int(np.prod(wald.shape))
-    _check(lib.gwas_wald_pvalues(wp, count, pp, wdev, stream or None), "gwas_wald_pvalues")
+    if dof is None:
+        _check(lib.gwas_wald_pvalues(wp, count, pp, wdev, stream or None), "gwas_wald_pvalues")
+    else:
+        _check(lib.gwas_wald_pvalues_dof(wp, count, int(dof), pp, wdev, stream or None),
+               "gwas_wald_pvalues_dof")
     return pval
+
+
+def gwas_wald_pvalues(wald, pval=None, stream=None):
+    """chi-square(1) upper-tail p-values of a float32 array or CUDA tensor of Wald statistics."""
+    return _pvalues(wald, pval, stream, None)
+
+
+def gwas_wald_pvalues_dof(wald, dof, pval=None, stream=None):
+    """chi-square(dof) upper-tail p-values, dof = 1 or 2 (gwas_genetic_columns of the handle)."""
+    return _pvalues(wald, pval, stream, dof)
 
 
 def gwas_sync(h) -> None:

@@ -942,19 +942,21 @@ GW_API gwas_status gwas_shard(int64_t m_total, int rank, int world, int64_t alig
   }
 }
 
-GW_API gwas_status gwas_wald_pvalues(const float* wald, int64_t count, float* pval, int on_device,
-                                     void* stream) {
+GW_API gwas_status gwas_wald_pvalues_dof(const float* wald, int64_t count, int dof, float* pval,
+                                         int on_device, void* stream) {
   try {
     GW_REQUIRE(count >= 0, GWAS_ERR_ARG, "count < 0");
+    GW_REQUIRE(dof == 1 || dof == 2, GWAS_ERR_ARG, "dof=%d: 1 or 2 degrees of freedom", dof);
     if (count == 0) return GWAS_OK;
     GW_REQUIRE(wald != nullptr && pval != nullptr, GWAS_ERR_ARG, "null wald or pval");
     if (on_device) {
-      wald_pvalues((cudaStream_t)stream, wald, count, pval);
+      wald_pvalues((cudaStream_t)stream, wald, count, dof, pval);
       return GWAS_OK;
     }
     for (int64_t e = 0; e < count; ++e) {
       const double x = wald[e];
-      pval[e] = x >= 0.0 ? (float)erfc(sqrt(0.5 * x)) : (x == x ? 1.f : (float)x);
+      pval[e] = x >= 0.0 ? (float)(dof == 2 ? exp(-0.5 * x) : erfc(sqrt(0.5 * x)))
+                         : (x == x ? 1.f : (float)x);
     }
     return GWAS_OK;
   } catch (const Fail& f) {
@@ -963,6 +965,11 @@ GW_API gwas_status gwas_wald_pvalues(const float* wald, int64_t count, float* pv
     set_error("unexpected C++ exception in gwas_wald_pvalues");
     return GWAS_ERR_CUDA;
   }
+}
+
+GW_API gwas_status gwas_wald_pvalues(const float* wald, int64_t count, float* pval, int on_device,
+                                     void* stream) {
+  return gwas_wald_pvalues_dof(wald, count, 1, pval, on_device, stream);
 }
 
 GW_API gwas_status gwas_estimate(const double* Phi, int n, const double* XL, int q,

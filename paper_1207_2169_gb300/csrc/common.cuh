@@ -263,6 +263,6 @@ void validate_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, int* f
 void snp_centres_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, float* mu, int pr,
                         const uint32_t* code);
 // pv[e] = erfc(sqrt(w[e] / 2)) (chi-square(1) upper tail); NaN stays NaN; in place allowed.
-void wald_pvalues(cudaStream_t s, const float* w, int64_t count, float* pv);
+void wald_pvalues(cudaStream_t s, const float* w, int64_t count, int dof, float* pv);
 
 }  // namespace gw

@@ -158,18 +158,20 @@ void snp_centres_packed(cudaStream_t s, const uint8_t* in, int64_t m, int n, flo
 // ------------------------------------------------------------------------------------------
 namespace gw {
 namespace {
-__global__ void pvalue_kernel(const float* __restrict__ w, int64_t count, float* __restrict__ pv) {
+// chi-square upper tail: dof 1 -> erfc(sqrt(x / 2)), dof 2 -> exp(-x / 2)
+__global__ void pvalue_kernel(const float* __restrict__ w, int64_t count, int dof,
+                              float* __restrict__ pv) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x) {
     const float x = w[e];
-    pv[e] = x >= 0.f ? erfcf(sqrtf(0.5f * x)) : (x == x ? 1.f : x);
+    pv[e] = x >= 0.f ? (dof == 2 ? expf(-0.5f * x) : erfcf(sqrtf(0.5f * x))) : (x == x ? 1.f : x);
   }
 }
 }  // namespace
 
-void wald_pvalues(cudaStream_t s, const float* w, int64_t count, float* pv) {
+void wald_pvalues(cudaStream_t s, const float* w, int64_t count, int dof, float* pv) {
   if (count <= 0) return;
-  pvalue_kernel<<<1184, 256, 0, s>>>(w, count, pv);
+  pvalue_kernel<<<1184, 256, 0, s>>>(w, count, dof, pv);
   GW_CHECK_LAUNCH();
 }
 }  // namespace gw

@@ -183,6 +183,20 @@ def test_wald_pvalues_host(g):
     assert g.lib.gwas_wald_pvalues(None, 0, None, 0, None) == 0
 
 
+def test_wald_pvalues_two_dof_host(g):
+    """The joint test of the two-column model: chi-square(2) upper tail (scipy), 5 % at 5.991."""
+    from scipy.stats import chi2
+    w = np.array([0.0, 5.991464547107979, 9.21034037197618, 0.5, 40.0, np.nan], np.float32)
+    pv = g.gwas_wald_pvalues_dof(w, 2)
+    ref = chi2.sf(w.astype(np.float64), 2)
+    assert np.isnan(pv[-1])
+    assert np.allclose(pv[:-1], ref[:-1], rtol=1e-6, atol=0)
+    assert abs(pv[1] - 0.05) < 1e-7 and abs(pv[2] - 0.01) < 1e-7 and pv[0] == 1.0
+    assert np.array_equal(g.gwas_wald_pvalues_dof(w, 1), g.gwas_wald_pvalues(w), equal_nan=True)
+    for dof in (0, 3):
+        assert g.lib.gwas_wald_pvalues_dof(w.ctypes.data, 6, dof, w.ctypes.data, 0, None) == -1
+
+
 def test_out_mode_option(g):
     o = g.gwas_default_options(out_mode="snp")
     assert o.out_mode == 1 and g.gwas_default_options().out_mode == 0

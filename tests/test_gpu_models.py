@@ -182,3 +182,18 @@ def test_split_eig_add_dom_workload2_shape(g):
     Bref, Wref, Vref = gls.gls_pairs(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2, pairs, model="add_dom")
     eb, ew = max_errors(B[pairs[:, 0], pairs[:, 1]], W[pairs[:, 0], pairs[:, 1]], Bref, Wref, Vref)
     assert eb < 1e-4 and ew < 1e-4, (eb, ew)
+
+
+def test_add_dom_pvalues_on_device(g):
+    """2-d.o.f. p-values of the joint statistics on the device: scipy's chi-square(2) tail of
+    the same statistics; NaN for the singular pairs."""
+    import torch
+    from scipy.stats import chi2
+    c = synth.small_problem(37, n=200, q=3, m=300, t=7)
+    _, W, _ = run(g, c, "eig", "split_bf16", model="add_dom")
+    w = torch.from_numpy(W.astype(np.float32)).cuda()
+    pv = g.gwas_wald_pvalues_dof(w, 2).cpu().numpy()
+    ref = chi2.sf(W.astype(np.float32).astype(np.float64), 2)
+    assert np.array_equal(np.isnan(pv), np.isnan(W))
+    ok = ~np.isnan(W)
+    assert np.allclose(pv[ok], ref[ok], rtol=2e-5, atol=1e-30)
