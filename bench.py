@@ -366,47 +366,42 @@ def parity_sample(c, Bd, Wd, count=256, every=False):
     return eb, ew, len(pairs)
 
 
-_LINK = {}
-
-
 def host_link():
-    """Bandwidth of this GPU's host link, measured here: 256 MB copies between pinned host memory
+    """Bandwidth of this GPU's host link, measured now: 256 MB copies between pinned host memory
     and the device, each direction alone (GB/s).  Several streams, or an SM copy kernel reading
     mapped host memory, reach the same rate on a GB300 machine, and the two directions share it
     (both at once add up to about the one-direction figure), so the e2e floor of a step is
-    h2d_bytes / h2d_gbs + d2h_bytes / d2h_gbs."""
-    if not _LINK:
-        import torch
-        nb = 256 << 20
-        h = torch.empty(nb, dtype=torch.uint8).pin_memory()
-        d = torch.empty(nb, dtype=torch.uint8, device="cuda")
-        h.fill_(1)
-        d.fill_(2)
-        for key, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+    h2d_bytes / h2d_gbs + d2h_bytes / d2h_gbs.  The rate moves with the host's other load (the
+    box shares its CPU memory with other tenants), so it is taken right after each e2e timing."""
+    import torch
+    nb = 256 << 20
+    h = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    h.fill_(1)
+    d.fill_(2)
+    link = {}
+    for key, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
             dst.copy_(src, non_blocking=True)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(5):
-                dst.copy_(src, non_blocking=True)
-            e1.record()
-            torch.cuda.synchronize()
-            _LINK[key] = 5 * nb / (e0.elapsed_time(e1) * 1e-3) / 1e9
-        del h, d
-    return dict(_LINK)
+        e1.record()
+        torch.cuda.synchronize()
+        link[key] = 5 * nb / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    return link
 
 
-def with_link_roof(e2e):
-    """Adds the host-link floor of an e2e entry: the time its copies take at the measured link
-    rate, and that floor over the measured e2e step (1.0 = the step runs at the link's rate)."""
-    if not e2e or not e2e.get("ms_per_step"):
-        return e2e
-    link = host_link()
+def link_roof(e2e, link):
+    """The host-link floor of an e2e entry: the time its copies take at the link rate measured
+    beside it, and that floor over the measured e2e step (1.0 = the step runs at the link's
+    rate)."""
     floor = (e2e["h2d_bytes_per_step"] / link["h2d_gbs"] + e2e["d2h_bytes_per_step"] / link["d2h_gbs"]) / 1e6
     e2e["host_link"] = {"h2d_gbs": link["h2d_gbs"], "d2h_gbs": link["d2h_gbs"],
                         "copy_floor_ms_per_step": floor, "frac": floor / e2e["ms_per_step"],
-                        "note": "pinned cudaMemcpyAsync rate measured in this run; the two "
-                                "directions share the link"}
+                        "note": "pinned cudaMemcpyAsync rate measured right after this e2e "
+                                "timing; the two directions share the link"}
     return e2e
 
 
@@ -498,6 +493,7 @@ def measure(idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=T
             for _ in range(e2e_steps):
                 scan(h, xr_h, B_h, W_h)
             e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
+            link = host_link()
             info1 = g.gwas_stream_info(h)
             stream = {"block_snps": info1["block_snps"], "block_chosen_by_timing": info1["tuned"],
                       "candidates_ms_h2d_scan_d2h": {str(k): v for k, v in info0["candidates"].items()},
@@ -512,11 +508,11 @@ def measure(idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=T
         "split_pieces": pieces if precision == "split_bf16" else None,
         "clocks": clk.summary(), "parity": {"max_rel_err_b": eb, "max_rel_err_wald": ew,
                                             "pairs_checked": npairs, "tolerance": TOL[precision]},
-        "e2e": None if e2e_s is None else {
+        "e2e": None if e2e_s is None else link_roof({
             "value": pairs * ws / e2e_s, "unit": "pairs/s",
             "h2d_bytes_per_step": mm * _row_bytes(n, fmt),
             "d2h_bytes_per_step": mm * t * (p + 1) * 4, "ms_per_step": e2e_s * 1e3,
-            "steps": e2e_steps, "matches_device_run": same, "streaming": stream},
+            "steps": e2e_steps, "matches_device_run": same, "streaming": stream}, link),
         "roofline": dom, "kernels": kernels,
         "gpu_launches": sum(v[1] for v in stages.values()),
         "stage_ms": {k: v[0] / steps for k, v in stages.items()},
@@ -528,7 +524,7 @@ def entry(res, precision, fmt, steps, warmup, **extra):
     """A workload's entry under other_workloads."""
     d = {"config": _config(res["s"], precision, res["m"], fmt, **extra.pop("config", {})),
          "value": res["value"], "unit": "pairs/s", "ms_per_step": res["ms"], "steps": steps,
-         "warmup": warmup, "e2e": with_link_roof(res["e2e"]), "parity": res["parity"],
+         "warmup": warmup, "e2e": res["e2e"], "parity": res["parity"],
          "setup_ms": res["setup_ms"],
          "roofline": res["roofline"], "gpu_launches": res["gpu_launches"],
          "stage_ms_per_step": res["stage_ms"], "clocks": res["clocks"],
@@ -627,6 +623,7 @@ def measure_stream3(local, ws, steps=2, warmup=1, m=None, out_mode="full", pinne
         for _ in range(steps):
             e2e_step()
         e2e_s = _max_over_ranks((time.perf_counter() - t0) / steps, ws)
+        link = host_link()
     finally:
         g.gwas_destroy(h)
     pairs = mm * t
@@ -637,9 +634,10 @@ def measure_stream3(local, ws, steps=2, warmup=1, m=None, out_mode="full", pinne
            "parity": {"max_rel_err_b": eb, "max_rel_err_wald": ew, "pairs_checked": 10000,
                       "tolerance": 1e-4,
                       "sample": "100 random traits x 100 random SNPs, grouped by trait"},
-           "e2e": {"value": pairs * ws / e2e_s, "unit": "pairs/s",
-                   "h2d_bytes_per_step": mm * _row_bytes(n, "packed"),
-                   "d2h_bytes_per_step": mm * t * (pw + 1) * 4, "ms_per_step": e2e_s * 1e3},
+           "e2e": link_roof({"value": pairs * ws / e2e_s, "unit": "pairs/s",
+                             "h2d_bytes_per_step": mm * _row_bytes(n, "packed"),
+                             "d2h_bytes_per_step": mm * t * (pw + 1) * 4,
+                             "ms_per_step": e2e_s * 1e3}, link),
            "roofline": dom, "kernels": kernels,
            "gpu_launches": sum(v[1] for v in stages.values()),
            "stage_ms": {k: v[0] / steps for k, v in stages.items()}}
@@ -923,7 +921,7 @@ def run_ours(args, ws, rank, local):
         "config": dict(_config(s, args.precision, res["m"], fmt),
                        **({"sharding": f"rank r scans SNPs [r*{res['m']}, (r+1)*{res['m']}) of a "
                                        f"{ws * res['m']}-SNP genome (gwas_shard)"} if ws > 1 else {})),
-        "e2e": with_link_roof(res["e2e"]), "gpu_launches": res["gpu_launches"],
+        "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
         "roofline": res["roofline"], "parity": res["parity"], "setup_ms": res["setup_ms"],
         "clocks": res["clocks"], "stage_ms_per_step": res["stage_ms"],
     }
