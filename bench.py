@@ -46,7 +46,9 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "(SNP x trait) GLS solves/s at <=1e-4 rel err vs FP64"
-TOL = {"split_bf16": 1e-4, "fp32": 1e-4, "fp64": 1e-6}
+TOL = {"split_bf16": 1e-4, "split_fp8": 1e-4, "fp32": 1e-4, "fp64": 1e-6}
+SPLIT = ("split_bf16", "split_fp8")
+DTYPE = {"split_bf16": "bf16x2->f32", "split_fp8": "f16+e4m3->f32", "fp32": "f32", "fp64": "f64"}
 
 
 def _peaks():
@@ -210,9 +212,12 @@ def algorithmic_flops(s, m):
     return sum(stage_flops(s, m).values())
 
 
-def stage_executed(s, m, pieces=2):
+def stage_executed(s, m, pieces=2, fp8=False):
     """Tensor-core FLOPs the split kernels issue per stage (split products, K and N padding);
-    `pieces`: BF16 pieces of L^-1 (CHOL) or U (EIG's a/c kernel), 2 or 3."""
+    `pieces`: BF16 pieces of L^-1 (CHOL) or U (EIG's a/c kernel), 2 or 3.  fp8 (CHOL,
+    SPLIT_FP8): an FP16 hi product and an E4M3 lo product over the same K steps, the
+    lo product counted at half weight (the FP8 rate is twice the BF16 one): BF16-equivalent
+    FLOPs, comparable with the BF16 peak."""
     n, q, t = s["n"], s["q"], s["t"]
     kpad = -(-n // 64) * 64
     rpad = -(-n // 256) * 256
@@ -225,7 +230,7 @@ def stage_executed(s, m, pieces=2):
             nk = min(4 * (nb + 1), kpad // 64)
             for ks in range(nk):
                 macs += 64 * (ncols - 64 * max(0, ks - 4 * nb))
-        return {"chol": pieces * 2 * macs * m * t}
+        return {"chol": (1.5 if fp8 else pieces) * 2 * macs * m * t}
     nac = -(-t // eig_ac_traits(q))
     return {"rot": 2 * 2 * rpad * kpad * m, "sq": 3 * 2 * kpad * (-(-t // 256) * 256) * m,
             "ac": pieces * 2 * kpad * 256 * nac * m}
@@ -258,10 +263,11 @@ def traffic_per_unit(kernel):
         return None, None
 
 
-def kernel_roofline(s, m, stage, ms_total, launches, peak_tf, peak_src, steps, pieces=2):
+def kernel_roofline(s, m, stage, ms_total, launches, peak_tf, peak_src, steps, pieces=2,
+                    fp8=False):
     """Roofline entry of one kernel stage from its CUDA-event time over the timed region."""
     alg = stage_flops(s, m)[stage] * steps
-    exe = stage_executed(s, m, pieces)[stage] * steps
+    exe = stage_executed(s, m, pieces, fp8)[stage] * steps
     per, unit = traffic_per_unit(KERNEL_NAMES[stage])
     units = m * steps * (s["t"] if unit == "pair" else 1)
     sec = ms_total * 1e-3
@@ -274,11 +280,12 @@ def kernel_roofline(s, m, stage, ms_total, launches, peak_tf, peak_src, steps, p
             "executed_tflops": exe / sec / 1e12, "executed_frac": exe / sec / 1e12 / peak_tf}
 
 
-def rooflines(s, m, stages, steps, precision, pieces=2):
+def rooflines(s, m, stages, steps, precision, pieces=2, fp8=False):
     """Per-kernel roofline entries of a tensor-core scan and the dominant one (largest time).
     The step's kernels are each timed alone per launch (a few ms at most), so the burst BF16 peak
-    applies."""
-    if precision != "split_bf16":
+    applies (FP16 has the BF16 rate; with fp8 the E4M3 lo product is counted at half weight in
+    the executed figure)."""
+    if precision not in SPLIT:
         ms = stages.get("simt", (0.0, 0))[0]
         alg = algorithmic_flops(s, m) * steps / (ms * 1e-3) / 1e12 if ms else None
         return {"bound": "alu", "kernel": s["algo"] + " CUDA-core scan", "achieved": alg,
@@ -287,8 +294,15 @@ def rooflines(s, m, stages, steps, precision, pieces=2):
     peaks, kind = _peaks()
     peak = peaks["bf16_tflops"]
     src = f"bf16_tflops (burst: each launch is timed alone), {kind} (MEASURED_PEAKS.json)"
-    entries = [kernel_roofline(s, m, st, stages[st][0], stages[st][1], peak, src, steps, pieces)
+    entries = [kernel_roofline(s, m, st, stages[st][0], stages[st][1], peak, src, steps, pieces,
+                               fp8 and st == "chol")
                for st in (["chol"] if s["algo"] == "chol" else ["rot", "sq", "ac"]) if st in stages]
+    if fp8:
+        for e in entries:
+            if e["kernel"] == "chol_tc_kernel":
+                e["note"] = ("FP16 hi x FP16 centred genotypes plus E4M3 lo x E4M3 genotypes into "
+                             "one accumulator; executed FLOPs count the E4M3 product at half "
+                             "weight (its nominal rate is twice the BF16 one)")
     dom = max(entries, key=lambda e: e["ms_per_launch"] * e["launches"])
     return dom, entries
 
@@ -441,6 +455,7 @@ def measure(idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=T
     try:
         setup_ms = g.gwas_setup_timing(h)
         pieces = max(g.gwas_split_pieces(h), 2)
+        fp8 = g.gwas_fp8_traits(h) > 0
         xr_d = torch.from_numpy(c.XR).cuda()
         scan = g.gwas_scan
         if fmt == "packed":  # packed once, outside the timed region: it is the input format
@@ -502,10 +517,10 @@ def measure(idx, precision, steps, warmup, local, ws, m=None, e2e_steps=5, e2e=T
     finally:
         g.gwas_destroy(h)
     pairs = mm * t
-    dom, kernels = rooflines(s, mm, stages, steps, precision, pieces)
+    dom, kernels = rooflines(s, mm, stages, steps, precision, pieces, fp8)
     res = {
         "s": s, "m": mm, "ms": ms, "value": pairs * ws / (ms * 1e-3), "setup_ms": setup_ms,
-        "split_pieces": pieces if precision == "split_bf16" else None,
+        "split_pieces": pieces if precision in SPLIT else None,
         "clocks": clk.summary(), "parity": {"max_rel_err_b": eb, "max_rel_err_wald": ew,
                                             "pairs_checked": npairs, "tolerance": TOL[precision]},
         "e2e": None if e2e_s is None else link_roof({
@@ -826,6 +841,16 @@ def other_workloads(args, ws, local, head):
         return entry(r, "split_bf16", "int8", k, w)
     add(int8_head)
 
+    # the headline workload with the FP16 hi + E4M3 lo split of L^-1 (SPLIT_FP8), oracle on 2,000
+    # sampled SNPs, and its speedup over the split-BF16 headline
+    def fp8_head():
+        r = measure(1, "split_fp8", k, w, local, ws, parity_count=2000)
+        e = entry(r, "split_fp8", "packed", k, w)
+        if args.precision == "split_bf16":
+            e["speedup_over_split_bf16"] = r["value"] / head["value"]
+        return e
+    add(fp8_head)
+
     # the plain FP32 CUDA-core form of the headline, and the speedup at equal accuracy
     def fp32_head():
         r = measure(1, "fp32", 3, w, local, ws, fmt="int8", e2e=False)
@@ -904,7 +929,8 @@ def run_ours(args, ws, rank, local):
         fmt = "packed"
     else:
         res = measure(args.workload, args.precision, args.steps, args.warmup, local, ws, m=args.m,
-                      fmt=args.format, every=args.workload == 0)
+                      fmt=args.format, every=args.workload == 0,
+                      parity_count=2000 if args.workload == 1 else 256)
         fmt = args.format
     s = res["s"]
     other = []
@@ -916,7 +942,7 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": res["value"], "unit": "pairs/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"split_bf16": "bf16x2->f32", "fp32": "f32", "fp64": "f64"}[args.precision],
+        "dtype": DTYPE[args.precision],
         "data": "synthetic",
         "config": dict(_config(s, args.precision, res["m"], fmt),
                        **({"sharding": f"rank r scans SNPs [r*{res['m']}, (r+1)*{res['m']}) of a "
@@ -942,7 +968,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=1)
-    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "fp64"])
+    ap.add_argument("--precision", default="split_bf16", choices=list(DTYPE))
     ap.add_argument("--format", default="packed", choices=["packed", "int8"],
                     help="genotype input format of the timed scans")
     ap.add_argument("--out-mode", default="full", choices=["full", "snp"],

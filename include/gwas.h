@@ -68,8 +68,15 @@ enum { GWAS_ALGO_AUTO = 0, GWAS_ALGO_CHOL = 1, GWAS_ALGO_EIG = 2 };
  *   SPLIT_BF16  tensor-core kernels (tcgen05, sm_103a): the non-integer operand of each
  *               contraction is split into hi + lo BF16 pieces (a third for a badly conditioned
  *               M_j, see gwas_split_pieces), genotypes are exact in BF16, accumulation is FP32;
- *               the p x p Schur solve runs in FP64 (CHOL) or FP32 (EIG).                      */
-enum { GWAS_PREC_FP64 = 0, GWAS_PREC_FP32 = 1, GWAS_PREC_SPLIT_BF16 = 2 };
+ *               the p x p Schur solve runs in FP64 (CHOL) or FP32 (EIG);
+ *   SPLIT_FP8   as SPLIT_BF16, except that CHOL splits the augmented L_j^-1 into an FP16 hi piece
+ *               and an E4M3 lo piece (each row group scaled by a power of two into FP16 range):
+ *               the hi product takes the centred genotypes in FP16 and the lo product the
+ *               uncentred ones in E4M3 (both exact), at the FP8 tensor rate, about 15 significant
+ *               bits in all (BF16 x 2: 16); the epilogue subtracts the centring term the lo
+ *               product misses.  A badly conditioned M_j takes three BF16 pieces as under
+ *               SPLIT_BF16, and EIG scans run exactly as under SPLIT_BF16.                     */
+enum { GWAS_PREC_FP64 = 0, GWAS_PREC_FP32 = 1, GWAS_PREC_SPLIT_BF16 = 2, GWAS_PREC_SPLIT_FP8 = 3 };
 
 /* What a scan writes per (SNP, trait) pair into B (wald is the same in all modes):
  *   FULL  all p coefficients: B is m x t x p;
@@ -91,9 +98,9 @@ enum { GWAS_OUT_FULL = 0, GWAS_OUT_SNP = 1, GWAS_OUT_VAR = 2 };
  * errors sqrt(Var_RR[k][k]) (2 p_R values).  ADD_DOM is solved in the basis of the genotype
  * indicators [x == 1], [x == 2] (the same columns, well conditioned when one homozygote class is
  * rare) and reported for (x, [x == 1]); the Wald statistic does not depend on the basis.  Every
- * precision takes every model, except that the tensor-core scans (SPLIT_BF16) of ADD_DOM need
- * column 0 of X_L to be the intercept (all ones), the paper's X = [1 | L | g]; without it gwas_setup
- * returns GWAS_ERR_UNSUPPORTED (use FP64 or FP32). */
+ * precision takes every model, except that the tensor-core scans (SPLIT_BF16, SPLIT_FP8) of
+ * ADD_DOM need column 0 of X_L to be the intercept (all ones), the paper's X = [1 | L | g];
+ * without it gwas_setup returns GWAS_ERR_UNSUPPORTED (use FP64 or FP32). */
 enum { GWAS_MODEL_ADDITIVE = 0, GWAS_MODEL_DOMINANT = 1, GWAS_MODEL_RECESSIVE = 2,
        GWAS_MODEL_ADD_DOM = 3 };
 
@@ -271,8 +278,8 @@ typedef struct {          /* one cohort's block: device pointers                
   float* wald;            /* m x t or NULL                                                   */
 } gwas_cohort_block;
 
-/* gwas_setup for every cohort (opt applies to all; precision must be SPLIT_BF16).  Fails with
- * the first failing cohort's status (message names the cohort) and creates nothing then. */
+/* gwas_setup for every cohort (opt applies to all; precision SPLIT_BF16 or SPLIT_FP8).  Fails
+ * with the first failing cohort's status (message names the cohort) and creates nothing then. */
 gwas_status gwas_setup_batch(int n_cohorts, const gwas_cohort* cohorts, const gwas_options* opt,
                              gwas_batch* out);
 
@@ -358,6 +365,11 @@ int gwas_genetic_columns(gwas_handle h);
  * intercept that the kinship's weighting determines far more precisely than the SNP effect
  * (|mu b_snp| >> se(intercept), mu the SNP's mean) carries that error amplified by the ratio. */
 int gwas_split_pieces(gwas_handle h);
+
+/* Number of traits whose CHOL scan runs the FP16 hi + E4M3 lo split (precision SPLIT_FP8: every
+ * trait whose M_j is not badly conditioned; the others take three BF16 pieces); 0 for other
+ * precisions and for EIG; -1 for a NULL handle. */
+int gwas_fp8_traits(gwas_handle h);
 
 /* Number of singular pairs (written as NaN) seen by completed scans of this handle, or -1. */
 int64_t gwas_singular_count(gwas_handle h);

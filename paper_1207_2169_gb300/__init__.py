@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgwasgb.so")
 
 ALGO = {"auto": 0, "chol": 1, "eig": 2}
-PRECISION = {"fp64": 0, "fp32": 1, "split_bf16": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "split_bf16": 2, "split_fp8": 3}
 OUT_MODE = {"full": 0, "snp": 1, "var": 2}
 GENETIC_MODEL = {"additive": 0, "dominant": 1, "recessive": 2, "add_dom": 3}
 STATUS = {0: "GWAS_OK", -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ERR_CUDA",
@@ -32,7 +32,7 @@ EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_wald_pvalues_dof",
            "gwas_estimate",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
-           "gwas_genetic_columns", "gwas_split_pieces", "gwas_stream_info",
+           "gwas_genetic_columns", "gwas_split_pieces", "gwas_fp8_traits", "gwas_stream_info",
            "gwas_stage_timing", "gwas_stage_times", "gwas_last_error", "gwas_destroy"]
 
 STAGES = ["pack", "centres", "chol", "rot", "sq", "ac", "simt"]
@@ -115,6 +115,8 @@ def _load():
     lib.gwas_stream_info.restype = i32
     lib.gwas_split_pieces.argtypes = [vp]
     lib.gwas_split_pieces.restype = i32
+    lib.gwas_fp8_traits.argtypes = [vp]
+    lib.gwas_fp8_traits.restype = i32
     lib.gwas_genetic_columns.argtypes = [vp]
     lib.gwas_genetic_columns.restype = i32
     lib.gwas_singular_count.argtypes = [vp]
@@ -417,6 +419,10 @@ def gwas_genetic_columns(h) -> int:
 
 def gwas_split_pieces(h) -> int:
     return int(lib.gwas_split_pieces(h))
+
+
+def gwas_fp8_traits(h) -> int:
+    return int(lib.gwas_fp8_traits(h))
 
 
 def gwas_stream_info(h) -> dict:

@@ -32,7 +32,10 @@ void set_error(const char* fmt, ...) {
 using namespace gw;
 
 struct gwas_handle_s {
-  int dev = 0, n = 0, q = 0, p = 0, t = 0, algo = 0, prec = 0, validate = 0;
+  // prec: the scan's path (SPLIT_FP8 runs the tensor-core path of SPLIT_BF16, so prec holds
+  // SPLIT_BF16 then and fp8 is set); prec_opt: the precision the caller asked for
+  int dev = 0, n = 0, q = 0, p = 0, t = 0, algo = 0, prec = 0, prec_opt = 0, validate = 0;
+  bool fp8 = false;
   int model = GWAS_MODEL_ADDITIVE;  // genetic model: the SNP's pr columns, p = q + pr
   GeneticModel gm;
   int out_snp = 0;  // GWAS_OUT_SNP: B holds (b_R, se_R) per pair
@@ -305,6 +308,7 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     ta.out_var = h->out_var;
     ta.gm = h->gm;
     ta.pieces = h->pieces.data();
+    ta.fp8_lo = h->fp8 && h->algo == GWAS_ALGO_CHOL ? 1 : 0;
     ta.intercept = 1;
     for (int i = 0; i < n; ++i)
       if (XL[i] != 1.0) ta.intercept = 0;
@@ -812,7 +816,7 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
     gwas_default_options(&o);
     if (opt) o = *opt;
     GW_REQUIRE(o.algo >= 0 && o.algo <= 2, GWAS_ERR_ARG, "bad algo %d", o.algo);
-    GW_REQUIRE(o.precision >= 0 && o.precision <= 2, GWAS_ERR_ARG, "bad precision %d", o.precision);
+    GW_REQUIRE(o.precision >= 0 && o.precision <= 3, GWAS_ERR_ARG, "bad precision %d", o.precision);
     GW_REQUIRE(o.block_snps >= 0, GWAS_ERR_ARG, "block_snps < 0");
     GW_REQUIRE(o.out_mode == GWAS_OUT_FULL || o.out_mode == GWAS_OUT_SNP ||
                    o.out_mode == GWAS_OUT_VAR,
@@ -827,7 +831,9 @@ GW_API gwas_status gwas_setup(const double* Phi, int n, const double* XL, int q,
     h->p = q + gm.pr;
     h->t = t;
     h->algo = o.algo == GWAS_ALGO_AUTO ? (t == 1 ? GWAS_ALGO_CHOL : GWAS_ALGO_EIG) : o.algo;
-    h->prec = o.precision;
+    h->prec_opt = o.precision;
+    h->fp8 = o.precision == GWAS_PREC_SPLIT_FP8;
+    h->prec = h->fp8 ? GWAS_PREC_SPLIT_BF16 : o.precision;
     h->validate = o.validate_genotypes ? 1 : 0;
     h->out_snp = o.out_mode == GWAS_OUT_SNP ? 1 : 0;
     h->out_var = o.out_mode == GWAS_OUT_VAR ? 1 : 0;
@@ -1128,7 +1134,7 @@ GW_API gwas_status gwas_info(gwas_handle h, int* n, int* q, int* t, int* algo, i
   if (q) *q = h->q;
   if (t) *t = h->t;
   if (algo) *algo = h->algo;
-  if (precision) *precision = h->prec;
+  if (precision) *precision = h->prec_opt;
   return GWAS_OK;
 }
 
@@ -1152,6 +1158,8 @@ GW_API gwas_status gwas_stream_info(gwas_handle h, int* block_snps, int* tuned,
   }
   return GWAS_OK;
 }
+
+GW_API int gwas_fp8_traits(gwas_handle h) { return h ? (h->tc ? tc_fp8_traits(h->tc) : 0) : -1; }
 
 GW_API int gwas_split_pieces(gwas_handle h) {
   if (!h) return -1;

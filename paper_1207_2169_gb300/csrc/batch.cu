@@ -225,8 +225,9 @@ GW_API gwas_status gwas_setup_batch(int n_cohorts, const gwas_cohort* cohorts,
     gwas_options o;
     gwas_default_options(&o);
     if (opt) o = *opt;
-    GW_REQUIRE(o.precision == GWAS_PREC_SPLIT_BF16, GWAS_ERR_UNSUPPORTED,
-               "batched scans run the tensor-core path (precision SPLIT_BF16)");
+    GW_REQUIRE(o.precision == GWAS_PREC_SPLIT_BF16 || o.precision == GWAS_PREC_SPLIT_FP8,
+               GWAS_ERR_UNSUPPORTED,
+               "batched scans run the tensor-core path (precision SPLIT_BF16 or SPLIT_FP8)");
     b = new gwas_batch_s();
     b->dev = o.device;
     // The cohorts' setups (FP64 eigendecompositions and per-trait packs, each on its handle's

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <string>
@@ -172,6 +173,22 @@ void split_bf16(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx
 void split_bf16_rows(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx, int gin,
                      int gout, int off, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo,
                      __nv_bfloat16* lo2 = nullptr);
+
+// The FP16 hi + E4M3 lo split (SPLIT_FP8) of the rows of a rows x cols row-major matrix: row r
+// is scaled by rscale[r] (a power of two, device array), hi = fp16(v), lo = e4m3(v - hi) with v
+// the scaled value; both store their columns in e4m3_k_slot order within each aligned group of
+// 16 (the order the tensor-core converters produce genotypes in).  Columns cols .. ldo-1 are
+// zero.
+// rowmax_abs writes max |x[r][c]| of each row into out[r].  e4m3_row_sums writes, per row r of
+// the lo matrix, the sum of its values over all ldo columns into out[r] (FP32).
+void rowmax_abs(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx, double* out);
+void split_f16_e4m3(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx,
+                    const double* rscale, __half* hi, uint8_t* lo, int64_t ldo);
+void e4m3_row_sums(cudaStream_t s, const uint8_t* lo, int rows, int64_t ldo, float* out);
+// w[c] = sum over r < rows of ls[r] (hi[r][c] + lo[r][c]) for the natural columns c < cols of the
+// split (hi and lo in their stored order), in FP64.
+void e4m3_weighted_col_sums(cudaStream_t s, const __half* hi, const uint8_t* lo, int rows,
+                            int64_t ldo, int cols, const float* ls, double* w);
 
 // ------------------------------------------------------------------------------------------
 // Genetic models: the block X_R,i a SNP contributes to X_i = [X_L | X_R,i] has pr columns

@@ -14,7 +14,10 @@
 
 #include <vector>
 
+#include <cuda_fp8.h>
+
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace gw {
 
@@ -703,6 +706,106 @@ double condition_estimate(cudaStream_t s, int n, const double* L, const double* 
 void split_bf16(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx,
                 __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, __nv_bfloat16* lo2) {
   split_bf16_kernel<<<1184, 256, 0, s>>>(x, rows, cols, ldx, hi, lo, lo2, ldo);
+  GW_CHECK_LAUNCH();
+}
+
+namespace {
+
+__global__ void rowmax_abs_kernel(const double* __restrict__ x, int cols, int64_t ldx,
+                                  double* __restrict__ out) {
+  __shared__ double red[32];
+  const double* row = x + (int64_t)blockIdx.x * ldx;
+  double v = 0.0;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) v = fmax(v, fabs(row[c]));
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+  }
+}
+
+// the position of column c in the lo matrix: e4m3_k_slot order within its group of 16
+__device__ __forceinline__ int64_t e4m3_col(int c) { return (c & ~15) | tc::e4m3_k_slot(c & 15); }
+
+__global__ void split_f16_e4m3_kernel(const double* __restrict__ x, int rows, int cols,
+                                      int64_t ldx, const double* __restrict__ rscale,
+                                      __half* __restrict__ hi, uint8_t* __restrict__ lo,
+                                      int64_t ldo) {
+  const int64_t total = (int64_t)rows * ldo;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ldo;
+    const int c = (int)(e % ldo);
+    const double v = c < cols ? x[r * ldx + c] * rscale[r] : 0.0;
+    const __half h = __double2half(v);
+    const double rem = v - (double)__half2float(h);
+    hi[r * ldo + e4m3_col(c)] = h;
+    lo[r * ldo + e4m3_col(c)] = (uint8_t)__nv_cvt_double_to_fp8(rem, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+__device__ __forceinline__ double e4m3_value(uint8_t b) {
+  const __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
+  return (double)__half2float(__half(hr));
+}
+
+__global__ void e4m3_weighted_col_sums_kernel(const __half* __restrict__ hi,
+                                              const uint8_t* __restrict__ lo, int rows,
+                                              int64_t ldo, int cols, const float* __restrict__ ls,
+                                              double* __restrict__ w) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+    const int64_t pos = e4m3_col(c);
+    double acc = 0.0;
+    for (int r = 0; r < rows; ++r)
+      acc += (double)ls[r] * ((double)__half2float(hi[r * ldo + pos]) + e4m3_value(lo[r * ldo + pos]));
+    w[c] = acc;
+  }
+}
+
+__global__ void e4m3_row_sums_kernel(const uint8_t* __restrict__ lo, int64_t ldo,
+                                     float* __restrict__ out) {
+  __shared__ double red[32];
+  const uint8_t* row = lo + (int64_t)blockIdx.x * ldo;
+  double v = 0.0;
+  for (int64_t c = threadIdx.x; c < ldo; c += blockDim.x) v += e4m3_value(row[c]);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) out[blockIdx.x] = (float)v;
+  }
+}
+
+}  // namespace
+
+void rowmax_abs(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx, double* out) {
+  if (rows <= 0) return;
+  rowmax_abs_kernel<<<rows, 256, 0, s>>>(x, cols, ldx, out);
+  GW_CHECK_LAUNCH();
+}
+
+void split_f16_e4m3(cudaStream_t s, const double* x, int rows, int cols, int64_t ldx,
+                    const double* rscale, __half* hi, uint8_t* lo, int64_t ldo) {
+  GW_REQUIRE(ldo % 16 == 0 && cols <= ldo, GWAS_ERR_ARG, "FP8 split: bad leading dimension");
+  split_f16_e4m3_kernel<<<1184, 256, 0, s>>>(x, rows, cols, ldx, rscale, hi, lo, ldo);
+  GW_CHECK_LAUNCH();
+}
+
+void e4m3_weighted_col_sums(cudaStream_t s, const __half* hi, const uint8_t* lo, int rows,
+                            int64_t ldo, int cols, const float* ls, double* w) {
+  if (cols <= 0) return;
+  e4m3_weighted_col_sums_kernel<<<ceil_div(cols, 128), 128, 0, s>>>(hi, lo, rows, ldo, cols, ls, w);
+  GW_CHECK_LAUNCH();
+}
+
+void e4m3_row_sums(cudaStream_t s, const uint8_t* lo, int rows, int64_t ldo, float* out) {
+  if (rows <= 0) return;
+  e4m3_row_sums_kernel<<<rows, 256, 0, s>>>(lo, ldo, out);
   GW_CHECK_LAUNCH();
 }
 

@@ -30,6 +30,7 @@ struct TcSetupArgs {
   int out_var;           // B holds the p values, then the p(p+1)/2 of Var(b) (packed upper)
   GeneticModel gm;       // the SNP's genetic columns (p = q + gm.pr)
   const int* pieces;     // CHOL: split pieces (2 or 3) per trait; EIG: pieces[0] for every U_j
+  int fp8_lo;            // CHOL: a two-piece trait is split FP16 hi + E4M3 lo (SPLIT_FP8)
 };
 
 struct TcScanArgs {
@@ -52,5 +53,7 @@ void tc_destroy(TcState* st);
 double tc_scan_work(const TcState* st, int64_t m);
 // Largest number of split pieces the state's kernels use (2 or 3).
 int tc_split_pieces(const TcState* st);
+// Number of CHOL traits whose split is FP16 hi + E4M3 lo (SPLIT_FP8).
+int tc_fp8_traits(const TcState* st);
 
 }  // namespace gw

@@ -11,7 +11,16 @@
 // into the matching accumulator columns), and the last block stops at row n + q.  The
 // augmented matrix is split into BF16 hi + lo pieces and genotypes are exact in BF16, so
 // D = X hi^T + X lo^T carries ~16 significant bits with FP32 accumulation (a third piece,
-// ~24 bits, for a trait whose M is badly conditioned).  The epilogue sums
+// ~24 bits, for a trait whose M is badly conditioned).  The FP8 variant (SPLIT_FP8) splits it
+// into an FP16 hi piece and an E4M3 lo piece instead (each row group scaled by a power of two):
+// the hi product takes the centred genotypes in FP16 (kind::f16), the lo product the uncentred
+// codes in E4M3 (kind::f8f6f4, twice the rate), both into the same accumulator, ~15 bits in
+// all; both 8- and 16-bit genotype tiles, and both pieces, hold their K columns in the order the
+// converters produce the E4M3 bytes in (e4m3_k_slot within every group of 16).  The lo product
+// misses the centring term mu (lo 1): accumulator row r holds x'_r + mu lsum_r.  One more
+// augmented row, w = sum_r lsum_r (hi + lo)_r, yields w . (x - mu) = sum_r lsum_r x'_r, from which
+// the epilogue corrects s, a and c with a few scalar operations per SNP; it also removes the
+// power-of-two scales.  The epilogue sums
 // s = x'^T x' out of TMEM (FP32 within a block, FP64 across blocks), picks up a and c, and
 // finishes each tile with the Schur-complement solve in FP64.  X' is never written to memory.
 // With an intercept in X_L each SNP is centred by mu, the multiple of 1/64 nearest its mean
@@ -23,8 +32,9 @@
 //   0-3  epilogue: one SNP per thread (TMEM lane 32*warp + lane)
 //   11   TMA producers: lane 0 the L^-1 tiles, lane 1 the 2-bit packed genotype slices
 //   7    MMA issuer (one elected lane); owns the 512 TMEM columns (two 256-column accumulators)
-//   4-6, 8-10, 12-13  genotype converters: packed slices (shared memory) -> BF16 tiles in the
-//        128-byte-swizzled K-major layout
+//   4-6, 8-10, 12-13  genotype converters: packed slices (shared memory) -> BF16 (FP8 variant:
+//        FP16) tiles in the 128-byte-swizzled K-major layout, and in the FP8 variant also E4M3
+//        tiles of 64-byte rows in the 64-byte-swizzled layout
 #include <mutex>
 
 #include "tc_kernels.cuh"
@@ -38,12 +48,11 @@ namespace {
 constexpr int BM = CHOL_TC_BM;
 constexpr int BN = 256;
 constexpr int BK = 64;
-constexpr int SA = 3;                   // genotype tile ring
-constexpr int SB = 5;                   // L^-1 tile ring (one piece per slot)
 constexpr int A_BYTES = BM * BK * 2;    // 16 KB
 constexpr int B_BYTES = BN * BK * 2;    // 32 KB
+constexpr int A8_BYTES = BM * BK;       // FP8 variant: E4M3 genotype tile, 8 KB
+constexpr int B8_BYTES = BN * BK;       // FP8 variant: E4M3 lo tile, 16 KB
 constexpr int QMAX = 7;
-constexpr int PR = 8;                   // packed-genotype slice ring
 constexpr int PK_BYTES = BM * 16;       // 64 genotypes of 128 SNPs, 2-bit codes: 2 KB
 constexpr int NCONV = 8;                // genotype converter warps: 2 threads per row
 constexpr int NUM_THREADS = 192 + 32 * NCONV;
@@ -58,7 +67,8 @@ __device__ __forceinline__ int conv_index(int warp) {
 constexpr int TMEM_COLS = 512;
 constexpr uint64_t WAIT_NS = 4000000000ull;
 
-struct __align__(8) Bars {
+template <int SA, int SB, int PR>
+struct __align__(8) BarsT {
   uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], pk_full[PR], pk_empty[PR];
   uint64_t acc_full[2], acc_empty[2], mu_full[2], mu_empty[2], done;
   uint32_t tmem_base;
@@ -66,8 +76,21 @@ struct __align__(8) Bars {
   float mu[2][BM];  // SNP centres of the tiles in flight (epilogue -> converters)
 };
 
-constexpr size_t SMEM_BYTES = 1024 + SA * A_BYTES + SB * B_BYTES + PR * PK_BYTES + sizeof(Bars);
-static_assert(SMEM_BYTES <= 232448, "shared memory over the sm_103 opt-in limit");
+// Shared-memory rings.  BF16: slots of one genotype tile (A) and of one piece of one K step (B).
+// FP8: an A slot holds the FP16 tile and then the E4M3 tile of one K step, a B slot the FP16 hi
+// tile and then the E4M3 lo tile of one K step.
+template <bool F8>
+struct Layout {
+  static constexpr int SA = 3;                                   // genotype slots
+  static constexpr int SB = F8 ? 3 : 5;                          // L^-1 slots
+  static constexpr int PR = F8 ? 4 : 8;                          // packed-slice slots
+  static constexpr int A_SLOT = F8 ? A_BYTES + A8_BYTES : A_BYTES;
+  static constexpr int B_SLOT = F8 ? B_BYTES + B8_BYTES : B_BYTES;
+  using Bars = BarsT<SA, SB, PR>;
+  static constexpr size_t SMEM =
+      1024 + (size_t)SA * A_SLOT + (size_t)SB * B_SLOT + (size_t)PR * PK_BYTES + sizeof(Bars);
+  static_assert(SMEM <= 232448, "shared memory over the sm_103 opt-in limit");
+};
 
 __device__ __forceinline__ int ksteps(int nb, int kpad) {
   const int k = (nb + 1) * (BN / BK);
@@ -81,10 +104,10 @@ __device__ __forceinline__ int diag_skip(int nb, int ks) {
   return j > 0 ? j : 0;
 }
 
-// Live accumulator columns of block nb: rows of the augmented matrix below n + q + 1, rounded
+// Live accumulator columns of block nb: rows of the augmented matrix below n + naug, rounded
 // up to the MMA's N granularity (16).
-__device__ __forceinline__ int block_cols(int nb, int n, int q) {
-  const int live = n + q + 1 - nb * BN;
+__device__ __forceinline__ int block_cols(int nb, int n, int naug) {
+  const int live = n + naug - nb * BN;
   const int c = (live + 15) & ~15;
   return c < BN ? c : BN;
 }
@@ -236,18 +259,22 @@ __device__ __noinline__ void solve_pair(const CholTcParams& p, const float* a0, 
 // QM: compile-time bound on q (3 or 7), so the epilogue's per-column arrays stay in registers.
 // GP: genetic columns per SNP (1, or 2 for a two-column genetic model).  NP: BF16 pieces of the
 // split matrix (2, or 3 for a badly conditioned M; a compile-time bound keeps the issuer's and
-// producer's piece loops unrolled).
-template <int QM, int GP, int NP>
+// producer's piece loops unrolled).  F8: the FP16 hi + E4M3 lo split (NP = 2).
+template <int QM, int GP, int NP, bool F8>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     chol_tc_kernel(const __grid_constant__ CholMaps lmaps, const __grid_constant__ CUtensorMap mapG,
                    const CholTcParams p) {
+  static_assert(!F8 || NP == 2, "the FP8 split has two pieces");
+  using L = Layout<F8>;
+  using Bars = typename L::Bars;
+  constexpr int SA = L::SA, SB = L::SB, PR = L::PR, A_SLOT = L::A_SLOT, B_SLOT = L::B_SLOT;
   constexpr int TS = BM / GP;        // SNPs per tile
   constexpr int PKB = TS * 16;       // bytes of one packed slice (64 genotypes of TS SNPs)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
-  uint8_t* sB = sA + SA * A_BYTES;
-  uint8_t* sP = sB + SB * B_BYTES;
+  uint8_t* sB = sA + SA * A_SLOT;
+  uint8_t* sP = sB + SB * B_SLOT;
   Bars* bars = (Bars*)(sP + PR * PK_BYTES);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t tiles_run = (p.m + TS - 1) / TS;
@@ -285,6 +312,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   if (warp == TMA_WARP && lane == 0) {
     for (int j = 0; j < 4; ++j) prefetch_tensormap(&lmaps.m[j]);
+    if (F8)
+      for (int j = 0; j < 4; ++j) prefetch_tensormap(&lmaps.m8[j]);
     prefetch_tensormap(&mapG);
   }
   tc_fence_before();
@@ -301,14 +330,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       bool ok = true;
       for (Step st{blockIdx.x, 0, 0}; st.tile < tiles_run && ok; advance(st, nblocks, p.kpad)) {
         const int j = diag_skip(st.nb, st.ks);  // rows 64 j .. 255 of the block
-        for (int piece = 0; piece < NP; ++piece) {
+        if constexpr (F8) {
+          // one slot: the FP16 hi tile, then the E4M3 lo tile (64-byte rows)
           ok = mbar_wait(&bars->b_empty[bs], bph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
-          const int y = piece * p.rpad + st.nb * BN + 64 * j;
-          uint8_t* dst = sB + bs * B_BYTES + (B_BYTES / 4) * j;
-          mbar_arrive_expect_tx(&bars->b_full[bs], (B_BYTES / 4) * (4 - j));
-          tma_load_2d(dst, &lmaps.m[j], &bars->b_full[bs], st.ks * BK, y);
+          const int y = st.nb * BN + 64 * j;
+          uint8_t* dst = sB + bs * B_SLOT;
+          mbar_arrive_expect_tx(&bars->b_full[bs], (B_BYTES / 4 + B8_BYTES / 4) * (4 - j));
+          tma_load_2d(dst + (B_BYTES / 4) * j, &lmaps.m[j], &bars->b_full[bs], st.ks * BK, y);
+          tma_load_2d(dst + B_BYTES + (B8_BYTES / 4) * j, &lmaps.m8[j], &bars->b_full[bs],
+                      st.ks * BK, y);
           if (++bs == SB) { bs = 0; bph ^= 1; }
+        } else {
+          for (int piece = 0; piece < NP; ++piece) {
+            ok = mbar_wait(&bars->b_empty[bs], bph ^ 1, abort, tflag, WAIT_NS);
+            if (!ok) break;
+            const int y = piece * p.rpad + st.nb * BN + 64 * j;
+            uint8_t* dst = sB + bs * B_BYTES + (B_BYTES / 4) * j;
+            mbar_arrive_expect_tx(&bars->b_full[bs], (B_BYTES / 4) * (4 - j));
+            tma_load_2d(dst, &lmaps.m[j], &bars->b_full[bs], st.ks * BK, y);
+            if (++bs == SB) { bs = 0; bph ^= 1; }
+          }
         }
       }
     } else if (lane == 1) {
@@ -336,27 +378,48 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (!ok) break;
           tc_fence_after();
           const uint32_t dt = tmem + buf * BN;
-          const int nk = ksteps(nb, p.kpad), ncols = block_cols(nb, p.n, p.q);
+          const int nk = ksteps(nb, p.kpad), ncols = block_cols(nb, p.n, p.naug);
           for (int ks = 0; ks < nk && ok; ++ks) {
             ok = mbar_wait(&bars->a_full[as], aph, abort, tflag, WAIT_NS);
             if (!ok) break;
             tc_fence_after();
-            const uint64_t ad = sw128_desc(sA + as * A_BYTES);
+            const uint64_t ad = sw128_desc(sA + as * A_SLOT);
             const int j = diag_skip(nb, ks);  // accumulator columns 64 j .. ncols - 1
-            const uint32_t idesc = idesc_bf16(BM, ncols - 64 * j);
-            for (int piece = 0; piece < NP; ++piece) {
+            if constexpr (F8) {
+              // (x - mu in FP16) x (hi in FP16), then (x in E4M3) x (lo in E4M3), one accumulator
+              const uint32_t idesc = idesc_f16(BM, ncols - 64 * j);
+              const uint64_t ad8 = sw64_desc(sA + as * A_SLOT + A_BYTES);
               ok = mbar_wait(&bars->b_full[bs], bph, abort, tflag, WAIT_NS);
               if (!ok) break;
               tc_fence_after();
-              const uint64_t bd = sw128_desc(sB + bs * B_BYTES + (B_BYTES / 4) * j);
+              const uint64_t bd = sw128_desc(sB + bs * B_SLOT + (B_BYTES / 4) * j);
+              const uint64_t bd8 = sw64_desc(sB + bs * B_SLOT + B_BYTES + (B8_BYTES / 4) * j);
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk)
-                mma_bf16(dt + 64 * j, ad + 2 * kk, bd + 2 * kk, idesc, (ks | piece | kk) != 0);
+                mma_bf16(dt + 64 * j, ad + 2 * kk, bd + 2 * kk, idesc, (ks | kk) != 0);
+#pragma unroll
+              for (int kk = 0; kk < BK / 32; ++kk)
+                mma_fp8(dt + 64 * j, ad8 + 2 * kk, bd8 + 2 * kk, idesc, 1u);
               mma_commit(&bars->b_empty[bs]);
               if (++bs == SB) { bs = 0; bph ^= 1; }
+              mma_commit(&bars->a_empty[as]);
+              if (++as == SA) { as = 0; aph ^= 1; }
+            } else {
+              const uint32_t idesc = idesc_bf16(BM, ncols - 64 * j);
+              for (int piece = 0; piece < NP; ++piece) {
+                ok = mbar_wait(&bars->b_full[bs], bph, abort, tflag, WAIT_NS);
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t bd = sw128_desc(sB + bs * B_SLOT + (B_BYTES / 4) * j);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                  mma_bf16(dt + 64 * j, ad + 2 * kk, bd + 2 * kk, idesc, (ks | piece | kk) != 0);
+                mma_commit(&bars->b_empty[bs]);
+                if (++bs == SB) { bs = 0; bph ^= 1; }
+              }
+              mma_commit(&bars->a_empty[as]);
+              if (++as == SA) { as = 0; aph ^= 1; }
             }
-            mma_commit(&bars->a_empty[as]);
-            if (++as == SA) { as = 0; aph ^= 1; }
           }
           if (ok) mma_commit(&bars->acc_full[buf]);
           if (++buf == 2) { buf = 0; accph ^= 1; }
@@ -368,12 +431,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   } else if (warp >= 4) {
     // ------------------------------------------------------------ genotype converters
     // Thread ct converts half hh of row r of each K step: packed bytes 8 hh .. 8 hh + 7 (32
-    // genotypes) into BF16 chunks 4 hh .. 4 hh + 3 of the row's swizzled 128-byte line.
+    // genotypes) into BF16 (FP8 variant: FP16) chunks 4 hh .. 4 hh + 3 of the row's swizzled
+    // 128-byte line, and in the FP8 variant into E4M3 chunks 2 hh, 2 hh + 1 of the row's
+    // 64-byte line (chunk c at c ^ ((r >> 1) & 3)).
     const int ct = conv_index(warp) * 32 + lane;
     const int r = ct >> 1, hh = ct & 1;
     const int srow = row_snp<GP>(r);             // the row's SNP within the tile
     const uint32_t code = p.code[row_col<GP>(r)];  // the row's genetic column
     const uint32_t line = (r >> 3) * 1024 + (r & 7) * 128;
+    const uint32_t line8 = r * 64;
+    const uint32_t t8 = coded_e4m3_table(code);  // the uncentred codes in E4M3
+    __half2 mu2 = __float2half2_rn(0.f);          // FP8 variant: the row's centre, twice
     int per_tile = 0;
     for (int nb = 0; nb < nblocks; ++nb) per_tile += ksteps(nb, p.kpad);
     int as = 0, ps = 0;
@@ -388,7 +456,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         ok = __all_sync(0xffffffffu,
                         mbar_wait(&bars->mu_full[mb], (ti >> 1) & 1, abort, tflag, WAIT_NS));
         if (!ok) break;
-        coded_lut(bars->mu[mb][r], code, lutlo, luthi);
+        if (F8)
+          mu2 = __float2half2_rn(bars->mu[mb][r]);  // a multiple of 1/64: exact
+        else
+          coded_lut(bars->mu[mb][r], code, lutlo, luthi);
         mbar_arrive(&bars->mu_empty[mb]);
       } else {
         coded_lut(0.f, code, lutlo, luthi);
@@ -403,15 +474,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->pk_empty[ps]);
         if (++ps == PR) { ps = 0; pph ^= 1; }
-        uint4 o[4];
-        packed8_to_bf16x32(w, lutlo, luthi, o);
+        uint4 o[4], e8[2];
+        if constexpr (F8) {
+          // E4M3 codes by byte permutes, then FP16 cd - mu from them, in the same K order
+          e8[0] = packed16_to_e4m3x16(w.x, t8);
+          e8[1] = packed16_to_e4m3x16(w.y, t8);
+          e4m3x16_to_f16_centred(e8[0], mu2, o[0], o[1]);
+          e4m3x16_to_f16_centred(e8[1], mu2, o[2], o[3]);
+        } else {
+          packed8_to_bf16x32(w, lutlo, luthi, o);
+        }
         ok = __all_sync(0xffffffffu, mbar_wait(&bars->a_empty[as], aph ^ 1, abort, tflag, WAIT_NS));
         if (!ok) break;
-        uint8_t* dst = sA + as * A_BYTES + line;
+        uint8_t* dst = sA + as * A_SLOT + line;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int j = 4 * hh + i;
           *reinterpret_cast<uint4*>(dst + ((j ^ (r & 7)) << 4)) = o[i];
+        }
+        if (F8) {
+          uint8_t* dst8 = sA + as * A_SLOT + A_BYTES + line8;
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const int j = 2 * hh + i;
+            *reinterpret_cast<uint4*>(dst8 + ((j ^ ((r >> 1) & 3)) << 4)) = e8[i];
+          }
         }
         // every lane's writes are ordered before the async proxy, then one arrive per warp
         fence_proxy_async_smem();
@@ -473,7 +560,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         ok = publish_centre(ti + 1, mu_next);
       }
       double S = 0.0, X = 0.0;  // s of this row; with GP = 2, the cross product with its partner
-      float A[QM], C = 0.f;
+      float A[QM], C = 0.f, Wd = 0.f;  // Wd (FP8 variant): w . (x - mu) + mu lsa[q + 1]
 #pragma unroll
       for (int k = 0; k < QM; ++k) A[k] = 0.f;
       for (int nb = 0; nb < nblocks; ++nb) {
@@ -481,7 +568,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (ok) {
           tc_fence_after();
           const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + buf * BN;
-          const int c0 = nb * BN, ncols = block_cols(nb, n, q);
+          const int c0 = nb * BN, ncols = block_cols(nb, n, p.naug);
           float bs_ = 0.f, bx_ = 0.f;
           uint32_t ra[32];
 #pragma unroll 1
@@ -512,6 +599,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 for (int k = 0; k < QM; ++k)
                   if (k < q && col == n + k) A[k] = x;
                 if (col == n + q) C = x;
+                if (F8 && col == n + q + 1) Wd = x;
               }
             }
             bs_ += ss;
@@ -524,6 +612,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
         }
         if (++buf == 2) { buf = 0; accph ^= 1; }
+      }
+      if constexpr (F8) {
+        // remove the lo product's centring term mu lsum_r from every row, then the power-of-two
+        // scales of the row groups (exact)
+        const float mu = p.centre ? mu_cur : 0.f;
+#pragma unroll
+        for (int k = 0; k < QM; ++k)
+          if (k < q) A[k] = (A[k] - mu * p.lsa[k]) * p.unscale[1 + k];
+        C = (C - mu * p.lsa[q]) * p.unscale[1 + q];
+        const double wx = (double)((Wd - mu * p.lsa[q + 1]) * p.unscale[2 + q]);
+        const double u0 = (double)p.unscale[0];
+        if (GP == 2) {
+          // the partner row: the SNP's other working column (16 lanes away)
+          const double wxp = __shfl_xor_sync(0xffffffffu, wx, 16);
+          const double mup = (double)__shfl_xor_sync(0xffffffffu, mu, 16);
+          X = (X - mup * wx - (double)mu * wxp - (double)mu * mup * p.k2) * u0 * u0;
+        }
+        S = (S - 2.0 * mu * wx - (double)mu * mu * p.k2) * u0 * u0;
       }
       const int64_t snp = tile * TS + row_snp<GP>(row);
       if (GP == 2) {
@@ -558,7 +664,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (p.W) p.W[snp * p.t + p.j] = (float)(bs * (double)C);
         } else if (sigma > 1e-5 * S) {
           const double bs = (double)C / sigma;
-#pragma unroll
           double bl[QM];
 #pragma unroll
           for (int k = 0; k < QM; ++k) bl[k] = k < q ? __ldg(&p.b0[k]) - v[k] * bs : 0.0;
@@ -615,9 +720,12 @@ int g_max_ctas[64][2];  // per device: co-resident CTAs of each instantiation
 
 template <int QM>
 int max_resident_ctas() {
-  int per_sm = 0, dev = 0, sms = 0;
-  GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_tc_kernel<QM, 1, 2>,
-                                                        NUM_THREADS, SMEM_BYTES));
+  int per_sm = 0, per_sm8 = 0, dev = 0, sms = 0;
+  GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_tc_kernel<QM, 1, 2, false>,
+                                                        NUM_THREADS, Layout<false>::SMEM));
+  GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm8, chol_tc_kernel<QM, 1, 2, true>,
+                                                        NUM_THREADS, Layout<true>::SMEM));
+  per_sm = per_sm8 < per_sm ? per_sm8 : per_sm;
   GW_REQUIRE(per_sm >= 1, GWAS_ERR_UNSUPPORTED, "the CHOL tensor-core kernel does not fit on an SM");
   GW_CUDA(cudaGetDevice(&dev));
   GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -631,19 +739,20 @@ int current_device() {
 }
 }  // namespace
 
-template <int QM, int GP, int NP>
+template <int QM, int GP, int NP, bool F8 = false>
 void set_smem() {
-  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QM, GP, NP>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+  GW_CUDA(cudaFuncSetAttribute(chol_tc_kernel<QM, GP, NP, F8>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<F8>::SMEM));
 }
 
-template <int GP, int NP>
+template <int GP, int NP, bool F8 = false>
 void launch_q(unsigned grid, cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& mapG,
               const CholTcParams& p) {
+  constexpr size_t SMEM = Layout<F8>::SMEM;
   if (p.q <= 3)
-    chol_tc_kernel<3, GP, NP><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+    chol_tc_kernel<3, GP, NP, F8><<<grid, NUM_THREADS, SMEM, s>>>(lmaps, mapG, p);
   else
-    chol_tc_kernel<QMAX, GP, NP><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(lmaps, mapG, p);
+    chol_tc_kernel<QMAX, GP, NP, F8><<<grid, NUM_THREADS, SMEM, s>>>(lmaps, mapG, p);
 }
 
 void chol_tc_prepare() {
@@ -659,6 +768,10 @@ void chol_tc_prepare() {
   set_smem<QMAX, 1, 3>();
   set_smem<3, 2, 3>();
   set_smem<QMAX, 2, 3>();
+  set_smem<3, 1, 2, true>();
+  set_smem<QMAX, 1, 2, true>();
+  set_smem<3, 2, 2, true>();
+  set_smem<QMAX, 2, 2, true>();
   mx[0] = max_resident_ctas<3>();
   mx[1] = max_resident_ctas<QMAX>();
 }
@@ -677,7 +790,12 @@ void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& ma
   int64_t cap = chol_tc_resident_ctas(p.q);
   if (cap <= 0 || cap > num_sms) cap = num_sms;
   const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
-  if (p.gp == 1 && p.pieces == 2)
+  GW_REQUIRE(!p.fp8 || p.pieces == 2, GWAS_ERR_ARG, "the FP8 split has two pieces");
+  if (p.fp8 && p.gp == 1)
+    launch_q<1, 2, true>(grid, s, lmaps, mapG, p);
+  else if (p.fp8)
+    launch_q<2, 2, true>(grid, s, lmaps, mapG, p);
+  else if (p.gp == 1 && p.pieces == 2)
     launch_q<1, 2>(grid, s, lmaps, mapG, p);
   else if (p.gp == 1)
     launch_q<1, 3>(grid, s, lmaps, mapG, p);

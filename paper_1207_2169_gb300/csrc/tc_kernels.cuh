@@ -30,13 +30,29 @@ struct CholTcParams {
   uint32_t code[2];   // coding of each genetic column: values of genotypes 0, 1, 2 in bytes 0-2
   float tm[4];        // gp = 2: reported coefficients = tm (row-major 2 x 2) x working ones
   int pieces;         // BF16 pieces of trait j's split matrix (2 or 3), rpad rows each
+  int fp8;            // nonzero: trait j's split is FP16 hi (lmaps.m) + E4M3 lo (lmaps.m8)
+  // fp8: the matrix has one more augmented row, w (row n + q + 1, below); row group g is held
+  // scaled by 2^e_g (g = 0: the rows of L^-1; g = 1 + k: augmented row n + k, k = 0 .. q + 1);
+  // unscale[g] = 2^-e_g.  lsa[k] = the sum of augmented row n + k's E4M3 lo piece (scaled), and
+  // k2 = sum over the rows r < n of lsum_r^2, lsum_r the sum of row r's lo piece (scaled).
+  // With the lo product taking uncentred codes, accumulator row r holds x'_r + mu lsum_r; the
+  // epilogue corrects s with w . (x - mu) = sum_r lsum_r x'_r (row n + q + 1 of the product):
+  // s = sum_r acc_r^2 - 2 mu (w . (x - mu)) - mu^2 k2, and a_k, c by -mu lsa[k].
+  float unscale[10];
+  float lsa[9];
+  double k2;
+  int naug;           // augmented rows below L^-1: q + 1, or q + 2 with fp8
 };
 constexpr int CHOL_TC_BM = 128;  // rows (SNP columns) per tile
 // Tensor maps of one trait's split augmented L^-1: rows = 2 * rpad (hi piece then lo piece),
 // cols = kpad, BF16, 128-byte swizzle, 64-column boxes of 256 - 64 j rows (m[j]: the rows
 // 64 j .. 255 of a block, which a K step on the block's diagonal meets).
+// With SPLIT_FP8, m[] covers the FP16 hi piece (rpad rows; the same boxes) and m8[] the E4M3 lo
+// piece: uint8 [rpad][kpad], 64-byte boxes of 256 - 64 j rows, 64-byte swizzle, its columns in
+// e4m3_k_slot order within each aligned group of 16.
 struct CholMaps {
   CUtensorMap m[4];
+  CUtensorMap m8[4];
 };
 // mapG: the 2-bit packed genotypes of the launch, uint8 [m][packed_row_bytes(n)], boxes of
 // 16 bytes x (128 / gp) rows, no swizzle.
@@ -44,6 +60,9 @@ void chol_tc_launch(cudaStream_t s, const CholMaps& lmaps, const CUtensorMap& ma
                     const CholTcParams& p, int num_sms);
 // uint8 map over packed genotype rows (boxes 16 bytes x box_rows rows).
 CUtensorMap make_map_packed(const void* base, int64_t rows, int row_bytes, int box_rows = 128);
+// uint8 map over [rows][cols] bytes (cols a multiple of 16, base 16-byte aligned), boxes of 64
+// bytes x box_rows rows, 64-byte swizzle; out-of-range reads are zero.
+CUtensorMap make_map_u8_sw64(const void* base, int64_t rows, int64_t cols, int box_rows);
 void chol_tc_prepare();
 // CTAs of the CHOL kernel that fit on the device at once (after chol_tc_prepare).
 int chol_tc_resident_ctas(int q);

@@ -8,6 +8,8 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 namespace gw {
@@ -156,10 +158,43 @@ __device__ __forceinline__ uint64_t sw128_desc(const void* tile) {
   return d;
 }
 
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 64 bytes: 64 FP8 values),
+// 8-row atoms 512 bytes apart.  Within an atom, 16-byte chunk c of row r sits at chunk
+// c ^ ((r >> 1) & 3): address bits 4-5 are XORed with bits 7-8, the layout a TMA load with
+// CU_TENSOR_MAP_SWIZZLE_64B produces.
+__device__ __forceinline__ uint64_t sw64_desc(const void* tile) {
+  const uint64_t addr = smem_u32(tile);
+  uint64_t d = 0;
+  d |= (addr & 0x3FFFFull) >> 4;        // start address
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;      // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;               // fixed 0b001 (descriptor version)
+  d |= (uint64_t)4 << 61;               // 64-byte swizzle
+  return d;
+}
+
 // Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both operands K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of kind::f16 with FP16 x FP16 -> FP32 (format code 0 for A and B), both
+// K-major.  The same bits describe E4M3 x E4M3 -> FP32 under kind::f8f6f4 (E4M3 is code 0 there).
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (FP32, TMEM) (+)= A B^T with 8-bit operands (kind::f8f6f4; K = 32 per instruction, i.e. 32
+// bytes of each operand row).  Accumulates into the same TMEM columns as kind::f16 products.
+__device__ __forceinline__ void mma_fp8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
@@ -290,6 +325,69 @@ __device__ __forceinline__ void coded_lut(float mu, uint32_t code, uint32_t& lo,
     lo |= (b & 0xFFu) << (8 * g);
     hi |= (b >> 8) << (8 * g);
   }
+}
+
+// FP16 form of coded_lut: byte tables of cd(g) - mu (g = 0, 1, 2) as FP16 values, exact when mu
+// is a multiple of 1/64 in [0, 2] (eight significant bits at most; FP16 carries eleven).
+__device__ __forceinline__ void coded_lut_f16(float mu, uint32_t code, uint32_t& lo, uint32_t& hi) {
+  lo = 0u;
+  hi = 0u;
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const float v = (float)((code >> (8 * g)) & 0xFFu) - mu;
+    const uint32_t b = __half_as_ushort(__float2half_rn(v));
+    lo |= (b & 0xFFu) << (8 * g);
+    hi |= (b >> 8) << (8 * g);
+  }
+}
+
+// Byte table of the uncentred coded genotype cd(g) in E4M3 (g = 0, 1, 2; cd(g) in {0, 1, 2}:
+// 0x00, 0x38 = 1.0, 0x40 = 2.0, all exact), byte g; byte 3 (the invalid code) is 0.
+__device__ __forceinline__ uint32_t coded_e4m3_table(uint32_t code) {
+  uint32_t t = 0u;
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const uint32_t v = (code >> (8 * g)) & 0xFFu;
+    t |= (v == 0u ? 0x00u : v == 1u ? 0x38u : 0x40u) << (8 * g);
+  }
+  return t;
+}
+
+// Sixteen 2-bit genotype codes (one 32-bit word of a packed row, call i in bits 2i..2i+1) ->
+// sixteen E4M3 bytes by table lookup, in the order of calls 0 2 4 6 1 3 5 7 8 10 12 14 9 11 13 15:
+// w & 0x33333333 holds the even calls one per nibble and (w >> 2) & 0x33333333 the odd ones, so
+// each byte permute turns four nibbles into four table bytes.  The 8-bit operand it feeds has
+// its K columns stored in the same order within every aligned group of 16 (e4m3_k_slot).
+__device__ __forceinline__ uint4 packed16_to_e4m3x16(uint32_t w, uint32_t table) {
+  const uint32_t ev = w & 0x33333333u, od = (w >> 2) & 0x33333333u;
+  return make_uint4(__byte_perm(table, 0u, ev), __byte_perm(table, 0u, od),
+                    __byte_perm(table, 0u, ev >> 16), __byte_perm(table, 0u, od >> 16));
+}
+
+// Sixteen E4M3 values (as from packed16_to_e4m3x16) -> sixteen FP16 values v - mu, in the same
+// order: each pair of bytes is widened by one e4m3x2 -> f16x2 conversion and mu2 (mu in both
+// halves) subtracted.  Exact for v in {0, 1, 2} and mu a multiple of 1/64 in [0, 2].
+__device__ __forceinline__ void e4m3x16_to_f16_centred(uint4 e, __half2 mu2, uint4& lo8,
+                                                       uint4& hi8) {
+  const uint32_t w[4] = {e.x, e.y, e.z, e.w};
+  uint32_t o[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const __half2_raw r = __nv_cvt_fp8x2_to_halfraw2(
+          (__nv_fp8x2_storage_t)((w[i] >> (16 * h)) & 0xFFFFu), __NV_E4M3);
+      const __half2 v = __hsub2(__half2(r), mu2);
+      o[2 * i + h] = *reinterpret_cast<const uint32_t*>(&v);
+    }
+  }
+  lo8 = make_uint4(o[0], o[1], o[2], o[3]);
+  hi8 = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
+// Position, within its aligned group of 16 K columns, at which packed16_to_e4m3x16 places call i.
+__host__ __device__ constexpr int e4m3_k_slot(int i) {
+  return (i & 8) | ((i & 1) << 2) | ((i >> 1) & 3);
 }
 
 // Counts of codes 1 and 2 in a word of sixteen 2-bit genotype codes (code 3 counts as neither).

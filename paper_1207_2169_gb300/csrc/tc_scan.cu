@@ -70,6 +70,29 @@ CUtensorMap make_map_packed(const void* base, int64_t rows, int row_bytes, int b
   return m;
 }
 
+// 2-D uint8 map over [rows][cols] bytes, boxes of 64 bytes x box_rows rows, 64-byte swizzle.
+CUtensorMap make_map_u8_sw64(const void* base, int64_t rows, int64_t cols, int box_rows) {
+  GW_REQUIRE(cols % 16 == 0 && ((uintptr_t)base & 15) == 0 && box_rows >= 1 && box_rows <= 256,
+             GWAS_ERR_ARG, "tensor map arguments not TMA-aligned");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims,
+                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  GW_REQUIRE(r == CUDA_SUCCESS, GWAS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return m;
+}
+
+// Per-trait constants of the FP16 + E4M3 split (SPLIT_FP8): see CholTcParams.
+struct FP8Consts {
+  std::vector<float> unscale, lsa;
+  double k2 = 0.0;
+};
+
 struct TcState {
   int algo = 0, n = 0, q = 0, t = 0;
   int kpad = 0, rpad = 0, num_sms = 0;
@@ -77,7 +100,11 @@ struct TcState {
   // CHOL, per trait: split L^-1 (hi rows then lo rows) and its tensor maps
   std::vector<CholMaps> lmaps;
   std::vector<int> lpieces;         // split pieces of each trait's matrix (2 or 3)
+  std::vector<uint8_t> lfp8;        // trait's split is FP16 hi + E4M3 lo (SPLIT_FP8)
+  std::vector<FP8Consts> lconst;    // per trait: the FP8 split's scales and lo-row sums
   __nv_bfloat16* Lsplit = nullptr;  // per trait (pieces rpad) x kpad, traits one after another
+                                    // (an FP8 trait: its FP16 hi piece, then the E4M3 lo bytes
+                                    // in the space of half a piece)
   const double* P = nullptr;        // t x q x q (owned by the handle)
   const double* b0 = nullptr;       // t x q
   // EIG: split operands, FP32 null-model blocks, per-block scratch and tensor maps
@@ -138,20 +165,97 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
       // Per trait, the split rows of [L^-1; (M^-1 X_L)^T; (M^-1 r)^T]: M^-1 X_L = L^-T (L^-1 X_L)
       // and M^-1 r = L^-T (L^-1 r) are linear in the genotypes, so the whitening product also
       // yields a_k and c (Algorithm 3) in q + 1 extra accumulator columns.
-      st->rpad = (int)round_up(n + q + 1, 256);
+      // (SPLIT_FP8: one more augmented row, w)
+      st->rpad = (int)round_up(n + q + 1 + (a.fp8_lo ? 1 : 0), 256);
       const size_t piece = (size_t)st->rpad * st->kpad;  // elements of one piece
       size_t total = 0;
       for (int j = 0; j < t; ++j) {
         st->lpieces.push_back(a.pieces && a.pieces[j] == 3 ? 3 : 2);
-        total += piece * st->lpieces[j];
+        st->lfp8.push_back(a.fp8_lo && st->lpieces[j] == 2 ? 1 : 0);
+        total += st->lfp8[j] ? piece + piece / 2 : piece * st->lpieces[j];
       }
       st->Lsplit = (__nv_bfloat16*)tc_alloc(st, total * 2);
       GW_CUDA(cudaMemsetAsync(st->Lsplit, 0, total * 2, s));
       double* Ut = (double*)tc_alloc(st, (size_t)(q + 1) * n * 8);
+      double* rmax = nullptr;  // FP8: row maxima, row scales, w (natural column order)
+      float* ls = nullptr;      // FP8: the sums of the lo rows of one trait
+      if (a.fp8_lo) {
+        rmax = (double*)tc_alloc(st, (size_t)(3 * n + 2 * (q + 2)) * 8);
+        ls = (float*)tc_alloc(st, (size_t)(n + q + 2) * 4);
+      }
       size_t off = 0;
       for (int j = 0; j < t; ++j) {
         const int np = st->lpieces[j];
         const double* Li = a.Linv + (size_t)j * n * n;
+        if (st->lfp8[j]) {
+          // FP16 hi + E4M3 lo.  Row groups (the rows of L^-1; each augmented row) are scaled by
+          // powers of two that bring their largest magnitude into (2^13, 2^14]: FP16 keeps its
+          // full precision there and lo (<= 2^-11 of it) stays inside E4M3's range.  One more
+          // augmented row, w = sum_{r < n} lsum_r (hi + lo)_r (lsum_r: the sum of row r's lo
+          // piece), lets the epilogue remove the centring term the lo product misses.
+          __half* hi = reinterpret_cast<__half*>(st->Lsplit + off);
+          uint8_t* lo = reinterpret_cast<uint8_t*>(st->Lsplit + off + piece);
+          off += piece + piece / 2;
+          gemm_f64(s, q, n, n, 1.0, a.XLw + (size_t)j * q * n, n, 1, Li, n, 1, 0.0, Ut, n, 1);
+          gemm_f64(s, 1, n, n, 1.0, a.rw + (size_t)j * n, n, 1, Li, n, 1, 0.0,
+                   Ut + (size_t)q * n, n, 1);
+          const int na = q + 2;  // augmented rows: X_L's q, the residual, w
+          double* dmax = rmax;
+          double* dsc = rmax + (n + na);
+          double* wnat = rmax + 2 * (n + na);
+          rowmax_abs(s, Li, n, n, n, dmax);
+          rowmax_abs(s, Ut, q + 1, n, n, dmax + n);
+          std::vector<double> hm(n + na), hs(n + na);
+          GW_CUDA(cudaMemcpyAsync(hm.data(), dmax, (size_t)(n + q + 1) * 8, cudaMemcpyDeviceToHost, s));
+          GW_CUDA(cudaStreamSynchronize(s));
+          auto exp_of = [](double mx) { return mx > 0.0 ? 14 - (int)ceil(log2(mx)) : 0; };
+          double mL = 0.0;
+          for (int r = 0; r < n; ++r) mL = hm[r] > mL ? hm[r] : mL;
+          std::vector<float> us(na + 1);
+          const int eL = exp_of(mL);
+          us[0] = ldexpf(1.f, -eL);
+          for (int r = 0; r < n; ++r) hs[r] = ldexp(1.0, eL);
+          for (int k = 0; k <= q; ++k) {
+            const int e = exp_of(hm[n + k]);
+            us[1 + k] = ldexpf(1.f, -e);
+            hs[n + k] = ldexp(1.0, e);
+          }
+          GW_CUDA(cudaMemcpyAsync(dsc, hs.data(), (size_t)(n + q + 1) * 8, cudaMemcpyHostToDevice, s));
+          const size_t aug = (size_t)n * st->kpad;
+          split_f16_e4m3(s, Li, n, n, n, dsc, hi, lo, st->kpad);
+          split_f16_e4m3(s, Ut, q + 1, n, n, dsc + n, hi + aug, lo + aug, st->kpad);
+          e4m3_row_sums(s, lo, n + q + 1, st->kpad, ls);
+          e4m3_weighted_col_sums(s, hi, lo, n, st->kpad, n, ls, wnat);
+          rowmax_abs(s, wnat, 1, n, n, dmax + n + q + 1);
+          GW_CUDA(cudaMemcpyAsync(hm.data() + n + q + 1, dmax + n + q + 1, 8,
+                                  cudaMemcpyDeviceToHost, s));
+          GW_CUDA(cudaStreamSynchronize(s));
+          const int ew = exp_of(hm[n + q + 1]);
+          us[na] = ldexpf(1.f, -ew);
+          hs[n + q + 1] = ldexp(1.0, ew);
+          GW_CUDA(cudaMemcpyAsync(dsc + n + q + 1, &hs[n + q + 1], 8, cudaMemcpyHostToDevice, s));
+          const size_t wrow = (size_t)(n + q + 1) * st->kpad;
+          split_f16_e4m3(s, wnat, 1, n, n, dsc + n + q + 1, hi + wrow, lo + wrow, st->kpad);
+          e4m3_row_sums(s, lo + wrow, 1, st->kpad, ls + n + q + 1);
+          std::vector<float> hls(n + na);
+          GW_CUDA(cudaMemcpyAsync(hls.data(), ls, hls.size() * 4, cudaMemcpyDeviceToHost, s));
+          // the stream must be done with hs before the next trait reuses the buffers
+          GW_CUDA(cudaStreamSynchronize(s));
+          FP8Consts fc;
+          fc.unscale = us;
+          fc.lsa.assign(hls.begin() + n, hls.end());
+          fc.k2 = 0.0;
+          for (int r = 0; r < n; ++r) fc.k2 += (double)hls[r] * hls[r];
+          st->lconst.push_back(fc);
+          CholMaps mp;
+          for (int r = 0; r < 4; ++r) {
+            mp.m[r] = make_map_bf16(hi, st->rpad, st->kpad, 256 - 64 * r);
+            mp.m8[r] = make_map_u8_sw64(lo, st->rpad, st->kpad, 256 - 64 * r);
+          }
+          st->lmaps.push_back(mp);
+          continue;
+        }
+        st->lconst.push_back(FP8Consts());
         __nv_bfloat16* hi = st->Lsplit + off;
         __nv_bfloat16* lo = hi + piece;
         __nv_bfloat16* lo2 = np == 3 ? lo + piece : nullptr;
@@ -163,13 +267,20 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
         const size_t aug = (size_t)n * st->kpad;  // the q + 1 augmented rows follow L^-1's n
         split_bf16(s, Ut, q + 1, n, n, hi + aug, lo + aug, st->kpad, lo2 ? lo2 + aug : nullptr);
         CholMaps mp;
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 4; ++r) {
           mp.m[r] = make_map_bf16(hi, (int64_t)np * st->rpad, st->kpad, 256 - 64 * r);
+          mp.m8[r] = mp.m[r];  // unused
+        }
         st->lmaps.push_back(mp);
       }
       GW_CUDA(cudaStreamSynchronize(s));
       cudaFree(Ut);
       st->allocs.erase(std::find(st->allocs.begin(), st->allocs.end(), (void*)Ut));
+      for (void* tmp : {(void*)rmax, (void*)ls}) {
+        if (!tmp) continue;
+        cudaFree(tmp);
+        st->allocs.erase(std::find(st->allocs.begin(), st->allocs.end(), tmp));
+      }
       chol_tc_prepare();
       return st;
     }
@@ -265,6 +376,14 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
       p.code[1] = st->gm.code_word(1);
       for (int e = 0; e < 4; ++e) p.tm[e] = st->gm.tm[e / 2][e % 2];
       p.pieces = st->lpieces[j];
+      p.fp8 = st->lfp8[j];
+      p.naug = st->q + 1 + (p.fp8 ? 1 : 0);
+      if (p.fp8) {
+        const FP8Consts& fc = st->lconst[j];
+        for (size_t g = 0; g < fc.unscale.size() && g < 10; ++g) p.unscale[g] = fc.unscale[g];
+        for (size_t g = 0; g < fc.lsa.size() && g < 9; ++g) p.lsa[g] = fc.lsa[g];
+        p.k2 = fc.k2;
+      }
       p.B = a.B;
       p.W = a.wald;
       p.flags = a.flags;
@@ -339,6 +458,13 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     eig_tc_launch(s, 2, st->mapU, st->mapU, mapG, p, ctas);
     if (ev) tm->end(s, ev);
   }
+}
+
+int tc_fp8_traits(const TcState* st) {
+  int k = 0;
+  if (st)
+    for (uint8_t v : st->lfp8) k += v;
+  return k;
 }
 
 int tc_split_pieces(const TcState* st) {
