@@ -119,7 +119,11 @@ __device__ __forceinline__ int row_snp(int r) { return GP == 1 ? r : (r >> 5) * 
 template <int GP>
 __device__ __forceinline__ int row_col(int r) { return GP == 1 ? 0 : (r >> 4) & 1; }
 
-// (tile, block, k-step) sequence shared by every role of a CTA.
+// (tile, block, k-step) sequence shared by every role of a CTA.  A tile's blocks run from the
+// last (the longest K range) down to the first: after a tile's last block the epilogue has its
+// per-tile work to do (the bordered solves of the tile, the centres of a later tile) while the
+// tensor cores start the next tile, and the two longest blocks give it the most time to do it
+// before it must hand an accumulator back.
 struct Step {
   int64_t tile;
   int nb, ks;
@@ -127,8 +131,8 @@ struct Step {
 __device__ __forceinline__ void advance(Step& s, int nblocks, int kpad) {
   if (++s.ks < ksteps(s.nb, kpad)) return;
   s.ks = 0;
-  if (++s.nb < nblocks) return;
-  s.nb = 0;
+  if (--s.nb >= 0) return;
+  s.nb = nblocks - 1;
   s.tile += gridDim.x;
 }
 
@@ -328,7 +332,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int bs = 0;
       uint32_t bph = 0;
       bool ok = true;
-      for (Step st{blockIdx.x, 0, 0}; st.tile < tiles_run && ok; advance(st, nblocks, p.kpad)) {
+      for (Step st{blockIdx.x, nblocks - 1, 0}; st.tile < tiles_run && ok;
+           advance(st, nblocks, p.kpad)) {
         const int j = diag_skip(st.nb, st.ks);  // rows 64 j .. 255 of the block
         if constexpr (F8) {
           // one slot: the FP16 hi tile, then the E4M3 lo tile (64-byte rows)
@@ -358,7 +363,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       // converters consume them; rows past m read as zero
       int ps = 0;
       uint32_t pph = 0;
-      for (Step st{blockIdx.x, 0, 0}; st.tile < tiles_run; advance(st, nblocks, p.kpad)) {
+      for (Step st{blockIdx.x, nblocks - 1, 0}; st.tile < tiles_run; advance(st, nblocks, p.kpad)) {
+        if (st.nb == nblocks - 1 && st.ks == 0) {
+          // two tiles ahead, the rows into L2: their slices, and the epilogue's reads of them
+          // for the SNP centres, then hit L2 instead of waiting on DRAM
+          const int64_t t2 = st.tile + 2 * (int64_t)gridDim.x;
+          if (t2 < tiles_run) {
+            const int64_t r0 = t2 * TS, r1 = r0 + TS < p.m ? r0 + TS : p.m;
+            prefetch_l2_range(p.G + r0 * p.row_bytes, p.G + r1 * p.row_bytes);
+          }
+        }
         if (!mbar_wait(&bars->pk_empty[ps], pph ^ 1, abort, tflag, WAIT_NS)) break;
         mbar_arrive_expect_tx(&bars->pk_full[ps], PKB);
         tma_load_2d(sP + ps * PK_BYTES, &mapG, &bars->pk_full[ps], st.ks * 16,
@@ -373,7 +387,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t aph = 0, bph = 0, accph = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < tiles_run && ok; tile += gridDim.x) {
-        for (int nb = 0; nb < nblocks && ok; ++nb) {
+        for (int nb = nblocks - 1; nb >= 0 && ok; --nb) {
           ok = mbar_wait(&bars->acc_empty[buf], accph ^ 1, abort, tflag, WAIT_NS);
           if (!ok) break;
           tc_fence_after();
@@ -563,38 +577,35 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       float A[QM], C = 0.f, Wd = 0.f;  // Wd (FP8 variant): w . (x - mu) + mu lsa[q + 1]
 #pragma unroll
       for (int k = 0; k < QM; ++k) A[k] = 0.f;
-      for (int nb = 0; nb < nblocks; ++nb) {
+      for (int nb = nblocks - 1; nb >= 0; --nb) {
         if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full[buf], accph, abort, tflag, WAIT_NS));
         if (ok) {
           tc_fence_after();
           const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + buf * BN;
           const int c0 = nb * BN, ncols = block_cols(nb, n, p.naug);
-          float bs_ = 0.f, bx_ = 0.f;
-          uint32_t ra[32];
-#pragma unroll 1
-          for (int c = 0; c < ncols; c += 32) {
-            tmem_ld32_async(base + c, ra);
-            tmem_wait32(ra);
-            float ss = 0.f, xs = 0.f;
+          // four partial sums each (no serial FMA chain); chunks of 32 columns loaded one
+          // ahead of the one being summed
+          float ss[4] = {0.f, 0.f, 0.f, 0.f}, xs[4] = {0.f, 0.f, 0.f, 0.f};
+          auto sum_chunk = [&](const uint32_t (&ra)[32], int c) {
             if (c0 + c + 32 <= n) {
 #pragma unroll
               for (int i = 0; i < 32; ++i) {
                 const float x = __uint_as_float(ra[i]);
-                ss = fmaf(x, x, ss);
+                ss[i & 3] = fmaf(x, x, ss[i & 3]);
                 // the partner row (the SNP's other genetic column) is 16 lanes away
-                if (GP == 2) xs = fmaf(x, __shfl_xor_sync(0xffffffffu, x, 16), xs);
+                if (GP == 2) xs[i & 3] = fmaf(x, __shfl_xor_sync(0xffffffffu, x, 16), xs[i & 3]);
               }
             } else {
-              // the chunk holding row n: genotype columns, then a_0 .. a_{q-1}, c
+              // the chunk holding row n: genotype columns, then a_0 .. a_{q-1}, c (and w)
 #pragma unroll
               for (int i = 0; i < 32; ++i) {
                 const int col = c0 + c + i;
                 const float x = __uint_as_float(ra[i]);
                 if (GP == 2) {
                   const float xp = __shfl_xor_sync(0xffffffffu, x, 16);
-                  if (col < n) xs = fmaf(x, xp, xs);
+                  if (col < n) xs[i & 3] = fmaf(x, xp, xs[i & 3]);
                 }
-                if (col < n) ss = fmaf(x, x, ss);
+                if (col < n) ss[i & 3] = fmaf(x, x, ss[i & 3]);
 #pragma unroll
                 for (int k = 0; k < QM; ++k)
                   if (k < q && col == n + k) A[k] = x;
@@ -602,14 +613,48 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 if (F8 && col == n + q + 1) Wd = x;
               }
             }
-            bs_ += ss;
-            bx_ += xs;
+          };
+          // every column of the block is in registers: hand the accumulator back to the issuer
+          auto release = [&]() {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
+          };
+          if constexpr (QM <= 3) {
+            uint32_t ra[32], rb[32];
+            tmem_ld32_async(base, ra);
+#pragma unroll 1
+            for (int c = 0; c < ncols; c += 64) {
+              const bool second = c + 32 < ncols;
+              tmem_wait32(ra);
+              if (second)
+                tmem_ld32_async(base + c + 32, rb);
+              else
+                release();
+              sum_chunk(ra, c);
+              if (second) {
+                tmem_wait32(rb);
+                if (c + 64 < ncols)
+                  tmem_ld32_async(base + c + 64, ra);
+                else
+                  release();
+                sum_chunk(rb, c + 32);
+              }
+            }
+          } else {
+            // q > 3: the registers of a second chunk are not to be had (the warps of an SMSP
+            // share its 16 K registers: 128 per thread here), so one chunk at a time
+            uint32_t ra[32];
+#pragma unroll 1
+            for (int c = 0; c < ncols; c += 32) {
+              tmem_ld32_async(base + c, ra);
+              tmem_wait32(ra);
+              if (c + 32 >= ncols) release();
+              sum_chunk(ra, c);
+            }
           }
-          S += bs_;
-          X += bx_;
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
+          S += (double)((ss[0] + ss[1]) + (ss[2] + ss[3]));
+          X += (double)((xs[0] + xs[1]) + (xs[2] + xs[3]));
         }
         if (++buf == 2) { buf = 0; accph ^= 1; }
       }
