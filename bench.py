@@ -268,11 +268,12 @@ def kernel_roofline(s, m, stage, ms_total, launches, peak_tf, peak_src, steps, p
     """Roofline entry of one kernel stage from its CUDA-event time over the timed region."""
     alg = stage_flops(s, m)[stage] * steps
     exe = stage_executed(s, m, pieces, fp8)[stage] * steps
-    per, unit = traffic_per_unit(KERNEL_NAMES[stage])
+    name = KERNEL_NAMES[stage] + ("<F8>" if fp8 else "")
+    per, unit = traffic_per_unit(name)
     units = m * steps * (s["t"] if unit == "pair" else 1)
     sec = ms_total * 1e-3
     achieved = alg / sec / 1e12
-    return {"bound": "tensor", "kernel": KERNEL_NAMES[stage],
+    return {"bound": "tensor", "kernel": name,
             "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
             "traffic": None if per is None else per * units / launches,
             "peak_source": peak_src, "launches": launches, "ms_per_launch": ms_total / launches,
@@ -299,7 +300,7 @@ def rooflines(s, m, stages, steps, precision, pieces=2, fp8=False):
                for st in (["chol"] if s["algo"] == "chol" else ["rot", "sq", "ac"]) if st in stages]
     if fp8:
         for e in entries:
-            if e["kernel"] == "chol_tc_kernel":
+            if e["kernel"] == "chol_tc_kernel<F8>":
                 e["note"] = ("FP16 hi x FP16 centred genotypes plus E4M3 lo x E4M3 genotypes into "
                              "one accumulator; executed FLOPs count the E4M3 product at half "
                              "weight (its nominal rate is twice the BF16 one)")
