@@ -690,6 +690,7 @@ def measure_batch(local, ws, steps, warmup, m=None):
         stream = torch.cuda.current_stream()
         g.gwas_scan_batch(b, blocks, stream=stream.cuda_stream)  # picks the launch plan
         plan, plan_ms = g.gwas_batch_plan(b)
+        tuning = g.gwas_batch_tuning(b)
         torch.cuda.synchronize()
         eb = ew = 0.0
         for (snps, j, Xs), c, (G, B, W) in zip(samples, cohorts, blocks):
@@ -745,6 +746,9 @@ def measure_batch(local, ws, steps, warmup, m=None):
         "batch": {"plan": plan, "plan_ms": plan_ms,
                   "plans": ["sequential", "concurrent, SM shares by work", "concurrent, all SMs",
                             "two lanes of half the SMs"],
+                  "eig_chunk_div": tuning["chunk_div"],
+                  "tuning_ms_by_chunk_div_and_plan": tuning["ms"],
+                  "gain_of_chunk_tuning": min(tuning["ms"][0]) / min(min(r) for r in tuning["ms"]),
                   "per_cohort_calls_ms": ms_seq, "speedup_vs_per_cohort_calls": ms_seq / ms,
                   "split_pieces": pieces},
         "roofline": {"bound": "tensor", "kernel": "whole batched step (16 cohorts' EIG kernels)",

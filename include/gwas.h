@@ -289,8 +289,16 @@ gwas_status gwas_setup_batch(int n_cohorts, const gwas_cohort* cohorts, const gw
  * Genotypes are not validated; use gwas_scan_packed with validate_genotypes for that. */
 gwas_status gwas_scan_batch(gwas_batch b, const gwas_cohort_block* blocks, void* stream);
 
-/* The chosen plan (0-3, -1 before the first scan) and the time of each plan (ms, 4 values). */
+/* The chosen plan (0-3, -1 before the first scan) and the time of each plan (ms, 4 values) with
+ * the chosen EIG chunk. */
 gwas_status gwas_batch_plan(gwas_batch b, int* plan, double* plan_ms);
+
+/* The whole tuning of the last new block shape: the chosen plan, the chosen EIG chunk divisor d
+ * (each EIG cohort's scan takes its SNPs in chunks of its scratch capacity / 2^d, d = 0, 1, 2;
+ * gwas_eig_chunk gives the SNPs), and the time (ms) of every (d, plan) candidate in
+ * ms[d * 4 + plan] (12 values).  The autotuner of the batched launch (no counterpart in the
+ * paper, which runs one cohort at a time). */
+gwas_status gwas_batch_tuning(gwas_batch b, int* plan, int* chunk_div, double* ms);
 
 /* The handle of cohort i (for gwas_info, gwas_singular_count; owned by the batch), or NULL. */
 gwas_handle gwas_batch_handle(gwas_batch b, int i);
@@ -370,6 +378,11 @@ int gwas_split_pieces(gwas_handle h);
  * trait whose M_j is not badly conditioned; the others take three BF16 pieces); 0 for other
  * precisions and for EIG; -1 for a NULL handle. */
 int gwas_fp8_traits(gwas_handle h);
+
+/* EIG tensor-core handles: SNPs per internal chunk of a scan (one launch of each EIG kernel per
+ * chunk; set by setup, or by the batch tuner for a batch's cohorts); 0 for other handles; -1 for
+ * a NULL handle. */
+int64_t gwas_eig_chunk(gwas_handle h);
 
 /* Number of singular pairs (written as NaN) seen by completed scans of this handle, or -1. */
 int64_t gwas_singular_count(gwas_handle h);

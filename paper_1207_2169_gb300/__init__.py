@@ -32,7 +32,8 @@ EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_wald_pvalues_dof",
            "gwas_estimate",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
-           "gwas_genetic_columns", "gwas_split_pieces", "gwas_fp8_traits", "gwas_stream_info",
+           "gwas_genetic_columns", "gwas_split_pieces", "gwas_fp8_traits", "gwas_eig_chunk",
+           "gwas_batch_tuning", "gwas_stream_info",
            "gwas_stage_timing", "gwas_stage_times", "gwas_last_error", "gwas_destroy"]
 
 STAGES = ["pack", "centres", "chol", "rot", "sq", "ac", "simt"]
@@ -117,6 +118,10 @@ def _load():
     lib.gwas_split_pieces.restype = i32
     lib.gwas_fp8_traits.argtypes = [vp]
     lib.gwas_fp8_traits.restype = i32
+    lib.gwas_eig_chunk.argtypes = [vp]
+    lib.gwas_eig_chunk.restype = i64
+    lib.gwas_batch_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), dp]
+    lib.gwas_batch_tuning.restype = i32
     lib.gwas_genetic_columns.argtypes = [vp]
     lib.gwas_genetic_columns.restype = i32
     lib.gwas_singular_count.argtypes = [vp]
@@ -423,6 +428,20 @@ def gwas_split_pieces(h) -> int:
 
 def gwas_fp8_traits(h) -> int:
     return int(lib.gwas_fp8_traits(h))
+
+
+def gwas_eig_chunk(h) -> int:
+    return int(lib.gwas_eig_chunk(h))
+
+
+def gwas_batch_tuning(b) -> dict:
+    """The batch autotuner's choice for the last new block shape: plan, EIG chunk divisor and
+    the time of every (divisor, plan) candidate (ms)."""
+    plan, div = ctypes.c_int(), ctypes.c_int()
+    ms = (ctypes.c_double * 12)()
+    _check(lib.gwas_batch_tuning(b, ctypes.byref(plan), ctypes.byref(div), ms), "gwas_batch_tuning")
+    return {"plan": plan.value, "chunk_div": div.value,
+            "ms": [[ms[4 * d + i] for i in range(4)] for d in range(3)]}
 
 
 def gwas_stream_info(h) -> dict:

@@ -1159,6 +1159,11 @@ GW_API gwas_status gwas_stream_info(gwas_handle h, int* block_snps, int* tuned,
   return GWAS_OK;
 }
 
+GW_API int64_t gwas_eig_chunk(gwas_handle h) {
+  if (!h) return -1;
+  return h->tc ? tc_eig_chunk(h->tc) : 0;
+}
+
 GW_API int gwas_fp8_traits(gwas_handle h) { return h ? (h->tc ? tc_fp8_traits(h->tc) : 0) : -1; }
 
 GW_API int gwas_split_pieces(gwas_handle h) {

@@ -8,6 +8,9 @@
 //   1  all at once, one stream each, each kernel capped at an SM share proportional to its work;
 //   2  all at once, one stream each, every kernel with every SM (the hardware interleaves CTAs);
 //   3  two lanes of half the SMs each, cohorts assigned longest first to the less loaded lane.
+// Each plan is timed with the EIG cohorts' internal SNP chunk (one ROT, SQ and AC launch per
+// chunk) at its capacity, half and a quarter of it: shorter launches interleave better when the
+// cohorts share the SMs, longer ones waste less at launch boundaries when they run alone.
 #include <algorithm>
 #include <atomic>
 #include <thread>
@@ -31,6 +34,7 @@ using namespace gw;
 
 namespace {
 constexpr int NPLANS = 4;
+constexpr int NCHUNK = 3;  // EIG chunk = capacity / 2^i, i < NCHUNK
 }
 
 struct gwas_batch_s {
@@ -42,8 +46,8 @@ struct gwas_batch_s {
   cudaEvent_t ev_fork = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
   // the graph of the current block shape
   std::vector<int64_t> shape;  // m per cohort
-  int plan = -1;
-  double plan_ms[NPLANS] = {0, 0, 0, 0};
+  int plan = -1, chunk_div = 0;  // chosen plan; chosen chunk = capacity >> chunk_div
+  double plan_ms[NCHUNK][NPLANS] = {};
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -181,27 +185,38 @@ gwas_status scan_batch_impl(gwas_batch b, const gwas_cohort_block* blk, cudaStre
         b->exec = nullptr;
       }
       double best = 0.0;
-      for (int plan = 0; plan < NPLANS; ++plan) {
-        cudaGraph_t g = capture_plan(b, blk, plan);
-        cudaGraphExec_t e = instantiate(g);
-        cudaGraphDestroy(g);
-        GW_CUDA(cudaGraphLaunch(e, s));
-        GW_CUDA(cudaEventRecord(b->ev_t0, s));
-        GW_CUDA(cudaGraphLaunch(e, s));
-        GW_CUDA(cudaEventRecord(b->ev_t1, s));
-        GW_CUDA(cudaEventSynchronize(b->ev_t1));
-        float ms = 0.f;
-        GW_CUDA(cudaEventElapsedTime(&ms, b->ev_t0, b->ev_t1));
-        b->plan_ms[plan] = ms;
-        if (!b->exec || ms < best) {
-          if (b->exec) cudaGraphExecDestroy(b->exec);
-          b->exec = e;
-          b->plan = plan;
-          best = ms;
-        } else {
-          cudaGraphExecDestroy(e);
+      auto set_chunks = [&](int div) {
+        for (gwas_handle h : b->h) {
+          TcState* st = handle_tc(h);
+          tc_set_eig_chunk(st, tc_eig_chunk_capacity(st) >> div);
+        }
+      };
+      for (int div = 0; div < NCHUNK; ++div) {
+        set_chunks(div);
+        for (int plan = 0; plan < NPLANS; ++plan) {
+          cudaGraph_t g = capture_plan(b, blk, plan);
+          cudaGraphExec_t e = instantiate(g);
+          cudaGraphDestroy(g);
+          GW_CUDA(cudaGraphLaunch(e, s));
+          GW_CUDA(cudaEventRecord(b->ev_t0, s));
+          GW_CUDA(cudaGraphLaunch(e, s));
+          GW_CUDA(cudaEventRecord(b->ev_t1, s));
+          GW_CUDA(cudaEventSynchronize(b->ev_t1));
+          float ms = 0.f;
+          GW_CUDA(cudaEventElapsedTime(&ms, b->ev_t0, b->ev_t1));
+          b->plan_ms[div][plan] = ms;
+          if (!b->exec || ms < best) {
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            b->exec = e;
+            b->plan = plan;
+            b->chunk_div = div;
+            best = ms;
+          } else {
+            cudaGraphExecDestroy(e);
+          }
         }
       }
+      set_chunks(b->chunk_div);  // later re-captures of this shape use the chosen chunks
       b->shape = shape;
     }
   } catch (...) {
@@ -302,7 +317,20 @@ GW_API gwas_status gwas_batch_plan(gwas_batch b, int* plan, double* plan_ms) {
   }
   if (plan) *plan = b->plan;
   if (plan_ms)
-    for (int i = 0; i < NPLANS; ++i) plan_ms[i] = b->plan_ms[i];
+    for (int i = 0; i < NPLANS; ++i) plan_ms[i] = b->plan_ms[b->chunk_div][i];
+  return GWAS_OK;
+}
+
+GW_API gwas_status gwas_batch_tuning(gwas_batch b, int* plan, int* chunk_div, double* ms) {
+  if (!b) {
+    set_error("null batch");
+    return GWAS_ERR_ARG;
+  }
+  if (plan) *plan = b->plan;
+  if (chunk_div) *chunk_div = b->chunk_div;
+  if (ms)
+    for (int d = 0; d < NCHUNK; ++d)
+      for (int i = 0; i < NPLANS; ++i) ms[d * NPLANS + i] = b->plan_ms[d][i];
   return GWAS_OK;
 }
 

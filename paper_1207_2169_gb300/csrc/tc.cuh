@@ -55,5 +55,11 @@ double tc_scan_work(const TcState* st, int64_t m);
 int tc_split_pieces(const TcState* st);
 // Number of CHOL traits whose split is FP16 hi + E4M3 lo (SPLIT_FP8).
 int tc_fp8_traits(const TcState* st);
+// EIG: SNPs per internal chunk of a tensor-core scan (the ROT, SQ, AC launches cover one chunk
+// each), the most the per-chunk scratch holds, and a new chunk (clamped to [128, capacity],
+// rounded up to 128).  CHOL: 0 / no effect.
+int64_t tc_eig_chunk(const TcState* st);
+int64_t tc_eig_chunk_capacity(const TcState* st);
+void tc_set_eig_chunk(TcState* st, int64_t snps);
 
 }  // namespace gw

@@ -112,7 +112,8 @@ struct TcState {
   float *P32 = nullptr, *b032 = nullptr, *sbuf = nullptr;
   // EIG: per-SNP centres of the current chunk (NULL: no intercept, no centring)
   float* mu = nullptr;
-  int64_t mcap = 0;
+  int64_t mcap = 0;    // SNPs per chunk the scratch holds
+  int64_t chunk = 0;   // SNPs per chunk the scan uses (<= mcap; 0: mcap)
   bool intercept = false;
   int out_snp = 0;
   int out_var = 0;
@@ -394,8 +395,9 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     return;
   }
   const int n = st->n, q = st->q, t = st->t, q1 = q + 1;
-  for (int64_t off = 0; off < a.m; off += st->mcap) {
-    const int64_t mm = a.m - off < st->mcap ? a.m - off : st->mcap;
+  const int64_t ck = st->chunk > 0 && st->chunk < st->mcap ? st->chunk : st->mcap;
+  for (int64_t off = 0; off < a.m; off += ck) {
+    const int64_t mm = a.m - off < ck ? a.m - off : ck;
     EigTcParams p{};
     p.m = mm;
     p.n = n;
@@ -458,6 +460,21 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     eig_tc_launch(s, 2, st->mapU, st->mapU, mapG, p, ctas);
     if (ev) tm->end(s, ev);
   }
+}
+
+int64_t tc_eig_chunk(const TcState* st) {
+  if (!st || st->algo == GWAS_ALGO_CHOL) return 0;
+  return st->chunk > 0 && st->chunk < st->mcap ? st->chunk : st->mcap;
+}
+
+int64_t tc_eig_chunk_capacity(const TcState* st) {
+  return st && st->algo != GWAS_ALGO_CHOL ? st->mcap : 0;
+}
+
+void tc_set_eig_chunk(TcState* st, int64_t snps) {
+  if (!st || st->algo == GWAS_ALGO_CHOL) return;
+  snps = round_up(snps < 128 ? 128 : snps, 128);
+  st->chunk = snps < st->mcap ? snps : st->mcap;
 }
 
 int tc_fp8_traits(const TcState* st) {

@@ -72,6 +72,43 @@ def test_batch_equals_single_scans(g, cohorts):
         for (G, B, W), (G2, B2, W2) in zip(blocks, blocks2):
             assert torch.equal(B, B2) and torch.equal(W, W2)
         assert g.gwas_batch_plan(b)[0] == plan
+        # the tuner's table: 3 EIG chunk sizes x 4 plans, the chosen pair its fastest entry
+        tun = g.gwas_batch_tuning(b)
+        assert tun["plan"] == plan and tun["chunk_div"] in (0, 1, 2)
+        ms_all = np.array(tun["ms"])
+        assert ms_all.shape == (3, 4) and np.all(ms_all > 0)
+        assert ms_all[tun["chunk_div"], plan] == ms_all.min()
+        assert list(ms) == list(ms_all[tun["chunk_div"]])
+        for i, c in enumerate(cohorts):
+            ck = g.gwas_eig_chunk(g.gwas_batch_handle(b, i))
+            assert (ck == 0) if c.t == 1 else (ck > 0 and ck % 128 == 0)
+    finally:
+        g.gwas_destroy_batch(b)
+
+
+def test_batch_tuned_chunk_equals_single_scan(g):
+    """An EIG cohort longer than the smallest candidate chunk: whatever chunk the tuner keeps,
+    the batch gives exactly the results of the cohort's own scan (each SNP's arithmetic does not
+    depend on the chunk it falls in), and the chunk is capacity >> chunk_div."""
+    import torch
+    cs = [synth.small_problem(71, n=150, q=3, m=20000, t=9),
+          synth.small_problem(72, n=97, q=1, m=300, t=1)]
+    b = g.gwas_setup_batch([(c.Phi, c.XL, c.Y, c.h2, c.s2) for c in cs])
+    try:
+        blocks = _blocks(g, cs)
+        g.gwas_scan_batch(b, blocks)
+        torch.cuda.synchronize()
+        tun = g.gwas_batch_tuning(b)
+        h_single = g.gwas_setup(cs[0].Phi, cs[0].XL, cs[0].Y, cs[0].h2, cs[0].s2,
+                                precision="split_bf16")
+        try:
+            cap = g.gwas_eig_chunk(h_single)
+        finally:
+            g.gwas_destroy(h_single)
+        assert g.gwas_eig_chunk(g.gwas_batch_handle(b, 0)) == cap >> tun["chunk_div"]
+        for c, (G, B, W) in zip(cs, blocks):
+            Bs, Ws = _single(g, c)
+            assert np.array_equal(B.cpu().numpy(), Bs) and np.array_equal(W.cpu().numpy(), Ws)
     finally:
         g.gwas_destroy_batch(b)
 
