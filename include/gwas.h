@@ -379,6 +379,13 @@ int gwas_split_pieces(gwas_handle h);
  * precisions and for EIG; -1 for a NULL handle. */
 int gwas_fp8_traits(gwas_handle h);
 
+/* EIG tensor-core handles: the number of traits whose M_j is conditioned past the point where
+ * the EIG contraction's FP32 accumulation keeps 1e-4 (lam_max / lam_min of M_j above 500, e.g.
+ * h^2 near 1 on a kinship with many eigenvalues at its ridge).  Setup also factors those traits'
+ * M_j (Algorithm 3's setup), and every scan runs the CHOL kernel on them after the EIG kernels,
+ * overwriting their outputs; 0 for other handles, -1 for a NULL handle. */
+int gwas_chol_routed_traits(gwas_handle h);
+
 /* EIG tensor-core handles: SNPs per internal chunk of a scan (one launch of each EIG kernel per
  * chunk; set by setup, or by the batch tuner for a batch's cohorts); 0 for other handles; -1 for
  * a NULL handle. */

@@ -33,6 +33,7 @@ EXPORTS = ["gwas_default_options", "gwas_setup", "gwas_scan", "gwas_scan_f64",
            "gwas_estimate",
            "gwas_scan_static", "gwas_setup_timing", "gwas_info", "gwas_singular_count",
            "gwas_genetic_columns", "gwas_split_pieces", "gwas_fp8_traits", "gwas_eig_chunk",
+           "gwas_chol_routed_traits",
            "gwas_batch_tuning", "gwas_stream_info",
            "gwas_stage_timing", "gwas_stage_times", "gwas_last_error", "gwas_destroy"]
 
@@ -118,6 +119,8 @@ def _load():
     lib.gwas_split_pieces.restype = i32
     lib.gwas_fp8_traits.argtypes = [vp]
     lib.gwas_fp8_traits.restype = i32
+    lib.gwas_chol_routed_traits.argtypes = [vp]
+    lib.gwas_chol_routed_traits.restype = i32
     lib.gwas_eig_chunk.argtypes = [vp]
     lib.gwas_eig_chunk.restype = i64
     lib.gwas_batch_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), dp]
@@ -428,6 +431,10 @@ def gwas_split_pieces(h) -> int:
 
 def gwas_fp8_traits(h) -> int:
     return int(lib.gwas_fp8_traits(h))
+
+
+def gwas_chol_routed_traits(h) -> int:
+    return int(lib.gwas_chol_routed_traits(h))
 
 
 def gwas_eig_chunk(h) -> int:

@@ -188,9 +188,59 @@ void check_timeout(gwas_handle h, cudaStream_t s) {
   }
 }
 
+// The CHOL route of an EIG handle (traits past KAPPA_CHOL_ROUTE): Algorithm 3's setup for those
+// traits only -- M_j, L_j, L_j^-1, L_j^-1 X_L, L_j^-1 y_j, S_TL, b0, the whitened residual --
+// then a CHOL tensor-core state over them (three BF16 pieces of each augmented L_j^-1), which the
+// EIG state runs after its own kernels.
+void attach_chol_route(gwas_handle h, cudaStream_t s, const std::vector<int>& route,
+                       const double* dPhi, const double* dXL, const double* dY, const double* h2,
+                       const double* s2, const TcSetupArgs& eig_args) {
+  const int n = h->n, q = h->q, tr = (int)route.size();
+  const size_t nn = (size_t)n * n;
+  double* Lr = dalloc_t<double>(h, (size_t)tr * nn);
+  double* XLwr = dalloc_t<double>(h, (size_t)tr * q * n);
+  double* ywr = dalloc_t<double>(h, (size_t)tr * n);
+  double* rwr = dalloc_t<double>(h, (size_t)tr * n);
+  double* Pr = dalloc_t<double>(h, (size_t)tr * q * q);  // kept: the CHOL kernel reads P_j, b0_j
+  double* b0r = dalloc_t<double>(h, (size_t)tr * q);
+  double* A = dalloc_t<double>(h, nn);
+  double* work = dalloc_t<double>(h, nn > 3 * (size_t)n + 1 ? nn : 3 * (size_t)n + 1);
+  for (int k = 0; k < tr; ++k) {
+    const int j = route[k];
+    double* Lk = Lr + (size_t)k * nn;
+    form_M(s, n, dPhi, h2[j], s2[j], A);
+    cholesky(s, n, A, h->flags);
+    tri_inverse(s, n, A, Lk, work);
+    gemm_f64(s, q, n, n, 1.0, dXL, n, 1, Lk, 1, n, 0.0, XLwr + (size_t)k * q * n, n, 1);
+    gemm_f64(s, 1, n, n, 1.0, dY + (size_t)j * n, 0, 1, Lk, 1, n, 0.0, ywr + (size_t)k * n, 0, 1);
+  }
+  TraitPackArgs tp{n, q, tr, XLwr, (int64_t)q * n, ywr, nullptr, Pr, b0r, rwr, h->flags};
+  trait_pack(s, tp);
+  TcSetupArgs ta = eig_args;
+  ta.algo = GWAS_ALGO_CHOL;
+  ta.t = tr;
+  ta.Linv = Lr;
+  ta.XLw = XLwr;
+  ta.rw = rwr;
+  ta.P = Pr;
+  ta.b0 = b0r;
+  std::vector<int> three(tr, 3);
+  ta.pieces = three.data();
+  ta.fp8_lo = 0;
+  TcState* rs = tc_setup(s, ta);
+  try {
+    tc_attach_chol_route(s, h->tc, rs, route);
+  } catch (...) {
+    tc_destroy(rs);
+    throw;
+  }
+  for (double* p : {Lr, XLwr, ywr, rwr, A, work}) dfree(h, p);
+}
+
 void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double* Y,
                 const double* h2, const double* s2) {
   const int n = h->n, q = h->q, t = h->t;
+  std::vector<int> route;  // EIG traits the CHOL kernel scans as well
   const size_t nn = (size_t)n * n;
   cudaStream_t s = h->st;
   double* dPhi = dalloc_t<double>(h, nn);
@@ -255,8 +305,10 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     gemm_f64(s, t, n, n, 1.0, dY, n, 1, h->Zt, 1, n, 0.0, yw, n, 1);
     double* d = dalloc_t<double>(h, (size_t)t * n);
     eig_weights(s, n, t, h->w, dh2, ds2, d, h->flags);
-    // conditioning of each M_j from the eigenvalues of Phi: one number decides the U pieces
+    // conditioning of each M_j from the eigenvalues of Phi: one number decides the U pieces;
+    // traits past KAPPA_CHOL_ROUTE are scanned by the CHOL kernel as well (route)
     h->pieces.assign(1, 2);
+    route.clear();
     if (h->prec == GWAS_PREC_SPLIT_BF16) {
       std::vector<double> hw(n);
       GW_CUDA(cudaMemcpyAsync(hw.data(), h->w, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
@@ -269,6 +321,7 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
       for (int j = 0; j < t; ++j) {
         const double lo = h2[j] * wmin + 1.0 - h2[j], hi = h2[j] * wmax + 1.0 - h2[j];
         if (lo > 0.0 && hi / lo > KAPPA_THIRD_PIECE) h->pieces[0] = 3;
+        if (lo > 0.0 && hi / lo > KAPPA_CHOL_ROUTE) route.push_back(j);
       }
     }
     TraitPackArgs ta{n, q, t, h->XLt, 0, yw, d, h->P, h->b0, h->rw, h->flags};
@@ -313,6 +366,7 @@ void setup_impl(gwas_handle h, const double* Phi, const double* XL, const double
     for (int i = 0; i < n; ++i)
       if (XL[i] != 1.0) ta.intercept = 0;
     h->tc = tc_setup(s, ta);
+    if (!route.empty()) attach_chol_route(h, s, route, dPhi, dXL, dY, h2, s2, ta);
   }
   GW_CUDA(cudaEventRecord(e1, s));
   GW_CUDA(cudaEventSynchronize(e1));
@@ -1162,6 +1216,10 @@ GW_API gwas_status gwas_stream_info(gwas_handle h, int* block_snps, int* tuned,
 GW_API int64_t gwas_eig_chunk(gwas_handle h) {
   if (!h) return -1;
   return h->tc ? tc_eig_chunk(h->tc) : 0;
+}
+
+GW_API int gwas_chol_routed_traits(gwas_handle h) {
+  return h ? (h->tc ? tc_chol_routed_traits(h->tc) : 0) : -1;
 }
 
 GW_API int gwas_fp8_traits(gwas_handle h) { return h ? (h->tc ? tc_fp8_traits(h->tc) : 0) : -1; }

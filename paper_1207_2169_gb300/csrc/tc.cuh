@@ -1,6 +1,8 @@
 // Tensor-core (tcgen05, sm_103a) split-BF16 scan path: state and entry points.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace gw {
@@ -13,6 +15,12 @@ struct TcState;
 // kappa when Phi has many eigenvalues at its ridge (a kinship from fewer SNPs than individuals):
 // ~3e-5 at kappa = 100, past 1e-4 near kappa = 600-1000, while three pieces stay near 2e-6.
 constexpr double KAPPA_THIRD_PIECE = 100.0;
+// Past this conditioning even three pieces leave the EIG contraction at its FP32 accumulation
+// floor (the error of a and c, amplified by the cancellation in sigma = s - a^T P a, passes 1e-4
+// near kappa = 1000-1500), while the CHOL kernel, which sums its blocks in FP64, stays well within
+// it: an EIG handle scans such traits with the CHOL kernel (three BF16 pieces of their own L_j^-1)
+// after the EIG kernels, overwriting their outputs.
+constexpr double KAPPA_CHOL_ROUTE = 500.0;
 
 struct TcSetupArgs {
   int algo, n, q, t;
@@ -55,6 +63,12 @@ double tc_scan_work(const TcState* st, int64_t m);
 int tc_split_pieces(const TcState* st);
 // Number of CHOL traits whose split is FP16 hi + E4M3 lo (SPLIT_FP8).
 int tc_fp8_traits(const TcState* st);
+// EIG: the traits `route` (a CHOL state over those traits only, set up from their own L_j^-1)
+// scans after the EIG kernels; route's local trait k writes global trait jmap[k] of t_global.
+// The EIG a/c kernel leaves those traits out of its singular count (their P_j is set to NaN in
+// its constants; the CHOL pass counts them).  st takes ownership of route.
+void tc_attach_chol_route(cudaStream_t s, TcState* st, TcState* route, const std::vector<int>& jmap);
+int tc_chol_routed_traits(const TcState* st);
 // EIG: SNPs per internal chunk of a tensor-core scan (the ROT, SQ, AC launches cover one chunk
 // each), the most the per-chunk scratch holds, and a new chunk (clamped to [128, capacity],
 // rounded up to 128).  CHOL: 0 / no effect.

@@ -680,9 +680,11 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
                 const int j = j0 + j8 + u;
                 if (egk == 0 && live) {
                   const float* sj = p.sbuf + (int64_t)j * p.lds;
-                  nsing += ac_pair<QQ>(p, cst + (j8 + u) * (QQ * QQ + QQ), a0, a1, __ldg(sj + snp),
-                                       __ldg(sj + p.xplane + snp), __ldg(sj + 2 * p.xplane + snp),
-                                       mu_snp, mu_pair, snp, j);
+                  // a trait the CHOL kernel scans afterwards (P_j[0] is NaN) is not counted here
+                  const float* Pu = cst + (j8 + u) * (QQ * QQ + QQ);
+                  nsing += (Pu[0] == Pu[0]) &
+                           ac_pair<QQ>(p, Pu, a0, a1, __ldg(sj + snp), __ldg(sj + p.xplane + snp),
+                                       __ldg(sj + 2 * p.xplane + snp), mu_snp, mu_pair, snp, j);
                 }
               }
               continue;
@@ -719,7 +721,8 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
 #pragma unroll
                 for (int k = 0; k <= QQ; ++k) o[k] = __int_as_float(0x7fc00000);
                 wv = __int_as_float(0x7fc00000);
-                nsing += live;
+                // a trait the CHOL kernel scans afterwards (P_j[0] is NaN) is not counted here
+                nsing += live && Pj[0] == Pj[0];
               }
               if (VAR) {
                 // b, then Var(b) as a packed upper triangle, written by this thread straight to

@@ -3,6 +3,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <limits>
 #include <mutex>
 #include <vector>
 
@@ -112,6 +113,11 @@ struct TcState {
   float *P32 = nullptr, *b032 = nullptr, *sbuf = nullptr;
   // EIG: per-SNP centres of the current chunk (NULL: no intercept, no centring)
   float* mu = nullptr;
+  // CHOL states of an EIG handle's badly conditioned traits: local trait k is global jmap[k] of
+  // tglobal traits (empty jmap: the identity)
+  TcState* route = nullptr;
+  std::vector<int> jmap;
+  int tglobal = 0;
   int64_t mcap = 0;    // SNPs per chunk the scratch holds
   int64_t chunk = 0;   // SNPs per chunk the scan uses (<= mcap; 0: mcap)
   bool intercept = false;
@@ -346,7 +352,29 @@ TcState* tc_setup(cudaStream_t s, const TcSetupArgs& a) {
 double tc_scan_work(const TcState* st, int64_t m) {
   const double kp = st->kpad, rp = st->rpad, t = st->t, q1 = st->q + 1;
   if (st->algo == GWAS_ALGO_CHOL) return 2.0 * kp * rp * t * (double)m;  // ~ half the square x 2 pieces x 2 flops
-  return (4.0 * rp * kp + t * kp * (6.0 + 4.0 * q1)) * (double)m;
+  return (4.0 * rp * kp + t * kp * (6.0 + 4.0 * q1)) * (double)m +
+         (st->route ? tc_scan_work(st->route, m) : 0.0);
+}
+
+void tc_attach_chol_route(cudaStream_t s, TcState* st, TcState* route,
+                          const std::vector<int>& jmap) {
+  GW_REQUIRE(st && route && st->algo == GWAS_ALGO_EIG && route->algo == GWAS_ALGO_CHOL &&
+                 (int)jmap.size() == route->t,
+             GWAS_ERR_ARG, "bad CHOL route");
+  route->jmap = jmap;
+  route->tglobal = st->t;
+  st->route = route;
+  // NaN as the first entry of P_j in the a/c kernel's FP32 constants: that kernel then leaves
+  // the trait out of its singular count (its outputs are overwritten by the CHOL pass)
+  const float nanv = std::numeric_limits<float>::quiet_NaN();
+  for (int j : jmap)
+    GW_CUDA(cudaMemcpyAsync(st->P32 + (size_t)j * st->q * st->q, &nanv, 4,
+                            cudaMemcpyHostToDevice, s));
+  GW_CUDA(cudaStreamSynchronize(s));
+}
+
+int tc_chol_routed_traits(const TcState* st) {
+  return st && st->route ? st->route->t : 0;
 }
 
 void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
@@ -361,8 +389,8 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
       p.m = a.m;
       p.n = st->n;
       p.q = st->q;
-      p.t = st->t;
-      p.j = j;
+      p.t = st->tglobal > 0 ? st->tglobal : st->t;
+      p.j = st->jmap.empty() ? j : st->jmap[j];
       p.kpad = st->kpad;
       p.rpad = st->rpad;
       p.P = st->P + (size_t)j * st->q * st->q;
@@ -460,6 +488,8 @@ void tc_scan(cudaStream_t s, TcState* st, const TcScanArgs& a) {
     eig_tc_launch(s, 2, st->mapU, st->mapU, mapG, p, ctas);
     if (ev) tm->end(s, ev);
   }
+  // the badly conditioned traits again, with the CHOL kernel (their outputs overwritten)
+  if (st->route) tc_scan(s, st->route, a);
 }
 
 int64_t tc_eig_chunk(const TcState* st) {
@@ -493,6 +523,7 @@ int tc_split_pieces(const TcState* st) {
 
 void tc_destroy(TcState* st) {
   if (!st) return;
+  tc_destroy(st->route);
   for (void* p : st->allocs) cudaFree(p);
   delete st;
 }

@@ -99,6 +99,7 @@ def test_null_handle_calls(g):
     assert g.lib.gwas_split_pieces(None) == -1
     assert g.lib.gwas_fp8_traits(None) == -1
     assert g.lib.gwas_eig_chunk(None) == -1
+    assert g.lib.gwas_chol_routed_traits(None) == -1
     assert g.lib.gwas_batch_tuning(None, None, None, None) == -1
     assert g.lib.gwas_stream_info(None, None, None, None, None, None, None) == -1
     assert g.lib.gwas_stage_timing(None, 1) == -1

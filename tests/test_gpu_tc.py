@@ -133,19 +133,10 @@ def test_split_without_intercept(g, algo, t):
     assert eb < TOL and ew < TOL, (eb, ew)
 
 
-@pytest.mark.parametrize("algo,t", [("chol", 1), ("eig", 24)])
-def test_split_near_one_heritability(g, algo, t):
-    """h2 up to 0.999 on a kinship from 200 SNPs for n = 500: 300 eigenvalues at the 1e-3 ridge,
-    so M_j^-1 weights those coordinates up to ~1000 times the others (lam_max / lam_min of M_j
-    near 3000 at h2 = 0.999, near 1000 at 0.995), the hardest case the split operands meet; some
-    SNPs are nearly collinear with the covariates (half their values copied from covariate 1's
-    sign) so that sigma = s - a^T P a cancels.  Setup takes a third BF16 piece of L_j^-1 / U_j here
-    (two would give 1.3e-4 / 2.9e-4).  CHOL then meets 1e-4 on every output at h2 = 0.999, and EIG
-    on every output of the traits with h2 <= 0.995.  At h2 = 0.999 EIG reaches the FP32
-    accumulation floor of its a/c contraction (~5e-6 of b_snp): ~1e-4 on the SNP effect, and on an
-    intercept that this kinship determines ~40 times more precisely than mu b_snp (the all-ones
-    vector lies in the ridge eigenspace of a kinship of standardised genotypes) that error
-    amplified, 1.2e-4 measured; bounded here at 2e-4 and 5e-4."""
+def _near_one_cohort(t):
+    """A kinship from 200 SNPs for n = 500 (300 eigenvalues at the 1e-3 ridge), h2 = 0.999 on the
+    first half of the traits, U(0.9, 0.995) on the rest, and SNPs nearly collinear with the
+    covariates (half their values copied from covariate 1's sign)."""
     rs = np.random.default_rng(12)
     n, q = 500, 3
     Phi = synth.kinship(synth.kinship_factor(rs, n, n_snps=200))
@@ -157,29 +148,71 @@ def test_split_near_one_heritability(g, algo, t):
     lead = np.flatnonzero(XL[:, 1] > 0)
     for i in range(0, 40, 4):  # genotype tracks covariate 1 on half the individuals
         XR[i, lead] = np.where(rs.random(lead.size) < 0.9, 2, XR[i, lead])
-    c = synth.Cohort(Phi=Phi, XL=XL, Y=Y, h2=h2, s2=s2, XR=XR, beta=None)
-    Bref, Wref, Vref = gls.gls_grid(Phi, XL, XR, Y, h2, s2)
-    B, W, _ = run(g, c, algo, "split_bf16", packed=True)
-    easy = h2 <= 0.995
-    if easy.any():
-        eb, ew = max_errors(B[:, easy], W[:, easy], Bref[:, easy], Wref[:, easy], Vref[:, easy])
-        assert eb < TOL and ew < TOL, ("h2 <= 0.995", eb, ew)
-    hard = ~easy
-    eb, ew = max_errors(B[:, hard, 1:], W[:, hard], Bref[:, hard, 1:], Wref[:, hard], Vref[:, hard, 1:])
-    e_int, _ = max_errors(B[:, hard, :1], W[:, hard], Bref[:, hard, :1], Wref[:, hard], Vref[:, hard, :1])
-    if algo == "chol":
-        assert max(eb, ew, e_int) < TOL, (eb, ew, e_int)
-    else:
-        assert eb < 2e-4 and ew < 2e-4 and e_int < 5e-4, (eb, ew, e_int)
-    # this cohort's M is conditioned ~3000: setup chose the three-piece split; a well conditioned
-    # one (h2 = 0.5 on the same kinship, kappa ~ 7) keeps two
-    h = g.gwas_setup(Phi, XL, Y, h2, s2, algo=algo, precision="split_bf16")
+    return synth.Cohort(Phi=Phi, XL=XL, Y=Y, h2=h2, s2=s2, XR=XR, beta=None)
+
+
+def _kappa(Phi, h2):
+    w = np.linalg.eigvalsh(Phi)
+    return (h2 * w.max() + 1 - h2) / (h2 * w.min() + 1 - h2)
+
+
+@pytest.mark.parametrize("algo,t", [("chol", 1), ("eig", 24)])
+def test_split_near_one_heritability(g, algo, t):
+    """h2 up to 0.999 on a kinship from 200 SNPs for n = 500: 300 eigenvalues at the 1e-3 ridge,
+    so M_j^-1 weights those coordinates up to ~1000 times the others (lam_max / lam_min of M_j
+    near 3000 at h2 = 0.999, near 500 at 0.995), the hardest case the split operands meet; some
+    SNPs are nearly collinear with the covariates so that sigma = s - a^T P a cancels.  Setup takes
+    a third BF16 piece of L_j^-1 / U_j here (two would give 1.3e-4 / 2.9e-4).  CHOL meets 1e-4 on
+    every output at h2 = 0.999.  On its own the EIG contraction reaches its FP32 accumulation floor
+    there (~1e-4 on the SNP effect, 1.2e-4 on the intercept): an EIG handle scans each trait with
+    lam_max / lam_min above 500 with the CHOL kernel as well, so every output of every trait
+    meets 1e-4, and the singular pairs are counted once."""
+    c = _near_one_cohort(t)
+    c.XR[7] = 1  # monomorphic: one singular pair per trait
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
+    for packed, device in ((True, True), (False, False)):
+        B, W, nsing = run(g, c, algo, "split_bf16", packed=packed, device=device, block_snps=128)
+        eb, ew = max_errors(B, W, Bref, Wref, Vref)
+        assert eb < TOL and ew < TOL, (packed, device, eb, ew)
+        assert nsing == t
+    # this cohort's M is conditioned ~3000: setup chose the three-piece split and, for EIG, the
+    # CHOL route of the traits past kappa 500; a well conditioned one (h2 = 0.5 on the same
+    # kinship, kappa ~ 7) keeps two pieces and no route
+    h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, algo=algo, precision="split_bf16")
     try:
         assert g.gwas_split_pieces(h) == 3
+        routed = int(np.sum(_kappa(c.Phi, c.h2) > 500)) if algo == "eig" else 0
+        assert g.gwas_chol_routed_traits(h) == routed
+        assert algo == "chol" or routed >= t // 2
     finally:
         g.gwas_destroy(h)
-    h = g.gwas_setup(Phi, XL, Y, np.full(t, 0.5), s2, algo=algo, precision="split_bf16")
+    h = g.gwas_setup(c.Phi, c.XL, c.Y, np.full(t, 0.5), c.s2, algo=algo, precision="split_bf16")
     try:
         assert g.gwas_split_pieces(h) == 2
+        assert g.gwas_chol_routed_traits(h) == 0
     finally:
         g.gwas_destroy(h)
+
+
+def test_eig_chol_route_in_every_output_mode(g):
+    """The traits an EIG handle routes through the CHOL kernel write the same outputs the CHOL
+    kernel writes for them alone, in the SNP and VAR modes too, and the other traits are those of
+    the EIG kernels (a handle without the routed traits gives them bit for bit)."""
+    c = _near_one_cohort(10)
+    kap = _kappa(c.Phi, c.h2)
+    rt = np.flatnonzero(kap > 500)
+    keep = np.flatnonzero(kap <= 500)
+    assert rt.size and keep.size
+    for mode in ("full", "snp", "var"):
+        B, W, _ = run(g, c, "eig", "split_bf16", out_mode=mode)
+        for j in rt[:2]:
+            cj = synth.Cohort(Phi=c.Phi, XL=c.XL, Y=c.Y[:, j:j + 1], h2=c.h2[j:j + 1],
+                              s2=c.s2[j:j + 1], XR=c.XR, beta=None)
+            Bj, Wj, _ = run(g, cj, "chol", "split_bf16", out_mode=mode)
+            assert np.array_equal(B[:, j], Bj[:, 0], equal_nan=True), (mode, j)
+            assert np.array_equal(W[:, j], Wj[:, 0], equal_nan=True), (mode, j)
+        ck = synth.Cohort(Phi=c.Phi, XL=c.XL, Y=c.Y[:, keep], h2=c.h2[keep], s2=c.s2[keep],
+                          XR=c.XR, beta=None)
+        Bk, Wk, _ = run(g, ck, "eig", "split_bf16", out_mode=mode)
+        assert np.array_equal(B[:, keep], Bk, equal_nan=True), mode
+        assert np.array_equal(W[:, keep], Wk, equal_nan=True), mode
