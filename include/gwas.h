@@ -368,10 +368,9 @@ int gwas_genetic_columns(gwas_handle h);
  * many eigenvalues at its ridge), where two pieces (~16 significant bits) would not hold the
  * 1e-4 bound.  CHOL chooses per trait (3 pieces of its augmented L_j^-1: one product in two
  * more); EIG per handle (3 pieces of every U_j = M_j^-1 [X_L | r_j]: the a/c kernel one product
- * in two more).  0 for CUDA-core handles, -1 for NULL.  At such conditioning the FP32
- * accumulation of the tensor cores bounds the relative error of the SNP effect near 1e-5; an
- * intercept that the kinship's weighting determines far more precisely than the SNP effect
- * (|mu b_snp| >> se(intercept), mu the SNP's mean) carries that error amplified by the ratio. */
+ * in two more).  0 for CUDA-core handles, -1 for NULL.  Past lam_max / lam_min = 500 the EIG
+ * contraction's FP32 accumulation, not its pieces, would bound the error near 1e-4: EIG handles
+ * scan those traits with the CHOL kernel as well (gwas_chol_routed_traits). */
 int gwas_split_pieces(gwas_handle h);
 
 /* Number of traits whose CHOL scan runs the FP16 hi + E4M3 lo split (precision SPLIT_FP8: every
