@@ -267,32 +267,36 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
 namespace gw {
 namespace {
 
-// y_c = sum_j v_j Z(k+1+j, c) for every column c (Z column-major), one warp per column; v is
-// reflector k, stored in A(k+1:n, k).
-__global__ void bt_dot_kernel(int n, int k, const double* __restrict__ A,
-                              const double* __restrict__ Z, double* __restrict__ y) {
-  const int m = n - k - 1;
-  const int c = blockIdx.x * (ET / 32) + threadIdx.x / 32, l = threadIdx.x % 32;
-  if (c >= n) return;
-  const double* v = A + (int64_t)k * n + k + 1;
-  const double* zc = Z + (int64_t)c * n + k + 1;
-  double acc = 0.0;
-  for (int j = l; j < m; j += 32) acc = fma(v[j], zc[j], acc);
-  acc = warp_sum(acc);
-  if (l == 0) y[c] = acc;
-}
-
-// Z(k+1+j, c) -= tau_k v_j y_c
-__global__ void bt_update_kernel(int n, int k, const double* __restrict__ A,
-                                 const double* __restrict__ tau, const double* __restrict__ y,
-                                 double* Z) {
-  const int m = n - k - 1;
-  const int j = blockIdx.x * 32 + threadIdx.x % 32;
-  const int c0 = blockIdx.y * 32 + threadIdx.x / 32;
-  if (j >= m) return;
-  const double tv = tau[k] * A[(int64_t)k * n + k + 1 + j];
-  for (int c = c0; c < n && c < (int)blockIdx.y * 32 + 32; c += ET / 32)
-    Z[(int64_t)c * n + k + 1 + j] -= tv * y[c];
+// Z(:, c) := H_0 H_1 ... H_{n-3} Z(:, c), one warp per column c with the column in shared memory:
+// the columns are independent, so each warp walks every reflector (from the last to the first)
+// with no step shared with other warps (no block or grid barrier between reflectors), reading the
+// reflectors from L1 / L2.  Per reflector k: y = v_k . Z(k+1:, c) (a warp reduction), then
+// Z(k+1:, c) -= tau_k y v_k.
+constexpr int BT_WARPS = 4;  // columns (warps) per CTA at most
+__global__ void __launch_bounds__(32 * BT_WARPS) bt_columns_kernel(int n,
+                                                                   const double* __restrict__ A,
+                                                                   const double* __restrict__ tau,
+                                                                   double* Zt) {
+  extern __shared__ double zs[];  // (blockDim.x / 32) x n
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  const int c = blockIdx.x * (blockDim.x / 32) + w;
+  if (c >= n) return;  // warp-uniform; no block barrier follows
+  double* z = zs + (int64_t)w * n;
+  const double* zc = Zt + (int64_t)c * n;
+  for (int r = l; r < n; r += 32) z[r] = zc[r];
+  __syncwarp();
+  for (int k = n - 3; k >= 0; --k) {
+    const int m = n - k - 1;
+    const double* v = A + (int64_t)k * n + k + 1;
+    double* zk = z + k + 1;
+    double dot = 0.0;
+    for (int r = l; r < m; r += 32) dot = fma(v[r], zk[r], dot);
+    const double y = tau[k] * warp_sum(dot);
+    for (int r = l; r < m; r += 32) zk[r] -= y * v[r];
+    __syncwarp();  // the next reflector's dot reads elements other lanes updated
+  }
+  double* zo = Zt + (int64_t)c * n;
+  for (int r = l; r < n; r += 32) zo[r] = z[r];
 }
 
 // Device buffers of one call, freed on every exit.
@@ -410,12 +414,17 @@ int eigh_tridiag(cudaStream_t s, int n, const double* Phi, double* Zt, double* w
   if (hflags[FLAG_NOT_SPD]) return -1;
   // 5. Z = H_0 H_1 ... H_{n-3} S (column c of Z = row c of Zt)
   GW_CUDA(cudaMemcpyAsync(Zt, Sc, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  for (int k = n - 3; k >= 0; --k) {
-    const int m = n - k - 1;
-    bt_dot_kernel<<<ceil_div(n, ET / 32), ET, 0, s>>>(n, k, A, Zt, pv);
-    bt_update_kernel<<<dim3(ceil_div(m, 32), ceil_div(n, 32)), ET, 0, s>>>(n, k, A, tau, pv, Zt);
+  if (n >= 3) {
+    // one warp per column; as many columns per CTA (up to BT_WARPS) as n doubles each fit in
+    // 200 KB of shared memory (n <= 16384: at least one)
+    const int warps = (int)std::max<int64_t>(
+        1, std::min<int64_t>(BT_WARPS, (int64_t)(200 * 1024) / ((int64_t)n * 8)));
+    const size_t smem = (size_t)warps * n * 8;
+    GW_CUDA(cudaFuncSetAttribute(bt_columns_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    bt_columns_kernel<<<ceil_div(n, warps), 32 * warps, smem, s>>>(n, A, tau, Zt);
+    GW_CHECK_LAUNCH();
   }
-  GW_CHECK_LAUNCH();
   GW_CUDA(cudaStreamSynchronize(s));
   return 0;
 }
