@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -115,6 +116,115 @@ __global__ void house_update_kernel(int n, int k, double* A, const double* __res
   for (int j = j0; j < m && j < blockIdx.y * 32 + 32; j += ET / 32) {
     double* a = A + (int64_t)(k + 1 + j) * n + k + 1 + i;
     *a -= vi * wv[j] + wi * v[j];
+  }
+}
+
+// Barrier of all CTAs of a cooperative launch (every CTA is resident): a counter and a generation
+// word in global memory.  The wait is bounded (limit_ns); on expiry it sets *gflag and returns
+// false, and so does every later barrier of the launch, so that the kernel unwinds.
+__device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, int* gflag,
+                             uint64_t limit_ns) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = *(volatile int*)gflag == 0;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd((unsigned*)gen, 1u);
+    } else if (ok) {
+      uint64_t t0;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      while (*gen == g) {
+        uint64_t t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        if (t1 - t0 > limit_ns || *(volatile int*)gflag) {
+          atomicExch(gflag, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// The whole Householder reduction in one cooperative launch: per column k, every CTA finds the
+// reflector of A(k+1:n, k) itself (the arithmetic of house_kernel, so every CTA holds the same v
+// and tau), the CTAs' warps share the rows of p = tau A v, then (after a barrier) every CTA forms
+// w = p - (tau/2)(p.v) v and updates its share of the trailing columns,
+// A(k+1:, k+1:) -= v w^T + w v^T, while CTA 0 stores v, tau, d, e; a second barrier ends the
+// step.  Two barriers per column instead of four launches.
+__global__ void __launch_bounds__(ET) house_coop_kernel(int n, double* A, double* pbuf,
+                                                        double* tau, double* d, double* e,
+                                                        unsigned* bar, int* gflag) {
+  __shared__ double red[ET / 32];
+  __shared__ double sh[3];  // v0, t, alpha
+  const int warps = ET / 32, gw = blockIdx.x * warps + threadIdx.x / 32, l = threadIdx.x % 32;
+  const int nw = gridDim.x * warps;
+  const uint64_t LIMIT = 2000000000ull;
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double* x = A + (int64_t)k * n + k + 1;
+    // the reflector, in every CTA (as house_kernel)
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < m; i += ET) ss = fma(x[i], x[i], ss);
+    ss = block_sum_all(ss, red);
+    if (threadIdx.x == 0) {
+      const double x0 = x[0];
+      double t = 0.0, alpha = x0, v0 = 0.0;
+      if (ss > 0.0 && ss - x0 * x0 > 0.0) {
+        alpha = -copysign(sqrt(ss), x0);
+        v0 = x0 - alpha;
+        t = 2.0 / (ss - x0 * x0 + v0 * v0);
+      }
+      sh[0] = v0;
+      sh[1] = t;
+      sh[2] = alpha;
+    }
+    __syncthreads();
+    const double v0 = sh[0], t = sh[1];
+    auto vat = [&](int j) -> double { return t != 0.0 ? (j == 0 ? v0 : x[j]) : 0.0; };
+    // p = tau A(k+1:, k+1:) v, one warp per row (A symmetric: row i = column k+1+i)
+    for (int i = gw; i < m; i += nw) {
+      const double* col = A + (int64_t)(k + 1 + i) * n + k + 1;
+      double acc = 0.0;
+      for (int j = l; j < m; j += 32) acc = fma(col[j], vat(j), acc);
+      acc = warp_sum(acc);
+      if (l == 0) pbuf[i] = t * acc;
+    }
+    if (!grid_barrier(bar, bar + 1, gflag, LIMIT)) return;
+    // w = p - (tau/2)(p.v) v, then the rank-2 update of this CTA's columns
+    double pv = 0.0;
+    for (int i = threadIdx.x; i < m; i += ET) pv = fma(pbuf[i], vat(i), pv);
+    pv = block_sum_all(pv, red);
+    const double K = 0.5 * t * pv;
+    for (int jc = blockIdx.x; jc < m; jc += gridDim.x) {
+      const double vj = vat(jc), wj = pbuf[jc] - K * vj;
+      double* a = A + (int64_t)(k + 1 + jc) * n + k + 1;
+      for (int i = threadIdx.x; i < m; i += ET) {
+        const double vi = vat(i), wi = pbuf[i] - K * vi;
+        a[i] -= vi * wj + wi * vj;
+      }
+    }
+    if (blockIdx.x == 0) {
+      // column k now takes the reflector (read by the back-transformation); no trailing
+      // column reads it
+      __syncthreads();  // every thread of this CTA is done reading x
+      const double dk = A[(int64_t)k * n + k];
+      for (int i = threadIdx.x; i < m; i += ET) x[i] = t != 0.0 ? (i == 0 ? v0 : x[i]) : 0.0;
+      if (threadIdx.x == 0) {
+        tau[k] = t;
+        d[k] = dk;
+        e[k] = sh[2];
+      }
+    }
+    if (!grid_barrier(bar, bar + 1, gflag, LIMIT)) return;
   }
 }
 
@@ -342,8 +452,35 @@ int eigh_tridiag(cudaStream_t s, int n, const double* Phi, double* Zt, double* w
   GW_CUDA(cudaMemsetAsync(e, 0, sizeof(double) * n, s));
   symmetrize_kernel<<<ceil_div((int64_t)nn, 256), 256, 0, s>>>(n, Phi, A);
   GW_CHECK_LAUNCH();
-  // 1. Householder reduction to tridiagonal form
-  for (int k = 0; k + 2 < n; ++k) {
+  // 1. Householder reduction to tridiagonal form: one cooperative launch (every CTA resident,
+  //    one per SM), or four launches per column where a cooperative launch is not available
+  bool coop = false;
+  if (n > 2) {
+    int dev = 0, can = 0, per_sm = 0, sms = 0;
+    GW_CUDA(cudaGetDevice(&dev));
+    GW_CUDA(cudaDeviceGetAttribute(&can, cudaDevAttrCooperativeLaunch, dev));
+    GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, house_coop_kernel, ET, 0));
+    if (can && per_sm >= 1) {
+      unsigned* bar = (unsigned*)mem.get(1);  // count, generation
+      GW_CUDA(cudaMemsetAsync(bar, 0, 8, s));
+      int n_arg = n;
+      int* tflag = flags + FLAG_TIMEOUT;
+      void* args[] = {&n_arg, &A, &pv, &tau, &d, &e, &bar, &tflag};
+      // one such launch at a time in the process (setups may run on several host threads): two
+      // grids that each hold part of the SMs while waiting for the rest could only time out
+      static std::mutex coop_mu;
+      std::lock_guard<std::mutex> lock(coop_mu);
+      const cudaError_t ce = cudaLaunchCooperativeKernel((const void*)house_coop_kernel,
+                                                         dim3(sms), dim3(ET), args, 0, s);
+      if (ce == cudaSuccess)
+        coop = true;
+      else
+        cudaGetLastError();
+      GW_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  for (int k = 0; !coop && k + 2 < n; ++k) {
     const int m = n - k - 1;
     house_kernel<<<1, ET, 0, s>>>(n, k, A, vb, tau, d, e);
     house_matvec_kernel<<<ceil_div(m, ET / 32), ET, 0, s>>>(n, k, A, vb, tau, pv);
@@ -352,6 +489,13 @@ int eigh_tridiag(cudaStream_t s, int n, const double* Phi, double* Zt, double* w
   }
   house_tail_kernel<<<1, 32, 0, s>>>(n, A, d, e);
   GW_CHECK_LAUNCH();
+  if (coop) {
+    int hf[FLAG_COUNT];
+    GW_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    GW_CUDA(cudaStreamSynchronize(s));
+    GW_REQUIRE(!hf[FLAG_TIMEOUT], GWAS_ERR_TIMEOUT,
+               "the Householder reduction gave up waiting at a grid barrier");
+  }
   // 2. eigenvalues by multisection within the Gershgorin interval
   std::vector<double> hd(n), he(n), he2(n), hw(n), hs(n);
   GW_CUDA(cudaMemcpyAsync(hd.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
