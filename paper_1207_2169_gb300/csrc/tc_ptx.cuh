@@ -327,20 +327,6 @@ __device__ __forceinline__ void coded_lut(float mu, uint32_t code, uint32_t& lo,
   }
 }
 
-// FP16 form of coded_lut: byte tables of cd(g) - mu (g = 0, 1, 2) as FP16 values, exact when mu
-// is a multiple of 1/64 in [0, 2] (eight significant bits at most; FP16 carries eleven).
-__device__ __forceinline__ void coded_lut_f16(float mu, uint32_t code, uint32_t& lo, uint32_t& hi) {
-  lo = 0u;
-  hi = 0u;
-#pragma unroll
-  for (int g = 0; g < 3; ++g) {
-    const float v = (float)((code >> (8 * g)) & 0xFFu) - mu;
-    const uint32_t b = __half_as_ushort(__float2half_rn(v));
-    lo |= (b & 0xFFu) << (8 * g);
-    hi |= (b >> 8) << (8 * g);
-  }
-}
-
 // Byte table of the uncentred coded genotype cd(g) in E4M3 (g = 0, 1, 2; cd(g) in {0, 1, 2}:
 // 0x00, 0x38 = 1.0, 0x40 = 2.0, all exact), byte g; byte 3 (the invalid code) is 0.
 __device__ __forceinline__ uint32_t coded_e4m3_table(uint32_t code) {

@@ -134,3 +134,33 @@ def test_batch_parity_and_skipped_cohort(g, cohorts):
         assert g.gwas_info(h0)["n"] == cs[0].n and g.gwas_singular_count(h0) == 0
     finally:
         g.gwas_destroy_batch(b)
+
+
+def test_batch_split_fp8_equals_single_scans(g, cohorts):
+    """A batch set up with SPLIT_FP8 (its CHOL cohorts on the FP16 + E4M3 split, its EIG cohorts as
+    SPLIT_BF16) gives every cohort exactly the results of its own SPLIT_FP8 scan, within 1e-4 of
+    the oracle."""
+    import torch
+    cs = cohorts[:3]
+    b = g.gwas_setup_batch([(c.Phi, c.XL, c.Y, c.h2, c.s2) for c in cs], precision="split_fp8")
+    try:
+        blocks = _blocks(g, cs)
+        g.gwas_scan_batch(b, blocks)
+        torch.cuda.synchronize()
+        for i, (c, (G, B, W)) in enumerate(zip(cs, blocks)):
+            h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, precision="split_fp8")
+            try:
+                assert g.gwas_fp8_traits(g.gwas_batch_handle(b, i)) == g.gwas_fp8_traits(h)
+                Bs = torch.empty_like(B)
+                Ws = torch.empty_like(W)
+                g.gwas_scan_packed(h, G, Bs, Ws)
+                torch.cuda.synchronize()
+            finally:
+                g.gwas_destroy(h)
+            assert torch.equal(B, Bs) and torch.equal(W, Ws), i
+            Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
+            eb, ew = max_errors(B.cpu().numpy().astype(np.float64),
+                                W.cpu().numpy().astype(np.float64), Bref, Wref, Vref)
+            assert eb < TOL and ew < TOL, (i, eb, ew)
+    finally:
+        g.gwas_destroy_batch(b)
