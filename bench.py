@@ -627,19 +627,29 @@ def measure_stream3(local, ws, steps=2, warmup=1, m=None, out_mode="full", pinne
                       torch.empty(blk * t, dtype=torch.float32, pin_memory=True))
         Bh, Wh = pinned
 
+        call_ms = []
+
         def e2e_step():
             for b in range(nblk):
                 lo, hi = b * blk, min(mm, (b + 1) * blk)
+                t1 = time.perf_counter()
                 g.gwas_scan_packed(h, G_h[lo:hi], Bh[:(hi - lo) * t * pw].view(hi - lo, t, pw),
                                    Wh[:(hi - lo) * t].view(hi - lo, t))
+                call_ms.append((time.perf_counter() - t1) * 1e3)
 
         e2e_step()
+        call_ms.clear()
         _barrier(ws)
         t0 = time.perf_counter()
         for _ in range(steps):
             e2e_step()
         e2e_s = _max_over_ranks((time.perf_counter() - t0) / steps, ws)
         link = host_link()
+        info = g.gwas_stream_info(h)
+        full = sorted(x for i, x in enumerate(call_ms) if (i % nblk) != nblk - 1)
+        stream_info = {"block_snps": info["block_snps"], "block_chosen_by_timing": info["tuned"],
+                       "ms_per_32Ki_call": {"min": full[0], "median": full[len(full) // 2],
+                                            "max": full[-1]}}
     finally:
         g.gwas_destroy(h)
     pairs = mm * t
@@ -653,7 +663,7 @@ def measure_stream3(local, ws, steps=2, warmup=1, m=None, out_mode="full", pinne
            "e2e": link_roof({"value": pairs * ws / e2e_s, "unit": "pairs/s",
                              "h2d_bytes_per_step": mm * _row_bytes(n, "packed"),
                              "d2h_bytes_per_step": mm * t * (pw + 1) * 4,
-                             "ms_per_step": e2e_s * 1e3}, link),
+                             "ms_per_step": e2e_s * 1e3, "streaming": stream_info}, link),
            "roofline": dom, "kernels": kernels,
            "gpu_launches": sum(v[1] for v in stages.values()),
            "stage_ms": {k: v[0] / steps for k, v in stages.items()}}
