@@ -7,7 +7,7 @@ import pytest
 
 import synth
 from oracle import gls
-from gpu_util import run
+from gpu_util import run, max_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -30,10 +30,15 @@ def test_snp_mode(g, algo, prec, n, q, m, t):
     Bs, Ws, ss = run(g, c, algo, prec, out_mode="snp")
     assert Bs.shape == (m, t, 2) and ss == sf
     assert np.array_equal(Bs[:, :, 0], Bf[:, :, -1]) and np.array_equal(Ws, Wf)
-    _, _, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
-    se_ref = np.sqrt(Vref[:, :, -1])
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
     tol = 1e-6 if prec == "fp64" else 1e-4
-    assert np.nanmax(np.abs(Bs[:, :, 1] - se_ref) / se_ref) < tol
+    eb, ew = max_errors(Bf, Wf, Bref, Wref, Vref)
+    assert eb < tol and ew < tol, (eb, ew)
+    # NaN exactly where the oracle has none (an unwritten pair stays NaN and fails here)
+    se_ref = np.sqrt(Vref[:, :, -1])
+    assert np.array_equal(np.isnan(Bs[:, :, 1]), np.isnan(se_ref))
+    ok = ~np.isnan(se_ref)
+    assert np.max(np.abs(Bs[:, :, 1][ok] - se_ref[ok]) / se_ref[ok]) < tol
 
 
 def test_snp_mode_streamed_and_pvalues(g):
