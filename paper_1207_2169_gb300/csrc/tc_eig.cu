@@ -30,7 +30,7 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int BK = 64;
-constexpr int SA_MAX = 4;
+constexpr int SA_MAX = 6;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int NCONV = 8;                 // genotype converter warps (ROT, AC): 2 threads per row
@@ -48,7 +48,12 @@ enum { EPI_ROT = 0, EPI_SQ = 1, EPI_AC = 2 };
 __host__ __device__ constexpr bool wide_of(int epi, int qq) { return epi == EPI_AC && qq <= 3; }
 __host__ __device__ constexpr int nwarps_of(int epi, int qq) { return wide_of(epi, qq) ? 20 : 14; }
 __host__ __device__ constexpr int nepi_of(int epi, int qq) { return wide_of(epi, qq) ? 8 : 4; }
-__host__ __device__ constexpr int sa_of(int epi, int qq) { return wide_of(epi, qq) ? 3 : 4; }
+// A-tile ring depth.  SQ reads its A tiles (the squared planes, rows 2 KB apart) by TMA, mostly
+// from DRAM: six slots (three K steps of hi + lo) keep more of them in flight than four (the
+// SQ kernel 9 % faster); its shared memory has room, having no packed-slice ring.
+__host__ __device__ constexpr int sa_of(int epi, int qq) {
+  return wide_of(epi, qq) ? 3 : epi == EPI_SQ ? 6 : 4;
+}
 // converter warps -> 0 .. 7
 template <bool WIDE>
 __device__ __forceinline__ int conv_index(int warp) {
@@ -83,6 +88,8 @@ __host__ __device__ constexpr int stg_rb(int qq) { return qq == 3 ? 36 : 8 * qp_
 __host__ __device__ constexpr int stg_b(int qq) { return 32 * stg_rb(qq); }
 constexpr int STG_W = 32 * 9;
 constexpr int PB_FLOATS = 2048;
+// q = 3: the 64 traits of a block fill the accumulator (the epilogue loads 8 of them at once)
+static_assert(eig_ac_traits(3) * 4 == BN, "AC block of q = 3 is not one accumulator");
 __host__ __device__ constexpr int cst_of(int epi, int qq) {
   return epi == EPI_AC ? PB_FLOATS + nepi_of(epi, qq) * (stg_b(qq) + STG_W) : 0;
 }
@@ -96,7 +103,7 @@ struct __align__(8) BarsT {
 };
 
 __host__ __device__ constexpr size_t smem_of(int epi, int qp) {
-  return 1024 + (size_t)sa_of(epi, qp) * A_BYTES + (size_t)sb_of(epi) * B_BYTES + PR * PK_BYTES +
+  return 1024 + (size_t)sa_of(epi, qp) * A_BYTES + (size_t)sb_of(epi) * B_BYTES + (epi == EPI_SQ ? 0 : PR * PK_BYTES) +
          (size_t)cst_of(epi, qp) * 4 + sizeof(BarsT<4>);
 }
 
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
   uint8_t* sA = smem;
   uint8_t* sB = sA + SA * A_BYTES;
   uint8_t* sP = sB + SB * B_BYTES;
-  float* cst = (float*)(sP + PR * PK_BYTES);
+  float* cst = (float*)(sP + (CONV ? PR * PK_BYTES : 0));
   Bars* bars = (Bars*)(cst + cst_of(EPI, QQ));
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t mtiles = (p.m + TS - 1) / TS;
@@ -645,12 +652,18 @@ __global__ void __launch_bounds__(32 * nwarps_of(EPI, QQ), 1)
               }
             }
             uint32_t r[8][QP];
+            if (QQ == 3) {
+              // q + 1 = 4 columns per trait: the batch's 32 columns are contiguous, one load
+              // (T = 64, so the batch ends at column 4 (j8 + 8) <= 256 of the accumulator)
+              tmem_ld32_async(base + j8 * 4, *reinterpret_cast<uint32_t(*)[32]>(&r[0][0]));
+            } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              // columns of traits past the block end are not read (their loads would leave the
-              // accumulator); those lanes of r are unused
-              const int jl = j8 + u < T ? j8 + u : 0;
-              tmem_ld_cols<QP>(base + jl * q1, r[u]);
+              for (int u = 0; u < 8; ++u) {
+                // columns of traits past the block end are not read (their loads would leave the
+                // accumulator); those lanes of r are unused
+                const int jl = j8 + u < T ? j8 + u : 0;
+                tmem_ld_cols<QP>(base + jl * q1, r[u]);
+              }
             }
             // the wait names every destination register, so no use is scheduled before it
 #pragma unroll

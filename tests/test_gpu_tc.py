@@ -216,3 +216,25 @@ def test_eig_chol_route_in_every_output_mode(g):
         Bk, Wk, _ = run(g, ck, "eig", "split_bf16", out_mode=mode)
         assert np.array_equal(B[:, keep], Bk, equal_nan=True), mode
         assert np.array_equal(W[:, keep], Wk, equal_nan=True), mode
+
+
+@pytest.mark.parametrize("algo,prec", [("chol", "split_bf16"), ("chol", "split_fp8"),
+                                       ("eig", "split_bf16"), ("chol", "fp32"), ("eig", "fp64")])
+@pytest.mark.parametrize("device,packed", [(True, False), (True, True), (False, False), (False, True)])
+def test_empty_scan_every_path(g, algo, prec, device, packed):
+    """m = 0 SNPs is a valid call on every path: nothing is written, nothing is counted."""
+    import torch
+    c = synth.small_problem(17, n=70, q=2, m=1, t=1 if algo == "chol" else 3)
+    h = g.gwas_setup(c.Phi, c.XL, c.Y, c.h2, c.s2, algo=algo, precision=prec)
+    try:
+        dev = "cuda" if device else "cpu"
+        cols = g.gwas_packed_row_bytes(c.n) if packed else c.n
+        X = torch.zeros((0, cols), dtype=torch.uint8 if packed else torch.int8, device=dev)
+        B = torch.full((1, c.t, c.p), 7.0, device=dev)
+        W = torch.full((1, c.t), 7.0, device=dev)
+        (g.gwas_scan_packed if packed else g.gwas_scan)(h, X, B, W, m=0)
+        torch.cuda.synchronize()
+        assert torch.all(B == 7.0) and torch.all(W == 7.0)
+        assert g.gwas_singular_count(h) == 0
+    finally:
+        g.gwas_destroy(h)
