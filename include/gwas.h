@@ -382,7 +382,11 @@ int gwas_fp8_traits(gwas_handle h);
  * the EIG contraction's FP32 accumulation keeps 1e-4 (lam_max / lam_min of M_j above 500, e.g.
  * h^2 near 1 on a kinship with many eigenvalues at its ridge).  Setup also factors those traits'
  * M_j (Algorithm 3's setup), and every scan runs the CHOL kernel on them after the EIG kernels,
- * overwriting their outputs; 0 for other handles, -1 for a NULL handle. */
+ * overwriting their outputs; 0 for other handles, -1 for a NULL handle.  A routed trait costs
+ * what a CHOL trait costs: setup holds its L_j^-1 in FP64 (8 n^2 bytes per routed trait, all at
+ * once) and keeps three BF16 pieces of it (6 n^2 bytes), and each scan adds one CHOL pass over
+ * the block's SNPs per routed trait (about n^2 multiply-adds per SNP and piece), so a cohort whose
+ * traits are mostly routed is better set up with GWAS_ALGO_CHOL. */
 int gwas_chol_routed_traits(gwas_handle h);
 
 /* EIG tensor-core handles: SNPs per internal chunk of a scan (one launch of each EIG kernel per
