@@ -385,7 +385,7 @@ int gwas_fp8_traits(gwas_handle h);
  * overwriting their outputs; 0 for other handles, -1 for a NULL handle.  A routed trait costs
  * what a CHOL trait costs: setup holds its L_j^-1 in FP64 (8 n^2 bytes per routed trait, all at
  * once) and keeps three BF16 pieces of it (6 n^2 bytes), and each scan adds one CHOL pass over
- * the block's SNPs per routed trait (about n^2 multiply-adds per SNP and piece), so a cohort whose
+ * the block's SNPs per routed trait (about n^2 / 2 multiply-adds per SNP and piece), so a cohort whose
  * traits are mostly routed is better set up with GWAS_ALGO_CHOL. */
 int gwas_chol_routed_traits(gwas_handle h);
 
