@@ -5,7 +5,8 @@ Full sizes (2,000,000 SNPs for the single-trait CHOL scan, 100,000 SNPs x 1,000 
 32 Ki-SNP block of 30,000 traits for EIG) are checked on sampled (SNP, trait) pairs that the
 oracle solves one by one, through the same calls and packed device-resident input as the bench.
 The smaller cases give every CTA several work items (several SNP tiles, or several column
-blocks of one tile), with every pair checked.
+blocks of one tile), with every pair checked.  The largest n that setup accepts (16384) is
+checked for the CHOL scan in both split precisions, and n = 4500 for EIG, every pair checked.
 """
 import numpy as np
 import pytest
@@ -89,3 +90,42 @@ def test_eig_workload3_block_sampled(g):
     """n = 1,000, t = 30,000, one 32,768-SNP block (the bench's block); 200 sampled pairs."""
     eb, ew = _full_sampled(g, 3, 32768, 200, "eig")
     assert eb < TOL and ew < TOL, (eb, ew)
+
+
+@pytest.fixture(scope="module")
+def max_n_cohort():
+    """n = 16384, the largest n that gwas_setup accepts.  The kinship comes from 256 standardised
+    SNPs (plus the ridge), so that building it stays cheap on the host; its non-zero eigenvalues
+    sit near n / 256, which at h2 = 0.5 keeps lam_max / lam_min of M below 100 (two pieces, and
+    the FP8 split)."""
+    rs = np.random.default_rng(16384)
+    n, q, m = 16384, 3, 300
+    Gs = synth.kinship_factor(rs, n, n_snps=256)
+    Phi = synth.kinship(Gs)
+    XL = synth.covariates(rs, n, q)
+    h2, s2 = np.array([0.5]), np.array([1.3])
+    Y, beta = synth.traits(rs, XL, Gs, h2, s2)
+    c = synth.Cohort(Phi=Phi, XL=XL, Y=Y, h2=h2, s2=s2, XR=synth.genotypes(rs, n, m), beta=beta)
+    return c, gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "split_fp8"])
+def test_chol_split_max_n(g, max_n_cohort, prec):
+    """The CHOL tensor-core scan at n = 16384: 65 blocks of 256 rows of the augmented L^-1 per
+    SNP tile, K ranges up to 16,384; every SNP checked against the oracle."""
+    c, (Bref, Wref, Vref) = max_n_cohort
+    B, W, nsing = run(g, c, "chol", prec, packed=True)
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < TOL and ew < TOL, (eb, ew)
+    assert nsing == 0
+
+
+def test_eig_split_large_n(g):
+    """EIG at n = 4500 (the eigendecomposition of a full-rank kinship, 71 K steps, 18 row blocks
+    of Z^T in the rotation), several traits, every pair checked."""
+    c = synth.small_problem(4500, n=4500, q=3, m=400, t=5)
+    Bref, Wref, Vref = gls.gls_grid(c.Phi, c.XL, c.XR, c.Y, c.h2, c.s2)
+    B, W, nsing = run(g, c, "eig", "split_bf16", packed=True)
+    eb, ew = max_errors(B, W, Bref, Wref, Vref)
+    assert eb < TOL and ew < TOL, (eb, ew)
+    assert nsing == 0
